@@ -1,0 +1,284 @@
+"""FP64 CPU oracle for the factorized M-scheme H*x (BIGSTICK, arXiv:1801.08432).
+
+TEST INFRASTRUCTURE ONLY: imported by tests/, by ``__graft_entry__.smoke()``
+and by the CPU-baseline leg of ``bench.py``.  It shares no code with the
+library in ``paper_1801_08432_gb300`` and never imports it (apart from the
+seeded input generators in ``paper_1801_08432_gb300.inputs``, which hold none
+of the method's arithmetic).
+
+Parts:
+  * ``bs_oracle.c`` (plain C, FP64): basis of occupation bitstrings, the
+    Clebsch-Gordan coefficient, reading of isospin-coupled TBMEs with their
+    symmetry phases, decoupling to M-scheme W tables, the explicit Hamiltonian
+    built column by column from creation/annihilation operators, on-the-fly
+    rows of H*x and J+.
+  * this module (numpy/scipy): Lanczos with full reorthogonalization (Sec.
+    "Standard Lanczos algorithm", steps (1)-(6) with alpha computed first and
+    then orthogonalization against every earlier vector), dense
+    diagonalization, <J^2>, traces and Hellmann-Feynman gradients.
+
+Parity pins: every function here is checked in tests/test_oracle_pins.py
+against closed forms, paper values or brute force (see that file's header).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "bs_oracle.c")
+_LIB = os.path.join(_HERE, "liboracle.so")
+_lock = threading.Lock()
+_lib = None
+
+i64p = ctypes.POINTER(ctypes.c_int64)
+u64p = ctypes.POINTER(ctypes.c_uint64)
+f64p = ctypes.POINTER(ctypes.c_double)
+i32p = ctypes.POINTER(ctypes.c_int)
+
+
+def build(force: bool = False) -> str:
+    """Compiles bs_oracle.c into liboracle.so next to it (gcc, OpenMP)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        tmp = _LIB + ".%d.tmp" % os.getpid()
+        subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = ctypes.CDLL(_LIB)
+            L.orc_create.argtypes = [ctypes.POINTER(ctypes.c_void_p), i32p, i32p, ctypes.c_int,
+                                     ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]
+            L.orc_create.restype = ctypes.c_int
+            L.orc_dim.argtypes = [ctypes.c_void_p]
+            L.orc_dim.restype = ctypes.c_int64
+            L.orc_ns.argtypes = [ctypes.c_void_p]
+            L.orc_ns.restype = ctypes.c_int
+            L.orc_sizes.argtypes = [ctypes.c_void_p, i32p]
+            L.orc_export_basis.argtypes = [ctypes.c_void_p, u64p, u64p, i64p, i64p, i64p]
+            L.orc_set_interaction.argtypes = [ctypes.c_void_p, f64p, i32p, f64p, ctypes.c_int]
+            L.orc_set_interaction.restype = ctypes.c_int
+            L.orc_get_w.argtypes = [ctypes.c_void_p, f64p, f64p]
+            L.orc_build_matrix.argtypes = [ctypes.c_void_p]
+            L.orc_build_matrix.restype = ctypes.c_int64
+            L.orc_export_matrix.argtypes = [ctypes.c_void_p, i64p, i64p, f64p]
+            L.orc_spmv.argtypes = [ctypes.c_void_p, f64p, f64p, ctypes.c_int]
+            L.orc_apply_rows.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64, f64p, ctypes.c_int, f64p]
+            L.orc_jplus.argtypes = [ctypes.c_void_p, ctypes.c_void_p, f64p, f64p]
+            L.orc_jplus.restype = ctypes.c_int
+            L.orc_cg.argtypes = [ctypes.c_int] * 6
+            L.orc_cg.restype = ctypes.c_double
+            L.orc_destroy.argtypes = [ctypes.c_void_p]
+            L.orc_apply_string.argtypes = [ctypes.c_uint64, i32p, ctypes.c_int, u64p]
+            L.orc_apply_string.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+def cg(tj1, tm1, tj2, tm2, tJ, tM) -> float:
+    """<j1 m1 j2 m2 | J M> (Edmonds), all arguments doubled."""
+    return lib().orc_cg(tj1, tm1, tj2, tm2, tJ, tM)
+
+
+def apply_string(mask: int, ops):
+    """Sign and result of an operator string on a bitstring (bit s = state s).
+
+    ops is a list of ('+', s) for a^dag_s or ('-', s) for a_s, written left
+    to right as in the paper; the rightmost acts first.  Returns (sign, mask),
+    sign 0 if the state vanishes."""
+    enc = np.array([(s + 1) if c == "+" else -(s + 1) for (c, s) in ops], dtype=np.int32)
+    out = ctypes.c_uint64(0)
+    sg = lib().orc_apply_string(ctypes.c_uint64(mask), _p(enc, i32p), len(enc), ctypes.byref(out))
+    return sg, (out.value if sg else None)
+
+
+class OracleError(RuntimeError):
+    pass
+
+
+class Oracle:
+    """One valence space, one nucleus (Z, N), one 2M and parity (0 = +, 1 = -)."""
+
+    def __init__(self, orbits, Z, N, twoM, parity=0):
+        L = lib()
+        self.orbits = list(orbits)
+        l = np.array([o.l for o in orbits], dtype=np.int32)
+        tj = np.array([o.twoj for o in orbits], dtype=np.int32)
+        h = ctypes.c_void_p()
+        rc = L.orc_create(ctypes.byref(h), _p(l, i32p), _p(tj, i32p), len(orbits), Z, N, twoM, parity)
+        if rc != 0:
+            raise OracleError("orc_create failed (%d)" % rc)
+        self.h = h
+        self.Z, self.N, self.twoM, self.parity = Z, N, twoM, parity
+        self.dim = int(L.orc_dim(h))
+        self.ns = int(L.orc_ns(h))
+        sz = np.zeros(5, dtype=np.int32)
+        L.orc_sizes(h, _p(sz, i32p))
+        self.n_psd, self.n_nsd, self.n_psec, self.n_nsec, self.n_blocks = (int(v) for v in sz)
+        self._csr = None
+
+    def __del__(self):
+        try:
+            if getattr(self, "h", None):
+                lib().orc_destroy(self.h)
+                self.h = None
+        except Exception:
+            pass
+
+    # -- basis -----------------------------------------------------------
+    def basis(self):
+        """dict: p_bits, n_bits (uint64), p_sec/n_sec rows (2M, par, start, count),
+        blocks rows (proton sector, neutron sector, offset)."""
+        pb = np.zeros(self.n_psd, dtype=np.uint64)
+        nb = np.zeros(self.n_nsd, dtype=np.uint64)
+        ps = np.zeros((self.n_psec, 4), dtype=np.int64)
+        nsec = np.zeros((self.n_nsec, 4), dtype=np.int64)
+        bl = np.zeros((self.n_blocks, 3), dtype=np.int64)
+        lib().orc_export_basis(self.h, _p(pb, u64p), _p(nb, u64p), _p(ps, i64p), _p(nsec, i64p), _p(bl, i64p))
+        return {"p_bits": pb, "n_bits": nb, "p_sec": ps, "n_sec": nsec, "blocks": bl}
+
+    def states(self):
+        """(basis index) -> (proton bits, neutron bits) for every basis state, as two arrays."""
+        B = self.basis()
+        P = np.zeros(self.dim, dtype=np.uint64)
+        Nn = np.zeros(self.dim, dtype=np.uint64)
+        for (ps, nsi, off) in B["blocks"]:
+            _, _, p0, pc = B["p_sec"][ps]
+            _, _, n0, nc = B["n_sec"][nsi]
+            pbits = B["p_bits"][p0:p0 + pc]
+            nbits = B["n_bits"][n0:n0 + nc]
+            P[off:off + pc * nc] = np.repeat(pbits, nc)
+            Nn[off:off + pc * nc] = np.tile(nbits, pc)
+        return P, Nn
+
+    # -- interaction -----------------------------------------------------
+    def set_interaction(self, spe, tbmes):
+        spe = np.ascontiguousarray(spe, dtype=np.float64)
+        lab = np.array([t[:6] for t in tbmes], dtype=np.int32).reshape(-1, 6)
+        val = np.array([t[6] for t in tbmes], dtype=np.float64)
+        rc = lib().orc_set_interaction(self.h, _p(spe, f64p), _p(lab, i32p), _p(val, f64p), len(tbmes))
+        if rc != 0:
+            raise OracleError("orc_set_interaction rejected the interaction (%d)" % rc)
+        self._csr = None
+        return self
+
+    def w_tables(self):
+        n4 = self.ns ** 4
+        wpp = np.zeros(n4)
+        wpn = np.zeros(n4)
+        lib().orc_get_w(self.h, _p(wpp, f64p), _p(wpn, f64p))
+        s = (self.ns,) * 4
+        return wpp.reshape(s), wpn.reshape(s)
+
+    # -- Hamiltonian -----------------------------------------------------
+    def matrix(self):
+        """Explicit H as scipy.sparse.csr_matrix (FP64)."""
+        import scipy.sparse as sp
+        if self._csr is None:
+            L = lib()
+            nnz = L.orc_build_matrix(self.h)
+            if nnz < 0:
+                raise OracleError("orc_build_matrix failed (%d)" % nnz)
+            cp = np.zeros(self.dim + 1, dtype=np.int64)
+            ri = np.zeros(max(nnz, 1), dtype=np.int64)
+            va = np.zeros(max(nnz, 1))
+            L.orc_export_matrix(self.h, _p(cp, i64p), _p(ri, i64p), _p(va, f64p))
+            # stored columns of H; csc -> csr through the transpose
+            self._csr = sp.csc_matrix((va[:nnz], ri[:nnz], cp), shape=(self.dim, self.dim)).tocsr()
+        return self._csr
+
+    def spmv(self, x):
+        """y = H x with the explicit matrix, x [dim] or [dim][k]."""
+        self.matrix()
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        k = 1 if x.ndim == 1 else x.shape[1]
+        y = np.zeros_like(x)
+        lib().orc_spmv(self.h, _p(x, f64p), _p(y, f64p), k)
+        return y
+
+    def apply_rows(self, rows, x):
+        """Rows of y = H x computed on the fly (no stored matrix)."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        k = 1 if x.ndim == 1 else x.shape[1]
+        y = np.zeros((len(rows), k))
+        lib().orc_apply_rows(self.h, _p(rows, i64p), len(rows), _p(x, f64p), k, _p(y, f64p))
+        return y[:, 0] if x.ndim == 1 else y
+
+    def dense(self):
+        return self.matrix().toarray()
+
+    def trace(self):
+        return float(self.matrix().diagonal().sum())
+
+    # -- eigen -----------------------------------------------------------
+    def lanczos(self, pivot, niter, nkeep=None, return_vectors=False):
+        """Lanczos with full reorthogonalization (FP64).
+
+        Per iteration: w = H v_i; alpha_i = <v_i|w>; w -= alpha_i v_i; then
+        w -= v_j <v_j|w> for every j <= i, twice (classical Gram-Schmidt);
+        beta_i = |w|; v_{i+1} = w / beta_i.  Eigenvalues of the tridiagonal
+        matrix by numpy.linalg.eigh; Ritz vectors from its eigenvectors.
+        """
+        H = self.matrix()
+        v = np.array(pivot, dtype=np.float64).reshape(-1)
+        v = v / np.linalg.norm(v)
+        niter = min(niter, self.dim)
+        V = np.zeros((niter, self.dim))
+        alpha = np.zeros(niter)
+        beta = np.zeros(niter)
+        n = 0
+        for i in range(niter):
+            V[i] = v
+            w = H @ v
+            alpha[i] = v @ w
+            w = w - alpha[i] * v
+            for _ in range(2):
+                w = w - V[: i + 1].T @ (V[: i + 1] @ w)
+            n = i + 1
+            beta[i] = np.linalg.norm(w)
+            if i + 1 == niter or beta[i] < 1e-12 * max(1.0, np.abs(alpha[: i + 1]).max()):
+                break
+            v = w / beta[i]
+        T = np.diag(alpha[:n]) + np.diag(beta[: n - 1], 1) + np.diag(beta[: n - 1], -1)
+        ev, U = np.linalg.eigh(T)
+        if not return_vectors:
+            return ev if nkeep is None else ev[:nkeep]
+        nk = n if nkeep is None else nkeep
+        X = V[:n].T @ U[:, :nk]
+        return ev[:nk], X
+
+    def eigh(self, nkeep=None):
+        ev, X = np.linalg.eigh(self.dense())
+        if nkeep is None:
+            return ev, X
+        return ev[:nkeep], X[:, :nkeep]
+
+    # -- J^2 ------------------------------------------------------------
+    def j2(self, psi, oracle_up):
+        """<J^2> = |J+ psi|^2 + M(M+1), with J+ psi evaluated in the 2M+2 basis."""
+        psi = np.ascontiguousarray(psi, dtype=np.float64)
+        out = np.zeros(oracle_up.dim)
+        rc = lib().orc_jplus(self.h, oracle_up.h, _p(psi, f64p), _p(out, f64p))
+        if rc != 0:
+            raise OracleError("orc_jplus failed")
+        M = self.twoM / 2.0
+        return float(out @ out) / float(psi @ psi) + M * (M + 1.0)
+
+
+def j_from_j2(j2):
+    """J from J(J+1)."""
+    return 0.5 * (-1.0 + np.sqrt(1.0 + 4.0 * np.asarray(j2)))

@@ -1,0 +1,304 @@
+"""Pins of the FP64 oracle to facts other than itself.
+
+Each test ties one part of the oracle to something the paper or mathematics
+fixes, so that a dropped term, a wrong phase or a transposed index fails:
+
+  * Clebsch-Gordan: sympy's exact routine, orthogonality;
+  * sign rule: the paper's worked bitstring examples (Sec. "Representation of
+    the basis");
+  * basis: dimensions and SD/sector counts printed in the paper
+    (tests/golden/basis_dims.txt), Table al27 row by row
+    (tests/golden/al27_sectors.txt), brute-force enumeration;
+  * decoupling, TBME phases, pn isospin combination (Eq. xpndef), sign rule:
+    one proton + one neutron gives exactly the union over (J,T) of the coupled
+    two-body channel spectra; two like particles give the T=1 channels;
+  * SPE path: with no TBMEs the spectrum is the multiset of SPE sums;
+  * rotational invariance of the whole chain: eig(M=1) inside eig(M=0) and
+    integer J from <J^2> = |J+ psi|^2 + M(M+1);
+  * assembly: H = H^T, trace from occupation counts, reading in any label order;
+  * Lanczos: dense diagonalization.
+"""
+import itertools
+import os
+
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1801_08432_gb300 import inputs as I
+from tests.helpers import channel_spectrum, match_subset, scrambled_tbmes
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# ----------------------------------------------------------------- CG
+def test_cg_matches_sympy():
+    sympy = pytest.importorskip("sympy")
+    from sympy.physics.wigner import clebsch_gordan
+    H = sympy.Rational(1, 2)
+    worst = 0.0
+    for tj1 in range(1, 8, 2):
+        for tj2 in range(1, 8, 2):
+            for tJ in range(abs(tj1 - tj2), tj1 + tj2 + 1, 2):
+                for tm1 in range(-tj1, tj1 + 1, 2):
+                    for tm2 in range(-tj2, tj2 + 1, 2):
+                        tM = tm1 + tm2
+                        if abs(tM) > tJ:
+                            continue
+                        ref = float(clebsch_gordan(tj1 * H, tj2 * H, tJ * H, tm1 * H, tm2 * H, tM * H))
+                        worst = max(worst, abs(O.cg(tj1, tm1, tj2, tm2, tJ, tM) - ref))
+    assert worst < 1e-13
+
+
+def test_cg_orthogonality():
+    for tj1, tj2 in [(7, 5), (5, 5), (3, 1), (7, 7)]:
+        for tM in range(-(tj1 + tj2), tj1 + tj2 + 1, 2):
+            Js = [tJ for tJ in range(abs(tj1 - tj2), tj1 + tj2 + 1, 2) if abs(tM) <= tJ]
+            ms = [(m1, tM - m1) for m1 in range(-tj1, tj1 + 1, 2) if abs(tM - m1) <= tj2]
+            C = np.array([[O.cg(tj1, m1, tj2, m2, tJ, tM) for (m1, m2) in ms] for tJ in Js])
+            assert C.shape[0] == C.shape[1]
+            assert np.allclose(C @ C.T, np.eye(len(Js)), atol=1e-13)
+
+
+def test_cg_closed_forms():
+    # <j m j -m | 0 0> = (-1)^(j-m) / sqrt(2j+1); stretched state = 1
+    for tj in (1, 3, 5, 7):
+        for tm in range(-tj, tj + 1, 2):
+            assert abs(O.cg(tj, tm, tj, -tm, 0, 0) - (-1) ** ((tj - tm) // 2) / np.sqrt(tj + 1)) < 1e-14
+        assert abs(O.cg(tj, tj, 5, 5, tj + 5, tj + 5) - 1.0) < 1e-14
+
+
+# ----------------------------------------------------------------- sign rule
+def _m(s):
+    return sum(1 << i for i, c in enumerate(s) if c == "1")
+
+
+def test_sign_rule_paper_examples():
+    # a_2 |110101> = -|100101> (states counted from 1 at the left)
+    assert O.apply_string(_m("110101"), [("-", 1)]) == (-1, _m("100101"))
+    # a_2 |100111> = 0
+    assert O.apply_string(_m("100111"), [("-", 1)])[0] == 0
+    # a+_3 |110001> = |110101> and a+_3 |100101> = 0: these two examples count
+    # states from 0 at the left (the paper mixes the two countings).
+    assert O.apply_string(_m("110001"), [("+", 3)]) == (1, _m("110101"))
+    assert O.apply_string(_m("100101"), [("+", 3)])[0] == 0
+    # a+_3 a+_5 a_4 a_1 |1101011> = -a+_3 a+_5 |0100011>, and the full string is negative
+    assert O.apply_string(_m("1101011"), [("-", 3), ("-", 0)]) == (-1, _m("0100011"))
+    sg, _ = O.apply_string(_m("1101011"), [("+", 2), ("+", 4), ("-", 3), ("-", 0)])
+    assert sg == -1
+
+
+# ----------------------------------------------------------------- basis
+def _golden_dims():
+    rows = []
+    for line in open(os.path.join(GOLD, "basis_dims.txt")):
+        if line.startswith("#") or not line.strip():
+            continue
+        f = line.split()
+        rows.append((f[0], *[int(v) for v in f[1:6]], *(None if v == "-" else int(v) for v in f[6:9])))
+    return rows
+
+
+@pytest.mark.parametrize("row", _golden_dims(), ids=lambda r: "%s-%dp%dn-2M%d" % (r[0], r[1], r[2], r[3]))
+def test_basis_dimensions_from_paper(row):
+    name, Z, N, twoM, par, dim, npsd, nnsd_used, npsec = row
+    orbits, _ = I.SPACES[name]
+    o = O.Oracle(orbits, Z, N, twoM, par)
+    assert o.dim == dim
+    B = o.basis()
+    if npsd is not None:
+        assert o.n_psd == npsd
+    if nnsd_used is not None:
+        used = sum(int(B["n_sec"][b[1]][3]) for b in B["blocks"])
+        assert used == nnsd_used
+    if npsec is not None:
+        assert o.n_psec == npsec
+
+
+def test_al27_sector_table():
+    rows = [tuple(int(v) for v in l.split()) for l in open(os.path.join(GOLD, "al27_sectors.txt"))
+            if l.strip() and not l.startswith("#")]
+    o = O.Oracle(I.SD_ORBITS, 5, 6, 1, 0)
+    B = o.basis()
+    got = set()
+    for (ps, ns_, off) in B["blocks"]:
+        mp, _, _, cp = B["p_sec"][ps]
+        mn, _, _, cn = B["n_sec"][ns_]
+        got.add((int(mp), int(cp), int(mn), int(cn), int(cp * cn)))
+    assert got == set(rows)
+    assert sum(r[4] for r in rows) == 80115 == o.dim
+
+
+def test_ne20_first_proton_sector():
+    # 20Ne .bas example: first proton sector 2Jz = -8, parity +, two proton SDs
+    o = O.Oracle(I.SD_ORBITS, 2, 2, 0, 0)
+    B = o.basis()
+    assert tuple(B["p_sec"][0][:2]) == (-8, 0) and B["p_sec"][0][3] == 2
+    assert o.n_psec == 9 and o.n_psd == 66
+
+
+@pytest.mark.parametrize("Z,N,twoM", [(2, 1, 1), (1, 2, -1), (3, 2, 3), (0, 2, 0), (2, 0, 2)])
+def test_basis_brute_force(Z, N, twoM):
+    orbits = I.SD_ORBITS
+    st = [(a, tm) for a, o in enumerate(orbits) for tm in range(-o.twoj, o.twoj + 1, 2)]
+    par = [orbits[a].l % 2 for a, _ in st]
+
+    def key(c):
+        return sum(st[s][1] for s in c), sum(par[s] for s in c) % 2
+
+    states = set()
+    for cp in itertools.combinations(range(len(st)), Z):
+        for cn in itertools.combinations(range(len(st)), N):
+            if key(cp)[0] + key(cn)[0] == twoM and (key(cp)[1] + key(cn)[1]) % 2 == 0:
+                states.add((sum(1 << s for s in cp), sum(1 << s for s in cn)))
+    o = O.Oracle(orbits, Z, N, twoM, 0)
+    P, Nn = o.states()
+    got = list(zip(P.tolist(), Nn.tolist()))
+    assert len(got) == len(set(got)) == len(states)
+    assert set(got) == states
+    # proton index outer, neutron inner; sectors by 2M ascending; bitmask order inside
+    B = o.basis()
+    for s in range(o.n_psec):
+        _, _, st0, c = B["p_sec"][s]
+        assert np.all(np.diff(B["p_bits"][st0:st0 + c].astype(np.int64)) > 0)
+    assert np.all(np.diff(B["p_sec"][:, 0] * 2 + B["p_sec"][:, 1]) > 0)
+
+
+# ----------------------------------------------------------------- two-body closed forms
+@pytest.mark.parametrize("name,twoM", [("sd", 0), ("sd", 2), ("pf", 0), ("pf", 4), ("p", 0)])
+def test_one_proton_one_neutron_closed_form(name, twoM):
+    orbits, spe, tb = I.space(name)
+    o = O.Oracle(orbits, 1, 1, twoM, 0)
+    o.set_interaction(spe, tb)
+    ev = np.linalg.eigvalsh(o.dense())
+    ref = []
+    jmax = max(x.twoj for x in orbits)
+    for T in (0, 1):
+        for J in range(abs(twoM) // 2, jmax + 1):
+            ref.extend(channel_spectrum(orbits, spe, tb, J, T))
+    ref = np.sort(ref)
+    assert len(ref) == o.dim
+    assert np.max(np.abs(ev - ref)) < 1e-11
+
+
+@pytest.mark.parametrize("name,Z,N", [("sd", 2, 0), ("sd", 0, 2), ("pf", 2, 0)])
+def test_two_like_particles_closed_form(name, Z, N):
+    orbits, spe, tb = I.space(name)
+    o = O.Oracle(orbits, Z, N, 0, 0)
+    o.set_interaction(spe, tb)
+    ev = np.linalg.eigvalsh(o.dense())
+    jmax = max(x.twoj for x in orbits)
+    ref = np.sort(np.concatenate([channel_spectrum(orbits, spe, tb, J, 1) for J in range(0, jmax + 1)]))
+    assert len(ref) == o.dim
+    assert np.max(np.abs(ev - ref)) < 1e-11
+
+
+def test_one_body_only_spectrum():
+    orbits, spe, _ = I.space("sd")
+    o = O.Oracle(orbits, 2, 3, 1, 0)
+    o.set_interaction(spe, [])
+    H = o.dense()
+    assert np.count_nonzero(H - np.diag(np.diag(H))) == 0
+    P, Nn = o.states()
+    st_e = [spe[a] for a, x in enumerate(orbits) for _ in range(x.twoj + 1)]
+    ref = [sum(st_e[s] for s in range(12) if (int(p) >> s) & 1) + sum(st_e[s] for s in range(12) if (int(n) >> s) & 1)
+           for p, n in zip(P, Nn)]
+    assert np.allclose(np.sort(np.linalg.eigvalsh(H)), np.sort(ref), atol=1e-13)
+    # lowest = best M-allowed filling
+    assert abs(np.min(ref) - np.linalg.eigvalsh(H)[0]) < 1e-13
+
+
+# ----------------------------------------------------------------- assembly
+@pytest.fixture(scope="module")
+def sd22():
+    orbits, spe, tb = I.space("sd")
+    o = O.Oracle(orbits, 2, 2, 0, 0).set_interaction(spe, tb)
+    return o
+
+
+def test_matrix_symmetric(sd22):
+    H = sd22.dense()
+    assert np.max(np.abs(H - H.T)) <= 1e-13 * np.max(np.abs(H))
+
+
+def test_any_label_order_same_matrix(sd22):
+    orbits, spe, tb = I.space("sd")
+    o2 = O.Oracle(orbits, 2, 2, 0, 0).set_interaction(spe, scrambled_tbmes(tb, orbits))
+    assert np.max(np.abs(o2.dense() - sd22.dense())) < 1e-13
+
+
+def test_rejects_invalid_elements():
+    orbits, spe, tb = I.space("sd")
+    o = O.Oracle(orbits, 2, 2, 0, 0)
+    for bad in [(1, 1, 1, 1, 1, 1, 1.0),     # d5/2^2 with J+T even (Pauli)
+                (1, 2, 1, 2, 0, 1, 1.0),     # d5/2 s1/2 cannot couple to J=0
+                (1, 1, 1, 4, 1, 0, 1.0),     # orbit 4 does not exist
+                (1, 1, 1, 1, 1, 2, 1.0)]:    # T = 2
+        with pytest.raises(O.OracleError):
+            o.set_interaction(spe, [bad])
+    with pytest.raises(O.OracleError):       # same element twice, once in another label order
+        a, b, c, d, J, T, v = tb[5]
+        o.set_interaction(spe, [tb[5], (c, d, a, b, J, T, v)])
+    mixed = (I.Orbit(0, 2, 5), I.Orbit(0, 3, 7))
+    with pytest.raises(O.OracleError):       # parity change d5/2 f7/2 -> d5/2 d5/2
+        O.Oracle(mixed, 2, 0, 0, 0).set_interaction([0.0, 0.0], [(1, 2, 1, 1, 2, 1, 1.0)])
+
+
+def test_trace_from_occupation_counts():
+    orbits, spe, tb = I.space("sd")
+    o = O.Oracle(orbits, 4, 3, 1, 0).set_interaction(spe, tb)
+    wpp, wpn = o.w_tables()
+    P, Nn = o.states()
+    ns = o.ns
+    occP = ((P[:, None] >> np.arange(ns, dtype=np.uint64)) & np.uint64(1)).astype(np.float64)
+    occN = ((Nn[:, None] >> np.arange(ns, dtype=np.uint64)) & np.uint64(1)).astype(np.float64)
+    st_e = np.array([spe[a] for a, x in enumerate(orbits) for _ in range(x.twoj + 1)])
+    tr = st_e @ occP.sum(0) + st_e @ occN.sum(0)
+    pairP = occP.T @ occP
+    pairN = occN.T @ occN
+    pn = occP.T @ occN
+    for s in range(ns):
+        for t in range(s + 1, ns):
+            tr += wpp[s, t, s, t] * (pairP[s, t] + pairN[s, t])
+    for i in range(ns):
+        for j in range(ns):
+            tr += wpn[i, j, i, j] * pn[i, j]
+    assert abs(o.trace() - tr) < 1e-9 * max(1.0, abs(tr))
+
+
+# ----------------------------------------------------------------- rotational invariance
+def test_m1_spectrum_inside_m0(sd22):
+    orbits, spe, tb = I.space("sd")
+    o1 = O.Oracle(orbits, 2, 2, 2, 0).set_interaction(spe, tb)
+    e0 = np.linalg.eigvalsh(sd22.dense())
+    e1 = np.linalg.eigvalsh(o1.dense())
+    worst, left = match_subset(e1, e0, 1e-9)
+    assert worst < 1e-9
+    assert len(left) == sd22.dim - o1.dim
+
+
+def test_j2_integer(sd22):
+    orbits, spe, tb = I.space("sd")
+    up = O.Oracle(orbits, 2, 2, 2, 0)
+    ev, X = np.linalg.eigh(sd22.dense())
+    for n in range(12):
+        j2 = sd22.j2(X[:, n], up)
+        J = O.j_from_j2(j2)
+        assert abs(J - round(J)) < 1e-8, (n, ev[n], j2)
+
+
+# ----------------------------------------------------------------- Lanczos
+def test_lanczos_matches_dense(sd22):
+    piv = I.random_block(sd22.dim, 1)[:, 0]
+    ev_l = sd22.lanczos(piv, 200, nkeep=5)
+    ev_d = np.linalg.eigvalsh(sd22.dense())[:5]
+    assert np.max(np.abs(ev_l - ev_d)) < 1e-9
+
+
+def test_lanczos_ritz_vectors_are_eigenvectors(sd22):
+    piv = I.random_block(sd22.dim, 1)[:, 0]
+    ev, X = sd22.lanczos(piv, 200, nkeep=3, return_vectors=True)
+    H = sd22.matrix()
+    for n in range(3):
+        r = H @ X[:, n] - ev[n] * X[:, n]
+        assert np.linalg.norm(r) < 1e-8
