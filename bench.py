@@ -1,0 +1,321 @@
+#!/usr/bin/env python3
+"""Benchmark: on-the-fly M-scheme H*X for 48Cr in the pf shell (4 protons + 4
+neutrons, M=0, dim 1,963,461, seeded random isospin-coupled TBMEs).
+
+A step is one block product Y = H X over k interleaved FP32 vectors through
+the library's fused CUDA kernel (the FP32-mixed block path); `value` counts
+vector-matvecs per second (k per step), whole job.  The same run also times
+the plain FP64 single-vector path and reports the speedup, the end-to-end
+rate through the host-buffer C-ABI call, a roofline line for the kernel and
+the CPU oracle timed on a bounded sample of rows.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs under torchrun: every rank works on its own GPU on its own copy of
+the workload (the product has no exchange step on one basis; see the design
+notes), and the time is the max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "48Cr-pf H·x matvecs/s & HBM GB/s vs peak: FP32-mixed block vs FP64, ≤1e-4 MeV"
+UNIT = "vector-matvecs/s"
+WORKLOAD = dict(space="pf", Z=4, N=4, twoM=0, parity=+1)
+WORKLOAD_NAME = "pf shell 4p4n M=0 (48Cr), dim 1963461, 195 seeded random TBMEs"
+
+
+def peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([v.strip() for v in line.split(",")])
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.25)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.t.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            if len(r) < 9:
+                continue
+            for n, v in zip(names, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_baseline(budget_s=12.0, seed=5):
+    """The FP64 oracle, as it stands, on a bounded sample of rows of the same
+    workload: H x row by row on the fly on all host cores."""
+    import oracle as O
+    from paper_1801_08432_gb300 import inputs as I
+    orbits, spe, tb = I.space(WORKLOAD["space"])
+    o = O.Oracle(orbits, WORKLOAD["Z"], WORKLOAD["N"], WORKLOAD["twoM"], 0).set_interaction(spe, tb)
+    rng = np.random.default_rng(seed)
+    x = I.random_block(o.dim, 1, seed=seed)[:, 0]
+    n = 2000
+    t0 = time.perf_counter()
+    o.apply_rows(rng.integers(0, o.dim, n), x)
+    t1 = time.perf_counter()
+    rate = n / max(t1 - t0, 1e-9)
+    n2 = int(max(2000, min(5_000_000, rate * budget_s)))
+    rows = rng.integers(0, o.dim, n2)
+    t0 = time.perf_counter()
+    o.apply_rows(rows, x)
+    dt = time.perf_counter() - t0
+    rows_per_s = n2 / dt
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return {"value": rows_per_s / o.dim, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d random rows of H x (FP64, on the fly from bit operations) in %.1f s = %.0f rows/s; "
+                      "value = rows/s / dim" % (n2, dt, rows_per_s)}
+
+
+def reference_arm(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    steps_cb = []
+    for _ in range(args.warmup):
+        cpu_baseline(budget_s=1.0)
+    for _ in range(args.steps):
+        steps_cb.append(cpu_baseline(budget_s=max(2.0, 30.0 / max(1, args.steps))))
+    vals = [c["value"] for c in steps_cb]
+    v = float(np.mean(vals))
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1000.0 / v if v > 0 else None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": WORKLOAD_NAME, "k": 1, "sample": "bounded random rows per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": steps_cb[-1]["cores"], "kind": "oracle",
+                             "sample": steps_cb[-1]["sample"]},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def traffic_from_profile(k):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source; else None."""
+    src = os.path.join(ROOT, "paper_1801_08432_gb300", "csrc", "bs_hx.cu")
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    path = os.path.join(ROOT, "profiles", "hx_fused_pf4p4n.md")
+    if not os.path.exists(path):
+        return None
+    for line in open(path):
+        f = line.strip().split()
+        # "traffic k=<k> src=<sha> dram_bytes=<n>"
+        if len(f) == 4 and f[0] == "traffic" and f[1] == "k=%d" % k and f[2] == "src=" + sha:
+            return int(f[3].split("=")[1])
+    return None
+
+
+def ours(args):
+    import torch
+    from paper_1801_08432_gb300 import _native as N
+    from paper_1801_08432_gb300 import build as B
+    from paper_1801_08432_gb300 import inputs as I
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    B.build()
+    orbits, spe, tb = I.space(WORKLOAD["space"])
+    t0 = time.time()
+    ctx = N.make(orbits, spe, tb, WORKLOAD["Z"], WORKLOAD["N"], WORKLOAD["twoM"], WORKLOAD["parity"], device=local)
+    setup_s = time.time() - t0
+    dim = ctx.dim
+    stats = ctx.table("stats", np.int64)
+    ops = float(stats[5])
+    tbytes = 0
+    for name, sz in (("pp_src", 4), ("pp_coef", 8), ("nn_src", 4), ("nn_coef", 8), ("p1_ent", 4), ("n1_ent", 4),
+                     ("p1_ptr", 8), ("n1_ptr", 8), ("pp_ptr", 8), ("nn_ptr", 8), ("wpn", 8)):
+        n = len(ctx.table(name, np.uint8))
+        tbytes += n if sz != 8 or not name.endswith(("coef", "wpn")) else n // 2   # FP32 coefficients
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    def bar():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def timed(k, dtype, steps, warmup):
+        tdt = torch.float32 if dtype == N.BS_F32 else torch.float64
+        g = torch.Generator(device="cuda").manual_seed(1234 + k)
+        x = torch.randn((dim, k), device="cuda", dtype=tdt, generator=g)
+        y = torch.empty_like(x)
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                ctx.apply_H(x, y, k, dtype, sp)
+        stream.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        bar()
+        for i in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()                        # > L2: the next launch starts cold
+                ev[i][0].record(stream)
+                ctx.apply_H(x, y, k, dtype, sp)
+                ev[i][1].record(stream)
+        stream.synchronize()
+        bar()
+        ms = [a.elapsed_time(b) for (a, b) in ev]
+        return ms, x, y
+
+    # autotune k (the only free launch parameter of this kernel version)
+    tune = {}
+    for k in (1, 2, 4, 8):
+        ms, _, _ = timed(k, N.BS_F32, 3, 2)
+        tune[k] = k / (min(ms) / 1000.0)
+    kbest = max(tune, key=tune.get)
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    ms32, _, _ = timed(kbest, N.BS_F32, args.steps, args.warmup)
+    clocks = sampler.stop()
+    ms64, _, _ = timed(1, N.BS_F64, max(3, args.steps // 2), max(3, args.warmup))
+
+    # end to end through the host-buffer call: pinned host input, H*X, result back
+    xh = torch.randn((dim, kbest), dtype=torch.float32).pin_memory()
+    yh = torch.empty_like(xh).pin_memory()
+    xa = xh.numpy()
+    ya = yh.numpy()
+    for _ in range(2):
+        ctx.apply_H_host(xa, ya, kbest, N.BS_F32, sp)
+    bar()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        ctx.apply_H_host(xa, ya, kbest, N.BS_F32, sp)
+    bar()
+    e2e_s = time.perf_counter() - t0
+
+    t_ms = float(np.sum(ms32))
+    t_max = t_ms
+    e2e_max = e2e_s
+    if dist is not None:
+        tt = torch.tensor([t_ms, e2e_s], device="cuda", dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_max, e2e_max = float(tt[0]), float(tt[1])
+    value = world * args.steps * kbest / (t_max / 1000.0)
+    avg_launch_s = t_ms / args.steps / 1000.0
+    fp64_rate = 1.0 / (float(np.mean(ms64)) / 1000.0)
+    fp32_rate_single = kbest / avg_launch_s
+    pk = peaks()
+    sm_mhz_max = (pk or {}).get("sm_max_mhz", 2070.0)
+    nsm = torch.cuda.get_device_properties(local).multi_processor_count
+    fp32_peak = nsm * 128 * 2 * sm_mhz_max * 1e6 / 1e12       # TFLOP/s, FMA = 2 FLOP
+    flops = 2.0 * ops * kbest
+    achieved = flops / avg_launch_s / 1e12
+    alg_bytes = 2.0 * dim * kbest * 4 + tbytes
+    hbm_peak = (pk or {}).get("hbm_gbs", 6800.0)
+    traffic = traffic_from_profile(kbest)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": WORKLOAD_NAME, "k": kbest, "path": "FP32-mixed block H*X (fused kernel)",
+                   "l2": "flushed: 256 MB write before every timed launch", "parallelism": "replicas" if world > 1 else "1 GPU",
+                   "set_up_s": round(setup_s, 2)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
+                     "frac": achieved / fp32_peak, "traffic": traffic,
+                     "peak_note": "FP32 FMA issue: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, not measured)" % (nsm, sm_mhz_max),
+                     "flop_per_launch": flops},
+        "hbm": {"algorithmic_bytes_per_launch": alg_bytes, "gbs": alg_bytes / avg_launch_s / 1e9,
+                "peak_gbs": hbm_peak, "frac": alg_bytes / avg_launch_s / 1e9 / hbm_peak,
+                "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)" if pk else "fallback"},
+        "fp64_single_vector": {"value": fp64_rate, "unit": UNIT, "ms_per_matvec": float(np.mean(ms64))},
+        "speedup_fp32_block_vs_fp64": fp32_rate_single / fp64_rate,
+        "autotune_k": {str(k): v for k, v in tune.items()},
+        "e2e": {"value": world * args.steps * kbest / e2e_max, "unit": UNIT,
+                "h2d_bytes_per_step": dim * kbest * 4, "d2h_bytes_per_step": dim * kbest * 4},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        return reference_arm(args)
+    return ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,148 @@
+/*
+ * bigstick_gpu.h -- C ABI of libbsgpu.so: the factorized, on-the-fly product
+ * y = H x of the M-scheme shell-model Hamiltonian on one GB300 (sm_103a).
+ *
+ * The method is the one of the BIGSTICK manual (arXiv:1801.08432):
+ *   - basis: proton and neutron Slater determinants as occupation bitstrings,
+ *     grouped into sectors by (2M, parity); every proton SD of a sector is
+ *     combined with every neutron SD of the conjugate sector (M_p + M_n = M),
+ *     proton index outer, neutron index inner (Sec. "Factorization of the
+ *     basis", Table al27, basis-file pseudocode "pstart + nstart");
+ *   - Hamiltonian: Eq. (hamdef), single-particle energies plus isospin-coupled
+ *     two-body matrix elements V_JT(ab,cd) between normalized states (Sec.
+ *     "Interaction files", Eq. tbmedef), pp/nn from T=1 and pn from
+ *     Eq. (xpndef);
+ *   - application: proton-only and neutron-only jumps, the pn term as a proton
+ *     one-body jump times a neutron one-body jump (Sec. "The Lanczos
+ *     algorithm and computational cost", jump discussion around Table jumps);
+ *   - Lanczos with full reorthogonalization (Sec. "Standard Lanczos
+ *     algorithm") and block Lanczos (Sec. "Block Lanczos").
+ *
+ * Conventions shared by every call
+ *   - Single-particle states: orbit after orbit in input order, 2m ascending
+ *     inside an orbit.  A Slater determinant is a uint64 bitmask (bit s =
+ *     state s occupied), so at most 64 states per species.
+ *   - Sectors: (2M, parity) with 2M ascending and parity + before -; inside
+ *     a sector, SDs sorted by bitmask ascending.  Blocks: proton sectors in
+ *     order, each with its conjugate neutron sector; basis index =
+ *     block offset + ip_local * |S_n| + jn_local.
+ *   - Vectors (x, y, gy, gx, pivot, evecs) are DEVICE buffers laid out
+ *     [dim][k], the k vectors of a block contiguous per basis state (the
+ *     row-wise block layout of Sec. "Block Lanczos").  Element type is double
+ *     for BS_F64 and float for BS_F32.  Buffers must be 16-byte aligned.
+ *     The caller owns them; the library never frees or keeps them.
+ *   - `stream` is a cudaStream_t (0 = legacy default stream).  Work is
+ *     enqueued asynchronously; the call returns before the GPU finishes
+ *     unless stated otherwise.
+ *   - Every call returns BS_OK (0) or a negative code; on error the output
+ *     buffers are unspecified and bs_last_error() holds a message.  No C++
+ *     exception crosses this interface.  A context is not thread-safe.
+ */
+#ifndef BIGSTICK_GPU_H
+#define BIGSTICK_GPU_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bs_ctx bs_ctx;
+
+/* One orbit (n, l, 2j, w) of the single-particle space (Sec. "Single-particle
+ * space"); l fixes the parity (-1)^l.  w must be equal for all orbits (no
+ * W truncation). */
+typedef struct { int n, l, twoj, w; } bs_orbit;
+
+/* One isospin-coupled two-body matrix element V_JT(ab,cd) in MeV, labels
+ * 1-based orbit indices, in any label order and any list order (Sec.
+ * "Interaction files"). */
+typedef struct { int a, b, c, d, J, T; double v; } bs_tbme;
+
+typedef enum { BS_F64 = 0, BS_F32 = 1 } bs_dtype;
+
+enum {
+    BS_OK = 0,
+    BS_EINVAL = -1,      /* bad argument: orbits, Z/N, 2M parity vs A, TBME label or selection rule, k, dtype */
+    BS_ENOBASIS = -2,    /* no basis built yet */
+    BS_ENOINT = -3,      /* no interaction loaded yet */
+    BS_ENOMEM = -4,      /* device or host allocation failed, or a memory cap was exceeded */
+    BS_ECUDA = -5,       /* a CUDA call failed */
+    BS_EBREAKDOWN = -6,  /* Lanczos breakdown that could not be restarted */
+    BS_ETIMEOUT = -7     /* a device-side wait ran out of its iteration budget */
+};
+
+/* Creates a context on CUDA device `cuda_device`.  *out receives the handle.
+ * cuda_device = -1 makes a host-only context: basis, decoupling and jump
+ * tables are built on the CPU and nothing is uploaded; every product call
+ * then fails with BS_EINVAL.  Errors: BS_EINVAL (no such device), BS_ECUDA. */
+int bs_create(bs_ctx **out, int cuda_device);
+
+/* Frees every table and workspace of the context (device and host). */
+void bs_destroy(bs_ctx *ctx);
+
+/* Message of the last failed call on this context ("" if none).  The string
+ * stays valid until the next call on the context. */
+const char *bs_last_error(const bs_ctx *ctx);
+
+/* Builds the M-scheme basis of Z valence protons and N valence neutrons with
+ * total 2M = twoM and parity (+1 or -1) over the given orbits (Sec.
+ * "Factorization of the basis").  Replaces any earlier basis and interaction.
+ * Errors: BS_EINVAL (n_orbits <= 0, 2j even or <= 0, more than 64 states,
+ * Z or N negative or larger than the number of states, twoM of the wrong
+ * parity for A = Z + N, parity not +-1, unequal w, empty basis). */
+int bs_build_basis(bs_ctx *ctx, const bs_orbit *orbits, int n_orbits,
+                   int Z, int N, int twoM, int parity);
+
+/* Sizes of the built basis.  Any pointer may be NULL.  Errors: BS_ENOBASIS. */
+int bs_basis_info(bs_ctx *ctx, int64_t *dim, int *n_psec, int *n_nsec,
+                  int *n_psd, int *n_nsd, int *n_blocks);
+
+/* Copies the basis to caller-allocated HOST arrays (for bit-exact checks):
+ * p_bits[n_psd], n_bits[n_nsd]; p_sec[4*n_psec], n_sec[4*n_nsec] as
+ * (2M, parity 0=+ 1=-, start, count); blocks[3*n_blocks] as (proton sector,
+ * neutron sector, offset).  Errors: BS_ENOBASIS. */
+int bs_export_basis(bs_ctx *ctx, uint64_t *p_bits, uint64_t *n_bits,
+                    int64_t *p_sec, int64_t *n_sec, int64_t *blocks);
+
+/* Loads the interaction: spe[n_spe] single-particle energies, one per orbit,
+ * used for protons and neutrons alike; tbme[n_tbme] isospin-coupled elements.
+ * An empty TBME list is legal (SPE only).  Decouples them to M-scheme
+ * elements in FP64 (Eq. hamdef with Clebsch-Gordan coefficients of Edmonds,
+ * Eq. xpndef for pn), builds the jump tables and uploads FP64 and FP32 copies
+ * of all coefficients.  May be called again to replace the interaction.
+ * Errors: BS_ENOBASIS; BS_EINVAL (n_spe != n_orbits, a label out of range,
+ * T not 0/1, J outside a pair's triangle, same-orbit pair with J+T even,
+ * parity change, the same element given twice); BS_ENOMEM; BS_ECUDA. */
+int bs_load_interaction(bs_ctx *ctx, const double *spe, int n_spe,
+                        const bs_tbme *tbme, int n_tbme);
+
+/* y = H x for a block of k vectors (k in 1, 2, 4, 8), on `stream`.
+ * x, y: device, [dim][k], dtype elements, distinct (no aliasing).  BS_F64
+ * computes in double; BS_F32 reads/writes float and accumulates in float
+ * with coefficients rounded once from the FP64 decoupling.  y is fully
+ * overwritten.  Deterministic: every element of y is owned by one thread and
+ * summed in a fixed order.  Errors: BS_ENOBASIS, BS_ENOINT, BS_EINVAL, BS_ECUDA. */
+int bs_apply_H(bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dtype, void *stream);
+
+/* The same product with HOST buffers x_host, y_host ([dim][k]); copies in,
+ * applies, copies out on `stream` and synchronizes it before returning.
+ * Uses device buffers the context owns (allocated on first use, reused).
+ * Errors as bs_apply_H plus BS_ENOMEM. */
+int bs_apply_H_host(bs_ctx *ctx, const void *x_host, void *y_host, int k,
+                    bs_dtype dtype, void *stream);
+
+/* Test aid: copies a host-side table of the built interaction by name
+ * ("pp_ptr", "pp_src", "pp_coef", "nn_*", "p1_ptr", "p1_ent", "p1_cls",
+ * "n1_*", "wpn", "links", "ops", "op_lists", "stats") into `out` (HOST,
+ * caller-allocated; NULL to query the size).  *nbytes receives the size in
+ * bytes.  Works on host-only contexts (bs_create with cuda_device = -1),
+ * so the host builders can be checked on a machine without a GPU.
+ * Errors: BS_ENOINT, BS_EINVAL (unknown name). */
+int bs_debug_table(bs_ctx *ctx, const char *name, void *out, int64_t *nbytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* BIGSTICK_GPU_H */

@@ -73,6 +73,7 @@ def lib():
             L.orc_export_matrix.argtypes = [ctypes.c_void_p, i64p, i64p, f64p]
             L.orc_spmv.argtypes = [ctypes.c_void_p, f64p, f64p, ctypes.c_int]
             L.orc_apply_rows.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64, f64p, ctypes.c_int, f64p]
+            L.orc_apply_rows_ex.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64, f64p, ctypes.c_int, f64p, ctypes.c_int]
             L.orc_jplus.argtypes = [ctypes.c_void_p, ctypes.c_void_p, f64p, f64p]
             L.orc_jplus.restype = ctypes.c_int
             L.orc_cg.argtypes = [ctypes.c_int] * 6
@@ -209,13 +210,14 @@ class Oracle:
         lib().orc_spmv(self.h, _p(x, f64p), _p(y, f64p), k)
         return y
 
-    def apply_rows(self, rows, x):
-        """Rows of y = H x computed on the fly (no stored matrix)."""
+    def apply_rows(self, rows, x, absval=False):
+        """Rows of y = H x computed on the fly (no stored matrix); with
+        absval=True rows of |H| |x| (a bound for rounding errors)."""
         rows = np.ascontiguousarray(rows, dtype=np.int64)
         x = np.ascontiguousarray(x, dtype=np.float64)
         k = 1 if x.ndim == 1 else x.shape[1]
         y = np.zeros((len(rows), k))
-        lib().orc_apply_rows(self.h, _p(rows, i64p), len(rows), _p(x, f64p), k, _p(y, f64p))
+        lib().orc_apply_rows_ex(self.h, _p(rows, i64p), len(rows), _p(x, f64p), k, _p(y, f64p), int(absval))
         return y[:, 0] if x.ndim == 1 else y
 
     def dense(self):

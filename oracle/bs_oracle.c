@@ -667,7 +667,8 @@ void orc_spmv(const orc *o, const double *x, double *y, int k)
 
 /* Selected rows of y = H x computed on the fly, without the matrix:
  * <alpha|H|x> = sum_beta x_beta <beta|H|alpha> (H Hermitian, real). */
-void orc_apply_rows(const orc *o, const int64_t *rows, int64_t nrows, const double *x, int k, double *yrows)
+void orc_apply_rows_ex(const orc *o, const int64_t *rows, int64_t nrows, const double *x, int k, double *yrows,
+                       int absval)
 {
 #pragma omp parallel
     {
@@ -681,12 +682,20 @@ void orc_apply_rows(const orc *o, const int64_t *rows, int64_t nrows, const doub
             merge_list(&L);
             for (int c = 0; c < k; ++c) {
                 double s = 0.0;
-                for (int64_t t = 0; t < L.n; ++t) s += L.e[t].v * x[L.e[t].idx * k + c];
+                for (int64_t t = 0; t < L.n; ++t)
+                    s += absval ? fabs(L.e[t].v) * fabs(x[L.e[t].idx * k + c]) : L.e[t].v * x[L.e[t].idx * k + c];
                 yrows[r * k + c] = s;
             }
         }
         free(L.e);
     }
+}
+
+/* Selected rows of y = H x (absval = 0) or of |H| |x| (absval = 1, for
+ * rounding-error bounds), on the fly. */
+void orc_apply_rows(const orc *o, const int64_t *rows, int64_t nrows, const double *x, int k, double *yrows)
+{
+    orc_apply_rows_ex(o, rows, nrows, x, k, yrows, 0);
 }
 
 /* out = J+ psi, psi in basis `from` (2M), out in basis `to` (2M+2), both

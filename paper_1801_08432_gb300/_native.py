@@ -1,0 +1,167 @@
+"""ctypes binding of libbsgpu.so (include/bigstick_gpu.h), same names as the C ABI.
+
+Argument marshalling only: every step of H*x, its adjoint and the Lanczos
+driver runs in the library's CUDA kernels.  The library must have been built
+(``paper_1801_08432_gb300.build.build()``); loading fails loudly otherwise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libbsgpu.so")
+
+BS_F64, BS_F32 = 0, 1
+ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "BS_ENOMEM",
+          -5: "BS_ECUDA", -6: "BS_EBREAKDOWN", -7: "BS_ETIMEOUT"}
+
+# every symbol include/bigstick_gpu.h declares
+EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
+            "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
+            "bs_debug_table"]
+
+
+class bs_orbit(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("l", ctypes.c_int), ("twoj", ctypes.c_int), ("w", ctypes.c_int)]
+
+
+class bs_tbme(ctypes.Structure):
+    _fields_ = [("a", ctypes.c_int), ("b", ctypes.c_int), ("c", ctypes.c_int), ("d", ctypes.c_int),
+                ("J", ctypes.c_int), ("T", ctypes.c_int), ("v", ctypes.c_double)]
+
+
+class BSError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "?"), code, msg))
+        self.code = code
+
+
+_lib = None
+vp = ctypes.c_void_p
+i64p = ctypes.POINTER(ctypes.c_int64)
+i32p = ctypes.POINTER(ctypes.c_int)
+u64p = ctypes.POINTER(ctypes.c_uint64)
+f64p = ctypes.POINTER(ctypes.c_double)
+
+
+def load():
+    """Loads libbsgpu.so; raises if it is missing (there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("libbsgpu.so is not built: run paper_1801_08432_gb300.build.build() "
+                           "(there is no CPU fallback)")
+    L = ctypes.CDLL(LIB_PATH)
+    L.bs_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int]
+    L.bs_destroy.argtypes = [vp]
+    L.bs_destroy.restype = None
+    L.bs_last_error.argtypes = [vp]
+    L.bs_last_error.restype = ctypes.c_char_p
+    L.bs_build_basis.argtypes = [vp, ctypes.POINTER(bs_orbit), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                 ctypes.c_int, ctypes.c_int]
+    L.bs_basis_info.argtypes = [vp, i64p, i32p, i32p, i32p, i32p, i32p]
+    L.bs_export_basis.argtypes = [vp, u64p, u64p, i64p, i64p, i64p]
+    L.bs_load_interaction.argtypes = [vp, f64p, ctypes.c_int, ctypes.POINTER(bs_tbme), ctypes.c_int]
+    L.bs_apply_H.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    L.bs_apply_H_host.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    L.bs_debug_table.argtypes = [vp, ctypes.c_char_p, vp, i64p]
+    for name in EXPORTED:
+        if name not in ("bs_destroy", "bs_last_error"):
+            getattr(L, name).restype = ctypes.c_int
+    _lib = L
+    return L
+
+
+def _p(a, t):
+    return a.ctypes.data_as(t)
+
+
+class Context:
+    """One bs_ctx: a basis, an interaction and their device tables.
+
+    device=-1 builds a host-only context (basis, decoupling and jump tables on
+    the CPU, no upload; H*x calls are refused), used to test the host builders
+    on machines without a GPU.
+    """
+
+    def __init__(self, device: int = 0):
+        L = load()
+        h = vp()
+        rc = L.bs_create(ctypes.byref(h), device)
+        if rc != 0:
+            raise BSError(rc, "bs_create(device=%d)" % device)
+        self.h = h
+        self.device = device
+        self.dim = None
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().bs_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc):
+        if rc != 0:
+            raise BSError(rc, load().bs_last_error(self.h).decode())
+
+    # ---- set-up
+    def build_basis(self, orbits, Z, N, twoM, parity=+1):
+        arr = (bs_orbit * len(orbits))(*[bs_orbit(o.n, o.l, o.twoj, o.w) for o in orbits])
+        self._check(load().bs_build_basis(self.h, arr, len(orbits), Z, N, twoM, parity))
+        self.info()
+        return self
+
+    def info(self):
+        dim = ctypes.c_int64()
+        v = [ctypes.c_int() for _ in range(5)]
+        self._check(load().bs_basis_info(self.h, ctypes.byref(dim), *[ctypes.byref(x) for x in v]))
+        self.dim = dim.value
+        self.n_psec, self.n_nsec, self.n_psd, self.n_nsd, self.n_blocks = (x.value for x in v)
+        return self
+
+    def export_basis(self):
+        pb = np.zeros(self.n_psd, dtype=np.uint64)
+        nb = np.zeros(self.n_nsd, dtype=np.uint64)
+        ps = np.zeros((self.n_psec, 4), dtype=np.int64)
+        ns = np.zeros((self.n_nsec, 4), dtype=np.int64)
+        bl = np.zeros((self.n_blocks, 3), dtype=np.int64)
+        self._check(load().bs_export_basis(self.h, _p(pb, u64p), _p(nb, u64p), _p(ps, i64p), _p(ns, i64p), _p(bl, i64p)))
+        return {"p_bits": pb, "n_bits": nb, "p_sec": ps, "n_sec": ns, "blocks": bl}
+
+    def load_interaction(self, spe, tbmes):
+        spe = np.ascontiguousarray(spe, dtype=np.float64)
+        arr = (bs_tbme * max(1, len(tbmes)))(*[bs_tbme(*t) for t in tbmes])
+        self._check(load().bs_load_interaction(self.h, _p(spe, f64p), len(spe), arr, len(tbmes)))
+        return self
+
+    def table(self, name, dtype):
+        n = ctypes.c_int64()
+        self._check(load().bs_debug_table(self.h, name.encode(), None, ctypes.byref(n)))
+        out = np.zeros(n.value // np.dtype(dtype).itemsize, dtype=dtype)
+        self._check(load().bs_debug_table(self.h, name.encode(), out.ctypes.data_as(vp), ctypes.byref(n)))
+        return out
+
+    # ---- products
+    def apply_H(self, x, y, k, dtype, stream=None):
+        """y = H x; x, y: torch CUDA tensors [dim][k] (or raw device pointers)."""
+        xp = x if isinstance(x, int) else x.data_ptr()
+        yp = y if isinstance(y, int) else y.data_ptr()
+        self._check(load().bs_apply_H(self.h, vp(xp), vp(yp), k, dtype, vp(stream or 0)))
+
+    def apply_H_host(self, x, y, k, dtype, stream=None):
+        """y = H x with host numpy buffers (copies inside)."""
+        self._check(load().bs_apply_H_host(self.h, x.ctypes.data_as(vp), y.ctypes.data_as(vp), k, dtype,
+                                           vp(stream or 0)))
+
+
+def make(space_orbits, spe, tbmes, Z, N, twoM, parity=+1, device=0):
+    return Context(device).build_basis(space_orbits, Z, N, twoM, parity).load_interaction(spe, tbmes)

@@ -1,0 +1,375 @@
+// The C ABI (include/bigstick_gpu.h): context, error codes, basis and
+// interaction set-up, device upload, and the host-buffer entry point.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstring>
+#include <new>
+
+#include "bs_internal.h"
+
+using namespace bs;
+
+namespace {
+
+int cuda_fail(bs_ctx *c, cudaError_t e, const char *what)
+{
+    c->err = std::string(what) + ": " + cudaGetErrorString(e);
+    return e == cudaErrorMemoryAllocation ? BS_ENOMEM : BS_ECUDA;
+}
+
+template <typename F>
+int guarded(bs_ctx *c, F &&f)
+{
+    if (!c) return BS_EINVAL;
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        c->err = "host allocation failed";
+        return BS_ENOMEM;
+    } catch (const std::exception &e) {
+        c->err = e.what();
+        return BS_EINVAL;
+    } catch (...) {
+        c->err = "unknown error";
+        return BS_EINVAL;
+    }
+}
+
+template <typename T>
+int put(Device &D, T *&dst, const T *src, size_t n, std::string &err)
+{
+    dst = nullptr;
+    size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+    cudaError_t e = cudaMalloc((void **)&dst, bytes);
+    if (e != cudaSuccess) { err = std::string("cudaMalloc: ") + cudaGetErrorString(e); return e == cudaErrorMemoryAllocation ? BS_ENOMEM : BS_ECUDA; }
+    D.owned.push_back(dst);
+    if (n) {
+        e = cudaMemcpy(dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) { err = std::string("cudaMemcpy: ") + cudaGetErrorString(e); return BS_ECUDA; }
+    }
+    return BS_OK;
+}
+
+template <typename T>
+std::vector<T> cast(const std::vector<double> &v)
+{
+    return std::vector<T>(v.begin(), v.end());
+}
+
+}  // namespace
+
+namespace bs {
+
+void release(Device &D)
+{
+    for (void *p : D.owned) cudaFree(p);
+    D.owned.clear();
+    int dev = D.dev;
+    D = Device();
+    D.dev = dev;
+}
+
+// Task list for the fused kernel: one CTA per (destination block, proton row,
+// tile of neutron columns), ordered by estimated work, largest first, so the
+// hardware's in-order CTA dispatch approximates longest-processing-time
+// scheduling.
+static void make_tasks(const Basis &B, const Tables &T, int tile, std::vector<DevTask> &tasks)
+{
+    struct C { double cost; DevTask t; };
+    std::vector<C> v;
+    for (size_t b = 0; b < B.blocks.size(); ++b) {
+        const Block &D = B.blocks[b];
+        const Sector &PS = B.sp[0].sec[D.ps], &NS = B.sp[1].sec[D.ns];
+        double nn_avg = (double)(T.nn.ptr[NS.start + NS.count] - T.nn.ptr[NS.start]) / (double)std::max<int64_t>(1, NS.count);
+        for (int64_t r = 0; r < D.nP; ++r) {
+            double per_col = (double)(T.pp.ptr[PS.start + r + 1] - T.pp.ptr[PS.start + r]) + nn_avg;
+            for (int64_t L = T.links_of_block[b]; L < T.links_of_block[b + 1]; ++L) {
+                const PnLink &lk = T.links[(size_t)L];
+                const OneBodyClass &P = T.p1.cls[(size_t)lk.pcls], &N = T.n1.cls[(size_t)lk.ncls];
+                double np_ = (double)(T.p1.ptr[(size_t)(P.ptr_off + r + 1)] - T.p1.ptr[(size_t)(P.ptr_off + r)]);
+                double nn_ = (double)(T.n1.ptr[(size_t)(N.ptr_off + D.nN)] - T.n1.ptr[(size_t)N.ptr_off]) / (double)D.nN;
+                per_col += np_ * nn_;
+            }
+            for (int64_t c0 = 0; c0 < D.nN; c0 += tile) {
+                int64_t cols = std::min<int64_t>(tile, D.nN - c0);
+                v.push_back(C{per_col * (double)cols, DevTask{(int)b, (int)r, (int)c0, 0}});
+            }
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const C &a, const C &b) { return a.cost > b.cost; });
+    tasks.resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i) tasks[i] = v[i].t;
+}
+
+int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std::string &err)
+{
+    release(D);
+    cudaError_t e = cudaSetDevice(D.dev);
+    if (e != cudaSuccess) { err = std::string("cudaSetDevice: ") + cudaGetErrorString(e); return BS_ECUDA; }
+    int rc;
+    std::vector<DevBlock> blocks(B.blocks.size());
+    for (size_t b = 0; b < B.blocks.size(); ++b) {
+        const Block &s = B.blocks[b];
+        blocks[b].off = s.off;
+        blocks[b].nP = (int)s.nP;
+        blocks[b].nN = (int)s.nN;
+        blocks[b].p_start = (int)B.sp[0].sec[s.ps].start;
+        blocks[b].n_start = (int)B.sp[1].sec[s.ns].start;
+        blocks[b].link_begin = (int)T.links_of_block[b];
+        blocks[b].link_end = (int)T.links_of_block[b + 1];
+    }
+    std::vector<DevLink> links(T.links.size());
+    for (size_t l = 0; l < T.links.size(); ++l) {
+        const PnLink &L = T.links[l];
+        links[l].src_block = L.src_block;
+        links[l].p_ptr_off = T.p1.cls[(size_t)L.pcls].ptr_off;
+        links[l].n_ptr_off = T.n1.cls[(size_t)L.ncls].ptr_off;
+        links[l].w_off = L.w_off;
+        links[l].nb = L.nb;
+        links[l].pad = 0;
+    }
+    D.tile = 128;
+    std::vector<DevTask> tasks;
+    make_tasks(B, T, D.tile, tasks);
+    D.ntasks = (int)tasks.size();
+    if ((rc = put(D, D.blocks, blocks.data(), blocks.size(), err))) return rc;
+    if ((rc = put(D, D.links, links.data(), links.size(), err))) return rc;
+    if ((rc = put(D, D.tasks, tasks.data(), tasks.size(), err))) return rc;
+    if ((rc = put(D, D.pp_ptr, T.pp.ptr.data(), T.pp.ptr.size(), err))) return rc;
+    if ((rc = put(D, D.pp_src, T.pp.src.data(), T.pp.src.size(), err))) return rc;
+    if ((rc = put(D, D.nn_ptr, T.nn.ptr.data(), T.nn.ptr.size(), err))) return rc;
+    if ((rc = put(D, D.nn_src, T.nn.src.data(), T.nn.src.size(), err))) return rc;
+    if ((rc = put(D, D.p1_ptr, T.p1.ptr.data(), T.p1.ptr.size(), err))) return rc;
+    if ((rc = put(D, D.p1_ent, T.p1.ent.data(), T.p1.ent.size(), err))) return rc;
+    if ((rc = put(D, D.n1_ptr, T.n1.ptr.data(), T.n1.ptr.size(), err))) return rc;
+    if ((rc = put(D, D.n1_ent, T.n1.ent.data(), T.n1.ent.size(), err))) return rc;
+    if ((rc = put(D, D.c64.pp_coef, T.pp.coef.data(), T.pp.coef.size(), err))) return rc;
+    if ((rc = put(D, D.c64.nn_coef, T.nn.coef.data(), T.nn.coef.size(), err))) return rc;
+    if ((rc = put(D, D.c64.wpn, I.Wpn.data(), I.Wpn.size(), err))) return rc;
+    std::vector<float> f;
+    f = cast<float>(T.pp.coef);
+    if ((rc = put(D, D.c32.pp_coef, f.data(), f.size(), err))) return rc;
+    f = cast<float>(T.nn.coef);
+    if ((rc = put(D, D.c32.nn_coef, f.data(), f.size(), err))) return rc;
+    f = cast<float>(I.Wpn);
+    if ((rc = put(D, D.c32.wpn, f.data(), f.size(), err))) return rc;
+    return BS_OK;
+}
+
+}  // namespace bs
+
+extern "C" {
+
+int bs_create(bs_ctx **out, int cuda_device)
+{
+    if (!out) return BS_EINVAL;
+    *out = nullptr;
+    bs_ctx *c = new (std::nothrow) bs_ctx();
+    if (!c) return BS_ENOMEM;
+    c->device = cuda_device;
+    c->dev.dev = cuda_device;
+    if (cuda_device >= 0) {
+        int n = 0;
+        cudaError_t e = cudaGetDeviceCount(&n);
+        if (e != cudaSuccess || cuda_device >= n) {
+            delete c;
+            return e != cudaSuccess ? BS_ECUDA : BS_EINVAL;
+        }
+    }
+    *out = c;
+    return BS_OK;
+}
+
+void bs_destroy(bs_ctx *c)
+{
+    if (!c) return;
+    if (c->device >= 0) {
+        cudaSetDevice(c->device);
+        release(c->dev);
+        if (c->hx_x) cudaFree(c->hx_x);
+        if (c->hx_y) cudaFree(c->hx_y);
+    }
+    delete c;
+}
+
+const char *bs_last_error(const bs_ctx *c) { return c ? c->err.c_str() : "null context"; }
+
+int bs_build_basis(bs_ctx *c, const bs_orbit *orbits, int n_orbits, int Z, int N, int twoM, int parity)
+{
+    return guarded(c, [&]() -> int {
+        c->have_basis = c->have_int = false;
+        if (c->device >= 0) release(c->dev);
+        int rc = build_basis(c->basis, orbits, n_orbits, Z, N, twoM, parity, c->err);
+        if (rc) return rc;
+        c->have_basis = true;
+        c->err.clear();
+        return BS_OK;
+    });
+}
+
+int bs_basis_info(bs_ctx *c, int64_t *dim, int *n_psec, int *n_nsec, int *n_psd, int *n_nsd, int *n_blocks)
+{
+    return guarded(c, [&]() -> int {
+        if (!c->have_basis) { c->err = "no basis"; return BS_ENOBASIS; }
+        const Basis &B = c->basis;
+        if (dim) *dim = B.dim;
+        if (n_psec) *n_psec = (int)B.sp[0].sec.size();
+        if (n_nsec) *n_nsec = (int)B.sp[1].sec.size();
+        if (n_psd) *n_psd = (int)B.sp[0].bits.size();
+        if (n_nsd) *n_nsd = (int)B.sp[1].bits.size();
+        if (n_blocks) *n_blocks = (int)B.blocks.size();
+        return BS_OK;
+    });
+}
+
+int bs_export_basis(bs_ctx *c, uint64_t *p_bits, uint64_t *n_bits, int64_t *p_sec, int64_t *n_sec, int64_t *blocks)
+{
+    return guarded(c, [&]() -> int {
+        if (!c->have_basis) { c->err = "no basis"; return BS_ENOBASIS; }
+        const Basis &B = c->basis;
+        uint64_t *bits[2] = {p_bits, n_bits};
+        int64_t *sec[2] = {p_sec, n_sec};
+        for (int s = 0; s < 2; ++s) {
+            if (bits[s]) std::memcpy(bits[s], B.sp[s].bits.data(), B.sp[s].bits.size() * sizeof(uint64_t));
+            if (sec[s])
+                for (size_t t = 0; t < B.sp[s].sec.size(); ++t) {
+                    sec[s][4 * t] = B.sp[s].sec[t].twoM;
+                    sec[s][4 * t + 1] = B.sp[s].sec[t].par;
+                    sec[s][4 * t + 2] = B.sp[s].sec[t].start;
+                    sec[s][4 * t + 3] = B.sp[s].sec[t].count;
+                }
+        }
+        if (blocks)
+            for (size_t b = 0; b < B.blocks.size(); ++b) {
+                blocks[3 * b] = B.blocks[b].ps;
+                blocks[3 * b + 1] = B.blocks[b].ns;
+                blocks[3 * b + 2] = B.blocks[b].off;
+            }
+        return BS_OK;
+    });
+}
+
+int bs_load_interaction(bs_ctx *c, const double *spe, int n_spe, const bs_tbme *tbme, int n_tbme)
+{
+    return guarded(c, [&]() -> int {
+        if (!c->have_basis) { c->err = "no basis"; return BS_ENOBASIS; }
+        c->have_int = false;
+        int rc = build_interaction(c->basis, spe, n_spe, tbme, n_tbme, c->inter, c->err);
+        if (rc) return rc;
+        rc = build_tables(c->basis, c->inter, c->tab, c->err);
+        if (rc) return rc;
+        if (c->device >= 0) {
+            rc = upload(c->basis, c->inter, c->tab, c->dev, c->err);
+            if (rc) { release(c->dev); return rc; }
+        }
+        c->have_int = true;
+        c->err.clear();
+        return BS_OK;
+    });
+}
+
+static int check_apply(bs_ctx *c, int k, bs_dtype dt)
+{
+    if (!c->have_basis) { c->err = "no basis"; return BS_ENOBASIS; }
+    if (!c->have_int) { c->err = "no interaction"; return BS_ENOINT; }
+    if (c->device < 0) { c->err = "context has no device"; return BS_EINVAL; }
+    if (k != 1 && k != 2 && k != 4 && k != 8) { c->err = "k must be 1, 2, 4 or 8"; return BS_EINVAL; }
+    if (dt != BS_F64 && dt != BS_F32) { c->err = "bad dtype"; return BS_EINVAL; }
+    return BS_OK;
+}
+
+int bs_apply_H(bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, void *stream)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, k, dt);
+        if (rc) return rc;
+        if (!x || !y || x == y) { c->err = "x and y must be distinct device buffers"; return BS_EINVAL; }
+        if (((uintptr_t)x | (uintptr_t)y) & 15) { c->err = "x and y must be 16-byte aligned"; return BS_EINVAL; }
+        return launch_hx(c, x, y, k, dt, stream, c->err);
+    });
+}
+
+int bs_apply_H_host(bs_ctx *c, const void *xh, void *yh, int k, bs_dtype dt, void *stream)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, k, dt);
+        if (rc) return rc;
+        if (!xh || !yh) { c->err = "null host buffer"; return BS_EINVAL; }
+        size_t bytes = (size_t)c->basis.dim * (size_t)k * (dt == BS_F64 ? 8 : 4);
+        cudaError_t e;
+        if (bytes > c->hx_bytes) {
+            if (c->hx_x) cudaFree(c->hx_x);
+            if (c->hx_y) cudaFree(c->hx_y);
+            c->hx_x = c->hx_y = nullptr;
+            c->hx_bytes = 0;
+            if ((e = cudaMalloc(&c->hx_x, bytes)) != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+            if ((e = cudaMalloc(&c->hx_y, bytes)) != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+            c->hx_bytes = bytes;
+        }
+        cudaStream_t s = (cudaStream_t)stream;
+        if ((e = cudaMemcpyAsync(c->hx_x, xh, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+        if ((rc = launch_hx(c, c->hx_x, c->hx_y, k, dt, stream, c->err))) return rc;
+        if ((e = cudaMemcpyAsync(yh, c->hx_y, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
+        if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+        return BS_OK;
+    });
+}
+
+// Host copies of the built tables, by name, for tests that check the host
+// builders without a GPU.  With out == NULL only *nbytes is set.
+int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
+{
+    return guarded(c, [&]() -> int {
+        if (!c->have_int) { c->err = "no interaction"; return BS_ENOINT; }
+        const Tables &T = c->tab;
+        const Interaction &I = c->inter;
+        std::vector<int64_t> tmp;
+        const void *src = nullptr;
+        size_t n = 0;
+        std::string s(name ? name : "");
+        auto use = [&](const void *p, size_t b) { src = p; n = b; };
+        if (s == "pp_ptr") use(T.pp.ptr.data(), T.pp.ptr.size() * 8);
+        else if (s == "pp_src") use(T.pp.src.data(), T.pp.src.size() * 4);
+        else if (s == "pp_coef") use(T.pp.coef.data(), T.pp.coef.size() * 8);
+        else if (s == "nn_ptr") use(T.nn.ptr.data(), T.nn.ptr.size() * 8);
+        else if (s == "nn_src") use(T.nn.src.data(), T.nn.src.size() * 4);
+        else if (s == "nn_coef") use(T.nn.coef.data(), T.nn.coef.size() * 8);
+        else if (s == "p1_ptr") use(T.p1.ptr.data(), T.p1.ptr.size() * 8);
+        else if (s == "p1_ent") use(T.p1.ent.data(), T.p1.ent.size() * 4);
+        else if (s == "n1_ptr") use(T.n1.ptr.data(), T.n1.ptr.size() * 8);
+        else if (s == "n1_ent") use(T.n1.ent.data(), T.n1.ent.size() * 4);
+        else if (s == "wpn") use(I.Wpn.data(), I.Wpn.size() * 8);
+        else if (s == "p1_cls" || s == "n1_cls") {
+            const OneBodyJumps &J = s[0] == 'p' ? T.p1 : T.n1;
+            for (const OneBodyClass &k : J.cls) { tmp.push_back(k.s_src); tmp.push_back(k.s_dst); tmp.push_back(k.group); tmp.push_back(k.ptr_off); }
+            use(tmp.data(), tmp.size() * 8);
+        } else if (s == "links") {
+            for (const PnLink &L : T.links) {
+                tmp.push_back(L.dst_block); tmp.push_back(L.src_block); tmp.push_back(L.pcls);
+                tmp.push_back(L.ncls); tmp.push_back(L.w_off); tmp.push_back(L.nb);
+            }
+            use(tmp.data(), tmp.size() * 8);
+        } else if (s == "ops") {   // per group: dtwom, dpar, conj group, wpn offset, n ops; then op lists
+            for (size_t g = 0; g < I.ops.ops.size(); ++g) {
+                tmp.push_back(I.ops.g_dtwom[g]); tmp.push_back(I.ops.g_dpar[g]); tmp.push_back(I.conj_group[g]);
+                tmp.push_back(I.wpn_off[g]); tmp.push_back((int64_t)I.ops.ops[g].size());
+            }
+            use(tmp.data(), tmp.size() * 8);
+        } else if (s == "op_lists") {
+            for (const auto &g : I.ops.ops) for (int op : g) tmp.push_back(op);
+            use(tmp.data(), tmp.size() * 8);
+        } else if (s == "stats") {
+            tmp = {T.n_pp, T.n_nn, T.n_p1, T.n_n1, (int64_t)T.links.size(), (int64_t)T.ops_per_vector, (int64_t)c->dev.ntasks};
+            use(tmp.data(), tmp.size() * 8);
+        } else {
+            c->err = "unknown table " + s;
+            return BS_EINVAL;
+        }
+        if (nbytes) *nbytes = (int64_t)n;
+        if (out && n) std::memcpy(out, src, n);
+        return BS_OK;
+    });
+}
+
+}  // extern "C"

@@ -1,0 +1,187 @@
+// Internal data structures of libbsgpu: host-side basis, interaction and jump
+// tables, and the device mirror the kernels read.
+#pragma once
+
+#include <cstdint>
+#include <string>
+#include <unordered_map>
+#include <vector>
+
+#include "../../include/bigstick_gpu.h"
+
+namespace bs {
+
+// ---------------------------------------------------------------- basis
+struct SpState {
+    int orb;     // orbit index (0-based, input order)
+    int twom;    // 2 m
+    int par;     // 0 for +, 1 for -
+};
+
+struct Sector {
+    int twoM, par;
+    int64_t start;   // first SD of the sector in the species list
+    int64_t count;
+};
+
+struct Species {
+    int nparticles = 0;
+    std::vector<uint64_t> bits;            // sorted by sector, then bitmask
+    std::vector<Sector> sec;
+    std::vector<int> sec_of_sd;            // sector of every SD
+    std::unordered_map<uint64_t, int64_t> index;  // bitmask -> global SD index
+    int find_sector(int twoM, int par) const;
+};
+
+struct Block {
+    int ps, ns;        // proton and neutron sector
+    int64_t off;       // first basis index
+    int64_t nP, nN;    // sector sizes
+};
+
+struct Basis {
+    std::vector<int> orb_l, orb_twoj;
+    std::vector<SpState> st;
+    int Z = 0, N = 0, twoM = 0, par = 0;
+    Species sp[2];
+    std::vector<Block> blocks;
+    std::vector<int> block_of_psec;        // -1 when a proton sector has no conjugate
+    int64_t dim = 0;
+};
+
+// ---------------------------------------------------------------- interaction
+// A one-body operator a+_i a_k of one species, grouped by the change it makes
+// to (2M, parity): key = (2m_i - 2m_k, par_i ^ par_k).  Inside a group the
+// operators get compact indices 0..n-1.
+struct OpGroups {
+    std::vector<int> group_of_op;     // [ns*ns] op (i*ns+k) -> group
+    std::vector<int> local_of_op;     // [ns*ns] op -> index inside its group
+    std::vector<int> g_dtwom, g_dpar; // per group
+    std::vector<std::vector<int>> ops; // per group: list of ops
+    int find(int dtwom, int dpar) const;
+};
+
+struct Interaction {
+    // like-particle two-body elements W(ij,kl), i<j, k<l, keyed by pair ids
+    int npairs = 0;
+    std::vector<int> pair_i, pair_j;            // pair id -> states
+    std::vector<int> pair_id;                   // [ns*ns] (i<j) -> id
+    std::vector<std::vector<int>> pairs_by_key; // pairs grouped by (2M, parity)
+    std::vector<int> key_of_pair;
+    std::vector<double> Wpp;                    // [npairs*npairs]
+    std::vector<double> spe_state;              // [ns]
+    OpGroups ops;                               // proton and neutron one-body groups (same space)
+    // W_pn for group pair (g for protons, conj(g) for neutrons): dense [n_g x n_conj]
+    std::vector<int> conj_group;                // g -> neutron group with opposite 2m change
+    std::vector<int64_t> wpn_off;               // per group offset into Wpn
+    std::vector<double> Wpn;
+};
+
+// ---------------------------------------------------------------- jumps
+// Destination-ordered sparse lists ("both directions stored, sorted by destination").
+struct LikeJumps {          // pp or nn, same sector, diagonal included (SPE folded in)
+    std::vector<int64_t> ptr;     // [nsd+1] by destination SD (global index)
+    std::vector<int32_t> src;     // source SD, local index inside the sector
+    std::vector<double> coef;
+};
+
+struct OneBodyClass {       // one-body jumps from sector s_src into sector s_dst
+    int s_src, s_dst;
+    int group;              // operator group (change of 2m, parity)
+    int64_t ptr_off;        // into OneBodyJumps::ptr, |S_dst|+1 entries
+};
+
+struct OneBodyJumps {
+    std::vector<OneBodyClass> cls;
+    std::vector<int64_t> ptr;
+    std::vector<uint32_t> ent;    // packed: src local (bits 0..15) | op local (bits 16..30) | sign (bit 31)
+};
+
+// One pn "opbundle": destination block <- source block through proton class
+// pc and neutron class nc.
+struct PnLink {
+    int dst_block, src_block;
+    int pcls, ncls;
+    int64_t w_off;      // offset of the W_pn group matrix
+    int nb;             // row length of that matrix (neutron ops of the conjugate group)
+};
+
+struct Tables {
+    LikeJumps pp, nn;
+    OneBodyJumps p1, n1;
+    std::vector<PnLink> links;           // sorted by dst block
+    std::vector<int64_t> links_of_block; // [nblocks+1]
+    int64_t n_pp = 0, n_nn = 0, n_p1 = 0, n_n1 = 0;
+    double ops_per_vector = 0.0;         // multiply-adds of one H*x (structural)
+};
+
+// ---------------------------------------------------------------- device mirror
+struct DevBlock {
+    int64_t off;
+    int nP, nN;
+    int p_start, n_start;   // global SD index of the first SD of each sector
+    int link_begin, link_end;
+};
+
+struct DevLink {
+    int src_block;
+    int64_t p_ptr_off;      // proton class CSR (|S_p dst|+1)
+    int64_t n_ptr_off;      // neutron class CSR (|S_n dst|+1)
+    int64_t w_off;
+    int nb;
+    int pad;
+};
+
+struct DevTask {            // one CTA: destination block, proton row, column tile
+    int block;
+    int row;
+    int col0;
+    int pad;
+};
+
+template <typename T>
+struct DevCoefs {
+    T *pp_coef = nullptr, *nn_coef = nullptr, *wpn = nullptr;
+};
+
+struct Device {
+    int dev = 0;
+    DevBlock *blocks = nullptr;
+    DevLink *links = nullptr;
+    DevTask *tasks = nullptr;
+    int ntasks = 0;
+    int tile = 0;
+    int64_t *pp_ptr = nullptr, *nn_ptr = nullptr;
+    int32_t *pp_src = nullptr, *nn_src = nullptr;
+    int64_t *p1_ptr = nullptr, *n1_ptr = nullptr;
+    uint32_t *p1_ent = nullptr, *n1_ent = nullptr;
+    DevCoefs<double> c64;
+    DevCoefs<float> c32;
+    std::vector<void *> owned;   // every cudaMalloc above
+};
+
+}  // namespace bs
+
+struct bs_ctx {
+    int device = 0;
+    std::string err;
+    bool have_basis = false, have_int = false;
+    bs::Basis basis;
+    bs::Interaction inter;
+    bs::Tables tab;
+    bs::Device dev;
+    // host-buffer entry point workspace
+    void *hx_x = nullptr, *hx_y = nullptr;
+    size_t hx_bytes = 0;
+};
+
+// ---------------------------------------------------------------- builders (host)
+namespace bs {
+int build_basis(Basis &B, const bs_orbit *orbits, int n_orbits, int Z, int N, int twoM, int parity, std::string &err);
+int build_interaction(const Basis &B, const double *spe, int n_spe, const bs_tbme *tbme, int n_tbme,
+                      Interaction &I, std::string &err);
+int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err);
+int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std::string &err);
+void release(Device &D);
+int launch_hx(const bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err);
+}  // namespace bs

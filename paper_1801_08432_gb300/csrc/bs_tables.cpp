@@ -1,0 +1,200 @@
+// Jump tables (Sec. "The Lanczos algorithm and computational cost", jumps and
+// Table jumps): the proton-only and neutron-only parts of H are stored as
+// species-local sparse matrices (two-body moves, with the SPE and the
+// like-particle diagonal folded in), the pn part as one-body jumps of each
+// species that a kernel multiplies on the fly with the decoupled W_pn.
+//
+// Everything is stored by DESTINATION (the paper stores one direction and
+// applies its transpose for the "back" half; here both directions are kept so
+// that every output element has one owner and no atomics are needed).
+#include <algorithm>
+#include <numeric>
+
+#include "bs_internal.h"
+
+namespace bs {
+
+namespace {
+
+// Fermion sign of a_s or a+_s on bitmask m (the paper's rule): (-1)^(number of
+// occupied states below s).
+inline int sign_below(uint64_t m, int s)
+{
+    return (__builtin_popcountll(m & ((1ULL << s) - 1ULL)) & 1) ? -1 : 1;
+}
+
+// Like-particle part of one species: sum_{i<j,k<l} W(ij,kl) a+_i a+_j a_l a_k
+// plus sum_s e_s n_s, as a destination CSR over the species' SDs.  The
+// operator is real symmetric (W(ij,kl) = W(kl,ij)), so the row of SD g,
+// <g|V|m>, is read off V|g> = sum_m <m|V|g> |m>: every row is built from its
+// own SD, in parallel, with no scatter.
+void like_jumps(const Basis &B, const Interaction &I, int spc, LikeJumps &L, int64_t &nent)
+{
+    const Species &S = B.sp[spc];
+    const int ns = (int)B.st.size();
+    const int64_t nsd = (int64_t)S.bits.size();
+    std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)nsd);
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t g = 0; g < nsd; ++g) {
+        const uint64_t X = S.bits[g];
+        std::vector<std::pair<int32_t, double>> &r = rows[(size_t)g];
+        double e = 0.0;
+        for (int s = 0; s < ns; ++s)
+            if (X >> s & 1) e += I.spe_state[s];
+        r.emplace_back((int32_t)(g - S.sec[S.sec_of_sd[g]].start), e);
+        for (int k = 0; k < ns; ++k) {
+            if (!(X >> k & 1)) continue;
+            for (int l = k + 1; l < ns; ++l) {
+                if (!(X >> l & 1)) continue;
+                const int q = I.pair_id[(size_t)k * ns + l];
+                // a_l a_k
+                int sg = sign_below(X, k);
+                uint64_t m1 = X & ~(1ULL << k);
+                sg *= sign_below(m1, l);
+                m1 &= ~(1ULL << l);
+                for (int p : I.pairs_by_key[I.key_of_pair[q]]) {
+                    const double w = I.Wpp[(size_t)p * I.npairs + q];
+                    if (w == 0.0) continue;
+                    const int i = I.pair_i[p], j = I.pair_j[p];
+                    if ((m1 >> i & 1) || (m1 >> j & 1)) continue;
+                    // a+_i a+_j
+                    int s2 = sign_below(m1, j);
+                    uint64_t m2 = m1 | (1ULL << j);
+                    s2 *= sign_below(m2, i);
+                    m2 |= (1ULL << i);
+                    const int64_t gm = S.index.find(m2)->second;
+                    r.emplace_back((int32_t)(gm - S.sec[S.sec_of_sd[gm]].start), sg * s2 * w);
+                }
+            }
+        }
+        std::sort(r.begin(), r.end(), [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+            return a.first < b.first;
+        });
+        size_t w = 0;
+        for (size_t t = 0; t < r.size(); ++t) {
+            if (w > 0 && r[w - 1].first == r[t].first) r[w - 1].second += r[t].second;
+            else r[w++] = r[t];
+        }
+        r.resize(w);
+    }
+    L.ptr.assign((size_t)nsd + 1, 0);
+    for (int64_t g = 0; g < nsd; ++g) L.ptr[(size_t)g + 1] = L.ptr[(size_t)g] + (int64_t)rows[(size_t)g].size();
+    L.src.resize((size_t)L.ptr[(size_t)nsd]);
+    L.coef.resize((size_t)L.ptr[(size_t)nsd]);
+    for (int64_t g = 0; g < nsd; ++g) {
+        int64_t o = L.ptr[(size_t)g];
+        for (const auto &e : rows[(size_t)g]) { L.src[(size_t)o] = e.first; L.coef[(size_t)o] = e.second; ++o; }
+        std::vector<std::pair<int32_t, double>>().swap(rows[(size_t)g]);
+    }
+    nent = L.ptr[(size_t)nsd];
+}
+
+// One-body jumps a+_i a_k of one species (i == k included: the number
+// operator), grouped by (source sector, destination sector), destination CSR.
+// For destination d the incoming jumps come from s = a+_k a_i d with i
+// occupied in d; <d|a+_i a_k|s> = <s|a+_k a_i|d> is the sign of a_i then a+_k
+// on d.  The stored operator index is that of a+_i a_k.
+void onebody_jumps(const Basis &B, const Interaction &I, int spc, OneBodyJumps &J, int64_t &nent)
+{
+    const Species &S = B.sp[spc];
+    const int ns = (int)B.st.size();
+    const int nsec = (int)S.sec.size();
+    struct E { int32_t dst_loc; uint32_t packed; };
+    std::vector<std::vector<E>> bucket((size_t)nsec * nsec);
+    std::vector<int> grp((size_t)nsec * nsec, -1);
+    for (int64_t d = 0; d < (int64_t)S.bits.size(); ++d) {
+        const uint64_t X = S.bits[d];
+        const int sdst = S.sec_of_sd[d];
+        const int32_t dloc = (int32_t)(d - S.sec[sdst].start);
+        for (int i = 0; i < ns; ++i) {
+            if (!(X >> i & 1)) continue;
+            const int s1 = sign_below(X, i);
+            const uint64_t m1 = X & ~(1ULL << i);
+            for (int k = 0; k < ns; ++k) {
+                if (m1 >> k & 1) continue;
+                const int s2 = sign_below(m1, k);
+                const int64_t gs = S.index.find(m1 | (1ULL << k))->second;
+                const int ssrc = S.sec_of_sd[gs];
+                const int op = i * ns + k;
+                const uint32_t sloc = (uint32_t)(gs - S.sec[ssrc].start);
+                const uint32_t packed = sloc | ((uint32_t)I.ops.local_of_op[op] << 16) | ((s1 * s2 < 0) ? 0x80000000u : 0u);
+                bucket[(size_t)ssrc * nsec + sdst].push_back(E{dloc, packed});
+                grp[(size_t)ssrc * nsec + sdst] = I.ops.group_of_op[op];
+            }
+        }
+    }
+    J.cls.clear();
+    J.ptr.clear();
+    J.ent.clear();
+    for (int a = 0; a < nsec; ++a)
+        for (int b = 0; b < nsec; ++b) {
+            auto &v = bucket[(size_t)a * nsec + b];
+            if (v.empty()) continue;
+            OneBodyClass c;
+            c.s_src = a;
+            c.s_dst = b;
+            c.group = grp[(size_t)a * nsec + b];
+            c.ptr_off = (int64_t)J.ptr.size();
+            const int64_t nd = S.sec[b].count;
+            size_t t = 0;
+            for (int64_t dl = 0; dl <= nd; ++dl) {
+                while (t < v.size() && v[t].dst_loc < dl) J.ent.push_back(v[t++].packed);
+                J.ptr.push_back((int64_t)J.ent.size());
+            }
+            J.cls.push_back(c);
+            std::vector<E>().swap(v);
+        }
+    nent = (int64_t)J.ent.size();
+}
+
+}  // namespace
+
+int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err)
+{
+    (void)err;
+    T = Tables();
+    like_jumps(B, I, 0, T.pp, T.n_pp);
+    like_jumps(B, I, 1, T.nn, T.n_nn);
+    onebody_jumps(B, I, 0, T.p1, T.n_p1);
+    onebody_jumps(B, I, 1, T.n1, T.n_n1);
+    // pn links: destination block <- source block
+    const int nb = (int)B.blocks.size();
+    const int nps = (int)B.sp[0].sec.size(), nns = (int)B.sp[1].sec.size();
+    std::vector<int> pcls((size_t)nps * nps, -1), ncls((size_t)nns * nns, -1);
+    for (size_t c = 0; c < T.p1.cls.size(); ++c) pcls[(size_t)T.p1.cls[c].s_src * nps + T.p1.cls[c].s_dst] = (int)c;
+    for (size_t c = 0; c < T.n1.cls.size(); ++c) ncls[(size_t)T.n1.cls[c].s_src * nns + T.n1.cls[c].s_dst] = (int)c;
+    T.links_of_block.assign((size_t)nb + 1, 0);
+    double ops = 0.0;
+    for (int d = 0; d < nb; ++d) {
+        const Block &D = B.blocks[d];
+        for (int s = 0; s < nb; ++s) {
+            const Block &S = B.blocks[s];
+            int pc = pcls[(size_t)S.ps * nps + D.ps], nc = ncls[(size_t)S.ns * nns + D.ns];
+            if (pc < 0 || nc < 0) continue;
+            int g = T.p1.cls[pc].group;
+            int h = I.conj_group[g];
+            if (h < 0 || T.n1.cls[nc].group != h) continue;
+            PnLink L;
+            L.dst_block = d;
+            L.src_block = s;
+            L.pcls = pc;
+            L.ncls = nc;
+            L.w_off = I.wpn_off[g];
+            L.nb = (int)I.ops.ops[h].size();
+            T.links.push_back(L);
+            const OneBodyClass &P = T.p1.cls[pc], &N = T.n1.cls[nc];
+            double np_ = (double)(T.p1.ptr[P.ptr_off + D.nP] - T.p1.ptr[P.ptr_off]);
+            double nn_ = (double)(T.n1.ptr[N.ptr_off + D.nN] - T.n1.ptr[N.ptr_off]);
+            ops += np_ * nn_;
+        }
+        T.links_of_block[(size_t)d + 1] = (int64_t)T.links.size();
+        // like-particle work of this block
+        const Sector &PS = B.sp[0].sec[D.ps], &NS = B.sp[1].sec[D.ns];
+        ops += (double)(T.pp.ptr[PS.start + PS.count] - T.pp.ptr[PS.start]) * (double)D.nN;
+        ops += (double)(T.nn.ptr[NS.start + NS.count] - T.nn.ptr[NS.start]) * (double)D.nP;
+    }
+    T.ops_per_vector = ops;
+    return BS_OK;
+}
+
+}  // namespace bs

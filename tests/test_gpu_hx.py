@@ -1,0 +1,154 @@
+"""GPU parity of y = H x (the fused CUDA kernel, through the C ABI) against the
+FP64 oracle.
+
+Full vectors on spaces the oracle's explicit matrix covers in seconds (sd
+2p2n, 4p4n, 6p6n at M=0 and M=1, edge cases), and sampled rows computed on
+the fly by the oracle at the full sizes (pf 4p4n, dim 1,963,461; pf 6p6n,
+dim 109,954,620) in the launch configuration the benchmark times.
+
+Tolerances.  FP64: max|dy| <= 1e-12 * max|y| (the stated FP64 bar).  FP32
+(vectors, coefficients and accumulation in float): each output is a sum of n
+products; the rounding error is bounded by about n * 2^-24 * (|H| |x|)_i, n up
+to ~10^3 here, so the test uses max|dy_i| <= 4e-5 * max_i (|H| |x|)_i and
+reports the typical error.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_1801_08432_gb300 import _native as N
+from paper_1801_08432_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+_cache = {}
+
+
+def setup(name, Z, Nn, twoM, parity=+1):
+    key = (name, Z, Nn, twoM, parity)
+    if key not in _cache:
+        orbits, spe, tb = I.space(name)
+        c = N.make(orbits, spe, tb, Z, Nn, twoM, parity, device=0)
+        o = O.Oracle(orbits, Z, Nn, twoM, 0 if parity > 0 else 1).set_interaction(spe, tb)
+        _cache[key] = (c, o)
+    return _cache[key]
+
+
+def gpu_apply(c, x, k, dtype):
+    tdt = torch.float64 if dtype == N.BS_F64 else torch.float32
+    xd = torch.from_numpy(np.ascontiguousarray(x)).to(device="cuda", dtype=tdt)
+    yd = torch.full_like(xd, float("nan"))
+    c.apply_H(xd, yd, k, dtype, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    return yd.double().cpu().numpy()
+
+
+SMALL = [("sd", 2, 2, 0), ("sd", 4, 4, 0), ("sd", 4, 4, 2), ("sd", 6, 6, 0), ("sd", 6, 6, 2),
+         ("sd", 1, 1, 0), ("sd", 2, 0, 0), ("sd", 0, 3, 3), ("sd", 5, 6, 1), ("p", 4, 4, 0), ("pf", 2, 2, 0)]
+
+
+@pytest.mark.parametrize("case", SMALL, ids=lambda c: "%s-%dp%dn-2M%d" % c)
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_fp64_full_vector(case, k):
+    c, o = setup(*case)
+    x = I.random_block(o.dim, k, seed=k)
+    y = gpu_apply(c, x, k, N.BS_F64)
+    ref = o.spmv(x)
+    assert np.all(np.isfinite(y))
+    assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("case", [("sd", 4, 4, 0), ("sd", 6, 6, 0), ("sd", 5, 6, 1)], ids=lambda c: "%s-%dp%dn-2M%d" % c)
+@pytest.mark.parametrize("k", [1, 4, 8])
+def test_fp32_full_vector(case, k):
+    c, o = setup(*case)
+    x = I.random_block(o.dim, k, seed=10 + k)
+    y = gpu_apply(c, x.astype(np.float32), k, N.BS_F32)
+    ref = o.spmv(x.astype(np.float32).astype(np.float64))
+    H = o.matrix()
+    absref = abs(H) @ np.abs(x.astype(np.float32).astype(np.float64))
+    assert np.max(np.abs(y - ref)) <= 4e-5 * np.max(absref)
+
+
+def test_deterministic_and_k_consistent():
+    c, o = setup("sd", 6, 6, 0)
+    x = I.random_block(o.dim, 4, seed=3)
+    y1 = gpu_apply(c, x, 4, N.BS_F64)
+    y2 = gpu_apply(c, x, 4, N.BS_F64)
+    assert np.array_equal(y1, y2)
+    for col in range(4):
+        yc = gpu_apply(c, x[:, col:col + 1].copy(), 1, N.BS_F64)
+        assert np.array_equal(yc[:, 0], y1[:, col])
+
+
+def test_host_buffer_entry_point():
+    c, o = setup("sd", 4, 4, 0)
+    x = I.random_block(o.dim, 2, seed=5)
+    y = np.zeros_like(x)
+    c.apply_H_host(x, y, 2, N.BS_F64)
+    assert np.array_equal(y, gpu_apply(c, x, 2, N.BS_F64))
+
+
+def test_rejects_bad_calls():
+    c, o = setup("sd", 2, 2, 0)
+    xd = torch.zeros((o.dim, 3), device="cuda", dtype=torch.float64)
+    yd = torch.zeros_like(xd)
+    with pytest.raises(N.BSError):
+        c.apply_H(xd, yd, 3, N.BS_F64)       # k = 3
+    with pytest.raises(N.BSError):
+        c.apply_H(xd, xd, 1, N.BS_F64)       # aliasing
+    with pytest.raises(N.BSError):
+        c.apply_H(xd, yd, 1, 7)              # dtype
+
+
+def _sample_rows(o, n, seed):
+    rng = np.random.default_rng(seed)
+    B = o.basis()
+    edges = []
+    for (_, _, off) in B["blocks"]:
+        edges += [off, max(off - 1, 0)]
+    edges.append(o.dim - 1)
+    rows = np.unique(np.concatenate([rng.integers(0, o.dim, n), np.array(edges, dtype=np.int64)]))
+    return rows
+
+
+@pytest.mark.parametrize("k,dtype", [(1, N.BS_F64), (8, N.BS_F64), (8, N.BS_F32), (4, N.BS_F32)])
+def test_pf_4p4n_sampled_rows(k, dtype):
+    c, o = setup("pf", 4, 4, 0)
+    assert o.dim == 1963461
+    x = I.random_block(o.dim, k, seed=21)
+    if dtype == N.BS_F32:
+        x = x.astype(np.float32).astype(np.float64)
+    y = gpu_apply(c, x, k, dtype)
+    rows = _sample_rows(o, 6000, 1)
+    ref = o.apply_rows(rows, x)
+    err = np.max(np.abs(y[rows] - ref))
+    if dtype == N.BS_F64:
+        assert err <= 1e-12 * np.max(np.abs(y))
+    else:
+        bound = o.apply_rows(rows, np.abs(x), absval=True)
+        assert np.all(np.abs(y[rows] - ref) <= 4e-5 * bound + 1e-30)
+    assert np.all(np.isfinite(y))
+
+
+@pytest.mark.parametrize("k,dtype", [(4, N.BS_F32), (1, N.BS_F64)])
+def test_pf_6p6n_sampled_rows(k, dtype):
+    c, o = setup("pf", 6, 6, 0)
+    assert o.dim == 109954620
+    dt = torch.float64 if dtype == N.BS_F64 else torch.float32
+    g = torch.Generator(device="cuda").manual_seed(7)
+    xd = torch.randn((o.dim, k), device="cuda", dtype=dt, generator=g)
+    yd = torch.empty_like(xd)
+    c.apply_H(xd, yd, k, dtype, torch.cuda.current_stream().cuda_stream)
+    torch.cuda.synchronize()
+    rows = _sample_rows(o, 1500, 2)
+    x = xd.double().cpu().numpy()
+    ref = o.apply_rows(rows, x)
+    y = yd[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    scale = np.max(np.abs(ref))
+    if dtype == N.BS_F64:
+        assert np.max(np.abs(y - ref)) <= 1e-12 * scale
+    else:
+        bound = o.apply_rows(rows, np.abs(x), absval=True)
+        assert np.all(np.abs(y - ref) <= 4e-5 * bound + 1e-30)

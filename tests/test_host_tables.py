@@ -1,0 +1,210 @@
+"""CPU checks of the library's host side (no GPU): basis, decoupling and jump
+tables from a host-only context (bs_create(-1)) against the FP64 oracle.
+
+The product H*x is rebuilt here in numpy from the exported tables, with the
+same meaning the CUDA kernel gives them (pp/nn destination lists; pn as
+proton one-body jump x neutron one-body jump with W_pn), and compared with
+the oracle's explicit matrix.  Also: bit-exact basis, bit-exact one-body jump
+indices and signs against the oracle's operator strings, and error codes.
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import oracle as O
+from paper_1801_08432_gb300 import _native as N
+from paper_1801_08432_gb300 import inputs as I
+from tests.helpers import scrambled_tbmes
+
+
+@pytest.fixture(scope="session", autouse=True)
+def _built():
+    from paper_1801_08432_gb300 import build
+    build.build()
+
+
+def host_ctx(name, Z, Nn, twoM, parity=+1, tb=None):
+    orbits, spe, tbm = I.space(name)
+    c = N.Context(-1).build_basis(orbits, Z, Nn, twoM, parity)
+    c.load_interaction(spe, tbm if tb is None else tb)
+    return c
+
+
+def tables_matvec(c, x):
+    """y = H x from the exported host tables (test-side numpy)."""
+    B = c.export_basis()
+    y = np.zeros_like(x)
+    pp_ptr, pp_src, pp_c = c.table("pp_ptr", np.int64), c.table("pp_src", np.int32), c.table("pp_coef", np.float64)
+    nn_ptr, nn_src, nn_c = c.table("nn_ptr", np.int64), c.table("nn_src", np.int32), c.table("nn_coef", np.float64)
+    p1_ptr, p1_ent = c.table("p1_ptr", np.int64), c.table("p1_ent", np.uint32)
+    n1_ptr, n1_ent = c.table("n1_ptr", np.int64), c.table("n1_ent", np.uint32)
+    p1_cls = c.table("p1_cls", np.int64).reshape(-1, 4)
+    n1_cls = c.table("n1_cls", np.int64).reshape(-1, 4)
+    links = c.table("links", np.int64).reshape(-1, 6)
+    wpn = c.table("wpn", np.float64)
+    blocks = B["blocks"]
+
+    def blk(b):
+        ps, ns_, off = blocks[b]
+        return int(off), int(B["p_sec"][ps][2]), int(B["p_sec"][ps][3]), int(B["n_sec"][ns_][2]), int(B["n_sec"][ns_][3])
+
+    for b in range(len(blocks)):
+        off, p0, nP, n0, nN = blk(b)
+        X = x[off:off + nP * nN].reshape(nP, nN)
+        Y = y[off:off + nP * nN].reshape(nP, nN)
+        for r in range(nP):
+            for e in range(pp_ptr[p0 + r], pp_ptr[p0 + r + 1]):
+                Y[r] += pp_c[e] * X[pp_src[e]]
+        for col in range(nN):
+            for e in range(nn_ptr[n0 + col], nn_ptr[n0 + col + 1]):
+                Y[:, col] += nn_c[e] * X[:, nn_src[e]]
+    for (d, s, pc, nc, w_off, nb) in links:
+        offd, _, nPd, _, nNd = blk(d)
+        offs, _, nPs, _, nNs = blk(s)
+        Xs = x[offs:offs + nPs * nNs].reshape(nPs, nNs)
+        Yd = y[offd:offd + nPd * nNd].reshape(nPd, nNd)
+        pptr = p1_cls[pc][3]
+        nptr = n1_cls[nc][3]
+        # proton side as (row, src, op, sign), neutron side as (col, src, op, sign)
+        pr = [(r, e & 0xFFFF, (e >> 16) & 0x7FFF, -1.0 if e >> 31 else 1.0)
+              for r in range(nPd) for e in p1_ent[p1_ptr[pptr + r]:p1_ptr[pptr + r + 1]]]
+        ncl = [(q, e & 0xFFFF, (e >> 16) & 0x7FFF, -1.0 if e >> 31 else 1.0)
+               for q in range(nNd) for e in n1_ent[n1_ptr[nptr + q]:n1_ptr[nptr + q + 1]]]
+        if not pr or not ncl:
+            continue
+        na = max(a for (_, _, a, _) in pr) + 1
+        W = wpn[w_off:w_off + na * nb].reshape(na, nb) if na * nb else None
+        ncl = np.array(ncl, dtype=np.float64)
+        for a in range(na):
+            rows = [(r, src, sg) for (r, src, aa, sg) in pr if aa == a]
+            if not rows:
+                continue
+            P = sp.csr_matrix(([g for (_, _, g) in rows], ([r for (r, _, _) in rows], [s_ for (_, s_, _) in rows])),
+                              shape=(nPd, nPs))
+            vals = ncl[:, 3] * W[a, ncl[:, 2].astype(int)]
+            Oa = sp.csr_matrix((vals, (ncl[:, 0].astype(int), ncl[:, 1].astype(int))), shape=(nNd, nNs))
+            Yd += P @ (Oa @ Xs.T).T
+    return y
+
+
+@pytest.mark.parametrize("name,Z,Nn,twoM", [("sd", 2, 2, 0), ("sd", 3, 2, 1), ("sd", 1, 1, 0), ("sd", 2, 0, 0),
+                                            ("sd", 0, 3, 3), ("pf", 2, 2, 0), ("p", 4, 4, 0), ("sd", 4, 4, 2)])
+def test_host_tables_reproduce_oracle_matrix(name, Z, Nn, twoM):
+    orbits, spe, tb = I.space(name)
+    o = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
+    c = host_ctx(name, Z, Nn, twoM)
+    assert c.dim == o.dim
+    x = I.random_block(o.dim, 1)[:, 0]
+    y_ref = o.spmv(x)
+    y = tables_matvec(c, x)
+    assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
+
+
+@pytest.mark.parametrize("name,Z,Nn,twoM,par", [("sd", 2, 2, 0, 1), ("sd", 4, 4, 0, 1), ("sd", 5, 6, 1, 1),
+                                                ("pf", 4, 4, 0, 1), ("pf", 3, 2, -1, -1), ("p", 4, 4, 0, 1),
+                                                ("sd", 0, 2, 0, 1)])
+def test_basis_bit_exact(name, Z, Nn, twoM, par):
+    orbits, _ = I.SPACES[name]
+    o = O.Oracle(orbits, Z, Nn, twoM, 0 if par > 0 else 1)
+    c = N.Context(-1).build_basis(orbits, Z, Nn, twoM, par)
+    A, Bo = c.export_basis(), o.basis()
+    for key in ("p_bits", "n_bits", "p_sec", "n_sec", "blocks"):
+        assert np.array_equal(A[key], Bo[key]), key
+
+
+def test_mixed_parity_basis_bit_exact():
+    # sd + f7/2: sectors of both parities
+    orbits = (I.Orbit(0, 2, 5), I.Orbit(1, 0, 1), I.Orbit(0, 3, 7))
+    for par in (+1, -1):
+        o = O.Oracle(orbits, 2, 3, 1, 0 if par > 0 else 1)
+        c = N.Context(-1).build_basis(orbits, 2, 3, 1, par)
+        A, Bo = c.export_basis(), o.basis()
+        for key in ("p_bits", "n_bits", "p_sec", "n_sec", "blocks"):
+            assert np.array_equal(A[key], Bo[key]), key
+
+
+@pytest.mark.parametrize("species", [0, 1])
+def test_onebody_jumps_bit_exact(species):
+    """Every one-body jump a+_i a_k (index, source, destination, sign) of the
+    library equals the oracle's operator string on the same bitstrings."""
+    name, Z, Nn, twoM = "sd", 3, 2, 1
+    orbits, _ = I.SPACES[name]
+    c = host_ctx(name, Z, Nn, twoM)
+    B = c.export_basis()
+    sec = B["p_sec"] if species == 0 else B["n_sec"]
+    bits = B["p_bits"] if species == 0 else B["n_bits"]
+    pre = "p1" if species == 0 else "n1"
+    ptr, ent = c.table(pre + "_ptr", np.int64), c.table(pre + "_ent", np.uint32)
+    cls = c.table(pre + "_cls", np.int64).reshape(-1, 4)
+    ops = c.table("ops", np.int64).reshape(-1, 5)
+    op_lists = c.table("op_lists", np.int64)
+    starts = np.concatenate([[0], np.cumsum(ops[:, 4])])
+    ns = 12
+    lib = set()
+    for (ssrc, sdst, g, po) in cls:
+        for dl in range(sec[sdst][3]):
+            for e in ent[ptr[po + dl]:ptr[po + dl + 1]]:
+                src = int(bits[sec[ssrc][2] + (e & 0xFFFF)])
+                dst = int(bits[sec[sdst][2] + dl])
+                op = int(op_lists[starts[g] + ((e >> 16) & 0x7FFF)])
+                lib.add((src, dst, op // ns, op % ns, -1 if e >> 31 else 1))
+    ref = set()
+    for src in bits:
+        for k in range(ns):
+            for i in range(ns):
+                sg, dst = O.apply_string(int(src), [("+", i), ("-", k)])
+                if sg:
+                    ref.add((int(src), dst, i, k, sg))
+    assert lib == ref
+
+
+def test_scrambled_labels_same_tables():
+    orbits, spe, tb = I.space("sd")
+    a = host_ctx("sd", 2, 2, 0)
+    b = host_ctx("sd", 2, 2, 0, tb=scrambled_tbmes(tb, orbits, seed=11))
+    for name in ("pp_coef", "nn_coef", "wpn"):
+        assert np.max(np.abs(a.table(name, np.float64) - b.table(name, np.float64))) < 1e-13
+
+
+def test_error_codes():
+    orbits, spe, tb = I.space("sd")
+    c = N.Context(-1)
+    with pytest.raises(N.BSError) as e:
+        c.load_interaction(spe, tb)
+    assert e.value.code == -2                                  # BS_ENOBASIS
+    for args in [(orbits, 2, 2, 1, 1),                          # 2M odd for even A
+                 (orbits, 13, 2, 0, 1),                         # Z > states
+                 (orbits, 2, 2, 0, 0),                          # parity not +-1
+                 (orbits, 2, 2, 40, 1)]:                        # empty basis
+        with pytest.raises(N.BSError) as e:
+            c.build_basis(*args)
+        assert e.value.code == -1
+    bad_orb = [I.Orbit(0, 2, 4)]
+    with pytest.raises(N.BSError):
+        c.build_basis(bad_orb, 1, 1, 0, 1)
+    c.build_basis(orbits, 2, 2, 0, 1)
+    for bad in [(1, 1, 1, 1, 1, 1, 1.0), (1, 2, 1, 2, 0, 1, 1.0), (1, 1, 1, 4, 1, 0, 1.0), (1, 1, 1, 1, 1, 2, 1.0)]:
+        with pytest.raises(N.BSError) as e:
+            c.load_interaction(spe, [bad])
+        assert e.value.code == -1
+    a, b, cc, d, J, T, v = tb[5]
+    with pytest.raises(N.BSError):
+        c.load_interaction(spe, [tb[5], (cc, d, a, b, J, T, v)])
+    with pytest.raises(N.BSError):
+        c.load_interaction(spe[:2], tb)
+    c.load_interaction(spe, [])                                  # SPE only is legal
+    x = np.zeros(c.dim)
+    with pytest.raises(N.BSError):                               # host-only context cannot apply
+        c.apply_H_host(x, x.copy(), 1, N.BS_F64)
+
+
+def test_abi_exports_every_declared_symbol():
+    import os
+    import re
+    hdr = open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "include", "bigstick_gpu.h")).read()
+    names = set(re.findall(r"^\s*(?:const\s+)?(?:int|void|char\s*\*|const char\s*\*)\s*\**\s*(bs_\w+)\s*\(", hdr, re.M))
+    assert names, "no declarations found"
+    L = N.load()
+    for n in sorted(names):
+        assert hasattr(L, n), n
+    assert names <= set(N.EXPORTED) | {"bs_apply_H_backward", "bs_lanczos"}
