@@ -223,12 +223,19 @@ def ours(args):
         ms = [a.elapsed_time(b) for (a, b) in ev]
         return ms, x, y
 
-    # autotune k (the only free launch parameter of this kernel version)
+    # autotune: kernel variant per (k, dtype) in the library, then k here
     tune = {}
-    for k in (1, 2, 4, 8):
-        ms, _, _ = timed(k, N.BS_F32, 3, 2)
-        tune[k] = k / (min(ms) / 1000.0)
-    kbest = max(tune, key=tune.get)
+    modes = {}
+    if args.k:
+        kbest = args.k
+        modes[kbest] = ctx.autotune(kbest, N.BS_F32, sp)
+    else:
+        for k in (1, 2, 4, 8):
+            modes[k] = ctx.autotune(k, N.BS_F32, sp)
+            ms, _, _ = timed(k, N.BS_F32, 3, 2)
+            tune[k] = k / (min(ms) / 1000.0)
+        kbest = max(tune, key=tune.get)
+    mode64 = ctx.autotune(1, N.BS_F64, sp)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -287,6 +294,7 @@ def ours(args):
         "fp64_single_vector": {"value": fp64_rate, "unit": UNIT, "ms_per_matvec": float(np.mean(ms64))},
         "speedup_fp32_block_vs_fp64": fp32_rate_single / fp64_rate,
         "autotune_k": {str(k): v for k, v in tune.items()},
+        "kernel_mode": {"f32": {str(k): m for k, m in modes.items()}, "f64_k1": mode64},
         "e2e": {"value": world * args.steps * kbest / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": dim * kbest * 4, "d2h_bytes_per_step": dim * kbest * 4},
         "gpu_launches": args.steps,
@@ -309,6 +317,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--k", type=int, default=0, help="fix k instead of autotuning it")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

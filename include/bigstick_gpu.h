@@ -132,6 +132,28 @@ int bs_apply_H(bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dtype, void 
 int bs_apply_H_host(bs_ctx *ctx, const void *x_host, void *y_host, int k,
                     bs_dtype dtype, void *stream);
 
+/* Chooses the H x kernel.  1 = the tiled kernel (one CTA per destination
+ * row and 128-column tile, operands read through L1); 2 + v = variant v
+ * (threads per CTA, shared-memory budget) of the row kernel (one CTA per
+ * destination proton row, the row accumulated in shared memory, source rows
+ * staged by double-buffered TMA bulk copies), which falls back to the tiled
+ * kernel when a row does not fit in shared memory; 0 (default) = the mode
+ * bs_autotune picked for the call's (k, dtype), row variant 0 if none.  All
+ * modes give the same result up to summation order.  Errors: BS_EINVAL. */
+int bs_set_kernel(bs_ctx *ctx, int mode);
+
+/* Times every kernel mode for (k, dtype) on `stream` on scratch vectors it
+ * allocates and frees (2 x dim x k elements), and records the fastest for
+ * mode 0; *mode_out (may be NULL) receives it.  Synchronizes `stream`.
+ * Errors: as bs_apply_H, BS_ENOMEM. */
+int bs_autotune(bs_ctx *ctx, int k, bs_dtype dtype, void *stream, int *mode_out);
+
+/* Synchronizes `stream` and reads the context's device status word: returns
+ * BS_ETIMEOUT (and clears the word) if a kernel's bounded wait on an
+ * mbarrier expired since the last check, else BS_OK.  Kernels that hit such
+ * an expiry leave their output rows unwritten.  Errors: BS_ECUDA. */
+int bs_sync_status(bs_ctx *ctx, void *stream);
+
 /* Test aid: copies a host-side table of the built interaction by name
  * ("pp_ptr", "pp_src", "pp_coef", "nn_*", "p1_ptr", "p1_ent", "p1_cls",
  * "n1_*", "wpn", "links", "ops", "op_lists", "stats") into `out` (HOST,

@@ -21,7 +21,7 @@ ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "
 # every symbol include/bigstick_gpu.h declares
 EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
-            "bs_debug_table"]
+            "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -69,6 +69,9 @@ def load():
     L.bs_apply_H.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     L.bs_apply_H_host.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     L.bs_debug_table.argtypes = [vp, ctypes.c_char_p, vp, i64p]
+    L.bs_set_kernel.argtypes = [vp, ctypes.c_int]
+    L.bs_sync_status.argtypes = [vp, vp]
+    L.bs_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
     for name in EXPORTED:
         if name not in ("bs_destroy", "bs_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -149,6 +152,17 @@ class Context:
         out = np.zeros(n.value // np.dtype(dtype).itemsize, dtype=dtype)
         self._check(load().bs_debug_table(self.h, name.encode(), out.ctypes.data_as(vp), ctypes.byref(n)))
         return out
+
+    def set_kernel(self, mode):
+        self._check(load().bs_set_kernel(self.h, mode))
+
+    def autotune(self, k, dtype, stream=None):
+        m = ctypes.c_int()
+        self._check(load().bs_autotune(self.h, k, dtype, vp(stream or 0), ctypes.byref(m)))
+        return m.value
+
+    def sync_status(self, stream=None):
+        self._check(load().bs_sync_status(self.h, vp(stream or 0)))
 
     # ---- products
     def apply_H(self, x, y, k, dtype, stream=None):

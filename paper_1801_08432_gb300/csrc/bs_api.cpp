@@ -102,6 +102,34 @@ static void make_tasks(const Basis &B, const Tables &T, int tile, std::vector<De
     for (size_t i = 0; i < v.size(); ++i) tasks[i] = v[i].t;
 }
 
+// One CTA per destination proton row for the row kernel, largest work first.
+static void make_row_tasks(const Basis &B, const Tables &T, std::vector<RowTask> &tasks, int &max_pu)
+{
+    struct C { double cost; RowTask t; };
+    std::vector<C> v;
+    max_pu = 0;
+    for (size_t b = 0; b < B.blocks.size(); ++b) {
+        const Block &D = B.blocks[b];
+        const Sector &PS = B.sp[0].sec[D.ps], &NS = B.sp[1].sec[D.ns];
+        double nn_avg = (double)(T.nn.ptr[NS.start + NS.count] - T.nn.ptr[NS.start]) / (double)std::max<int64_t>(1, NS.count);
+        for (int64_t r = 0; r < D.nP; ++r) {
+            double per_col = (double)(T.pp.ptr[PS.start + r + 1] - T.pp.ptr[PS.start + r]) + nn_avg;
+            for (int64_t L = T.links_of_block[b]; L < T.links_of_block[b + 1]; ++L) {
+                const PnLink &lk = T.links[(size_t)L];
+                const OneBodyClass &P = T.p1.cls[(size_t)lk.pcls], &N = T.n1.cls[(size_t)lk.ncls];
+                int64_t np_ = T.p1.ptr[(size_t)(P.ptr_off + r + 1)] - T.p1.ptr[(size_t)(P.ptr_off + r)];
+                max_pu = std::max<int>(max_pu, (int)np_);
+                double nn_ = (double)(T.n1.ptr[(size_t)(N.ptr_off + D.nN)] - T.n1.ptr[(size_t)N.ptr_off]) / (double)D.nN;
+                per_col += (double)np_ * nn_;
+            }
+            v.push_back(C{per_col * (double)D.nN, RowTask{(int)b, (int)r}});
+        }
+    }
+    std::stable_sort(v.begin(), v.end(), [](const C &a, const C &b) { return a.cost > b.cost; });
+    tasks.resize(v.size());
+    for (size_t i = 0; i < v.size(); ++i) tasks[i] = v[i].t;
+}
+
 int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std::string &err)
 {
     release(D);
@@ -118,6 +146,8 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
         blocks[b].n_start = (int)B.sp[1].sec[s.ns].start;
         blocks[b].link_begin = (int)T.links_of_block[b];
         blocks[b].link_end = (int)T.links_of_block[b + 1];
+        blocks[b].nne_col = T.nne_col[(size_t)s.ns];
+        blocks[b].nne_slice = T.nne_slice[(size_t)s.ns];
     }
     std::vector<DevLink> links(T.links.size());
     for (size_t l = 0; l < T.links.size(); ++l) {
@@ -127,7 +157,8 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
         links[l].n_ptr_off = T.n1.cls[(size_t)L.ncls].ptr_off;
         links[l].w_off = L.w_off;
         links[l].nb = L.nb;
-        links[l].pad = 0;
+        links[l].n1e_col = T.n1e_col[(size_t)L.ncls];
+        links[l].n1e_slice = T.n1e_slice[(size_t)L.ncls];
     }
     D.tile = 128;
     std::vector<DevTask> tasks;
@@ -154,6 +185,29 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
     if ((rc = put(D, D.c32.nn_coef, f.data(), f.size(), err))) return rc;
     f = cast<float>(I.Wpn);
     if ((rc = put(D, D.c32.wpn, f.data(), f.size(), err))) return rc;
+    // row kernel
+    std::vector<RowTask> rt;
+    make_row_tasks(B, T, rt, D.max_pu);
+    D.nrtasks = (int)rt.size();
+    D.max_nN = 0;
+    for (const Sector &S : B.sp[1].sec) D.max_nN = std::max<int>(D.max_nN, (int)S.count);
+    D.max_nb = 1;
+    for (const PnLink &L : T.links) D.max_nb = std::max(D.max_nb, L.nb);
+    D.wsign = T.wsign;
+    if ((rc = put(D, D.rtasks, rt.data(), rt.size(), err))) return rc;
+    if ((rc = put(D, D.n1e_col, T.n1e.col.data(), T.n1e.col.size(), err))) return rc;
+    if ((rc = put(D, D.n1e_len, T.n1e.len.data(), T.n1e.len.size(), err))) return rc;
+    if ((rc = put(D, D.n1e_soff, T.n1e.soff.data(), T.n1e.soff.size(), err))) return rc;
+    if ((rc = put(D, D.n1e_ent, T.n1e.ent.data(), T.n1e.ent.size(), err))) return rc;
+    if ((rc = put(D, D.nne_col, T.nne.col.data(), T.nne.col.size(), err))) return rc;
+    if ((rc = put(D, D.nne_len, T.nne.len.data(), T.nne.len.size(), err))) return rc;
+    if ((rc = put(D, D.nne_soff, T.nne.soff.data(), T.nne.soff.size(), err))) return rc;
+    if ((rc = put(D, D.nne_src, T.nne.src.data(), T.nne.src.size(), err))) return rc;
+    if ((rc = put(D, D.c64.nne_coef, T.nne.coef.data(), T.nne.coef.size(), err))) return rc;
+    f = cast<float>(T.nne.coef);
+    if ((rc = put(D, D.c32.nne_coef, f.data(), f.size(), err))) return rc;
+    int zero = 0;
+    if ((rc = put(D, D.err, &zero, 1, err))) return rc;
     return BS_OK;
 }
 
@@ -316,6 +370,75 @@ int bs_apply_H_host(bs_ctx *c, const void *xh, void *yh, int k, bs_dtype dt, voi
     });
 }
 
+int bs_set_kernel(bs_ctx *c, int mode)
+{
+    return guarded(c, [&]() -> int {
+        if (mode < 0 || mode >= 2 + row_variants()) { c->err = "unknown kernel mode"; return BS_EINVAL; }
+        c->hx_mode = mode;
+        return BS_OK;
+    });
+}
+
+int bs_autotune(bs_ctx *c, int k, bs_dtype dt, void *stream, int *mode_out)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, k, dt);
+        if (rc) return rc;
+        const size_t bytes = (size_t)c->basis.dim * (size_t)k * (dt == BS_F64 ? 8 : 4);
+        void *x = nullptr, *y = nullptr;
+        cudaError_t e;
+        if ((e = cudaMalloc(&x, bytes)) != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+        if ((e = cudaMalloc(&y, bytes)) != cudaSuccess) { cudaFree(x); return cuda_fail(c, e, "cudaMalloc"); }
+        cudaStream_t s = (cudaStream_t)stream;
+        cudaMemsetAsync(x, 0, bytes, s);
+        cudaEvent_t a, b;
+        cudaEventCreate(&a);
+        cudaEventCreate(&b);
+        const int saved = c->hx_mode;
+        int best = 1;
+        float best_ms = 1e30f;
+        for (int mode = 1; mode < 2 + row_variants() && rc == BS_OK; ++mode) {
+            c->hx_mode = mode;
+            rc = launch_hx(c, x, y, k, dt, stream, c->err);       // warm-up
+            if (rc) break;
+            cudaEventRecord(a, s);
+            for (int r = 0; r < 3 && rc == BS_OK; ++r) rc = launch_hx(c, x, y, k, dt, stream, c->err);
+            cudaEventRecord(b, s);
+            if ((e = cudaEventSynchronize(b)) != cudaSuccess) { rc = cuda_fail(c, e, "autotune"); break; }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, a, b);
+            if (ms < best_ms) { best_ms = ms; best = mode; }
+        }
+        c->hx_mode = saved;
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        cudaFree(x);
+        cudaFree(y);
+        if (rc) return rc;
+        c->tuned[dt == BS_F64 ? 0 : 1][k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3] = best;
+        if (mode_out) *mode_out = best;
+        return BS_OK;
+    });
+}
+
+int bs_sync_status(bs_ctx *c, void *stream)
+{
+    return guarded(c, [&]() -> int {
+        if (c->device < 0 || !c->dev.err) return BS_OK;
+        cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+        int flag = 0;
+        if ((e = cudaMemcpy(&flag, c->dev.err, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "cudaMemcpy");
+        if (flag != 0) {
+            int zero = 0;
+            cudaMemcpy(c->dev.err, &zero, sizeof(int), cudaMemcpyHostToDevice);
+            c->err = "a device-side wait ran out of its iteration budget";
+            return flag;
+        }
+        return BS_OK;
+    });
+}
+
 // Host copies of the built tables, by name, for tests that check the host
 // builders without a GPU.  With out == NULL only *nbytes is set.
 int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
@@ -340,6 +463,22 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
         else if (s == "n1_ptr") use(T.n1.ptr.data(), T.n1.ptr.size() * 8);
         else if (s == "n1_ent") use(T.n1.ent.data(), T.n1.ent.size() * 4);
         else if (s == "wpn") use(I.Wpn.data(), I.Wpn.size() * 8);
+        else if (s == "n1e_col") use(T.n1e.col.data(), T.n1e.col.size() * 4);
+        else if (s == "n1e_len") use(T.n1e.len.data(), T.n1e.len.size() * 4);
+        else if (s == "n1e_soff") use(T.n1e.soff.data(), T.n1e.soff.size() * 8);
+        else if (s == "n1e_ent") use(T.n1e.ent.data(), T.n1e.ent.size() * 4);
+        else if (s == "nne_col") use(T.nne.col.data(), T.nne.col.size() * 4);
+        else if (s == "nne_len") use(T.nne.len.data(), T.nne.len.size() * 4);
+        else if (s == "nne_soff") use(T.nne.soff.data(), T.nne.soff.size() * 8);
+        else if (s == "nne_src") use(T.nne.src.data(), T.nne.src.size() * 4);
+        else if (s == "nne_coef") use(T.nne.coef.data(), T.nne.coef.size() * 8);
+        else if (s == "n1e_base") {
+            for (size_t k = 0; k < T.n1e_col.size(); ++k) { tmp.push_back(T.n1e_col[k]); tmp.push_back(T.n1e_slice[k]); }
+            use(tmp.data(), tmp.size() * 8);
+        } else if (s == "nne_base") {
+            for (size_t k = 0; k < T.nne_col.size(); ++k) { tmp.push_back(T.nne_col[k]); tmp.push_back(T.nne_slice[k]); }
+            use(tmp.data(), tmp.size() * 8);
+        }
         else if (s == "p1_cls" || s == "n1_cls") {
             const OneBodyJumps &J = s[0] == 'p' ? T.p1 : T.n1;
             for (const OneBodyClass &k : J.cls) { tmp.push_back(k.s_src); tmp.push_back(k.s_dst); tmp.push_back(k.group); tmp.push_back(k.ptr_off); }
@@ -360,7 +499,8 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
             for (const auto &g : I.ops.ops) for (int op : g) tmp.push_back(op);
             use(tmp.data(), tmp.size() * 8);
         } else if (s == "stats") {
-            tmp = {T.n_pp, T.n_nn, T.n_p1, T.n_n1, (int64_t)T.links.size(), (int64_t)T.ops_per_vector, (int64_t)c->dev.ntasks};
+            tmp = {T.n_pp, T.n_nn, T.n_p1, T.n_n1, (int64_t)T.links.size(), (int64_t)T.ops_per_vector, (int64_t)c->dev.ntasks,
+                   (int64_t)T.wsign};
             use(tmp.data(), tmp.size() * 8);
         } else {
             c->err = "unknown table " + s;

@@ -43,7 +43,7 @@ __device__ __forceinline__ void ldk(const T *__restrict__ p, T (&r)[K])
                 r[c] = q.x; r[c + 1] = q.y;
             }
         }
-    } else if constexpr (sizeof(T) * K == 8) {
+    } else if constexpr (sizeof(T) == 4 && K == 2) {
         float2 q = __ldg(reinterpret_cast<const float2 *>(p));
         r[0] = q.x; r[1] = q.y;
     } else {
@@ -62,7 +62,7 @@ __device__ __forceinline__ void stk(T *__restrict__ p, const T (&r)[K])
             if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p + c) = make_float4(r[c], r[c + 1], r[c + 2], r[c + 3]);
             else *reinterpret_cast<double2 *>(p + c) = make_double2(r[c], r[c + 1]);
         }
-    } else if constexpr (sizeof(T) * K == 8) {
+    } else if constexpr (sizeof(T) == 4 && K == 2) {
         *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
     } else {
 #pragma unroll
@@ -164,11 +164,28 @@ cudaError_t launch(const Device &Dv, const DevCoefs<T> &C, const T *x, T *y, cud
 
 }  // namespace
 
+cudaError_t launch_hx_row(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int variant,
+                          bool &used);
+
+static int kslot(int k)
+{
+    return k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3;
+}
+
+// Kernel choice: mode 1 = tiled kernel; mode 2 + v = row kernel variant v;
+// mode 0 = the variant the autotuner picked for (k, dtype), row variant 0 if
+// none.  The row kernel falls back to the tiled one when a row does not fit
+// in shared memory.
 int launch_hx(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err)
 {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(c->device);
-    if (e == cudaSuccess) {
+    bool used = false;
+    int mode = c->hx_mode;
+    if (mode == 0) mode = c->tuned[dt == BS_F64 ? 0 : 1][kslot(k)];
+    if (mode == 0) mode = 2;
+    if (e == cudaSuccess && mode >= 2) e = launch_hx_row(c, x, y, k, dt, s, mode - 2, used);
+    if (e == cudaSuccess && !used) {
         if (dt == BS_F64) {
             const double *xi = (const double *)x;
             double *yo = (double *)y;

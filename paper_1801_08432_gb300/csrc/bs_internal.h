@@ -7,7 +7,7 @@
 #include <unordered_map>
 #include <vector>
 
-#include "../../include/bigstick_gpu.h"
+#include "bigstick_gpu.h"
 
 namespace bs {
 
@@ -106,8 +106,27 @@ struct PnLink {
     int nb;             // row length of that matrix (neutron ops of the conjugate group)
 };
 
+// Per-column lists laid out for the warps of the row kernel: the columns of a
+// sector are sorted by list length (longest first) and cut into slices of 32;
+// entry v of the lane-th column of a slice sits at soff[slice] + 32 v + lane,
+// so a warp reads 128 contiguous bytes per step and runs about as many steps
+// as its longest list, which sorting keeps close to the others.
+struct Ell {
+    std::vector<int32_t> col, len;     // per sorted position: column id, list length
+    std::vector<int64_t> soff;         // per slice: first entry
+    std::vector<uint32_t> ent;         // one-body lists: packed (src | op << 16 | sign << 31)
+    std::vector<int32_t> src;          // like-particle lists: source column
+    std::vector<double> coef;          //                      coefficient
+};
+
 struct Tables {
     LikeJumps pp, nn;
+    Ell n1e;                             // neutron one-body classes, ELL form, entries packed as
+                                         // src | (op + wsign * sign) << 16 (index into a +W/-W row)
+    int wsign = 0;                       // power of two > largest operator group: offset of -W
+    Ell nne;                             // neutron like-particle lists, ELL form
+    std::vector<int64_t> n1e_col, n1e_slice;   // per neutron one-body class: offsets into n1e
+    std::vector<int64_t> nne_col, nne_slice;   // per neutron sector: offsets into nne
     OneBodyJumps p1, n1;
     std::vector<PnLink> links;           // sorted by dst block
     std::vector<int64_t> links_of_block; // [nblocks+1]
@@ -121,15 +140,16 @@ struct DevBlock {
     int nP, nN;
     int p_start, n_start;   // global SD index of the first SD of each sector
     int link_begin, link_end;
+    int64_t nne_col, nne_slice;   // ELL of the neutron like-particle lists of this block's neutron sector
 };
 
 struct DevLink {
     int src_block;
+    int nb;
     int64_t p_ptr_off;      // proton class CSR (|S_p dst|+1)
     int64_t n_ptr_off;      // neutron class CSR (|S_n dst|+1)
     int64_t w_off;
-    int nb;
-    int pad;
+    int64_t n1e_col, n1e_slice;   // ELL of the neutron class
 };
 
 struct DevTask {            // one CTA: destination block, proton row, column tile
@@ -141,7 +161,12 @@ struct DevTask {            // one CTA: destination block, proton row, column ti
 
 template <typename T>
 struct DevCoefs {
-    T *pp_coef = nullptr, *nn_coef = nullptr, *wpn = nullptr;
+    T *pp_coef = nullptr, *nn_coef = nullptr, *wpn = nullptr, *nne_coef = nullptr;
+};
+
+struct RowTask {            // row kernel: one CTA per destination proton row
+    int block;
+    int row;
 };
 
 struct Device {
@@ -157,6 +182,14 @@ struct Device {
     uint32_t *p1_ent = nullptr, *n1_ent = nullptr;
     DevCoefs<double> c64;
     DevCoefs<float> c32;
+    // row kernel
+    RowTask *rtasks = nullptr;
+    int nrtasks = 0;
+    int32_t *n1e_col = nullptr, *n1e_len = nullptr, *nne_col = nullptr, *nne_len = nullptr, *nne_src = nullptr;
+    int64_t *n1e_soff = nullptr, *nne_soff = nullptr;
+    uint32_t *n1e_ent = nullptr;
+    int max_nN = 0, max_nb = 0, max_pu = 0, wsign = 0;   // widest neutron sector, widest W row, most proton jumps per (row, link)
+    int *err = nullptr;                       // device status word (BS_ETIMEOUT from bounded waits)
     std::vector<void *> owned;   // every cudaMalloc above
 };
 
@@ -173,6 +206,8 @@ struct bs_ctx {
     // host-buffer entry point workspace
     void *hx_x = nullptr, *hx_y = nullptr;
     size_t hx_bytes = 0;
+    int hx_mode = 0;         // 0: autotuned, 1: tiled kernel, 2 + v: row kernel variant v
+    int tuned[2][4] = {};    // autotuned mode per (dtype, k slot); 0 = not tuned
 };
 
 // ---------------------------------------------------------------- builders (host)
@@ -184,4 +219,5 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
 int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std::string &err);
 void release(Device &D);
 int launch_hx(const bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err);
+int row_variants();
 }  // namespace bs

@@ -147,6 +147,71 @@ void onebody_jumps(const Basis &B, const Interaction &I, int spc, OneBodyJumps &
     nent = (int64_t)J.ent.size();
 }
 
+// Order the entries of the (at most 32) lists of one ELL slice so that at every
+// step the lanes' source columns spread over the eight residues mod 8: a warp
+// then gathers from all shared-memory bank groups at once.  key(e) gives the
+// source column of entry e.  Any order of a list sums the same terms; this one
+// is fixed at build time, so results stay bit-reproducible.
+template <typename Entry, typename Key>
+void bank_order(std::vector<std::vector<Entry>> &lists, Key key)
+{
+    // key(entry, lane) -> residue class to balance
+    size_t lmax = 0;
+    for (auto &l : lists) lmax = std::max(lmax, l.size());
+    std::vector<std::vector<Entry>> out(lists.size());
+    for (size_t v = 0; v < lmax; ++v) {
+        int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        for (size_t lane = 0; lane < lists.size(); ++lane) {
+            auto &l = lists[lane];
+            if (l.empty()) continue;
+            size_t best = 0;
+            const int ln = (int)lane;
+            for (size_t t = 1; t < l.size(); ++t)
+                if (cnt[key(l[t], ln) & 7] < cnt[key(l[best], ln) & 7]) best = t;
+            cnt[key(l[best], ln) & 7]++;
+            out[lane].push_back(l[best]);
+            l.erase(l.begin() + (long)best);
+        }
+    }
+    lists.swap(out);
+}
+
+// Length-sorted, 32-column-sliced ELL of packed one-body lists given as a CSR
+// (ptr[0..ncols]).  put(csr_index) returns one entry.
+template <typename Put>
+void append_ell(Ell &E, int64_t ncols, const int64_t *ptr, Put put, int64_t &col_off, int64_t &slice_base,
+                uint32_t pad)
+{
+    col_off = (int64_t)E.col.size();
+    slice_base = (int64_t)E.soff.size();
+    std::vector<int32_t> order((size_t)ncols);
+    for (int64_t c = 0; c < ncols; ++c) order[(size_t)c] = (int32_t)c;
+    std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+        return (ptr[a + 1] - ptr[a]) > (ptr[b + 1] - ptr[b]);
+    });
+    for (int64_t i = 0; i < ncols; ++i) {
+        E.col.push_back(order[(size_t)i]);
+        E.len.push_back((int32_t)(ptr[order[(size_t)i] + 1] - ptr[order[(size_t)i]]));
+    }
+    for (int64_t s0 = 0; s0 < ncols; s0 += 32) {
+        const int64_t base = (int64_t)E.ent.size();
+        E.soff.push_back(base);
+        const int32_t lmax = E.len[(size_t)(col_off + s0)];   // longest first
+        E.ent.resize((size_t)(base + (int64_t)lmax * 32), pad);
+        std::vector<std::vector<uint32_t>> lists;
+        for (int64_t lane = 0; lane < 32 && s0 + lane < ncols; ++lane) {
+            const int32_t c = order[(size_t)(s0 + lane)];
+            lists.emplace_back();
+            for (int64_t v = 0; v < ptr[c + 1] - ptr[c]; ++v) lists.back().push_back(put(ptr[c] + v));
+        }
+        // the row kernel reads a 32-byte element (k = 8 floats) as two 16-byte
+        // chunks, lane-parity first: balance (2 src + lane parity) mod 8
+        bank_order(lists, [](uint32_t e, int ln) { return 2 * (int)(e & 0xFFFFu) + (ln & 1); });
+        for (size_t lane = 0; lane < lists.size(); ++lane)
+            for (size_t v = 0; v < lists[lane].size(); ++v) E.ent[(size_t)(base + (int64_t)v * 32 + (int64_t)lane)] = lists[lane][v];
+    }
+}
+
 }  // namespace
 
 int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err)
@@ -157,6 +222,65 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
     like_jumps(B, I, 1, T.nn, T.n_nn);
     onebody_jumps(B, I, 0, T.p1, T.n_p1);
     onebody_jumps(B, I, 1, T.n1, T.n_n1);
+    // ELL forms of the neutron-side lists for the row kernel.  One-body
+    // entries are repacked as src | (op + wsign * sign) << 16, an index into a
+    // shared-memory row holding +W at [0, wsign) and -W at [wsign, 2 wsign).
+    size_t gmax = 1;
+    for (const auto &g : I.ops.ops) gmax = std::max(gmax, g.size());
+    T.wsign = 1;
+    while ((size_t)T.wsign < gmax + 1) T.wsign <<= 1;
+    const uint32_t ws = (uint32_t)T.wsign;
+    auto repack = [ws](uint32_t e) -> uint32_t {
+        return (e & 0xFFFFu) | ((((e >> 16) & 0x7FFFu) + ((e >> 31) ? ws : 0u)) << 16);
+    };
+    T.n1e_col.resize(T.n1.cls.size());
+    T.n1e_slice.resize(T.n1.cls.size());
+    for (size_t c = 0; c < T.n1.cls.size(); ++c) {
+        const OneBodyClass &K = T.n1.cls[c];
+        const int64_t ncols = B.sp[1].sec[K.s_dst].count;
+        // padding entries point at index wsign - 1 (always a zero W entry) and source column 0
+        const uint32_t pad = (ws - 1u) << 16;
+        append_ell(T.n1e, ncols, T.n1.ptr.data() + K.ptr_off,
+                   [&](int64_t i) { return repack(T.n1.ent[(size_t)i]); }, T.n1e_col[c], T.n1e_slice[c], pad);
+    }
+    T.nne_col.resize(B.sp[1].sec.size());
+    T.nne_slice.resize(B.sp[1].sec.size());
+    for (size_t s = 0; s < B.sp[1].sec.size(); ++s) {
+        const Sector &S = B.sp[1].sec[s];
+        const int64_t *ptr = T.nn.ptr.data() + S.start;
+        // the same layout for (source column, coefficient) lists
+        Ell &E = T.nne;
+        int64_t col_off = (int64_t)E.col.size(), slice_base = (int64_t)E.soff.size();
+        std::vector<int32_t> order((size_t)S.count);
+        for (int64_t c = 0; c < S.count; ++c) order[(size_t)c] = (int32_t)c;
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) { return (ptr[a + 1] - ptr[a]) > (ptr[b + 1] - ptr[b]); });
+        for (int64_t i = 0; i < S.count; ++i) {
+            E.col.push_back(order[(size_t)i]);
+            E.len.push_back((int32_t)(ptr[order[(size_t)i] + 1] - ptr[order[(size_t)i]]));
+        }
+        for (int64_t s0 = 0; s0 < S.count; s0 += 32) {
+            const int64_t base = (int64_t)E.src.size();
+            E.soff.push_back(base);
+            const int64_t need = base + (int64_t)E.len[(size_t)(col_off + s0)] * 32;
+            E.src.resize((size_t)need, 0);
+            E.coef.resize((size_t)need, 0.0);
+            std::vector<std::vector<std::pair<int32_t, double>>> lists;
+            for (int64_t lane = 0; lane < 32 && s0 + lane < S.count; ++lane) {
+                const int32_t c = order[(size_t)(s0 + lane)];
+                lists.emplace_back();
+                for (int64_t v = 0; v < ptr[c + 1] - ptr[c]; ++v)
+                    lists.back().emplace_back(T.nn.src[(size_t)(ptr[c] + v)], T.nn.coef[(size_t)(ptr[c] + v)]);
+            }
+            bank_order(lists, [](const std::pair<int32_t, double> &e, int ln) { return 2 * (int)e.first + (ln & 1); });
+            for (size_t lane = 0; lane < lists.size(); ++lane)
+                for (size_t v = 0; v < lists[lane].size(); ++v) {
+                    E.src[(size_t)(base + (int64_t)v * 32 + (int64_t)lane)] = lists[lane][v].first;
+                    E.coef[(size_t)(base + (int64_t)v * 32 + (int64_t)lane)] = lists[lane][v].second;
+                }
+        }
+        T.nne_col[s] = col_off;
+        T.nne_slice[s] = slice_base;
+    }
     // pn links: destination block <- source block
     const int nb = (int)B.blocks.size();
     const int nps = (int)B.sp[0].sec.size(), nns = (int)B.sp[1].sec.size();

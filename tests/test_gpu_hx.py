@@ -68,7 +68,7 @@ def test_fp32_full_vector(case, k):
     ref = o.spmv(x.astype(np.float32).astype(np.float64))
     H = o.matrix()
     absref = abs(H) @ np.abs(x.astype(np.float32).astype(np.float64))
-    assert np.max(np.abs(y - ref)) <= 4e-5 * np.max(absref)
+    assert np.all(np.abs(y - ref) <= 4e-5 * absref + 1e-30)
 
 
 def test_deterministic_and_k_consistent():
@@ -77,9 +77,11 @@ def test_deterministic_and_k_consistent():
     y1 = gpu_apply(c, x, 4, N.BS_F64)
     y2 = gpu_apply(c, x, 4, N.BS_F64)
     assert np.array_equal(y1, y2)
+    # the k columns are independent products; the staging chunk size (and so
+    # the summation order) depends on k, so equality is to rounding
     for col in range(4):
         yc = gpu_apply(c, x[:, col:col + 1].copy(), 1, N.BS_F64)
-        assert np.array_equal(yc[:, 0], y1[:, col])
+        assert np.max(np.abs(yc[:, 0] - y1[:, col])) <= 1e-14 * np.max(np.abs(y1))
 
 
 def test_host_buffer_entry_point():
@@ -152,3 +154,38 @@ def test_pf_6p6n_sampled_rows(k, dtype):
     else:
         bound = o.apply_rows(rows, np.abs(x), absval=True)
         assert np.all(np.abs(y - ref) <= 4e-5 * bound + 1e-30)
+
+
+@pytest.mark.parametrize("case", [("sd", 4, 4, 0), ("sd", 5, 6, 1), ("sd", 0, 3, 3), ("pf", 2, 2, 0)],
+                         ids=lambda c: "%s-%dp%dn-2M%d" % c)
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_row_and_tiled_kernels_agree_with_oracle(case, k):
+    c, o = setup(*case)
+    x = I.random_block(o.dim, k, seed=30 + k)
+    ref = o.spmv(x)
+    for mode in (1, 2, 3, 4, 5, 0):
+        c.set_kernel(mode)
+        y = gpu_apply(c, x, k, N.BS_F64)
+        c.sync_status()
+        assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref)), mode
+    c.set_kernel(0)
+    xf = x.astype(np.float32)
+    for mode in (1, 2, 3, 4, 5):
+        c.set_kernel(mode)
+        yf = gpu_apply(c, xf, k, N.BS_F32)
+        bound = abs(o.matrix()) @ np.abs(xf.astype(np.float64))
+        assert np.all(np.abs(yf - ref) <= 4e-5 * bound + 1e-6 * np.max(np.abs(ref)))
+    c.set_kernel(0)
+
+
+def test_autotune_picks_a_valid_mode():
+    c, o = setup("sd", 6, 6, 0)
+    s = torch.cuda.current_stream().cuda_stream
+    for k, dt in ((1, N.BS_F64), (8, N.BS_F32)):
+        m = c.autotune(k, dt, s)
+        assert 1 <= m <= 5
+    x = I.random_block(o.dim, 8, seed=4).astype(np.float32)
+    y = gpu_apply(c, x, 8, N.BS_F32)
+    ref = o.spmv(x.astype(np.float64))
+    assert np.max(np.abs(y - ref)) <= 1e-5 * np.max(np.abs(ref)) * 10
+    c.sync_status()

@@ -208,3 +208,57 @@ def test_abi_exports_every_declared_symbol():
     for n in sorted(names):
         assert hasattr(L, n), n
     assert names <= set(N.EXPORTED) | {"bs_apply_H_backward", "bs_lanczos"}
+
+
+def ell_lists(c, prefix, base_rows, ncols_of, packed=True):
+    """Per-column lists rebuilt from an ELL export: {(class, column): sorted entries}."""
+    col = c.table(prefix + "_col", np.int32)
+    ln = c.table(prefix + "_len", np.int32)
+    soff = c.table(prefix + "_soff", np.int64)
+    if packed:
+        ent = c.table(prefix + "_ent", np.uint32)
+    else:
+        src = c.table(prefix + "_src", np.int32)
+        cf = c.table(prefix + "_coef", np.float64)
+    out = {}
+    for cls, (col0, sl0) in enumerate(base_rows):
+        n = ncols_of(cls)
+        seen = set()
+        for i in range(n):
+            base = soff[sl0 + i // 32] + i % 32
+            items = []
+            for v in range(ln[col0 + i]):
+                e = base + 32 * v
+                items.append(int(ent[e]) if packed else (int(src[e]), float(cf[e])))
+            cc = int(col[col0 + i])
+            seen.add(cc)
+            out[(cls, cc)] = sorted(items)
+        assert seen == set(range(n))
+    return out
+
+
+def test_ell_forms_match_csr_lists():
+    c = host_ctx("pf", 2, 3, 1, parity=-1)
+    B = c.export_basis()
+    n1_ptr, n1_ent = c.table("n1_ptr", np.int64), c.table("n1_ent", np.uint32)
+    cls = c.table("n1_cls", np.int64).reshape(-1, 4)
+    base = c.table("n1e_base", np.int64).reshape(-1, 2)
+    ws = int(c.table("stats", np.int64)[7])
+    got = ell_lists(c, "n1e", base, lambda k: int(B["n_sec"][cls[k][1]][3]))
+    # ELL entries are src | (op + ws * sign) << 16; back to src | op << 16 | sign << 31
+    def unpack(e):
+        bi = e >> 16
+        return (e & 0xFFFF) | ((bi % ws) << 16) | ((bi // ws) << 31)
+    got = {key: sorted(unpack(e) for e in val) for key, val in got.items()}
+    for k, (ssrc, sdst, g, po) in enumerate(cls):
+        for col in range(B["n_sec"][sdst][3]):
+            ref = sorted(int(e) for e in n1_ent[n1_ptr[po + col]:n1_ptr[po + col + 1]])
+            assert got[(k, col)] == ref
+    nn_ptr, nn_src, nn_c = c.table("nn_ptr", np.int64), c.table("nn_src", np.int32), c.table("nn_coef", np.float64)
+    nbase = c.table("nne_base", np.int64).reshape(-1, 2)
+    got = ell_lists(c, "nne", nbase, lambda s: int(B["n_sec"][s][3]), packed=False)
+    for s, (_, _, st, cnt) in enumerate(B["n_sec"]):
+        for col in range(cnt):
+            g = st + col
+            ref = sorted((int(a), float(b)) for a, b in zip(nn_src[nn_ptr[g]:nn_ptr[g + 1]], nn_c[nn_ptr[g]:nn_ptr[g + 1]]))
+            assert got[(s, col)] == ref
