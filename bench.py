@@ -226,16 +226,17 @@ def ours(args):
     # autotune: kernel variant per (k, dtype) in the library, then k here
     tune = {}
     modes = {}
+    mode_ms = {}
     if args.k:
         kbest = args.k
-        modes[kbest] = ctx.autotune(kbest, N.BS_F32, sp)
+        modes[kbest], mode_ms[kbest] = ctx.autotune(kbest, N.BS_F32, sp, times=True)
     else:
         for k in (1, 2, 4, 8):
-            modes[k] = ctx.autotune(k, N.BS_F32, sp)
+            modes[k], mode_ms[k] = ctx.autotune(k, N.BS_F32, sp, times=True)
             ms, _, _ = timed(k, N.BS_F32, 3, 2)
             tune[k] = k / (min(ms) / 1000.0)
         kbest = max(tune, key=tune.get)
-    mode64 = ctx.autotune(1, N.BS_F64, sp)
+    mode64, ms64modes = ctx.autotune(1, N.BS_F64, sp, times=True)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -294,7 +295,8 @@ def ours(args):
         "fp64_single_vector": {"value": fp64_rate, "unit": UNIT, "ms_per_matvec": float(np.mean(ms64))},
         "speedup_fp32_block_vs_fp64": fp32_rate_single / fp64_rate,
         "autotune_k": {str(k): v for k, v in tune.items()},
-        "kernel_mode": {"f32": {str(k): m for k, m in modes.items()}, "f64_k1": mode64},
+        "kernel_mode": {"f32": {str(k): m for k, m in modes.items()}, "f64_k1": mode64,
+                        "ms_per_mode_f32": {str(k): v for k, v in mode_ms.items()}, "ms_per_mode_f64_k1": ms64modes},
         "e2e": {"value": world * args.steps * kbest / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": dim * kbest * 4, "d2h_bytes_per_step": dim * kbest * 4},
         "gpu_launches": args.steps,

@@ -133,20 +133,26 @@ int bs_apply_H_host(bs_ctx *ctx, const void *x_host, void *y_host, int k,
                     bs_dtype dtype, void *stream);
 
 /* Chooses the H x kernel.  1 = the tiled kernel (one CTA per destination
- * row and 128-column tile, operands read through L1); 2 + v = variant v
+ * row and 128-column tile, operands read through L1); 2..5 = variants
  * (threads per CTA, shared-memory budget) of the row kernel (one CTA per
  * destination proton row, the row accumulated in shared memory, source rows
- * staged by double-buffered TMA bulk copies), which falls back to the tiled
- * kernel when a row does not fit in shared memory; 0 (default) = the mode
- * bs_autotune picked for the call's (k, dtype), row variant 0 if none.  All
- * modes give the same result up to summation order.  Errors: BS_EINVAL. */
+ * staged by double-buffered TMA bulk copies); 6..10 = variants (consumer
+ * warps, columns per thread, ring depth, shared-memory budget) of the
+ * pipelined kernel (a producer warp fills a ring of shared-memory slots by
+ * TMA, consumer warps keep their columns' sums in registers; needs k values
+ * of 16 bytes or more per basis state).  A mode that does not fit the basis
+ * falls back to the tiled kernel.  0 (default) = the mode bs_autotune picked
+ * for the call's (k, dtype), else the first pipelined variant, else the first
+ * row variant.  All modes give the same result up to summation order.
+ * Errors: BS_EINVAL. */
 int bs_set_kernel(bs_ctx *ctx, int mode);
 
-/* Times every kernel mode for (k, dtype) on `stream` on scratch vectors it
- * allocates and frees (2 x dim x k elements), and records the fastest for
- * mode 0; *mode_out (may be NULL) receives it.  Synchronizes `stream`.
- * Errors: as bs_apply_H, BS_ENOMEM. */
-int bs_autotune(bs_ctx *ctx, int k, bs_dtype dtype, void *stream, int *mode_out);
+/* Times every kernel mode 1..10 for (k, dtype) on `stream` on scratch
+ * vectors it allocates and frees (2 x dim x k elements), and records the
+ * fastest for mode 0; *mode_out (may be NULL) receives it, ms_out (may be
+ * NULL, else 10 floats) the mean milliseconds per product of each mode.
+ * Synchronizes `stream`.  Errors: as bs_apply_H, BS_ENOMEM. */
+int bs_autotune(bs_ctx *ctx, int k, bs_dtype dtype, void *stream, int *mode_out, float *ms_out);
 
 /* Synchronizes `stream` and reads the context's device status word: returns
  * BS_ETIMEOUT (and clears the word) if a kernel's bounded wait on an

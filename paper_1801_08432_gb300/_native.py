@@ -71,7 +71,8 @@ def load():
     L.bs_debug_table.argtypes = [vp, ctypes.c_char_p, vp, i64p]
     L.bs_set_kernel.argtypes = [vp, ctypes.c_int]
     L.bs_sync_status.argtypes = [vp, vp]
-    L.bs_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int)]
+    L.bs_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
+                              ctypes.POINTER(ctypes.c_float)]
     for name in EXPORTED:
         if name not in ("bs_destroy", "bs_last_error"):
             getattr(L, name).restype = ctypes.c_int
@@ -156,9 +157,14 @@ class Context:
     def set_kernel(self, mode):
         self._check(load().bs_set_kernel(self.h, mode))
 
-    def autotune(self, k, dtype, stream=None):
+    def autotune(self, k, dtype, stream=None, times=False):
+        """Picks the fastest kernel mode for (k, dtype); with times=True also
+        returns {mode: ms per product}."""
         m = ctypes.c_int()
-        self._check(load().bs_autotune(self.h, k, dtype, vp(stream or 0), ctypes.byref(m)))
+        ms = (ctypes.c_float * 10)()
+        self._check(load().bs_autotune(self.h, k, dtype, vp(stream or 0), ctypes.byref(m), ms))
+        if times:
+            return m.value, {i + 1: round(float(ms[i]), 4) for i in range(10)}
         return m.value
 
     def sync_status(self, stream=None):

@@ -148,6 +148,9 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
         blocks[b].link_end = (int)T.links_of_block[b + 1];
         blocks[b].nne_col = T.nne_col[(size_t)s.ns];
         blocks[b].nne_slice = T.nne_slice[(size_t)s.ns];
+        blocks[b].perm_off = T.pe.perm_off[(size_t)s.ns];
+        blocks[b].pe_nn_ent = T.pe.sec_nn_ent[(size_t)s.ns];
+        blocks[b].pe_nn_sinfo = T.pe.sec_nn_sinfo[(size_t)s.ns];
     }
     std::vector<DevLink> links(T.links.size());
     for (size_t l = 0; l < T.links.size(); ++l) {
@@ -159,6 +162,9 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
         links[l].nb = L.nb;
         links[l].n1e_col = T.n1e_col[(size_t)L.ncls];
         links[l].n1e_slice = T.n1e_slice[(size_t)L.ncls];
+        links[l].pe_ent = T.pe.cls_ent[(size_t)L.ncls];
+        links[l].pe_sinfo = T.pe.cls_sinfo[(size_t)L.ncls];
+        links[l].ww_off = T.ww_off[(size_t)T.p1.cls[(size_t)L.pcls].group];
     }
     D.tile = 128;
     std::vector<DevTask> tasks;
@@ -208,6 +214,18 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
     if ((rc = put(D, D.c32.nne_coef, f.data(), f.size(), err))) return rc;
     int zero = 0;
     if ((rc = put(D, D.err, &zero, 1, err))) return rc;
+    // pipelined kernel
+    if ((rc = put(D, D.pe_perm, T.pe.perm.data(), T.pe.perm.size(), err))) return rc;
+    if ((rc = put(D, D.pe_sinfo, T.pe.sinfo.data(), T.pe.sinfo.size(), err))) return rc;
+    if ((rc = put(D, D.pe_ent, T.pe.ent.data(), T.pe.ent.size(), err))) return rc;
+    if ((rc = put(D, D.pe_nn_src, T.pe.nn_src.data(), T.pe.nn_src.size(), err))) return rc;
+    if ((rc = put(D, D.pe_nn_sinfo, T.pe.nn_sinfo.data(), T.pe.nn_sinfo.size(), err))) return rc;
+    if ((rc = put(D, D.pe_nn_coef64, T.pe.nn_coef.data(), T.pe.nn_coef.size(), err))) return rc;
+    f = cast<float>(T.pe.nn_coef);
+    if ((rc = put(D, D.pe_nn_coef32, f.data(), f.size(), err))) return rc;
+    if ((rc = put(D, D.ww64, T.ww.data(), T.ww.size(), err))) return rc;
+    f = cast<float>(T.ww);
+    if ((rc = put(D, D.ww32, f.data(), f.size(), err))) return rc;
     return BS_OK;
 }
 
@@ -373,13 +391,13 @@ int bs_apply_H_host(bs_ctx *c, const void *xh, void *yh, int k, bs_dtype dt, voi
 int bs_set_kernel(bs_ctx *c, int mode)
 {
     return guarded(c, [&]() -> int {
-        if (mode < 0 || mode >= 2 + row_variants()) { c->err = "unknown kernel mode"; return BS_EINVAL; }
+        if (mode < 0 || mode >= 2 + row_variants() + pipe_variants()) { c->err = "unknown kernel mode"; return BS_EINVAL; }
         c->hx_mode = mode;
         return BS_OK;
     });
 }
 
-int bs_autotune(bs_ctx *c, int k, bs_dtype dt, void *stream, int *mode_out)
+int bs_autotune(bs_ctx *c, int k, bs_dtype dt, void *stream, int *mode_out, float *ms_out)
 {
     return guarded(c, [&]() -> int {
         int rc = check_apply(c, k, dt);
@@ -397,7 +415,7 @@ int bs_autotune(bs_ctx *c, int k, bs_dtype dt, void *stream, int *mode_out)
         const int saved = c->hx_mode;
         int best = 1;
         float best_ms = 1e30f;
-        for (int mode = 1; mode < 2 + row_variants() && rc == BS_OK; ++mode) {
+        for (int mode = 1; mode < 2 + row_variants() + pipe_variants() && rc == BS_OK; ++mode) {
             c->hx_mode = mode;
             rc = launch_hx(c, x, y, k, dt, stream, c->err);       // warm-up
             if (rc) break;
@@ -407,6 +425,8 @@ int bs_autotune(bs_ctx *c, int k, bs_dtype dt, void *stream, int *mode_out)
             if ((e = cudaEventSynchronize(b)) != cudaSuccess) { rc = cuda_fail(c, e, "autotune"); break; }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, a, b);
+            ms /= 3.0f;
+            if (ms_out) ms_out[mode - 1] = ms;
             if (ms < best_ms) { best_ms = ms; best = mode; }
         }
         c->hx_mode = saved;
@@ -472,6 +492,18 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
         else if (s == "nne_soff") use(T.nne.soff.data(), T.nne.soff.size() * 8);
         else if (s == "nne_src") use(T.nne.src.data(), T.nne.src.size() * 4);
         else if (s == "nne_coef") use(T.nne.coef.data(), T.nne.coef.size() * 8);
+        else if (s == "pe_perm") use(T.pe.perm.data(), T.pe.perm.size() * 4);
+        else if (s == "pe_sinfo") use(T.pe.sinfo.data(), T.pe.sinfo.size() * 4);
+        else if (s == "pe_ent") use(T.pe.ent.data(), T.pe.ent.size() * 4);
+        else if (s == "pe_nn_src") use(T.pe.nn_src.data(), T.pe.nn_src.size() * 4);
+        else if (s == "pe_nn_coef") use(T.pe.nn_coef.data(), T.pe.nn_coef.size() * 8);
+        else if (s == "pe_nn_sinfo") use(T.pe.nn_sinfo.data(), T.pe.nn_sinfo.size() * 4);
+        else if (s == "ww") use(T.ww.data(), T.ww.size() * 8);
+        else if (s == "pe_base") {   // per neutron sector: perm_off, nn_ent, nn_sinfo; then per class: ent, sinfo
+            for (size_t k = 0; k < T.pe.perm_off.size(); ++k) { tmp.push_back(T.pe.perm_off[k]); tmp.push_back(T.pe.sec_nn_ent[k]); tmp.push_back(T.pe.sec_nn_sinfo[k]); }
+            for (size_t k = 0; k < T.pe.cls_ent.size(); ++k) { tmp.push_back(T.pe.cls_ent[k]); tmp.push_back(T.pe.cls_sinfo[k]); }
+            use(tmp.data(), tmp.size() * 8);
+        } else if (s == "ww_off") use(T.ww_off.data(), T.ww_off.size() * 8);
         else if (s == "n1e_base") {
             for (size_t k = 0; k < T.n1e_col.size(); ++k) { tmp.push_back(T.n1e_col[k]); tmp.push_back(T.n1e_slice[k]); }
             use(tmp.data(), tmp.size() * 8);

@@ -167,24 +167,33 @@ cudaError_t launch(const Device &Dv, const DevCoefs<T> &C, const T *x, T *y, cud
 cudaError_t launch_hx_row(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int variant,
                           bool &used);
 
+cudaError_t launch_hx_pipe(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
+                           bool &used);
+
 static int kslot(int k)
 {
     return k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3;
 }
 
 // Kernel choice: mode 1 = tiled kernel; mode 2 + v = row kernel variant v;
-// mode 0 = the variant the autotuner picked for (k, dtype), row variant 0 if
-// none.  The row kernel falls back to the tiled one when a row does not fit
-// in shared memory.
+// mode 2 + R + v = pipelined kernel variant v (R = number of row variants);
+// mode 0 = the variant the autotuner picked for (k, dtype), else the first
+// pipelined variant, else the first row variant.  A row or pipelined variant
+// that does not fit the basis falls back to the tiled kernel.
 int launch_hx(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err)
 {
     cudaStream_t s = (cudaStream_t)stream;
     cudaError_t e = cudaSetDevice(c->device);
     bool used = false;
     int mode = c->hx_mode;
+    const int R = row_variants();
     if (mode == 0) mode = c->tuned[dt == BS_F64 ? 0 : 1][kslot(k)];
-    if (mode == 0) mode = 2;
-    if (e == cudaSuccess && mode >= 2) e = launch_hx_row(c, x, y, k, dt, s, mode - 2, used);
+    if (mode == 0 && e == cudaSuccess) {
+        e = launch_hx_pipe(c, x, y, k, dt, s, 0, used);
+        if (!used) mode = 2;
+    }
+    if (e == cudaSuccess && !used && mode >= 2 + R) e = launch_hx_pipe(c, x, y, k, dt, s, mode - 2 - R, used);
+    if (e == cudaSuccess && !used && mode >= 2 && mode < 2 + R) e = launch_hx_row(c, x, y, k, dt, s, mode - 2, used);
     if (e == cudaSuccess && !used) {
         if (dt == BS_F64) {
             const double *xi = (const double *)x;

@@ -119,8 +119,28 @@ struct Ell {
     std::vector<double> coef;          //                      coefficient
 };
 
+// The same neutron-side lists for the pipelined kernel: the columns of each
+// neutron sector in ONE fixed order shared by every list kind (sorted
+// lexicographically by the column's list lengths over the incoming classes,
+// so neighbouring columns have similar lengths), cut into 32-column slices;
+// per class and slice: offset of the slice's first entry and its longest list.
+struct PermEll {
+    std::vector<int32_t> perm;          // per sector: position -> column (sector offset in perm_off)
+    std::vector<int64_t> perm_off;      // per neutron sector
+    std::vector<uint32_t> ent;          // one-body entries, packed like Tables::n1e
+    std::vector<int32_t> sinfo;         // per class and slice: (entry offset from class base, lmax)
+    std::vector<int64_t> cls_ent, cls_sinfo;   // per one-body class: base of its entries / slice info
+    std::vector<int32_t> nn_src;        // like-particle lists in the same order
+    std::vector<double> nn_coef;
+    std::vector<int32_t> nn_sinfo;      // per sector and slice: (entry offset, lmax)
+    std::vector<int64_t> sec_nn_ent, sec_nn_sinfo;
+};
+
 struct Tables {
     LikeJumps pp, nn;
+    PermEll pe;                          // pipelined kernel's neutron lists
+    std::vector<double> ww;              // per group g, op a, proton sign: a row of 2*wsign W values
+    std::vector<int64_t> ww_off;         // per group
     Ell n1e;                             // neutron one-body classes, ELL form, entries packed as
                                          // src | (op + wsign * sign) << 16 (index into a +W/-W row)
     int wsign = 0;                       // power of two > largest operator group: offset of -W
@@ -141,6 +161,8 @@ struct DevBlock {
     int p_start, n_start;   // global SD index of the first SD of each sector
     int link_begin, link_end;
     int64_t nne_col, nne_slice;   // ELL of the neutron like-particle lists of this block's neutron sector
+    int64_t perm_off;             // pipelined kernel: column order of the neutron sector
+    int64_t pe_nn_ent, pe_nn_sinfo;
 };
 
 struct DevLink {
@@ -150,6 +172,8 @@ struct DevLink {
     int64_t n_ptr_off;      // neutron class CSR (|S_n dst|+1)
     int64_t w_off;
     int64_t n1e_col, n1e_slice;   // ELL of the neutron class
+    int64_t pe_ent, pe_sinfo;     // pipelined kernel: class entries and slice info
+    int64_t ww_off;               // pipelined kernel: signed W rows of the proton group
 };
 
 struct DevTask {            // one CTA: destination block, proton row, column tile
@@ -190,6 +214,11 @@ struct Device {
     uint32_t *n1e_ent = nullptr;
     int max_nN = 0, max_nb = 0, max_pu = 0, wsign = 0;   // widest neutron sector, widest W row, most proton jumps per (row, link)
     int *err = nullptr;                       // device status word (BS_ETIMEOUT from bounded waits)
+    // pipelined kernel
+    int32_t *pe_perm = nullptr, *pe_sinfo = nullptr, *pe_nn_src = nullptr, *pe_nn_sinfo = nullptr;
+    uint32_t *pe_ent = nullptr;
+    double *pe_nn_coef64 = nullptr, *ww64 = nullptr;
+    float *pe_nn_coef32 = nullptr, *ww32 = nullptr;
     std::vector<void *> owned;   // every cudaMalloc above
 };
 
@@ -220,4 +249,5 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
 void release(Device &D);
 int launch_hx(const bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err);
 int row_variants();
+int pipe_variants();
 }  // namespace bs

@@ -159,16 +159,19 @@ void bank_order(std::vector<std::vector<Entry>> &lists, Key key)
     size_t lmax = 0;
     for (auto &l : lists) lmax = std::max(lmax, l.size());
     std::vector<std::vector<Entry>> out(lists.size());
+    // a 16-byte shared-memory load is served a quarter warp (8 lanes) at a
+    // time: balance the residues inside each quarter
     for (size_t v = 0; v < lmax; ++v) {
-        int cnt[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+        int cnt[4][8] = {};
         for (size_t lane = 0; lane < lists.size(); ++lane) {
             auto &l = lists[lane];
             if (l.empty()) continue;
             size_t best = 0;
             const int ln = (int)lane;
+            int *c = cnt[(lane >> 3) & 3];
             for (size_t t = 1; t < l.size(); ++t)
-                if (cnt[key(l[t], ln) & 7] < cnt[key(l[best], ln) & 7]) best = t;
-            cnt[key(l[best], ln) & 7]++;
+                if (c[key(l[t], ln) & 7] < c[key(l[best], ln) & 7]) best = t;
+            c[key(l[best], ln) & 7]++;
             out[lane].push_back(l[best]);
             l.erase(l.begin() + (long)best);
         }
@@ -209,6 +212,124 @@ void append_ell(Ell &E, int64_t ncols, const int64_t *ptr, Put put, int64_t &col
         bank_order(lists, [](uint32_t e, int ln) { return 2 * (int)(e & 0xFFFFu) + (ln & 1); });
         for (size_t lane = 0; lane < lists.size(); ++lane)
             for (size_t v = 0; v < lists[lane].size(); ++v) E.ent[(size_t)(base + (int64_t)v * 32 + (int64_t)lane)] = lists[lane][v];
+    }
+}
+
+// Lists of the pipelined kernel (see PermEll) and its pre-signed W rows.
+void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
+{
+    PermEll &P = T.pe;
+    P = PermEll();
+    const uint32_t ws = (uint32_t)T.wsign;
+    auto repack = [ws](uint32_t e) -> uint32_t {
+        return (e & 0xFFFFu) | ((((e >> 16) & 0x7FFFu) + ((e >> 31) ? ws : 0u)) << 16);
+    };
+    const Species &NS = B.sp[1];
+    const size_t nsec = NS.sec.size();
+    std::vector<std::vector<int>> into(nsec);
+    for (size_t c = 0; c < T.n1.cls.size(); ++c) into[(size_t)T.n1.cls[c].s_dst].push_back((int)c);
+    P.perm_off.assign(nsec, 0);
+    P.cls_ent.assign(T.n1.cls.size(), 0);
+    P.cls_sinfo.assign(T.n1.cls.size(), 0);
+    P.sec_nn_ent.assign(nsec, 0);
+    P.sec_nn_sinfo.assign(nsec, 0);
+    for (size_t s = 0; s < nsec; ++s) {
+        const int64_t n = NS.sec[s].count;
+        // column order: lexicographic (descending) by the per-class list lengths
+        std::vector<int32_t> order((size_t)n);
+        for (int64_t c = 0; c < n; ++c) order[(size_t)c] = (int32_t)c;
+        auto len = [&](int cls, int32_t col) {
+            const int64_t po = T.n1.cls[(size_t)cls].ptr_off;
+            return T.n1.ptr[(size_t)(po + col + 1)] - T.n1.ptr[(size_t)(po + col)];
+        };
+        std::stable_sort(order.begin(), order.end(), [&](int32_t a, int32_t b) {
+            for (int cls : into[s]) {
+                const int64_t la = len(cls, a), lb = len(cls, b);
+                if (la != lb) return la > lb;
+            }
+            return false;
+        });
+        while (P.perm.size() % 4) P.perm.push_back(0);
+        P.perm_off[s] = (int64_t)P.perm.size();
+        P.perm.insert(P.perm.end(), order.begin(), order.end());
+        const int64_t nsl = (n + 31) / 32;
+        // one-body classes into this sector
+        for (int cls : into[s]) {
+            while (P.sinfo.size() % 4) P.sinfo.push_back(0);
+            P.cls_ent[(size_t)cls] = (int64_t)P.ent.size();
+            P.cls_sinfo[(size_t)cls] = (int64_t)P.sinfo.size();
+            const int64_t po = T.n1.cls[(size_t)cls].ptr_off;
+            for (int64_t sl = 0; sl < nsl; ++sl) {
+                std::vector<std::vector<uint32_t>> lists;
+                size_t lmax = 0;
+                for (int64_t lane = 0; lane < 32; ++lane) {
+                    lists.emplace_back();
+                    const int64_t pos = sl * 32 + lane;
+                    if (pos >= n) continue;
+                    const int32_t col = order[(size_t)pos];
+                    for (int64_t e = T.n1.ptr[(size_t)(po + col)]; e < T.n1.ptr[(size_t)(po + col + 1)]; ++e)
+                        lists.back().push_back(repack(T.n1.ent[(size_t)e]));
+                    lmax = std::max(lmax, lists.back().size());
+                }
+                bank_order(lists, [](uint32_t e, int ln) { return 2 * (int)(e & 0xFFFFu) + (ln & 1); });
+                P.sinfo.push_back((int32_t)((int64_t)P.ent.size() - P.cls_ent[(size_t)cls]));
+                P.sinfo.push_back((int32_t)lmax);
+                const size_t base = P.ent.size();
+                P.ent.resize(base + lmax * 32, (ws - 1u) << 16);   // padding: a zero W entry, source column 0
+                for (size_t lane = 0; lane < 32; ++lane)
+                    for (size_t v = 0; v < lists[lane].size(); ++v) P.ent[base + v * 32 + lane] = lists[lane][v];
+            }
+        }
+        // like-particle lists of the sector, same order
+        while (P.nn_sinfo.size() % 4) P.nn_sinfo.push_back(0);
+        P.sec_nn_ent[s] = (int64_t)P.nn_src.size();
+        P.sec_nn_sinfo[s] = (int64_t)P.nn_sinfo.size();
+        const int64_t *ptr = T.nn.ptr.data() + NS.sec[s].start;
+        for (int64_t sl = 0; sl < nsl; ++sl) {
+            std::vector<std::vector<std::pair<int32_t, double>>> lists;
+            size_t lmax = 0;
+            for (int64_t lane = 0; lane < 32; ++lane) {
+                lists.emplace_back();
+                const int64_t pos = sl * 32 + lane;
+                if (pos >= n) continue;
+                const int32_t col = order[(size_t)pos];
+                for (int64_t e = ptr[col]; e < ptr[col + 1]; ++e)
+                    lists.back().emplace_back(T.nn.src[(size_t)e], T.nn.coef[(size_t)e]);
+                lmax = std::max(lmax, lists.back().size());
+            }
+            bank_order(lists, [](const std::pair<int32_t, double> &e, int ln) { return 2 * (int)e.first + (ln & 1); });
+            P.nn_sinfo.push_back((int32_t)((int64_t)P.nn_src.size() - P.sec_nn_ent[s]));
+            P.nn_sinfo.push_back((int32_t)lmax);
+            const size_t base = P.nn_src.size();
+            P.nn_src.resize(base + lmax * 32, 0);
+            P.nn_coef.resize(base + lmax * 32, 0.0);
+            for (size_t lane = 0; lane < 32; ++lane)
+                for (size_t v = 0; v < lists[lane].size(); ++v) {
+                    P.nn_src[base + v * 32 + lane] = lists[lane][v].first;
+                    P.nn_coef[base + v * 32 + lane] = lists[lane][v].second;
+                }
+        }
+    }
+    // pre-signed W rows: group g, operator a, proton sign sp -> [ sp W[a][.] | -sp W[a][.] ]
+    const size_t ng = I.ops.ops.size();
+    T.ww_off.assign(ng, 0);
+    T.ww.clear();
+    for (size_t g = 0; g < ng; ++g) {
+        T.ww_off[g] = (int64_t)T.ww.size();
+        const int h = I.conj_group[g];
+        if (h < 0) continue;
+        const size_t na = I.ops.ops[g].size(), nb = I.ops.ops[(size_t)h].size();
+        for (size_t a = 0; a < na; ++a)
+            for (int sp = 0; sp < 2; ++sp) {
+                const double sg = sp ? -1.0 : 1.0;
+                const size_t base = T.ww.size();
+                T.ww.resize(base + 2 * (size_t)ws, 0.0);
+                for (size_t b = 0; b < nb; ++b) {
+                    const double w = sg * I.Wpn[(size_t)I.wpn_off[g] + a * nb + b];
+                    T.ww[base + b] = w;
+                    T.ww[base + ws + b] = -w;
+                }
+            }
     }
 }
 
@@ -281,6 +402,7 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
         T.nne_col[s] = col_off;
         T.nne_slice[s] = slice_base;
     }
+    build_perm_ell(B, I, T);
     // pn links: destination block <- source block
     const int nb = (int)B.blocks.size();
     const int nps = (int)B.sp[0].sec.size(), nns = (int)B.sp[1].sec.size();

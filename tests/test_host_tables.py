@@ -262,3 +262,76 @@ def test_ell_forms_match_csr_lists():
             g = st + col
             ref = sorted((int(a), float(b)) for a, b in zip(nn_src[nn_ptr[g]:nn_ptr[g + 1]], nn_c[nn_ptr[g]:nn_ptr[g + 1]]))
             assert got[(s, col)] == ref
+
+
+def pipe_tables_matvec(c, x):
+    """y = H x from the pipelined kernel's tables (one column order per neutron
+    sector, sliced ELL with +W/-W indices, pre-signed W rows), test-side numpy."""
+    B = c.export_basis()
+    blocks = B["blocks"]
+    nsec = len(B["n_sec"])
+    st = c.table("stats", np.int64)
+    ws = int(st[7])
+    base = c.table("pe_base", np.int64)
+    sec_base = base[:3 * nsec].reshape(-1, 3)
+    cls_base = base[3 * nsec:].reshape(-1, 2)
+    perm = c.table("pe_perm", np.int32)
+    sinfo = c.table("pe_sinfo", np.int32)
+    ent = c.table("pe_ent", np.uint32)
+    nsrc, ncoef, nsinfo = c.table("pe_nn_src", np.int32), c.table("pe_nn_coef", np.float64), c.table("pe_nn_sinfo", np.int32)
+    ww = c.table("ww", np.float64)
+    ww_off = c.table("ww_off", np.int64)
+    pp_ptr, pp_src, pp_c = c.table("pp_ptr", np.int64), c.table("pp_src", np.int32), c.table("pp_coef", np.float64)
+    p1_ptr, p1_ent = c.table("p1_ptr", np.int64), c.table("p1_ent", np.uint32)
+    p1_cls = c.table("p1_cls", np.int64).reshape(-1, 4)
+    links = c.table("links", np.int64).reshape(-1, 6)
+    y = np.zeros_like(x)
+
+    def blk(b):
+        ps, ns_, off = blocks[b]
+        return int(off), int(B["p_sec"][ps][2]), int(B["p_sec"][ps][3]), int(ns_), int(B["n_sec"][ns_][3])
+
+    for b in range(len(blocks)):
+        off, p0, nP, ns_, nN = blk(b)
+        X = x[off:off + nP * nN].reshape(nP, nN)
+        Y = y[off:off + nP * nN].reshape(nP, nN)
+        for r in range(nP):
+            for e in range(pp_ptr[p0 + r], pp_ptr[p0 + r + 1]):
+                Y[r] += pp_c[e] * X[pp_src[e]]
+        po, ne0, ns0 = sec_base[ns_]
+        for p in range(nN):
+            col = perm[po + p]
+            o, lmax = nsinfo[ns0 + 2 * (p // 32)], nsinfo[ns0 + 2 * (p // 32) + 1]
+            idx = ne0 + o + 32 * np.arange(lmax) + p % 32
+            Y[:, col] += X[:, nsrc[idx]] @ ncoef[idx]
+    for (d, s, pc, nc, w_off, nb) in links:
+        offd, _, nPd, nsd, nNd = blk(d)
+        offs, _, nPs, _, nNs = blk(s)
+        Xs = x[offs:offs + nPs * nNs].reshape(nPs, nNs)
+        Yd = y[offd:offd + nPd * nNd].reshape(nPd, nNd)
+        pptr = p1_cls[pc][3]
+        wo = ww_off[p1_cls[pc][2]]
+        ce, cs = cls_base[nc]
+        po = sec_base[nsd][0]
+        for r in range(nPd):
+            for e in p1_ent[p1_ptr[pptr + r]:p1_ptr[pptr + r + 1]]:
+                ip, a, sp_ = int(e & 0xFFFF), int((e >> 16) & 0x7FFF), int(e >> 31)
+                wrow = ww[wo + (2 * a + sp_) * 2 * ws: wo + (2 * a + sp_ + 1) * 2 * ws]
+                for p in range(nNd):
+                    col = perm[po + p]
+                    o, lmax = sinfo[cs + 2 * (p // 32)], sinfo[cs + 2 * (p // 32) + 1]
+                    es = ent[ce + o + 32 * np.arange(lmax) + p % 32]
+                    Yd[r, col] += np.dot(wrow[es >> 16], Xs[ip, es & 0xFFFF])
+    return y
+
+
+@pytest.mark.parametrize("name,Z,Nn,twoM", [("sd", 2, 2, 0), ("sd", 3, 2, 1), ("sd", 0, 3, 3), ("sd", 1, 1, 0),
+                                            ("pf", 2, 2, 0)])
+def test_pipe_tables_reproduce_oracle_matrix(name, Z, Nn, twoM):
+    orbits, spe, tb = I.space(name)
+    o = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
+    c = host_ctx(name, Z, Nn, twoM)
+    x = I.random_block(o.dim, 1, seed=9)[:, 0]
+    y_ref = o.spmv(x)
+    y = pipe_tables_matvec(c, x)
+    assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
