@@ -132,6 +132,52 @@ int bs_apply_H(bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dtype, void 
 int bs_apply_H_host(bs_ctx *ctx, const void *x_host, void *y_host, int k,
                     bs_dtype dtype, void *stream);
 
+/* Options of bs_lanczos. */
+typedef struct {
+    int k;              /* block size: 1 (standard Lanczos), 2, 4 or 8 */
+    bs_dtype dtype;     /* precision of the stored Lanczos vectors and of H x */
+    int niter;          /* block iterations; clamped to dim / k */
+    int nkeep;          /* eigenvalues returned (lowest first) */
+    int refine;         /* 1: FP64 H psi of the lowest min(nkeep, 8) Ritz vectors,
+                           evals become FP64 Rayleigh quotients, residuals reported */
+    int reorth_passes;  /* Gram-Schmidt passes against all stored blocks (2 = default) */
+    void *stream;       /* cudaStream_t the work runs on */
+} bs_lanczos_opts;
+
+/* What bs_lanczos did. */
+typedef struct {
+    int iterations;          /* block iterations done */
+    int breakdowns;          /* Gram eigenvalues below 1e-24 of the largest, restarted with random columns */
+    int n_kept;              /* pairs with Ritz vectors / refinement (<= 8) */
+    double residual[64];     /* |H psi - E psi| / |psi| in FP64, per refined pair */
+    double delta_conv;       /* sum_{i <= nkeep+5} |E_i(n) - E_i(n-1)| / sqrt(nkeep+5) over the last iteration */
+    double ms_matvec;        /* GPU time in H x */
+    double ms_reorth;        /* GPU time in alpha, reorthogonalization, Gram and normalization */
+    double ms_total;         /* wall time of the call */
+} bs_lanczos_report;
+
+/* Block Lanczos with full reorthogonalization (Sec. "Standard Lanczos
+ * algorithm": alpha first, then orthogonalization against every earlier
+ * vector; Sec. "Block Lanczos": A_n = V_n^T W, O = W'^T W' = U L U^T,
+ * B_n = L^(1/2) U^T, V_(n+1) = W' U L^(-1/2)), all on the GPU.
+ * pivot: device [dim][k] block in opts->dtype (any full-rank block; it is
+ * orthonormalized).  evals: host array of nkeep doubles (lowest first).
+ * evecs: device [dim][nkeep] FP64 Ritz vectors of the lowest min(nkeep, 8)
+ * pairs, or NULL.  report may be NULL.  Inner products accumulate in
+ * extended precision (FP64, or exact FP32 products summed in double-float);
+ * T is diagonalized in FP64 on the host.  Allocates its workspace (about
+ * (niter+2) dim k elements) for the call and frees it.  Synchronizes the
+ * stream.  Errors: BS_ENOBASIS, BS_ENOINT, BS_EINVAL (k, dtype, niter,
+ * nkeep), BS_ENOMEM, BS_ECUDA, BS_EBREAKDOWN (eigensolver failure). */
+int bs_lanczos(bs_ctx *ctx, const bs_lanczos_opts *opts, const void *pivot, double *evals, double *evecs,
+               bs_lanczos_report *report);
+
+/* Test aid: all eigenvalues (ascending, w[n]) and the eigenvectors of the
+ * lowest nvec (columns of Z, n x nvec row-major) of the symmetric n x n
+ * matrix A (row-major, HOST), by the host FP64 solver bs_lanczos uses for T.
+ * Errors: BS_EINVAL, BS_EBREAKDOWN. */
+int bs_debug_eigh(int n, const double *A, double *w, double *Z, int nvec);
+
 /* Chooses the H x kernel.  1 = the tiled kernel (one CTA per destination
  * row and 128-column tile, operands read through L1); 2..5 = variants
  * (threads per CTA, shared-memory budget) of the row kernel (one CTA per

@@ -21,7 +21,8 @@ ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "
 # every symbol include/bigstick_gpu.h declares
 EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
-            "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune"]
+            "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_lanczos",
+            "bs_debug_eigh"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -31,6 +32,17 @@ class bs_orbit(ctypes.Structure):
 class bs_tbme(ctypes.Structure):
     _fields_ = [("a", ctypes.c_int), ("b", ctypes.c_int), ("c", ctypes.c_int), ("d", ctypes.c_int),
                 ("J", ctypes.c_int), ("T", ctypes.c_int), ("v", ctypes.c_double)]
+
+
+class bs_lanczos_opts(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_int), ("dtype", ctypes.c_int), ("niter", ctypes.c_int), ("nkeep", ctypes.c_int),
+                ("refine", ctypes.c_int), ("reorth_passes", ctypes.c_int), ("stream", ctypes.c_void_p)]
+
+
+class bs_lanczos_report(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("breakdowns", ctypes.c_int), ("n_kept", ctypes.c_int),
+                ("residual", ctypes.c_double * 64), ("delta_conv", ctypes.c_double),
+                ("ms_matvec", ctypes.c_double), ("ms_reorth", ctypes.c_double), ("ms_total", ctypes.c_double)]
 
 
 class BSError(RuntimeError):
@@ -70,6 +82,8 @@ def load():
     L.bs_apply_H_host.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     L.bs_debug_table.argtypes = [vp, ctypes.c_char_p, vp, i64p]
     L.bs_set_kernel.argtypes = [vp, ctypes.c_int]
+    L.bs_lanczos.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, f64p, vp, ctypes.POINTER(bs_lanczos_report)]
+    L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.bs_sync_status.argtypes = [vp, vp]
     L.bs_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_float)]
@@ -154,6 +168,21 @@ class Context:
         self._check(load().bs_debug_table(self.h, name.encode(), out.ctypes.data_as(vp), ctypes.byref(n)))
         return out
 
+    def lanczos(self, pivot, k, dtype, niter, nkeep, refine=True, evecs=None, stream=None, reorth_passes=2):
+        """Block Lanczos on the GPU.  pivot: device tensor [dim][k] (dtype);
+        evecs: optional device float64 tensor [dim][nkeep].  Returns
+        (eigenvalues as numpy, report dict)."""
+        o = bs_lanczos_opts(k, dtype, niter, nkeep, int(refine), reorth_passes, vp(stream or 0))
+        ev = np.zeros(nkeep)
+        rep = bs_lanczos_report()
+        pp = pivot if isinstance(pivot, int) else pivot.data_ptr()
+        ep = None if evecs is None else vp(evecs if isinstance(evecs, int) else evecs.data_ptr())
+        self._check(load().bs_lanczos(self.h, ctypes.byref(o), vp(pp), ev.ctypes.data_as(f64p), ep, ctypes.byref(rep)))
+        r = {"iterations": rep.iterations, "breakdowns": rep.breakdowns, "n_kept": rep.n_kept,
+             "residual": [rep.residual[i] for i in range(rep.n_kept)], "delta_conv": rep.delta_conv,
+             "ms_matvec": rep.ms_matvec, "ms_reorth": rep.ms_reorth, "ms_total": rep.ms_total}
+        return ev, r
+
     def set_kernel(self, mode):
         self._check(load().bs_set_kernel(self.h, mode))
 
@@ -185,3 +214,15 @@ class Context:
 
 def make(space_orbits, spe, tbmes, Z, N, twoM, parity=+1, device=0):
     return Context(device).build_basis(space_orbits, Z, N, twoM, parity).load_interaction(spe, tbmes)
+
+
+def debug_eigh(A, nvec):
+    """The library's host FP64 symmetric eigensolver (test aid)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(n)
+    Z = np.zeros((n, max(nvec, 1)))
+    rc = load().bs_debug_eigh(n, A.ctypes.data_as(vp), w.ctypes.data_as(vp), Z.ctypes.data_as(vp), nvec)
+    if rc != 0:
+        raise BSError(rc, "bs_debug_eigh")
+    return w, Z[:, :nvec]

@@ -388,6 +388,22 @@ int bs_apply_H_host(bs_ctx *c, const void *xh, void *yh, int k, bs_dtype dt, voi
     });
 }
 
+int bs_lanczos(bs_ctx *c, const bs_lanczos_opts *o, const void *pivot, double *evals, double *evecs,
+               bs_lanczos_report *rep)
+{
+    return guarded(c, [&]() -> int {
+        if (!o) { c->err = "null options"; return BS_EINVAL; }
+        int rc = check_apply(c, o->k, o->dtype);
+        if (rc) return rc;
+        if (o->niter < 1 || o->nkeep < 1 || o->nkeep > 64 || !pivot || !evals) {
+            c->err = "lanczos: need niter >= 1, 1 <= nkeep <= 64, a pivot and an evals array";
+            return BS_EINVAL;
+        }
+        if (rep) std::memset(rep, 0, sizeof(*rep));
+        return run_lanczos(c, *o, pivot, evals, evecs, rep);
+    });
+}
+
 int bs_set_kernel(bs_ctx *c, int mode)
 {
     return guarded(c, [&]() -> int {

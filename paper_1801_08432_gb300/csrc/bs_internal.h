@@ -249,5 +249,7 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
 void release(Device &D);
 int launch_hx(const bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err);
 int row_variants();
+int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
+                bs_lanczos_report *rep);
 int pipe_variants();
 }  // namespace bs

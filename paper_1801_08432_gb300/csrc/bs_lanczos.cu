@@ -1,0 +1,587 @@
+// Block Lanczos with full reorthogonalization on the GPU (sm_103a).
+//
+// Sec. "Standard Lanczos algorithm" and Sec. "Block Lanczos": for block n,
+//   W   = H V_n                        (the H x kernels, k vectors at once)
+//   A_n = V_n^T W,   W -= V_n A_n       (alpha first)
+//   W  -= V_m (V_m^T W) for every stored block m <= n, twice
+//                                      (full reorthogonalization, classical
+//                                       Gram-Schmidt repeated once)
+//   O   = W^T W = U Lambda U^T,  B_n = Lambda^(1/2) U^T,
+//   V_{n+1} = W U Lambda^(-1/2)
+// and T (A_n on the diagonal, B_n below, B_n^T above) is diagonalized in FP64
+// on the host.  k = 1 is the standard Lanczos of steps (1)-(6), with
+// beta_n = sqrt(O).
+//
+// Precision.  Vectors are stored in the caller's dtype (FP32: the paper's
+// single-precision Lanczos vectors; FP64).  Every inner product (A_n, O and
+// the reorthogonalization coefficients) is accumulated in extended precision:
+// FP64 vectors use FP64 fused multiply-adds; FP32 vectors form each product
+// exactly (a*b and the fma residual) and sum it in a double-float (hi + lo
+// FP32) accumulator, which carries about 48 bits -- FP64-grade dots at FP32
+// throughput on a part whose FP64 rate is a small fraction of its FP32 rate.
+// Block results are reduced across CTAs in FP64 in a fixed order.  Updates of
+// the stored vectors run in their own precision.  The small eigenproblems
+// (O, k <= 8, on the device; T on the host) are FP64.
+//
+// Reading of the paper where it is silent: the pivot block is the caller's
+// (random) block, orthonormalized; a Gram eigenvalue below 1e-24 of the
+// largest marks a breakdown: that column is replaced by a counter-based
+// random vector orthogonalized against every stored block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "bs_internal.h"
+
+namespace bs {
+
+bool host_eigh(int n, const double *A, double *w, double *Z, int nvec);
+
+namespace {
+
+constexpr int kDotThreads = 256;
+
+// ---- extended-precision accumulation
+struct DF {   // double-float: value = hi + lo
+    float hi, lo;
+};
+
+__device__ __forceinline__ void df_add_prod(DF &acc, float a, float b)
+{
+    const float p = a * b;
+    const float e = fmaf(a, b, -p);           // a*b = p + e exactly
+    const float s = acc.hi + p;               // two-sum of hi and p
+    const float bb = s - acc.hi;
+    const float err = (acc.hi - (s - bb)) + (p - bb);
+    acc.hi = s;
+    acc.lo += err + e;
+}
+
+__device__ __forceinline__ double df_value(const DF &a) { return (double)a.hi + (double)a.lo; }
+
+template <typename T>
+struct Accum;
+template <>
+struct Accum<float> {
+    DF v{0.f, 0.f};
+    __device__ __forceinline__ void add(float a, float b) { df_add_prod(v, a, b); }
+    __device__ __forceinline__ double get() const { return df_value(v); }
+};
+template <>
+struct Accum<double> {
+    double v = 0.0;
+    __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ double get() const { return v; }
+};
+
+// partial[cta][b][i][j] = sum over this CTA's rows alpha of V_b[alpha][i] * W[alpha][j],
+// for blocks b = b0 .. b0+nb-1 of the stored basis (stride `bstride` elements).
+// Thread (row slot r, column j): K threads share a row, one W column each.
+template <typename T, int K>
+__global__ void __launch_bounds__(kDotThreads) blk_dots(const T *__restrict__ V, int64_t bstride, int nb,
+                                                        const T *__restrict__ W, int64_t dim,
+                                                        double *__restrict__ partial)
+{
+    constexpr int RPS = kDotThreads / K;   // rows per CTA step
+    __shared__ double red[kDotThreads / 32][K * K];
+    const int tid = threadIdx.x, j = tid % K, r = tid / K;
+    const int warp = tid >> 5, lane = tid & 31;
+    for (int b = 0; b < nb; ++b) {
+        const T *Vb = V + (int64_t)b * bstride;
+        Accum<T> acc[K];
+        for (int64_t a = (int64_t)blockIdx.x * RPS + r; a < dim; a += (int64_t)gridDim.x * RPS) {
+            const T w = W[a * K + j];
+#pragma unroll
+            for (int i = 0; i < K; ++i) acc[i].add(Vb[a * K + i], w);
+        }
+        // reduce over the rows of the warp (lanes with equal j), then over warps
+        double s[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) {
+            s[i] = acc[i].get();
+#pragma unroll
+            for (int o = 16; o >= K; o >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+        }
+        if (lane < K) {
+#pragma unroll
+            for (int i = 0; i < K; ++i) red[warp][i * K + j] = s[i];
+        }
+        __syncthreads();
+        if (tid < K * K) {
+            double t = 0.0;
+            for (int w2 = 0; w2 < kDotThreads / 32; ++w2) t += red[w2][tid];
+            partial[((int64_t)blockIdx.x * nb + b) * K * K + tid] = t;
+        }
+        __syncthreads();
+    }
+}
+
+// out[e] = sum over CTAs of partial[cta][e], e < n (fixed order)
+__global__ void dots_reduce(const double *__restrict__ partial, int ncta, int n, double *__restrict__ out)
+{
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= n) return;
+    double t = 0.0;
+    for (int c = 0; c < ncta; ++c) t += partial[(int64_t)c * n + e];
+    out[e] = t;
+}
+
+// W[alpha][j] -= sum_b sum_i V_b[alpha][i] C[b][i][j]   (C: nb blocks of K x K, FP64)
+template <typename T, int K>
+__global__ void blk_update(const T *__restrict__ V, int64_t bstride, int nb, const double *__restrict__ C,
+                           T *__restrict__ W, int64_t dim)
+{
+    extern __shared__ __align__(16) unsigned char sm_raw[];
+    T *Cs = reinterpret_cast<T *>(sm_raw);
+    for (int e = threadIdx.x; e < nb * K * K; e += blockDim.x) Cs[e] = (T)C[e];
+    __syncthreads();
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < dim; a += (int64_t)gridDim.x * blockDim.x) {
+        T w[K];
+#pragma unroll
+        for (int j = 0; j < K; ++j) w[j] = W[a * K + j];
+        for (int b = 0; b < nb; ++b) {
+            const T *v = V + (int64_t)b * bstride + a * K;
+            const T *c = Cs + b * K * K;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const T vi = v[i];
+#pragma unroll
+                for (int j = 0; j < K; ++j) w[j] = fma(-vi, c[i * K + j], w[j]);
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < K; ++j) W[a * K + j] = w[j];
+    }
+}
+
+// Vout[alpha][:] = W[alpha][:] M   (M: K x K, FP64)
+template <typename T, int K>
+__global__ void blk_scale(const T *__restrict__ W, const double *__restrict__ M, T *__restrict__ Vout, int64_t dim)
+{
+    __shared__ T Ms[K * K];
+    if (threadIdx.x < K * K) Ms[threadIdx.x] = (T)M[threadIdx.x];
+    __syncthreads();
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < dim; a += (int64_t)gridDim.x * blockDim.x) {
+        T w[K], o[K];
+#pragma unroll
+        for (int i = 0; i < K; ++i) { w[i] = W[a * K + i]; o[i] = T(0); }
+#pragma unroll
+        for (int i = 0; i < K; ++i)
+#pragma unroll
+            for (int j = 0; j < K; ++j) o[j] = fma(w[i], Ms[i * K + j], o[j]);
+#pragma unroll
+        for (int j = 0; j < K; ++j) Vout[a * K + j] = o[j];
+    }
+}
+
+// X[alpha][m] = sum_b sum_i V_b[alpha][i] Y[b*K+i][m], m < nm, FP64 output [dim][ldx]
+template <typename T, int K>
+__global__ void blk_combine(const T *__restrict__ V, int64_t bstride, int nb, const double *__restrict__ Y, int nm,
+                            double *__restrict__ X, int ldx, int64_t dim)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < dim; a += (int64_t)gridDim.x * blockDim.x) {
+        double o[8];
+        for (int m = 0; m < 8; ++m) o[m] = 0.0;
+        for (int b = 0; b < nb; ++b) {
+            const T *v = V + (int64_t)b * bstride + a * K;
+#pragma unroll
+            for (int i = 0; i < K; ++i) {
+                const double vi = (double)v[i];
+                const double *y = Y + (int64_t)(b * K + i) * nm;
+                for (int m = 0; m < nm; ++m) o[m] = fma(vi, y[m], o[m]);
+            }
+        }
+        for (int m = 0; m < nm; ++m) X[a * ldx + m] = o[m];
+    }
+}
+
+// R[alpha][m] -= e[m] X[alpha][m] for m < nm, row length ld (FP64): the
+// residual H psi - E psi formed in place of H psi
+__global__ void resid_inplace(double *__restrict__ R, const double *__restrict__ X, const double *__restrict__ e,
+                              int nm, int ld, int64_t dim)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < dim; a += (int64_t)gridDim.x * blockDim.x)
+        for (int m = 0; m < nm; ++m) R[a * ld + m] -= e[m] * X[a * ld + m];
+}
+
+// One thread: symmetric Jacobi on the K x K Gram matrix O (FP64).  Writes
+// M = U Lambda^(-1/2) (to normalize) and B = Lambda^(1/2) U^T; columns whose
+// eigenvalue is below rel * max are flagged (bit i of *flags) and get a zero
+// column in M and a zero row in B.  Also symmetrizes A in place when given.
+__global__ void small_gram(int K, const double *__restrict__ O, double rel, double *__restrict__ M,
+                           double *__restrict__ B, int *__restrict__ flags, double *__restrict__ A)
+{
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a[64], u[64];
+    for (int i = 0; i < K; ++i)
+        for (int j = 0; j < K; ++j) {
+            a[i * K + j] = 0.5 * (O[i * K + j] + O[j * K + i]);
+            u[i * K + j] = i == j ? 1.0 : 0.0;
+        }
+    if (A) {
+        for (int i = 0; i < K; ++i)
+            for (int j = i + 1; j < K; ++j) {
+                const double s = 0.5 * (A[i * K + j] + A[j * K + i]);
+                A[i * K + j] = A[j * K + i] = s;
+            }
+    }
+    for (int sweep = 0; sweep < 30; ++sweep) {
+        double off = 0.0, tot = 0.0;
+        for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j) {
+                tot += a[i * K + j] * a[i * K + j];
+                if (i != j) off += a[i * K + j] * a[i * K + j];
+            }
+        if (off <= 1e-32 * tot) break;
+        for (int p = 0; p < K; ++p)
+            for (int q = p + 1; q < K; ++q) {
+                const double apq = a[p * K + q];
+                if (apq == 0.0) continue;
+                // rotation angle that zeroes a[p][q]
+                const double theta = 0.5 * (a[q * K + q] - a[p * K + p]) / apq;
+                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
+                for (int r = 0; r < K; ++r) {   // columns p, q
+                    const double arp = a[r * K + p], arq = a[r * K + q];
+                    a[r * K + p] = c * arp - s * arq;
+                    a[r * K + q] = s * arp + c * arq;
+                }
+                for (int r = 0; r < K; ++r) {   // rows p, q
+                    const double apr = a[p * K + r], aqr = a[q * K + r];
+                    a[p * K + r] = c * apr - s * aqr;
+                    a[q * K + r] = s * apr + c * aqr;
+                }
+                for (int r = 0; r < K; ++r) {
+                    const double urp = u[r * K + p], urq = u[r * K + q];
+                    u[r * K + p] = c * urp - s * urq;
+                    u[r * K + q] = s * urp + c * urq;
+                }
+            }
+    }
+    double lmax = 0.0;
+    for (int i = 0; i < K; ++i) lmax = fmax(lmax, a[i * K + i]);
+    int fl = 0;
+    for (int i = 0; i < K; ++i) {
+        const double lam = a[i * K + i];
+        const bool bad = !(lam > rel * lmax) || !(lam > 0.0);
+        if (bad) fl |= 1 << i;
+        const double sq = bad ? 0.0 : sqrt(lam), isq = bad ? 0.0 : 1.0 / sqrt(lam);
+        for (int r = 0; r < K; ++r) {
+            M[r * K + i] = u[r * K + i] * isq;
+            B[i * K + r] = sq * u[r * K + i];
+        }
+    }
+    *flags = fl;
+}
+
+// Column `col` of the [dim][K] block X <- Gaussian numbers from a SplitMix64
+// counter stream (seed, alpha) with a Box-Muller step.
+template <typename T, int K>
+__global__ void fill_random_col(T *__restrict__ X, int col, uint64_t seed, int64_t dim)
+{
+    for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < dim; a += (int64_t)gridDim.x * blockDim.x) {
+        uint64_t z = seed + 0x9E3779B97F4A7C15ull * (uint64_t)(2 * a + 1);
+        auto mix = [](uint64_t v) {
+            v = (v ^ (v >> 30)) * 0xBF58476D1CE4E5B9ull;
+            v = (v ^ (v >> 27)) * 0x94D049BB133111EBull;
+            return v ^ (v >> 31);
+        };
+        const uint64_t r1 = mix(z), r2 = mix(z + 0x9E3779B97F4A7C15ull);
+        const double u1 = ((r1 >> 11) + 1) * (1.0 / 9007199254740992.0), u2 = (r2 >> 11) * (1.0 / 9007199254740992.0);
+        X[a * K + col] = (T)(sqrt(-2.0 * log(u1)) * cos(6.283185307179586 * u2));
+    }
+}
+
+struct LState {
+    int k = 1, dt = 0, ncta = 304;
+    int64_t dim = 0, bstride = 0;
+    void *V = nullptr, *W = nullptr;      // basis blocks and work block
+    double *partial = nullptr, *C = nullptr, *M = nullptr, *Bn = nullptr, *Ahist = nullptr, *Bhist = nullptr;
+    int *flags = nullptr;
+    cudaStream_t s = 0;
+};
+
+template <typename T, int K>
+void dots(LState &L, const T *V, int nb, const T *W, double *out)
+{
+    blk_dots<T, K><<<L.ncta, kDotThreads, 0, L.s>>>(V, L.bstride, nb, W, L.dim, L.partial);
+    const int n = nb * K * K;
+    dots_reduce<<<(n + 255) / 256, 256, 0, L.s>>>(L.partial, L.ncta, n, out);
+}
+
+template <typename T, int K>
+void update(LState &L, const T *V, int nb, const double *C, T *W)
+{
+    const size_t smem = (size_t)nb * K * K * sizeof(T);
+    blk_update<T, K><<<L.ncta, 256, smem, L.s>>>(V, L.bstride, nb, C, W, L.dim);
+}
+
+}  // namespace
+
+template <typename T, int K>
+static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
+                       bs_lanczos_report *rep)
+{
+    LState L;
+    L.k = K;
+    L.dim = c->basis.dim;
+    L.bstride = L.dim * K;
+    L.s = (cudaStream_t)o.stream;
+    int dev = 0;
+    cudaGetDevice(&dev);
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    L.ncta = 2 * nsm;
+    int niter = std::max(1, o.niter);
+    niter = (int)std::min<int64_t>(niter, std::max<int64_t>(1, L.dim / K));
+    const size_t es = sizeof(T);
+    std::vector<void *> owned;
+    auto alloc = [&](size_t bytes) -> void * {
+        void *p = nullptr;
+        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        owned.push_back(p);
+        return p;
+    };
+    auto cleanup = [&]() {
+        for (void *p : owned) cudaFree(p);
+        owned.clear();
+    };
+    L.V = alloc((size_t)(niter + 1) * L.bstride * es);
+    L.W = alloc((size_t)L.bstride * es);
+    // dot scratch: (niter+1) blocks of K x K, or one 8 x 8 block for the refinement
+    const size_t ndot = std::max<size_t>((size_t)(niter + 1) * K * K, 64);
+    L.partial = (double *)alloc((size_t)L.ncta * ndot * sizeof(double));
+    L.C = (double *)alloc(ndot * sizeof(double));
+    L.M = (double *)alloc(K * K * sizeof(double));
+    L.Bn = (double *)alloc(K * K * sizeof(double));
+    L.Ahist = (double *)alloc((size_t)niter * K * K * sizeof(double));
+    L.Bhist = (double *)alloc((size_t)niter * K * K * sizeof(double));
+    L.flags = (int *)alloc(sizeof(int));
+    for (void *p : owned)
+        if (!p) { cleanup(); c->err = "lanczos: device allocation failed"; return BS_ENOMEM; }
+    {
+        cudaError_t e = cudaFuncSetAttribute(blk_update<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)std::min<size_t>((size_t)(niter + 1) * K * K * es, 227 * 1024));
+        if (e != cudaSuccess) { cleanup(); c->err = std::string("lanczos: ") + cudaGetErrorString(e); return BS_ECUDA; }
+        if ((size_t)(niter + 1) * K * K * es > 227 * 1024) { cleanup(); c->err = "lanczos: too many blocks for the reorthogonalization kernel"; return BS_EINVAL; }
+    }
+    T *V = (T *)L.V, *W = (T *)L.W;
+    const double rel = 1e-24;
+    cudaEvent_t ev[4];
+    for (auto &e : ev) cudaEventCreate(&e);
+    float ms_mv = 0.f, ms_or = 0.f;
+    int breakdowns = 0, done = 0;
+    std::vector<double> Ah((size_t)niter * K * K), Bh((size_t)niter * K * K);
+    int rc = BS_OK;
+    const auto t0 = std::chrono::steady_clock::now();
+    const int passes = std::max(1, o.reorth_passes);
+
+    // orthonormalize the pivot block (FP64 Gram, one reorthogonalization-free QR)
+    cudaMemcpyAsync(W, pivot, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
+    dots<T, K>(L, W, 1, W, L.C);
+    small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bn, L.flags, nullptr);
+    blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V, L.dim);
+
+    for (int n = 0; n < niter && rc == BS_OK; ++n) {
+        T *Vn = V + (int64_t)n * L.bstride;
+        cudaEventRecord(ev[0], L.s);
+        if ((rc = launch_hx(c, Vn, W, K, o.dtype, L.s, c->err))) break;
+        cudaEventRecord(ev[1], L.s);
+        // alpha first: A_n = V_n^T W, W -= V_n A_n
+        double *An = L.Ahist + (size_t)n * K * K;
+        dots<T, K>(L, Vn, 1, W, An);
+        update<T, K>(L, Vn, 1, An, W);
+        for (int p = 0; p < passes; ++p) {
+            dots<T, K>(L, V, n + 1, W, L.C);
+            update<T, K>(L, V, n + 1, L.C, W);
+        }
+        dots<T, K>(L, W, 1, W, L.C);
+        small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist + (size_t)n * K * K, L.flags, An);
+        blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V + (int64_t)(n + 1) * L.bstride, L.dim);
+        cudaEventRecord(ev[2], L.s);
+        int flags = 0;
+        cudaError_t e = cudaMemcpyAsync(&flags, L.flags, sizeof(int), cudaMemcpyDeviceToHost, L.s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(L.s);
+        if (e != cudaSuccess) { c->err = std::string("lanczos: ") + cudaGetErrorString(e); rc = BS_ECUDA; break; }
+        float a = 0.f, b = 0.f;
+        cudaEventElapsedTime(&a, ev[0], ev[1]);
+        cudaEventElapsedTime(&b, ev[1], ev[2]);
+        ms_mv += a;
+        ms_or += b;
+        done = n + 1;
+        if (flags && n + 1 < niter) {
+            // breakdown: flagged columns of V_{n+1} are zero; refill them with
+            // random vectors, orthogonalize against V_0..V_n, renormalize the
+            // block, and fold the change of basis into B_n
+            ++breakdowns;
+            T *Vn1 = V + (int64_t)(n + 1) * L.bstride;
+            for (int i = 0; i < K; ++i)
+                if (flags >> i & 1)
+                    fill_random_col<T, K><<<L.ncta, 256, 0, L.s>>>(Vn1, i, 0xB5297A4D3F84D5B5ull + 7919ull * (uint64_t)(n * K + i), L.dim);
+            for (int p = 0; p < 2; ++p) {
+                dots<T, K>(L, V, n + 1, Vn1, L.C);
+                update<T, K>(L, V, n + 1, L.C, Vn1);
+            }
+            cudaMemcpyAsync(W, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
+            dots<T, K>(L, W, 1, W, L.C);
+            small_gram<<<1, 1, 0, L.s>>>(K, L.C, 1e-20, L.M, L.Bn, L.flags, nullptr);
+            blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, Vn1, L.dim);
+            // B_n <- G B_n with G = Bn (the Gram factor of the refilled block: W = Vnew G)
+            std::vector<double> G(K * K), Bn(K * K), out(K * K, 0.0);
+            int fl2 = 0;
+            cudaMemcpyAsync(G.data(), L.Bn, K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+            cudaMemcpyAsync(Bn.data(), L.Bhist + (size_t)n * K * K, K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+            cudaMemcpyAsync(&fl2, L.flags, sizeof(int), cudaMemcpyDeviceToHost, L.s);
+            cudaStreamSynchronize(L.s);
+            if (fl2) { niter = n + 1; break; }   // the Krylov space is exhausted
+            for (int i = 0; i < K; ++i)
+                for (int j = 0; j < K; ++j)
+                    for (int l = 0; l < K; ++l) out[i * K + j] += G[i * K + l] * Bn[l * K + j];
+            cudaMemcpyAsync(L.Bhist + (size_t)n * K * K, out.data(), K * K * sizeof(double), cudaMemcpyHostToDevice, L.s);
+            cudaStreamSynchronize(L.s);
+        }
+    }
+    if (rc == BS_OK) {
+        cudaMemcpyAsync(Ah.data(), L.Ahist, (size_t)done * K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+        cudaMemcpyAsync(Bh.data(), L.Bhist, (size_t)done * K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+        if (cudaStreamSynchronize(L.s) != cudaSuccess) { rc = BS_ECUDA; c->err = "lanczos: copy failed"; }
+    }
+    std::vector<double> wT, Z;
+    const int nkeep = std::max(1, o.nkeep);
+    int nT = done * K;
+    if (rc == BS_OK) {
+        std::vector<double> T_((size_t)nT * nT, 0.0);
+        for (int n = 0; n < done; ++n)
+            for (int i = 0; i < K; ++i)
+                for (int j = 0; j < K; ++j) {
+                    T_[(size_t)(n * K + i) * nT + n * K + j] = Ah[(size_t)n * K * K + i * K + j];
+                    if (n + 1 < done) {
+                        const double b = Bh[(size_t)n * K * K + i * K + j];   // B_n: row i of block n+1, column j of block n
+                        T_[(size_t)((n + 1) * K + i) * nT + n * K + j] = b;
+                        T_[(size_t)(n * K + j) * nT + (n + 1) * K + i] = b;
+                    }
+                }
+        wT.resize(nT);
+        const int nv = std::min(nkeep, nT);
+        Z.resize((size_t)nT * nv);
+        if (!host_eigh(nT, T_.data(), wT.data(), Z.data(), nv)) { rc = BS_EBREAKDOWN; c->err = "lanczos: eigensolver failed"; }
+        // convergence measure of the paper: the lowest nkeep+5 eigenvalues of
+        // T now and one block iteration earlier
+        if (rc == BS_OK && rep) {
+            const int nprev = (done - 1) * K, m = std::min(nkeep + 5, nprev);
+            double delta = 0.0;
+            if (m > 0) {
+                std::vector<double> Tp((size_t)nprev * nprev), wp(nprev);
+                for (int i = 0; i < nprev; ++i)
+                    for (int j = 0; j < nprev; ++j) Tp[(size_t)i * nprev + j] = T_[(size_t)i * nT + j];
+                std::vector<double> dummy(1);
+                host_eigh(nprev, Tp.data(), wp.data(), dummy.data(), 0);
+                for (int i = 0; i < m; ++i) delta += std::fabs(wT[i] - wp[i]);
+                delta /= std::sqrt((double)m);
+            }
+            rep->delta_conv = delta;
+        }
+    }
+    int nk = std::min(nkeep, nT);
+    if (rc == BS_OK) {
+        for (int i = 0; i < nk; ++i) evals[i] = wT[i];
+        for (int i = nk; i < nkeep; ++i) evals[i] = NAN;
+    }
+    // Ritz vectors (FP64) and the FP64 refinement of the kept pairs
+    if (rc == BS_OK && (evecs || o.refine)) {
+        const int kref = nk <= 1 ? 1 : nk <= 2 ? 2 : nk <= 4 ? 4 : 8;
+        double *X = evecs;
+        double *Xown = nullptr, *HX = nullptr, *Yd = nullptr, *R = nullptr;
+        if (nk > 8) { nk = 8; }
+        Yd = (double *)alloc((size_t)nT * nk * sizeof(double));
+        Xown = (double *)alloc((size_t)L.dim * kref * sizeof(double));
+        HX = (double *)alloc((size_t)L.dim * kref * sizeof(double));
+        R = (double *)alloc(2 * 64 * sizeof(double));
+        if (!Yd || !Xown || !HX || !R) { rc = BS_ENOMEM; c->err = "lanczos: allocation failed"; }
+        if (rc == BS_OK) {
+            std::vector<double> Yh((size_t)nT * nk);
+            for (int r = 0; r < nT; ++r)
+                for (int m = 0; m < nk; ++m) Yh[(size_t)r * nk + m] = Z[(size_t)r * std::min(nkeep, nT) + m];
+            cudaMemcpyAsync(Yd, Yh.data(), Yh.size() * sizeof(double), cudaMemcpyHostToDevice, L.s);
+            cudaMemsetAsync(Xown, 0, (size_t)L.dim * kref * sizeof(double), L.s);
+            blk_combine<T, K><<<L.ncta, 256, 0, L.s>>>(V, L.bstride, done, Yd, nk, Xown, kref, L.dim);
+        }
+        if (rc == BS_OK && o.refine) {
+            // FP64 H psi, Rayleigh quotients and residuals
+            if ((rc = launch_hx(c, Xown, HX, kref, BS_F64, L.s, c->err)) == BS_OK) {
+                LState L2 = L;
+                L2.bstride = L.dim * kref;
+                std::vector<double> xx(kref * kref), xh(kref * kref), hh(kref * kref);
+                auto dots64 = [&](const double *A, const double *Bm, double *out) {
+                    switch (kref) {
+                    case 1: dots<double, 1>(L2, A, 1, Bm, out); break;
+                    case 2: dots<double, 2>(L2, A, 1, Bm, out); break;
+                    case 4: dots<double, 4>(L2, A, 1, Bm, out); break;
+                    default: dots<double, 8>(L2, A, 1, Bm, out); break;
+                    }
+                };
+                dots64(Xown, Xown, L.C);
+                cudaMemcpyAsync(xx.data(), L.C, kref * kref * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+                dots64(Xown, HX, L.C);
+                cudaMemcpyAsync(xh.data(), L.C, kref * kref * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+                cudaStreamSynchronize(L.s);
+                std::vector<double> e(kref, 0.0);
+                for (int m = 0; m < nk; ++m) e[m] = xh[m * kref + m] / xx[m * kref + m];   // Rayleigh quotient
+                cudaMemcpyAsync(R, e.data(), kref * sizeof(double), cudaMemcpyHostToDevice, L.s);
+                resid_inplace<<<L.ncta, 256, 0, L.s>>>(HX, Xown, R, nk, kref, L.dim);
+                dots64(HX, HX, L.C);
+                cudaMemcpyAsync(hh.data(), L.C, kref * kref * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+                cudaStreamSynchronize(L.s);
+                for (int m = 0; m < nk; ++m) {
+                    evals[m] = e[m];
+                    if (rep) rep->residual[m] = std::sqrt(std::max(hh[m * kref + m], 0.0) / xx[m * kref + m]);
+                }
+            }
+        }
+        if (rc == BS_OK && X) {
+            // copy the kept columns to the caller's [dim][nkeep] buffer
+            cudaMemcpy2DAsync(X, (size_t)nkeep * sizeof(double), Xown, (size_t)kref * sizeof(double),
+                              (size_t)nk * sizeof(double), (size_t)L.dim, cudaMemcpyDeviceToDevice, L.s);
+        }
+        cudaStreamSynchronize(L.s);
+    }
+    for (auto &e : ev) cudaEventDestroy(e);
+    cleanup();
+    const auto t1 = std::chrono::steady_clock::now();
+    if (rep) {
+        rep->iterations = done;
+        rep->breakdowns = breakdowns;
+        rep->ms_matvec = ms_mv;
+        rep->ms_reorth = ms_or;
+        rep->ms_total = std::chrono::duration<double, std::milli>(t1 - t0).count();
+        rep->n_kept = nk;
+    }
+    return rc;
+}
+
+int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
+                bs_lanczos_report *rep)
+{
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return BS_ECUDA; }
+    if (o.dtype == BS_F64) {
+        switch (o.k) {
+        case 1: return lanczos_run<double, 1>(c, o, pivot, evals, evecs, rep);
+        case 2: return lanczos_run<double, 2>(c, o, pivot, evals, evecs, rep);
+        case 4: return lanczos_run<double, 4>(c, o, pivot, evals, evecs, rep);
+        default: return lanczos_run<double, 8>(c, o, pivot, evals, evecs, rep);
+        }
+    }
+    switch (o.k) {
+    case 1: return lanczos_run<float, 1>(c, o, pivot, evals, evecs, rep);
+    case 2: return lanczos_run<float, 2>(c, o, pivot, evals, evecs, rep);
+    case 4: return lanczos_run<float, 4>(c, o, pivot, evals, evecs, rep);
+    default: return lanczos_run<float, 8>(c, o, pivot, evals, evecs, rep);
+    }
+}
+
+}  // namespace bs
