@@ -132,6 +132,22 @@ int bs_apply_H(bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dtype, void 
 int bs_apply_H_host(bs_ctx *ctx, const void *x_host, void *y_host, int k,
                     bs_dtype dtype, void *stream);
 
+/* Adjoint of y = H(theta) x, theta = (spe[n_spe], tbme values in the order
+ * they were loaded).  gx = H gy (H is symmetric; device, [dim][k], dtype),
+ * and if gtheta != NULL (HOST, n_spe + n_tbme doubles):
+ *   gtheta[t] += sum over the k columns of gy^T (dH/dtheta_t) x,
+ * the derivative of the pairing gy . H x -- with x = gy = psi (normalized) it
+ * is the Hellmann-Feynman derivative dE/dtheta_t, the paper's "diagonal"
+ * two-body density X_J(ab,cd) = dE/dV_J(ab,cd) for a TBME slot.  H is linear
+ * in theta, so the transition densities gy . x over all jumps (pp and nn per
+ * jump, pn per pair of decoupled operators; GPU kernels, FP64 accumulation)
+ * are contracted on the host with dW/dtheta, built once per label set by
+ * decoupling unit interactions.  x, gy, gx: distinct except x may equal gy.
+ * Synchronizes the stream when gtheta != NULL.  Errors: as bs_apply_H,
+ * BS_ENOMEM. */
+int bs_apply_H_backward(bs_ctx *ctx, const void *x, const void *gy, void *gx, double *gtheta, int k,
+                        bs_dtype dtype, void *stream);
+
 /* Options of bs_lanczos. */
 typedef struct {
     int k;              /* block size: 1 (standard Lanczos), 2, 4 or 8 */

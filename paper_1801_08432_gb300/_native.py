@@ -22,7 +22,7 @@ ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "
 EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_lanczos",
-            "bs_debug_eigh"]
+            "bs_debug_eigh", "bs_apply_H_backward"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -84,6 +84,7 @@ def load():
     L.bs_set_kernel.argtypes = [vp, ctypes.c_int]
     L.bs_lanczos.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, f64p, vp, ctypes.POINTER(bs_lanczos_report)]
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
+    L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]
     L.bs_sync_status.argtypes = [vp, vp]
     L.bs_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_float)]
@@ -205,6 +206,16 @@ class Context:
         xp = x if isinstance(x, int) else x.data_ptr()
         yp = y if isinstance(y, int) else y.data_ptr()
         self._check(load().bs_apply_H(self.h, vp(xp), vp(yp), k, dtype, vp(stream or 0)))
+
+    def apply_H_backward(self, x, gy, gx, k, dtype, n_theta=None, stream=None):
+        """gx = H gy; returns gtheta (numpy, n_spe + n_tbme) = sum gy^T dH/dtheta x,
+        or None when n_theta is None."""
+        ptr = lambda t: vp(t if isinstance(t, int) else t.data_ptr())
+        g = None if n_theta is None else np.zeros(n_theta)
+        self._check(load().bs_apply_H_backward(self.h, ptr(x), ptr(gy), ptr(gx),
+                                               None if g is None else g.ctypes.data_as(f64p), k, dtype,
+                                               vp(stream or 0)))
+        return g
 
     def apply_H_host(self, x, y, k, dtype, stream=None):
         """y = H x with host numpy buffers (copies inside)."""

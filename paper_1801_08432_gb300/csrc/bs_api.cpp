@@ -259,6 +259,9 @@ void bs_destroy(bs_ctx *c)
     if (c->device >= 0) {
         cudaSetDevice(c->device);
         release(c->dev);
+        if (c->adj_gpp) cudaFree(c->adj_gpp);
+        if (c->adj_gnn) cudaFree(c->adj_gnn);
+        if (c->adj_rho) cudaFree(c->adj_rho);
         if (c->hx_x) cudaFree(c->hx_x);
         if (c->hx_y) cudaFree(c->hx_y);
     }
@@ -328,10 +331,22 @@ int bs_load_interaction(bs_ctx *c, const double *spe, int n_spe, const bs_tbme *
         if (!c->have_basis) { c->err = "no basis"; return BS_ENOBASIS; }
         c->have_int = false;
         int rc = build_interaction(c->basis, spe, n_spe, tbme, n_tbme, c->inter, c->err);
+        if (rc == BS_OK) {
+            std::vector<bs_tbme> tb(tbme, tbme + std::max(0, n_tbme));
+            bool same_labels = tb.size() == c->tbme_in.size() && c->spe_in.size() == (size_t)n_spe;
+            for (size_t i = 0; same_labels && i < tb.size(); ++i)
+                same_labels = tb[i].a == c->tbme_in[i].a && tb[i].b == c->tbme_in[i].b && tb[i].c == c->tbme_in[i].c &&
+                              tb[i].d == c->tbme_in[i].d && tb[i].J == c->tbme_in[i].J && tb[i].T == c->tbme_in[i].T;
+            if (!same_labels) c->have_dW = false;   // derivative tables depend on the labels only
+            c->spe_in.assign(spe, spe + n_spe);
+            c->tbme_in.swap(tb);
+        }
         if (rc) return rc;
         rc = build_tables(c->basis, c->inter, c->tab, c->err);
         if (rc) return rc;
         if (c->device >= 0) {
+            if (c->adj_gpp) { cudaFree(c->adj_gpp); cudaFree(c->adj_gnn); cudaFree(c->adj_rho); }
+            c->adj_gpp = c->adj_gnn = c->adj_rho = nullptr;
             rc = upload(c->basis, c->inter, c->tab, c->dev, c->err);
             if (rc) { release(c->dev); return rc; }
         }
@@ -385,6 +400,18 @@ int bs_apply_H_host(bs_ctx *c, const void *xh, void *yh, int k, bs_dtype dt, voi
         if ((e = cudaMemcpyAsync(yh, c->hx_y, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
         return BS_OK;
+    });
+}
+
+int bs_apply_H_backward(bs_ctx *c, const void *x, const void *gy, void *gx, double *gtheta, int k, bs_dtype dt,
+                        void *stream)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, k, dt);
+        if (rc) return rc;
+        if (!x || !gy || !gx || gy == gx) { c->err = "x, gy and gx must be device buffers, gy != gx"; return BS_EINVAL; }
+        if (((uintptr_t)x | (uintptr_t)gy | (uintptr_t)gx) & 15) { c->err = "buffers must be 16-byte aligned"; return BS_EINVAL; }
+        return run_backward(c, x, gy, gx, gtheta, k, dt, stream);
     });
 }
 

@@ -237,6 +237,14 @@ struct bs_ctx {
     size_t hx_bytes = 0;
     int hx_mode = 0;         // 0: autotuned, 1: tiled kernel, 2 + v: row kernel variant v
     int tuned[2][4] = {};    // autotuned mode per (dtype, k slot); 0 = not tuned
+    // the loaded interaction as given (for the parameter derivatives of the adjoint)
+    std::vector<double> spe_in;
+    std::vector<bs_tbme> tbme_in;
+    // adjoint: derivative of the decoupled tables w.r.t. each TBME, sparse, built on first use
+    bool have_dW = false;
+    std::vector<std::vector<std::pair<int64_t, double>>> dWpp, dWpn;
+    // adjoint device buffers
+    double *adj_gpp = nullptr, *adj_gnn = nullptr, *adj_rho = nullptr;
 };
 
 // ---------------------------------------------------------------- builders (host)
@@ -249,6 +257,8 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
 void release(Device &D);
 int launch_hx(const bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err);
 int row_variants();
+int run_backward(bs_ctx *c, const void *x, const void *gy, void *gx, double *gtheta, int k, bs_dtype dt,
+                 void *stream);
 int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
                 bs_lanczos_report *rep);
 int pipe_variants();
