@@ -148,6 +148,19 @@ int bs_apply_H_host(bs_ctx *ctx, const void *x_host, void *y_host, int k,
 int bs_apply_H_backward(bs_ctx *ctx, const void *x, const void *gy, void *gx, double *gtheta, int k,
                         bs_dtype dtype, void *stream);
 
+/* Inner products of basis vectors with FP64-grade accumulation (overlaps of
+ * wave functions; the alpha, Gram and reorthogonalization products of
+ * bs_lanczos): for b < nb, C[b][i][j] = sum_alpha V_b[alpha][i] W[alpha][j],
+ * where V holds nb consecutive [dim][k] blocks and W one [dim][k] block
+ * (device, dtype).  C: device, nb*k*k doubles.  FP64 vectors use FP64 fused
+ * multiply-adds; FP32 vectors sum exact products in double-float; the
+ * per-CTA partial sums (2 x SMs x nb x k x k doubles, allocated and freed
+ * stream-ordered by the call) are reduced in FP64 in a fixed order, so the
+ * result is bit-reproducible.  Errors: BS_ENOBASIS, BS_ENOINT, BS_EINVAL,
+ * BS_ENOMEM, BS_ECUDA. */
+int bs_block_dots(bs_ctx *ctx, const void *V, int nb, const void *W, int k, bs_dtype dtype, double *C,
+                  void *stream);
+
 /* Options of bs_lanczos. */
 typedef struct {
     int k;              /* block size: 1 (standard Lanczos), 2, 4 or 8 */

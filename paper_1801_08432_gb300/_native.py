@@ -22,7 +22,7 @@ ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "
 EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_lanczos",
-            "bs_debug_eigh", "bs_apply_H_backward"]
+            "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -85,6 +85,7 @@ def load():
     L.bs_lanczos.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, f64p, vp, ctypes.POINTER(bs_lanczos_report)]
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]
+    L.bs_block_dots.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
     L.bs_sync_status.argtypes = [vp, vp]
     L.bs_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_float)]
@@ -216,6 +217,12 @@ class Context:
                                                None if g is None else g.ctypes.data_as(f64p), k, dtype,
                                                vp(stream or 0)))
         return g
+
+    def block_dots(self, V, nb, W, k, dtype, C, stream=None):
+        """C[b][i][j] = sum_alpha V_b[alpha][i] W[alpha][j]; V, W, C device tensors
+        (C float64 with nb*k*k elements)."""
+        ptr = lambda t: vp(t if isinstance(t, int) else t.data_ptr())
+        self._check(load().bs_block_dots(self.h, ptr(V), nb, ptr(W), k, dtype, ptr(C), vp(stream or 0)))
 
     def apply_H_host(self, x, y, k, dtype, stream=None):
         """y = H x with host numpy buffers (copies inside)."""

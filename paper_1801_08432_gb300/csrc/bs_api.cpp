@@ -403,6 +403,16 @@ int bs_apply_H_host(bs_ctx *c, const void *xh, void *yh, int k, bs_dtype dt, voi
     });
 }
 
+int bs_block_dots(bs_ctx *c, const void *V, int nb, const void *W, int k, bs_dtype dt, double *C, void *stream)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, k, dt);
+        if (rc) return rc;
+        if (!V || !W || !C || nb < 1) { c->err = "block dots: need V, W, C and nb >= 1"; return BS_EINVAL; }
+        return run_block_dots(c, V, nb, W, k, dt, C, stream);
+    });
+}
+
 int bs_apply_H_backward(bs_ctx *c, const void *x, const void *gy, void *gx, double *gtheta, int k, bs_dtype dt,
                         void *stream)
 {

@@ -563,6 +563,46 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
     return rc;
 }
 
+template <typename T, int K>
+static int block_dots_run(bs_ctx *c, const void *V, int nb, const void *W, double *C, cudaStream_t s)
+{
+    LState L;
+    L.dim = c->basis.dim;
+    L.bstride = L.dim * K;
+    L.s = s;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    L.ncta = 2 * nsm;
+    cudaError_t e = cudaMallocAsync((void **)&L.partial, (size_t)L.ncta * nb * K * K * sizeof(double), s);
+    if (e != cudaSuccess) { c->err = std::string("block dots: ") + cudaGetErrorString(e); return BS_ENOMEM; }
+    dots<T, K>(L, (const T *)V, nb, (const T *)W, C);
+    cudaFreeAsync(L.partial, s);
+    if ((e = cudaGetLastError()) != cudaSuccess) { c->err = std::string("block dots: ") + cudaGetErrorString(e); return BS_ECUDA; }
+    return BS_OK;
+}
+
+int run_block_dots(bs_ctx *c, const void *V, int nb, const void *W, int k, bs_dtype dt, double *C, void *stream)
+{
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return BS_ECUDA; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dt == BS_F64) {
+        switch (k) {
+        case 1: return block_dots_run<double, 1>(c, V, nb, W, C, s);
+        case 2: return block_dots_run<double, 2>(c, V, nb, W, C, s);
+        case 4: return block_dots_run<double, 4>(c, V, nb, W, C, s);
+        default: return block_dots_run<double, 8>(c, V, nb, W, C, s);
+        }
+    }
+    switch (k) {
+    case 1: return block_dots_run<float, 1>(c, V, nb, W, C, s);
+    case 2: return block_dots_run<float, 2>(c, V, nb, W, C, s);
+    case 4: return block_dots_run<float, 4>(c, V, nb, W, C, s);
+    default: return block_dots_run<float, 8>(c, V, nb, W, C, s);
+    }
+}
+
 int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
                 bs_lanczos_report *rep)
 {

@@ -99,3 +99,22 @@ def test_breakdown_restart_and_exhaustion():
     ev, rep = c.lanczos(pivot(c.dim, 1, N.BS_F64), 1, N.BS_F64, 50, 3, refine=True)
     assert rep["iterations"] <= c.dim
     assert np.max(np.abs(ev - np.linalg.eigvalsh(o.dense())[:3])) < 1e-9
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k,dtype", [(1, N.BS_F64), (4, N.BS_F32), (8, N.BS_F32), (2, N.BS_F64)])
+def test_block_dots_match_fp64_numpy(k, dtype):
+    c, _ = ctx_oracle("sd", 4, 4, 0, with_oracle=False)
+    nb = 5
+    rng = np.random.default_rng(k)
+    tdt = torch.float64 if dtype == N.BS_F64 else torch.float32
+    V = torch.from_numpy(rng.standard_normal((nb, c.dim, k))).to("cuda", tdt)
+    W = torch.from_numpy(rng.standard_normal((c.dim, k))).to("cuda", tdt)
+    C = torch.zeros(nb * k * k, device="cuda", dtype=torch.float64)
+    c.block_dots(V, nb, W, k, dtype, C)
+    ref = np.einsum("bai,aj->bij", V.double().cpu().numpy(), W.double().cpu().numpy()).reshape(-1)
+    got = C.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    C2 = torch.zeros_like(C)
+    c.block_dots(V, nb, W, k, dtype, C2)
+    assert torch.equal(C, C2)
