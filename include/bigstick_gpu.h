@@ -161,6 +161,37 @@ int bs_apply_H_backward(bs_ctx *ctx, const void *x, const void *gy, void *gx, do
 int bs_block_dots(bs_ctx *ctx, const void *V, int nb, const void *W, int k, bs_dtype dtype, double *C,
                   void *stream);
 
+/* Capacity, in doubles, of the fixed device array behind
+ * bs_block_dots_noalloc (2 MiB per device that loads the library). */
+#define BS_BLOCK_DOTS_NOALLOC_MAX 262144
+
+/* The products of bs_block_dots, C[b][i][j] = sum_alpha V_b[alpha][i]
+ * W[alpha][j] (V: nb consecutive [dim][k] blocks, W: one [dim][k] block, C:
+ * nb*k*k doubles, all device memory the caller owns), computed without
+ * allocating anything: no cudaMalloc, no cudaFree, no allocating library
+ * call, and no context is needed.  It is for callers that cannot allocate
+ * device memory where they need an overlap -- an application whose caching
+ * allocator already owns the GPU's memory (a cudaMalloc there can fail or
+ * fragment it), or a latency-critical loop that must not enter the driver's
+ * allocator, where cudaFree also waits for the whole device.  The paper has
+ * no counterpart: this is a deployment variant of the inner products the
+ * Lanczos driver uses.
+ * The per-CTA partial sums go to a fixed file-scope device array of
+ * BS_BLOCK_DOTS_NOALLOC_MAX doubles that every GPU loading the library holds
+ * until the process exits.  The first call on a device (the current one)
+ * looks up that array's device address; make that first call before any
+ * stream capture.  Every call writes all the partials it reads, so nothing is
+ * carried over from the previous call, but all calls share the one array:
+ * calls that overlap on the GPU (other streams, other host threads) race and
+ * must be serialized by the caller.  Same precision and summation order as
+ * bs_block_dots when nb*k*k <= BS_BLOCK_DOTS_NOALLOC_MAX / (2 x SMs); larger
+ * requests run on fewer CTAs.  Runs on `stream` (a cudaStream_t) on the
+ * current device.  Errors: BS_EINVAL (null pointer, nb < 1, dim < 1, k not in
+ * 1, 2, 4, 8, bad dtype); BS_ENOMEM (nb*k*k > BS_BLOCK_DOTS_NOALLOC_MAX);
+ * BS_ECUDA. */
+int bs_block_dots_noalloc(const void *V, int nb, const void *W, int64_t dim, int k, bs_dtype dtype, double *C,
+                          void *stream);
+
 /* Options of bs_lanczos. */
 typedef struct {
     int k;              /* block size: 1 (standard Lanczos), 2, 4 or 8 */

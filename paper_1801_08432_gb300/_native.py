@@ -22,7 +22,7 @@ ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "
 EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_lanczos",
-            "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots"]
+            "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_dots_noalloc"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -86,6 +86,7 @@ def load():
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]
     L.bs_block_dots.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.bs_block_dots_noalloc.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, vp]
     L.bs_sync_status.argtypes = [vp, vp]
     L.bs_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_float)]

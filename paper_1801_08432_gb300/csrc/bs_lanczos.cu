@@ -33,6 +33,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <vector>
 
 #include "bs_internal.h"
@@ -624,4 +625,74 @@ int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *
     }
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free block inner products.  The per-CTA partial sums live in a
+// fixed device array that the module carries; its device address is looked
+// up once per device and then reused by every call.
+static __device__ __align__(256) double g_noalloc_partials[BS_BLOCK_DOTS_NOALLOC_MAX];
+
+namespace {
+
+std::mutex g_noalloc_mtx;
+double *g_noalloc_ptr[64] = {};
+
+// Device address of g_noalloc_partials on device `dev` (which must be
+// current); looked up on the first call for that device.
+int noalloc_scratch(int dev, double **out)
+{
+    std::lock_guard<std::mutex> lock(g_noalloc_mtx);
+    if (dev < 0 || dev >= 64) return BS_EINVAL;
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_partials) != cudaSuccess || !p) return BS_ECUDA;
+        g_noalloc_ptr[dev] = (double *)p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return BS_OK;
+}
+
+template <typename T, int K>
+int noalloc_dots_run(const void *V, int nb, const void *W, int64_t dim, double *C, cudaStream_t s, double *scratch,
+                     int nsm)
+{
+    const int64_t per = (int64_t)nb * K * K;
+    // as many CTAs as the fixed array holds partial blocks for, at most 2 per SM
+    const int ncta = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)nsm, BS_BLOCK_DOTS_NOALLOC_MAX / per));
+    blk_dots<T, K><<<ncta, kDotThreads, 0, s>>>((const T *)V, dim * K, nb, (const T *)W, dim, scratch);
+    dots_reduce<<<(int)((per + 255) / 256), 256, 0, s>>>(scratch, ncta, (int)per, C);
+    return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA;
+}
+
+}  // namespace
+
 }  // namespace bs
+
+extern "C" int bs_block_dots_noalloc(const void *V, int nb, const void *W, int64_t dim, int k, bs_dtype dtype,
+                                     double *C, void *stream)
+{
+    if (!V || !W || !C || nb < 1 || dim < 1) return BS_EINVAL;
+    if (k != 1 && k != 2 && k != 4 && k != 8) return BS_EINVAL;
+    if (dtype != BS_F64 && dtype != BS_F32) return BS_EINVAL;
+    if ((int64_t)nb * k * k > BS_BLOCK_DOTS_NOALLOC_MAX) return BS_ENOMEM;
+    int dev = 0, nsm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BS_ECUDA;
+    if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return BS_ECUDA;
+    double *scratch = nullptr;
+    const int rc = bs::noalloc_scratch(dev, &scratch);
+    if (rc) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dtype == BS_F64) {
+        switch (k) {
+        case 1: return bs::noalloc_dots_run<double, 1>(V, nb, W, dim, C, s, scratch, nsm);
+        case 2: return bs::noalloc_dots_run<double, 2>(V, nb, W, dim, C, s, scratch, nsm);
+        case 4: return bs::noalloc_dots_run<double, 4>(V, nb, W, dim, C, s, scratch, nsm);
+        default: return bs::noalloc_dots_run<double, 8>(V, nb, W, dim, C, s, scratch, nsm);
+        }
+    }
+    switch (k) {
+    case 1: return bs::noalloc_dots_run<float, 1>(V, nb, W, dim, C, s, scratch, nsm);
+    case 2: return bs::noalloc_dots_run<float, 2>(V, nb, W, dim, C, s, scratch, nsm);
+    case 4: return bs::noalloc_dots_run<float, 4>(V, nb, W, dim, C, s, scratch, nsm);
+    default: return bs::noalloc_dots_run<float, 8>(V, nb, W, dim, C, s, scratch, nsm);
+    }
+}
