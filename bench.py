@@ -151,6 +151,38 @@ def reference_arm(args):
     return 0
 
 
+def aggregate_max(values, dist=None):
+    """Element-wise max over ranks (the job time is the slowest rank's)."""
+    if dist is None or not dist.is_initialized() or dist.get_world_size() == 1:
+        return list(values)
+    import torch
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor(list(values), dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.cpu()]
+
+
+def lanczos_check(ctx, N, I, torch, stream):
+    """FP32-mixed block Lanczos (k=8) against FP64 single-vector Lanczos on the
+    same space: lowest 5 eigenvalues after the FP64 refinement, residuals and
+    the time split."""
+    out = {}
+    runs = {"fp64_k1": (1, N.BS_F64, 150), "fp32_k8": (8, N.BS_F32, 80)}
+    for name, (k, dt, niter) in runs.items():
+        p = torch.from_numpy(I.random_block(ctx.dim, k, seed=I.PIVOT_SEED)).to(
+            "cuda", torch.float64 if dt == N.BS_F64 else torch.float32)
+        ev, rep = ctx.lanczos(p, k, dt, niter, 5, refine=True, stream=stream)
+        out[name] = {"k": k, "block_iterations": rep["iterations"], "vector_matvecs": rep["iterations"] * k,
+                     "evals_mev": [round(float(e), 9) for e in ev], "residual_mev": rep["residual"],
+                     "ms_total": round(rep["ms_total"], 1), "ms_matvec": round(rep["ms_matvec"], 1),
+                     "ms_reorth_alpha_gram": round(rep["ms_reorth"], 1), "delta_conv": rep["delta_conv"]}
+    d = [abs(a - b) for a, b in zip(out["fp32_k8"]["evals_mev"], out["fp64_k1"]["evals_mev"])]
+    out["max_abs_diff_mev"] = max(d)
+    out["within_1e-4_mev"] = bool(max(d) <= 1e-4)
+    out["speedup_fp32_k8_vs_fp64_k1_wall"] = out["fp64_k1"]["ms_total"] / out["fp32_k8"]["ms_total"]
+    return out
+
+
 def traffic_from_profile(k):
     """DRAM bytes per launch from the committed ncu summary, if it was taken
     on the current kernel source; else None."""
@@ -227,9 +259,20 @@ def ours(args):
     tune = {}
     modes = {}
     mode_ms = {}
+    if args.mode:
+        ctx.set_kernel(args.mode)
+    if args.profile_only:
+        # a fixed kernel mode and k, warm-up launches then the timed ones, nothing else (for ncu)
+        ms, _, _ = timed(args.k or 8, N.BS_F32, args.steps, args.warmup)
+        if rank == 0:
+            print(json.dumps({"profile_only": True, "mode": args.mode, "k": args.k or 8, "ms": ms}), flush=True)
+        ctx.close()
+        return 0
     if args.k:
         kbest = args.k
         modes[kbest], mode_ms[kbest] = ctx.autotune(kbest, N.BS_F32, sp, times=True)
+        if args.mode:
+            ctx.set_kernel(args.mode)
     else:
         for k in (1, 2, 4, 8):
             modes[k], mode_ms[k] = ctx.autotune(k, N.BS_F32, sp, times=True)
@@ -259,12 +302,7 @@ def ours(args):
     e2e_s = time.perf_counter() - t0
 
     t_ms = float(np.sum(ms32))
-    t_max = t_ms
-    e2e_max = e2e_s
-    if dist is not None:
-        tt = torch.tensor([t_ms, e2e_s], device="cuda", dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_max, e2e_max = float(tt[0]), float(tt[1])
+    t_max, e2e_max = aggregate_max([t_ms, e2e_s], dist)
     value = world * args.steps * kbest / (t_max / 1000.0)
     avg_launch_s = t_ms / args.steps / 1000.0
     fp64_rate = 1.0 / (float(np.mean(ms64)) / 1000.0)
@@ -302,6 +340,8 @@ def ours(args):
         "gpu_launches": args.steps,
         "clocks": clocks,
     }
+    if not args.no_lanczos:
+        line["lanczos"] = lanczos_check(ctx, N, I, torch, sp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
@@ -320,6 +360,9 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--k", type=int, default=0, help="fix k instead of autotuning it")
+    ap.add_argument("--no-lanczos", action="store_true", help="skip the Lanczos accuracy check")
+    ap.add_argument("--mode", type=int, default=0, help="fix the H x kernel mode (bs_set_kernel) instead of autotuning")
+    ap.add_argument("--profile-only", action="store_true", help="only the FP32 H*X launches (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
