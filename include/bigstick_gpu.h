@@ -201,7 +201,10 @@ typedef struct {
     int refine;         /* 1: FP64 H psi of the lowest min(nkeep, 8) Ritz vectors,
                            evals become FP64 Rayleigh quotients, residuals reported */
     int reorth_passes;  /* Gram-Schmidt passes against all stored blocks (2 = default) */
-    void *stream;       /* cudaStream_t the work runs on */
+    int use_graph;      /* 1: capture one block iteration in a CUDA graph (kernels read the
+                           iteration number from a device counter) and replay it */
+    void *stream;       /* cudaStream_t the work runs on (not the legacy default stream
+                           when use_graph = 1: capture needs a created stream) */
 } bs_lanczos_opts;
 
 /* What bs_lanczos did. */
@@ -237,6 +240,14 @@ int bs_lanczos(bs_ctx *ctx, const bs_lanczos_opts *opts, const void *pivot, doub
  * matrix A (row-major, HOST), by the host FP64 solver bs_lanczos uses for T.
  * Errors: BS_EINVAL, BS_EBREAKDOWN. */
 int bs_debug_eigh(int n, const double *A, double *w, double *Z, int nvec);
+
+/* Test aid: the lowest nval eigenvalues (ascending, w[nval]) and the
+ * eigenvectors of the lowest nvec <= nval (Z, n x nvec row-major) of the
+ * symmetric n x n matrix A (row-major, HOST) whose entries vanish beyond
+ * bandwidth bw, by the banded solver bs_lanczos uses for the block-tridiagonal
+ * T (bisection on inertia counts, inverse iteration).  Errors: BS_EINVAL,
+ * BS_EBREAKDOWN. */
+int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, double *Z, int nvec);
 
 /* Chooses the H x kernel.  1 = the tiled kernel (one CTA per destination
  * row and 128-column tile, operands read through L1); 2..5 = variants

@@ -22,7 +22,8 @@ ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "
 EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_lanczos",
-            "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_dots_noalloc"]
+            "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_dots_noalloc",
+            "bs_debug_eigh_banded"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -36,7 +37,8 @@ class bs_tbme(ctypes.Structure):
 
 class bs_lanczos_opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("dtype", ctypes.c_int), ("niter", ctypes.c_int), ("nkeep", ctypes.c_int),
-                ("refine", ctypes.c_int), ("reorth_passes", ctypes.c_int), ("stream", ctypes.c_void_p)]
+                ("refine", ctypes.c_int), ("reorth_passes", ctypes.c_int), ("use_graph", ctypes.c_int),
+                ("stream", ctypes.c_void_p)]
 
 
 class bs_lanczos_report(ctypes.Structure):
@@ -84,6 +86,7 @@ def load():
     L.bs_set_kernel.argtypes = [vp, ctypes.c_int]
     L.bs_lanczos.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, f64p, vp, ctypes.POINTER(bs_lanczos_report)]
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
+    L.bs_debug_eigh_banded.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]
     L.bs_block_dots.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
     L.bs_block_dots_noalloc.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, vp]
@@ -171,11 +174,12 @@ class Context:
         self._check(load().bs_debug_table(self.h, name.encode(), out.ctypes.data_as(vp), ctypes.byref(n)))
         return out
 
-    def lanczos(self, pivot, k, dtype, niter, nkeep, refine=True, evecs=None, stream=None, reorth_passes=2):
+    def lanczos(self, pivot, k, dtype, niter, nkeep, refine=True, evecs=None, stream=None, reorth_passes=2,
+                use_graph=False):
         """Block Lanczos on the GPU.  pivot: device tensor [dim][k] (dtype);
         evecs: optional device float64 tensor [dim][nkeep].  Returns
         (eigenvalues as numpy, report dict)."""
-        o = bs_lanczos_opts(k, dtype, niter, nkeep, int(refine), reorth_passes, vp(stream or 0))
+        o = bs_lanczos_opts(k, dtype, niter, nkeep, int(refine), reorth_passes, int(use_graph), vp(stream or 0))
         ev = np.zeros(nkeep)
         rep = bs_lanczos_report()
         pp = pivot if isinstance(pivot, int) else pivot.data_ptr()
@@ -245,3 +249,15 @@ def debug_eigh(A, nvec):
     if rc != 0:
         raise BSError(rc, "bs_debug_eigh")
     return w, Z[:, :nvec]
+
+
+def debug_eigh_banded(A, bw, nval, nvec):
+    """The library's banded host FP64 eigensolver (test aid)."""
+    A = np.ascontiguousarray(A, dtype=np.float64)
+    n = A.shape[0]
+    w = np.zeros(max(nval, 1))
+    Z = np.zeros((n, max(nvec, 1)))
+    rc = load().bs_debug_eigh_banded(n, bw, A.ctypes.data_as(vp), nval, w.ctypes.data_as(vp), Z.ctypes.data_as(vp), nvec)
+    if rc != 0:
+        raise BSError(rc, "bs_debug_eigh_banded")
+    return w[:nval], Z[:, :nvec]

@@ -182,7 +182,138 @@ bool host_eigh(int n, const double *A, double *w, double *Z, int nvec)
     return true;
 }
 
+// Banded symmetric matrix (half-bandwidth bw, row-major full n x n storage):
+// the lowest nval eigenvalues by bisection on inertia counts and the
+// eigenvectors of the lowest nvec by inverse iteration, without forming a
+// tridiagonal matrix.  The inertia count of A - x I is the number of negative
+// pivots of its elimination without pivoting (Sylvester's law of inertia);
+// fill stays inside the band, so a count costs O(n bw^2).  Inverse iteration
+// solves (A - lambda I) y = b by Gaussian elimination with row pivoting on
+// the band (upper bandwidth grows to 2 bw).
+bool host_eigh_banded(int n, int bw, const double *A, int nval, double *w, double *Z, int nvec)
+{
+    if (n <= 0) return true;
+    nval = std::min(nval, n);
+    nvec = std::min(nvec, nval);
+    const int W = 2 * bw + 1;   // band storage: B[i][bw + j - i] = A[i][j]
+    std::vector<double> band((size_t)n * W, 0.0);
+    double scale = 0.0, lo = 1e300, hi = -1e300;
+    for (int i = 0; i < n; ++i) {
+        double r = 0.0;
+        for (int j = std::max(0, i - bw); j <= std::min(n - 1, i + bw); ++j) {
+            band[(size_t)i * W + bw + j - i] = A[(size_t)i * n + j];
+            if (j != i) r += std::fabs(A[(size_t)i * n + j]);
+        }
+        const double d = A[(size_t)i * n + i];
+        lo = std::min(lo, d - r);
+        hi = std::max(hi, d + r);
+        scale = std::max(scale, std::fabs(d) + r);
+    }
+    if (scale == 0.0) scale = 1.0;
+    const double tiny = 1e-300 + 1e-30 * scale;
+    lo -= 1e-12 * scale;
+    hi += 1e-12 * scale;
+    std::vector<double> M((size_t)n * W);
+    auto below = [&](double x) {
+        // elimination without pivoting on the band of A - x I
+        std::copy(band.begin(), band.end(), M.begin());
+        for (int i = 0; i < n; ++i) M[(size_t)i * W + bw] -= x;
+        int neg = 0;
+        for (int k = 0; k < n; ++k) {
+            double piv = M[(size_t)k * W + bw];
+            if (std::fabs(piv) < tiny) piv = M[(size_t)k * W + bw] = -tiny;
+            if (piv < 0.0) ++neg;
+            for (int i = k + 1; i <= std::min(n - 1, k + bw); ++i) {
+                const double f = M[(size_t)i * W + bw + k - i] / piv;
+                if (f == 0.0) continue;
+                for (int j = k + 1; j <= std::min(n - 1, k + bw); ++j)
+                    M[(size_t)i * W + bw + j - i] -= f * M[(size_t)k * W + bw + j - k];
+            }
+        }
+        return neg;
+    };
+    for (int j = 0; j < nval; ++j) {
+        double a = lo, b = hi;
+        for (int it = 0; it < 200 && b - a > 4e-16 * scale; ++it) {
+            const double mid = 0.5 * (a + b);
+            if (below(mid) > j) b = mid;
+            else a = mid;
+        }
+        w[j] = 0.5 * (a + b);
+    }
+    // inverse iteration; LU with row pivoting in a band of upper width 2 bw
+    const int U = 2 * bw, LW = bw + U + 1;   // columns i-bw .. i+U
+    std::vector<double> L((size_t)n * LW), y(n), Y((size_t)nvec * n);
+    std::vector<int> perm(n);
+    for (int v = 0; v < nvec; ++v) {
+        const double lam = w[v] + 1e-13 * scale;
+        // factor: row i of L holds A[i][i-bw .. i+U] at offset (j - i + bw)
+        std::fill(L.begin(), L.end(), 0.0);
+        for (int i = 0; i < n; ++i)
+            for (int j = std::max(0, i - bw); j <= std::min(n - 1, i + bw); ++j)
+                L[(size_t)i * LW + j - i + bw] = A[(size_t)i * n + j] - (i == j ? lam : 0.0);
+        auto at = [&](int i, int j) -> double & { return L[(size_t)i * LW + j - i + bw]; };
+        std::vector<double> mult((size_t)n * bw, 0.0);   // multipliers of column k for rows k+1..k+bw
+        for (int k = 0; k < n; ++k) {
+            int p = k;
+            for (int i = k + 1; i <= std::min(n - 1, k + bw); ++i)
+                if (std::fabs(at(i, k)) > std::fabs(at(p, k))) p = i;
+            perm[k] = p;
+            if (p != k)
+                for (int j = k; j <= std::min(n - 1, k + U); ++j) {
+                    // rows k and p share the column range k..k+U inside the band (p <= k+bw)
+                    if (j - p + bw < 0 || j - p + bw >= LW) continue;
+                    std::swap(at(k, j), at(p, j));
+                }
+            if (std::fabs(at(k, k)) < tiny) at(k, k) = tiny;
+            for (int i = k + 1; i <= std::min(n - 1, k + bw); ++i) {
+                const double f = at(i, k) / at(k, k);
+                mult[(size_t)k * bw + (i - k - 1)] = f;
+                at(i, k) = 0.0;
+                if (f == 0.0) continue;
+                for (int j = k + 1; j <= std::min(n - 1, k + U); ++j)
+                    if (j - i + bw < LW) at(i, j) -= f * at(k, j);
+            }
+        }
+        for (int i = 0; i < n; ++i) y[i] = 1.0 + 0.1 * std::sin(1.0 + 7.0 * i + 13.0 * v);
+        for (int it = 0; it < 4; ++it) {
+            // forward: apply the row swaps and multipliers in order
+            for (int k = 0; k < n; ++k) {
+                if (perm[k] != k) std::swap(y[k], y[perm[k]]);
+                for (int i = k + 1; i <= std::min(n - 1, k + bw); ++i) y[i] -= mult[(size_t)k * bw + (i - k - 1)] * y[k];
+            }
+            for (int i = n - 1; i >= 0; --i) {
+                double s = y[i];
+                for (int j = i + 1; j <= std::min(n - 1, i + U); ++j) s -= at(i, j) * y[j];
+                y[i] = s / at(i, i);
+            }
+            for (int p = 0; p < v; ++p) {
+                if (std::fabs(w[p] - w[v]) > 1e-6 * scale) continue;
+                double dot = 0.0;
+                for (int i = 0; i < n; ++i) dot += Y[(size_t)p * n + i] * y[i];
+                for (int i = 0; i < n; ++i) y[i] -= dot * Y[(size_t)p * n + i];
+            }
+            double nrm = 0.0;
+            for (int i = 0; i < n; ++i) nrm += y[i] * y[i];
+            nrm = std::sqrt(nrm);
+            if (!(nrm > 0.0)) return false;
+            for (int i = 0; i < n; ++i) y[i] /= nrm;
+        }
+        std::copy(y.begin(), y.end(), Y.begin() + (size_t)v * n);
+    }
+    for (int r = 0; r < n; ++r)
+        for (int v = 0; v < nvec; ++v) Z[(size_t)r * nvec + v] = Y[(size_t)v * n + r];
+    return true;
+}
+
 }  // namespace bs
+
+extern "C" int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, double *Z, int nvec)
+{
+    if (n < 0 || bw < 0 || nval < 0 || nvec < 0 || nvec > nval || (n > 0 && (!A || !w || (nvec > 0 && !Z))))
+        return BS_EINVAL;
+    return bs::host_eigh_banded(n, bw, A, nval, w, Z, nvec) ? BS_OK : BS_EBREAKDOWN;
+}
 
 extern "C" int bs_debug_eigh(int n, const double *A, double *w, double *Z, int nvec)
 {

@@ -30,7 +30,7 @@ namespace bs {
 namespace {
 
 constexpr uint32_t kPipeWaitLimit = 1u << 22;
-constexpr int kPipeMaxList = 24;
+constexpr int kPipeMaxList = 16;
 
 __device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -461,7 +461,7 @@ cudaError_t launch_pipe_t(const Device &Dv, const DevCoefs<T> &C, const T *ww, c
 
 // variants: consumer warps, columns per thread (largest sector must fit), ring slots, smem target
 constexpr PipeVariant kPipeVariants[] = {
-    {8, 4, 3, 110 * 1024}, {8, 4, 4, 75 * 1024}, {16, 2, 3, 110 * 1024}, {16, 8, 2, 200 * 1024}, {8, 1, 3, 75 * 1024},
+    {8, 3, 3, 110 * 1024}, {8, 4, 3, 110 * 1024}, {16, 2, 3, 110 * 1024}, {16, 8, 2, 200 * 1024}, {8, 1, 3, 75 * 1024},
 };
 constexpr int kNumPipe = 5;
 
@@ -470,6 +470,7 @@ cudaError_t launch_pipe_k(const Device &Dv, const DevCoefs<T> &C, const T *ww, c
                           cudaStream_t s, int v, bool &used)
 {
     const PipeVariant P = kPipeVariants[v];
+    if (P.nw == 8 && P.cpt == 3) return launch_pipe_t<T, K, 8, 3>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);
     if (P.nw == 8 && P.cpt == 4) return launch_pipe_t<T, K, 8, 4>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);
     if (P.nw == 16 && P.cpt == 2) return launch_pipe_t<T, K, 16, 2>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);
     if (P.nw == 16 && P.cpt == 8) return launch_pipe_t<T, K, 16, 8>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);

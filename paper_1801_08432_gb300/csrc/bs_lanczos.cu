@@ -41,6 +41,7 @@
 namespace bs {
 
 bool host_eigh(int n, const double *A, double *w, double *Z, int nvec);
+bool host_eigh_banded(int n, int bw, const double *A, int nval, double *w, double *Z, int nvec);
 
 namespace {
 
@@ -79,51 +80,63 @@ struct Accum<double> {
     __device__ __forceinline__ double get() const { return v; }
 };
 
-// partial[cta][b][i][j] = sum over this CTA's rows alpha of V_b[alpha][i] * W[alpha][j],
-// for blocks b = b0 .. b0+nb-1 of the stored basis (stride `bstride` elements).
+// partial[cta][b][i][j] = sum over this CTA's rows alpha of V_b[alpha][i] * W[alpha][j]
+// for the nb blocks V_b of the stored basis (stride `bstride` elements).
 // Thread (row slot r, column j): K threads share a row, one W column each.
+// Blocks are taken BG = 16 / K at a time, so W is read once per group and a
+// thread carries BG x K extended-precision sums.
 template <typename T, int K>
 __global__ void __launch_bounds__(kDotThreads) blk_dots(const T *__restrict__ V, int64_t bstride, int nb,
                                                         const T *__restrict__ W, int64_t dim,
-                                                        double *__restrict__ partial)
+                                                        double *__restrict__ partial, const int *__restrict__ nb_iter)
 {
+    if (nb_iter) nb = *nb_iter + 1;   // graph replay: blocks 0..n of iteration n
+    constexpr int BG = 16 / K;
     constexpr int RPS = kDotThreads / K;   // rows per CTA step
-    __shared__ double red[kDotThreads / 32][K * K];
+    __shared__ double red[kDotThreads / 32][BG * K * K];
     const int tid = threadIdx.x, j = tid % K, r = tid / K;
     const int warp = tid >> 5, lane = tid & 31;
-    for (int b = 0; b < nb; ++b) {
-        const T *Vb = V + (int64_t)b * bstride;
-        Accum<T> acc[K];
+    for (int b0 = 0; b0 < nb; b0 += BG) {
+        const int nbg = min(BG, nb - b0);
+        Accum<T> acc[BG][K];
         for (int64_t a = (int64_t)blockIdx.x * RPS + r; a < dim; a += (int64_t)gridDim.x * RPS) {
             const T w = W[a * K + j];
 #pragma unroll
-            for (int i = 0; i < K; ++i) acc[i].add(Vb[a * K + i], w);
+            for (int g = 0; g < BG; ++g) {
+                if (g < nbg) {
+                    const T *v = V + (int64_t)(b0 + g) * bstride + a * K;
+#pragma unroll
+                    for (int i = 0; i < K; ++i) acc[g][i].add(v[i], w);
+                }
+            }
         }
         // reduce over the rows of the warp (lanes with equal j), then over warps
-        double s[K];
 #pragma unroll
-        for (int i = 0; i < K; ++i) {
-            s[i] = acc[i].get();
+        for (int g = 0; g < BG; ++g) {
 #pragma unroll
-            for (int o = 16; o >= K; o >>= 1) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
-        }
-        if (lane < K) {
+            for (int i = 0; i < K; ++i) {
+                double sv = acc[g][i].get();
 #pragma unroll
-            for (int i = 0; i < K; ++i) red[warp][i * K + j] = s[i];
+                for (int o = 16; o >= K; o >>= 1) sv += __shfl_xor_sync(0xffffffffu, sv, o);
+                if (lane < K) red[warp][(g * K + i) * K + j] = sv;
+            }
         }
         __syncthreads();
-        if (tid < K * K) {
+        for (int e = tid; e < nbg * K * K; e += kDotThreads) {
             double t = 0.0;
-            for (int w2 = 0; w2 < kDotThreads / 32; ++w2) t += red[w2][tid];
-            partial[((int64_t)blockIdx.x * nb + b) * K * K + tid] = t;
+            for (int w2 = 0; w2 < kDotThreads / 32; ++w2) t += red[w2][e];
+            partial[((int64_t)blockIdx.x * nb + b0) * K * K + e] = t;
         }
         __syncthreads();
     }
 }
 
 // out[e] = sum over CTAs of partial[cta][e], e < n (fixed order)
-__global__ void dots_reduce(const double *__restrict__ partial, int ncta, int n, double *__restrict__ out)
+__global__ void dots_reduce(const double *__restrict__ partial, int ncta, int n, double *__restrict__ out,
+                            const int *__restrict__ nb_iter, const int *__restrict__ out_iter, int kk)
 {
+    if (nb_iter) n = (*nb_iter + 1) * kk;       // graph replay: n+1 blocks of k x k
+    if (out_iter) out += (int64_t)(*out_iter) * kk;   // graph replay: block n of a history array
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     double t = 0.0;
@@ -134,8 +147,11 @@ __global__ void dots_reduce(const double *__restrict__ partial, int ncta, int n,
 // W[alpha][j] -= sum_b sum_i V_b[alpha][i] C[b][i][j]   (C: nb blocks of K x K, FP64)
 template <typename T, int K>
 __global__ void blk_update(const T *__restrict__ V, int64_t bstride, int nb, const double *__restrict__ C,
-                           T *__restrict__ W, int64_t dim)
+                           T *__restrict__ W, int64_t dim, const int *__restrict__ nb_iter,
+                           const int *__restrict__ c_iter)
 {
+    if (nb_iter) nb = *nb_iter + 1;
+    if (c_iter) C += (int64_t)(*c_iter) * K * K;
     extern __shared__ __align__(16) unsigned char sm_raw[];
     T *Cs = reinterpret_cast<T *>(sm_raw);
     for (int e = threadIdx.x; e < nb * K * K; e += blockDim.x) Cs[e] = (T)C[e];
@@ -161,8 +177,10 @@ __global__ void blk_update(const T *__restrict__ V, int64_t bstride, int nb, con
 
 // Vout[alpha][:] = W[alpha][:] M   (M: K x K, FP64)
 template <typename T, int K>
-__global__ void blk_scale(const T *__restrict__ W, const double *__restrict__ M, T *__restrict__ Vout, int64_t dim)
+__global__ void blk_scale(const T *__restrict__ W, const double *__restrict__ M, T *__restrict__ Vout, int64_t dim,
+                          const int *__restrict__ iter, int64_t bstride, T *__restrict__ Vout2)
 {
+    if (iter) Vout += (int64_t)(*iter + 1) * bstride;   // graph replay: block n+1
     __shared__ T Ms[K * K];
     if (threadIdx.x < K * K) Ms[threadIdx.x] = (T)M[threadIdx.x];
     __syncthreads();
@@ -176,7 +194,16 @@ __global__ void blk_scale(const T *__restrict__ W, const double *__restrict__ M,
             for (int j = 0; j < K; ++j) o[j] = fma(w[i], Ms[i * K + j], o[j]);
 #pragma unroll
         for (int j = 0; j < K; ++j) Vout[a * K + j] = o[j];
+        if (Vout2) {
+#pragma unroll
+            for (int j = 0; j < K; ++j) Vout2[a * K + j] = o[j];
+        }
     }
+}
+
+__global__ void iter_advance(int *iter)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) ++*iter;
 }
 
 // X[alpha][m] = sum_b sum_i V_b[alpha][i] Y[b*K+i][m], m < nm, FP64 output [dim][ldx]
@@ -214,9 +241,14 @@ __global__ void resid_inplace(double *__restrict__ R, const double *__restrict__
 // eigenvalue is below rel * max are flagged (bit i of *flags) and get a zero
 // column in M and a zero row in B.  Also symmetrizes A in place when given.
 __global__ void small_gram(int K, const double *__restrict__ O, double rel, double *__restrict__ M,
-                           double *__restrict__ B, int *__restrict__ flags, double *__restrict__ A)
+                           double *__restrict__ B, int *__restrict__ flags, double *__restrict__ A,
+                           const int *__restrict__ iter)
 {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    if (iter) {   // graph replay: B_n and A_n of iteration n
+        B += (int64_t)(*iter) * K * K;
+        if (A) A += (int64_t)(*iter) * K * K;
+    }
     double a[64], u[64];
     for (int i = 0; i < K; ++i)
         for (int j = 0; j < K; ++j) {
@@ -306,19 +338,24 @@ struct LState {
     cudaStream_t s = 0;
 };
 
+// nb_iter / out_iter (device, may be null): take the block count n+1 or the
+// output slot n from the iteration counter, for graph replay.  nb_max bounds
+// the launch when the count comes from the device.
 template <typename T, int K>
-void dots(LState &L, const T *V, int nb, const T *W, double *out)
+void dots(LState &L, const T *V, int nb, const T *W, double *out, const int *nb_iter = nullptr,
+          const int *out_iter = nullptr, int nb_max = 0)
 {
-    blk_dots<T, K><<<L.ncta, kDotThreads, 0, L.s>>>(V, L.bstride, nb, W, L.dim, L.partial);
-    const int n = nb * K * K;
-    dots_reduce<<<(n + 255) / 256, 256, 0, L.s>>>(L.partial, L.ncta, n, out);
+    blk_dots<T, K><<<L.ncta, kDotThreads, 0, L.s>>>(V, L.bstride, nb, W, L.dim, L.partial, nb_iter);
+    const int n = (nb_iter ? nb_max : nb) * K * K;
+    dots_reduce<<<(n + 255) / 256, 256, 0, L.s>>>(L.partial, L.ncta, nb * K * K, out, nb_iter, out_iter, K * K);
 }
 
 template <typename T, int K>
-void update(LState &L, const T *V, int nb, const double *C, T *W)
+void update(LState &L, const T *V, int nb, const double *C, T *W, const int *nb_iter = nullptr,
+            const int *c_iter = nullptr, int nb_max = 0)
 {
-    const size_t smem = (size_t)nb * K * K * sizeof(T);
-    blk_update<T, K><<<L.ncta, 256, smem, L.s>>>(V, L.bstride, nb, C, W, L.dim);
+    const size_t smem = (size_t)(nb_iter ? nb_max : nb) * K * K * sizeof(T);
+    blk_update<T, K><<<L.ncta, 256, smem, L.s>>>(V, L.bstride, nb, C, W, L.dim, nb_iter, c_iter);
 }
 
 }  // namespace
@@ -384,11 +421,57 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
     // orthonormalize the pivot block (FP64 Gram, one reorthogonalization-free QR)
     cudaMemcpyAsync(W, pivot, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
     dots<T, K>(L, W, 1, W, L.C);
-    small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bn, L.flags, nullptr);
-    blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V, L.dim);
+    small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bn, L.flags, nullptr, nullptr);
+    blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V, L.dim, nullptr, 0, nullptr);
+
+    // Graph mode: the whole block iteration (H X, alpha, reorthogonalization,
+    // Gram eigen-decomposition, normalization) is captured once in a CUDA
+    // graph whose kernels read the iteration number n from a device counter;
+    // each iteration is one graph launch.  H X reads a fixed copy of V_n
+    // (Xcur, written by the normalization of the previous iteration).
+    T *Xcur = nullptr;
+    int *d_iter = nullptr;
+    cudaGraphExec_t gexec = nullptr;
+    if (o.use_graph) {
+        Xcur = (T *)alloc((size_t)L.bstride * es);
+        d_iter = (int *)alloc(sizeof(int));
+        if (!Xcur || !d_iter) { cleanup(); c->err = "lanczos: device allocation failed"; return BS_ENOMEM; }
+        cudaMemcpyAsync(Xcur, V, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
+        cudaMemsetAsync(d_iter, 0, sizeof(int), L.s);
+        cudaGraph_t graph = nullptr;
+        cudaError_t e = cudaStreamBeginCapture(L.s, cudaStreamCaptureModeThreadLocal);
+        if (e == cudaSuccess) {
+            cudaEventRecord(ev[0], L.s);
+            rc = launch_hx(c, Xcur, W, K, o.dtype, L.s, c->err);
+            cudaEventRecord(ev[1], L.s);
+            dots<T, K>(L, Xcur, 1, W, L.Ahist, nullptr, d_iter, 1);
+            update<T, K>(L, Xcur, 1, L.Ahist, W, nullptr, d_iter, 1);
+            for (int p = 0; p < passes; ++p) {
+                dots<T, K>(L, V, 1, W, L.C, d_iter, nullptr, niter + 1);
+                update<T, K>(L, V, 1, L.C, W, d_iter, nullptr, niter + 1);
+            }
+            dots<T, K>(L, W, 1, W, L.C);
+            small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist, L.flags, L.Ahist, d_iter);
+            blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V, L.dim, d_iter, L.bstride, Xcur);
+            iter_advance<<<1, 1, 0, L.s>>>(d_iter);
+            cudaEventRecord(ev[2], L.s);
+            e = cudaStreamEndCapture(L.s, &graph);
+        }
+        if (e == cudaSuccess && rc == BS_OK) e = cudaGraphInstantiate(&gexec, graph, 0);
+        if (graph) cudaGraphDestroy(graph);
+        if (e != cudaSuccess || rc != BS_OK) {
+            if (rc == BS_OK) { c->err = std::string("lanczos graph: ") + cudaGetErrorString(e); rc = BS_ECUDA; }
+            cleanup();
+            return rc;
+        }
+    }
 
     for (int n = 0; n < niter && rc == BS_OK; ++n) {
         T *Vn = V + (int64_t)n * L.bstride;
+        if (gexec) {
+            cudaError_t e = cudaGraphLaunch(gexec, L.s);
+            if (e != cudaSuccess) { c->err = std::string("lanczos graph launch: ") + cudaGetErrorString(e); rc = BS_ECUDA; break; }
+        } else {
         cudaEventRecord(ev[0], L.s);
         if ((rc = launch_hx(c, Vn, W, K, o.dtype, L.s, c->err))) break;
         cudaEventRecord(ev[1], L.s);
@@ -401,9 +484,10 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
             update<T, K>(L, V, n + 1, L.C, W);
         }
         dots<T, K>(L, W, 1, W, L.C);
-        small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist + (size_t)n * K * K, L.flags, An);
-        blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V + (int64_t)(n + 1) * L.bstride, L.dim);
+        small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist + (size_t)n * K * K, L.flags, An, nullptr);
+        blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V + (int64_t)(n + 1) * L.bstride, L.dim, nullptr, 0, nullptr);
         cudaEventRecord(ev[2], L.s);
+        }
         int flags = 0;
         cudaError_t e = cudaMemcpyAsync(&flags, L.flags, sizeof(int), cudaMemcpyDeviceToHost, L.s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(L.s);
@@ -429,8 +513,8 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
             }
             cudaMemcpyAsync(W, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
             dots<T, K>(L, W, 1, W, L.C);
-            small_gram<<<1, 1, 0, L.s>>>(K, L.C, 1e-20, L.M, L.Bn, L.flags, nullptr);
-            blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, Vn1, L.dim);
+            small_gram<<<1, 1, 0, L.s>>>(K, L.C, 1e-20, L.M, L.Bn, L.flags, nullptr, nullptr);
+            blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, Vn1, L.dim, nullptr, 0, nullptr);
             // B_n <- G B_n with G = Bn (the Gram factor of the refilled block: W = Vnew G)
             std::vector<double> G(K * K), Bn(K * K), out(K * K, 0.0);
             int fl2 = 0;
@@ -443,6 +527,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
                 for (int j = 0; j < K; ++j)
                     for (int l = 0; l < K; ++l) out[i * K + j] += G[i * K + l] * Bn[l * K + j];
             cudaMemcpyAsync(L.Bhist + (size_t)n * K * K, out.data(), K * K * sizeof(double), cudaMemcpyHostToDevice, L.s);
+            if (Xcur) cudaMemcpyAsync(Xcur, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
             cudaStreamSynchronize(L.s);
         }
     }
@@ -466,21 +551,30 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
                         T_[(size_t)(n * K + j) * nT + (n + 1) * K + i] = b;
                     }
                 }
-        wT.resize(nT);
+        // T is banded: B_n = Lambda^1/2 Q^T from the Gram eigendecomposition
+        // is a full k x k block, so the half-bandwidth is up to 2k - 1 (read
+        // off T).  Eigenvalues by bisection on inertia counts, eigenvectors by
+        // inverse iteration, O(nT bw^2) each.
+        int bw = 0;
+        for (int i = 0; i < nT; ++i)
+            for (int j = 0; j < i - bw; ++j)
+                if (T_[(size_t)i * nT + j] != 0.0) { bw = i - j; break; }
+        const int nval = std::min(nT, nkeep + 5);
+        wT.assign(std::max(nval, 1), 0.0);
         const int nv = std::min(nkeep, nT);
         Z.resize((size_t)nT * nv);
-        if (!host_eigh(nT, T_.data(), wT.data(), Z.data(), nv)) { rc = BS_EBREAKDOWN; c->err = "lanczos: eigensolver failed"; }
+        if (!host_eigh_banded(nT, bw, T_.data(), nval, wT.data(), Z.data(), nv)) { rc = BS_EBREAKDOWN; c->err = "lanczos: eigensolver failed"; }
         // convergence measure of the paper: the lowest nkeep+5 eigenvalues of
         // T now and one block iteration earlier
         if (rc == BS_OK && rep) {
             const int nprev = (done - 1) * K, m = std::min(nkeep + 5, nprev);
             double delta = 0.0;
             if (m > 0) {
-                std::vector<double> Tp((size_t)nprev * nprev), wp(nprev);
+                std::vector<double> Tp((size_t)nprev * nprev), wp(std::max(m, 1));
                 for (int i = 0; i < nprev; ++i)
                     for (int j = 0; j < nprev; ++j) Tp[(size_t)i * nprev + j] = T_[(size_t)i * nT + j];
                 std::vector<double> dummy(1);
-                host_eigh(nprev, Tp.data(), wp.data(), dummy.data(), 0);
+                host_eigh_banded(nprev, bw, Tp.data(), m, wp.data(), dummy.data(), 0);
                 for (int i = 0; i < m; ++i) delta += std::fabs(wT[i] - wp[i]);
                 delta /= std::sqrt((double)m);
             }
@@ -551,6 +645,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         cudaStreamSynchronize(L.s);
     }
     for (auto &e : ev) cudaEventDestroy(e);
+    if (gexec) cudaGraphExecDestroy(gexec);
     cleanup();
     const auto t1 = std::chrono::steady_clock::now();
     if (rep) {
@@ -604,11 +699,21 @@ int run_block_dots(bs_ctx *c, const void *V, int nb, const void *W, int k, bs_dt
     }
 }
 
-int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
+int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o_in, const void *pivot, double *evals, double *evecs,
                 bs_lanczos_report *rep)
 {
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return BS_ECUDA; }
+    bs_lanczos_opts o = o_in;
+    cudaStream_t own = nullptr;
+    if (o.use_graph && !o.stream) {   // capture needs a created stream
+        if ((e = cudaStreamCreateWithFlags(&own, cudaStreamNonBlocking)) != cudaSuccess) { c->err = cudaGetErrorString(e); return BS_ECUDA; }
+        o.stream = own;
+    }
+    struct Own {
+        cudaStream_t s;
+        ~Own() { if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); } }
+    } guard{own};
     if (o.dtype == BS_F64) {
         switch (o.k) {
         case 1: return lanczos_run<double, 1>(c, o, pivot, evals, evecs, rep);
@@ -658,8 +763,8 @@ int noalloc_dots_run(const void *V, int nb, const void *W, int64_t dim, double *
     const int64_t per = (int64_t)nb * K * K;
     // as many CTAs as the fixed array holds partial blocks for, at most 2 per SM
     const int ncta = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)nsm, BS_BLOCK_DOTS_NOALLOC_MAX / per));
-    blk_dots<T, K><<<ncta, kDotThreads, 0, s>>>((const T *)V, dim * K, nb, (const T *)W, dim, scratch);
-    dots_reduce<<<(int)((per + 255) / 256), 256, 0, s>>>(scratch, ncta, (int)per, C);
+    blk_dots<T, K><<<ncta, kDotThreads, 0, s>>>((const T *)V, dim * K, nb, (const T *)W, dim, scratch, nullptr);
+    dots_reduce<<<(int)((per + 255) / 256), 256, 0, s>>>(scratch, ncta, (int)per, C, nullptr, nullptr, K * K);
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA;
 }
 

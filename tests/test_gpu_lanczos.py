@@ -42,6 +42,25 @@ def test_host_eigensolver_matches_numpy():
         assert np.max(np.abs(A @ Z - Z * w[:Z.shape[1]])) < 1e-11 * max(1, np.abs(w).max())
 
 
+def test_banded_host_eigensolver_matches_numpy():
+    rng = np.random.default_rng(4)
+    for k, nb in ((1, 200), (2, 30), (4, 25), (8, 40)):
+        n = k * nb
+        T = np.zeros((n, n))
+        for b in range(nb):
+            A = rng.standard_normal((k, k))
+            T[b * k:(b + 1) * k, b * k:(b + 1) * k] = A + A.T
+            if b + 1 < nb:
+                B = rng.standard_normal((k, k))   # full, as Lambda^1/2 Q^T of a Gram eig
+                T[(b + 1) * k:(b + 2) * k, b * k:(b + 1) * k] = B
+                T[b * k:(b + 1) * k, (b + 1) * k:(b + 2) * k] = B.T
+        w, Z = N.debug_eigh_banded(T, 2 * k - 1 if k > 1 else 1, 10, 6)
+        ref = np.linalg.eigvalsh(T)[:10]
+        assert np.max(np.abs(w - ref)) < 1e-12 * np.max(np.abs(ref))
+        assert np.max(np.abs(T @ Z - Z * w[:6])) < 1e-11 * np.max(np.abs(ref))
+        assert np.max(np.abs(Z.T @ Z - np.eye(6))) < 1e-10
+
+
 @pytest.mark.gpu
 def test_fp64_lanczos_sd22_equals_dense():
     c, o = ctx_oracle("sd", 2, 2, 0)
@@ -118,3 +137,18 @@ def test_block_dots_match_fp64_numpy(k, dtype):
     C2 = torch.zeros_like(C)
     c.block_dots(V, nb, W, k, dtype, C2)
     assert torch.equal(C, C2)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("k,dtype", [(1, N.BS_F64), (8, N.BS_F32)])
+def test_graph_captured_iteration_equals_plain_loop(k, dtype):
+    c, _ = ctx_oracle("sd", 4, 4, 0, with_oracle=False)
+    s = torch.cuda.Stream()
+    p = pivot(c.dim, k, dtype)
+    torch.cuda.synchronize()
+    ev_a, rep_a = c.lanczos(p, k, dtype, 40, 4, refine=True, stream=s.cuda_stream)
+    ev_b, rep_b = c.lanczos(p, k, dtype, 40, 4, refine=True, stream=s.cuda_stream, use_graph=True)
+    assert rep_b["iterations"] == rep_a["iterations"] == 40
+    assert np.max(np.abs(ev_a - ev_b)) <= 1e-12 * np.max(np.abs(ev_a))
+    ev_c, rep_c = c.lanczos(p, k, dtype, 40, 4, refine=True, use_graph=True)   # default stream -> own stream
+    assert np.max(np.abs(ev_a - ev_c)) <= 1e-12 * np.max(np.abs(ev_a))
