@@ -15,6 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbsgpu.so")
 
 BS_F64, BS_F32 = 0, 1
+KERNEL_MODES = 12          # BS_KERNEL_MODES: selectable H x kernel modes 1..12
 ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "BS_ENOMEM",
           -5: "BS_ECUDA", -6: "BS_EBREAKDOWN", -7: "BS_ETIMEOUT"}
 
@@ -197,10 +198,10 @@ class Context:
         """Picks the fastest kernel mode for (k, dtype); with times=True also
         returns {mode: ms per product}."""
         m = ctypes.c_int()
-        ms = (ctypes.c_float * 10)()
+        ms = (ctypes.c_float * KERNEL_MODES)()
         self._check(load().bs_autotune(self.h, k, dtype, vp(stream or 0), ctypes.byref(m), ms))
         if times:
-            return m.value, {i + 1: round(float(ms[i]), 4) for i in range(10)}
+            return m.value, {i + 1: round(float(ms[i]), 4) for i in range(KERNEL_MODES)}
         return m.value
 
     def sync_status(self, stream=None):

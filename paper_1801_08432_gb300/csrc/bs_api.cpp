@@ -224,6 +224,13 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
     f = cast<float>(T.pe.nn_coef);
     if ((rc = put(D, D.pe_nn_coef32, f.data(), f.size(), err))) return rc;
     if ((rc = put(D, D.ww64, T.ww.data(), T.ww.size(), err))) return rc;
+    // core-grouped pn kernel
+    D.ncunits = (int)T.cunits.size();
+    D.nz = D.ncunits ? B.sp[0].nparticles : 0;
+    if ((rc = put(D, D.cunits, T.cunits.data(), T.cunits.size(), err))) return rc;
+    if ((rc = put(D, D.csrc, T.csrc.data(), T.csrc.size(), err))) return rc;
+    f = cast<float>(T.wc);
+    if ((rc = put(D, D.wc32, f.data(), f.size(), err))) return rc;
     f = cast<float>(T.ww);
     if ((rc = put(D, D.ww32, f.data(), f.size(), err))) return rc;
     return BS_OK;
@@ -264,6 +271,7 @@ void bs_destroy(bs_ctx *c)
         if (c->adj_rho) cudaFree(c->adj_rho);
         if (c->hx_x) cudaFree(c->hx_x);
         if (c->hx_y) cudaFree(c->hx_y);
+        if (c->core_part) cudaFree(c->core_part);
     }
     delete c;
 }
@@ -444,7 +452,7 @@ int bs_lanczos(bs_ctx *c, const bs_lanczos_opts *o, const void *pivot, double *e
 int bs_set_kernel(bs_ctx *c, int mode)
 {
     return guarded(c, [&]() -> int {
-        if (mode < 0 || mode >= 2 + row_variants() + pipe_variants()) { c->err = "unknown kernel mode"; return BS_EINVAL; }
+        if (mode < 0 || mode > BS_KERNEL_MODES) { c->err = "unknown kernel mode"; return BS_EINVAL; }
         c->hx_mode = mode;
         return BS_OK;
     });
@@ -468,7 +476,7 @@ int bs_autotune(bs_ctx *c, int k, bs_dtype dt, void *stream, int *mode_out, floa
         const int saved = c->hx_mode;
         int best = 1;
         float best_ms = 1e30f;
-        for (int mode = 1; mode < 2 + row_variants() + pipe_variants() && rc == BS_OK; ++mode) {
+        for (int mode = 1; mode <= BS_KERNEL_MODES && rc == BS_OK; ++mode) {
             c->hx_mode = mode;
             rc = launch_hx(c, x, y, k, dt, stream, c->err);       // warm-up
             if (rc) break;
@@ -557,6 +565,9 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
             for (size_t k = 0; k < T.pe.cls_ent.size(); ++k) { tmp.push_back(T.pe.cls_ent[k]); tmp.push_back(T.pe.cls_sinfo[k]); }
             use(tmp.data(), tmp.size() * 8);
         } else if (s == "ww_off") use(T.ww_off.data(), T.ww_off.size() * 8);
+        else if (s == "core_units") use(T.cunits.data(), T.cunits.size() * sizeof(CoreUnit));
+        else if (s == "core_src") use(T.csrc.data(), T.csrc.size() * sizeof(CoreSrc));
+        else if (s == "wc") use(T.wc.data(), T.wc.size() * 8);
         else if (s == "n1e_base") {
             for (size_t k = 0; k < T.n1e_col.size(); ++k) { tmp.push_back(T.n1e_col[k]); tmp.push_back(T.n1e_slice[k]); }
             use(tmp.data(), tmp.size() * 8);

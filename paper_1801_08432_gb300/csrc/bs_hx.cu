@@ -169,6 +169,8 @@ cudaError_t launch_hx_row(const bs_ctx *c, const void *x, void *y, int k, bs_dty
 
 cudaError_t launch_hx_pipe(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
                            bool &used);
+cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
+                           bool &used);
 
 static int kslot(int k)
 {
@@ -192,7 +194,10 @@ int launch_hx(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, void 
         e = launch_hx_pipe(c, x, y, k, dt, s, 0, used);
         if (!used) mode = 2;
     }
-    if (e == cudaSuccess && !used && mode >= 2 + R) e = launch_hx_pipe(c, x, y, k, dt, s, mode - 2 - R, used);
+    const int P = pipe_variants();
+    if (e == cudaSuccess && !used && mode >= 2 + R + P) e = launch_hx_core(c, x, y, k, dt, s, mode - 2 - R - P, used);
+    if (e == cudaSuccess && !used && mode >= 2 + R && mode < 2 + R + P)
+        e = launch_hx_pipe(c, x, y, k, dt, s, mode - 2 - R, used);
     if (e == cudaSuccess && !used && mode >= 2 && mode < 2 + R) e = launch_hx_row(c, x, y, k, dt, s, mode - 2, used);
     if (e == cudaSuccess && !used) {
         if (dt == BS_F64) {

@@ -24,143 +24,15 @@
 #include <cuda_runtime.h>
 
 #include "bs_internal.h"
+#include "bs_tma.cuh"
 
 namespace bs {
 
+using namespace tma;
+
 namespace {
 
-constexpr uint32_t kPipeWaitLimit = 1u << 22;
 constexpr int kPipeMaxList = 16;
-
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bar_init(uint32_t b, uint32_t n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(b), "r"(n) : "memory");
-}
-
-__device__ __forceinline__ void bar_expect_tx(uint32_t b, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(b), "r"(bytes) : "memory");
-}
-
-__device__ __forceinline__ void bar_arrive(uint32_t b)
-{
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(b) : "memory");
-}
-
-__device__ __forceinline__ bool bar_try(uint32_t b, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(b), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// bounded wait; true if it expired
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity)
-{
-    uint32_t spins = 0;
-    while (!bar_try(b, parity))
-        if (++spins > kPipeWaitLimit) return true;
-    return false;
-}
-
-__device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t b)
-{
-    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
-                 "l"(src), "r"(bytes), "r"(b)
-                 : "memory");
-}
-
-// K values of element jn of a staged row.  32- and 64-byte elements are read
-// in 16-byte chunks starting at chunk `rot` (fixed per lane) so that the
-// first load of a quarter warp spreads over the bank groups; the registers
-// then hold the values rotated by `rot` and prot_fix() restores the order of
-// a finished sum.
-template <typename T, int K>
-__device__ __forceinline__ void pld(const T *row, int jn, int rot, T (&r)[K])
-{
-    constexpr int E = K * (int)sizeof(T);
-    if constexpr (E == 32 || E == 64) {
-        constexpr int NC = E / 16, W = 16 / (int)sizeof(T);
-        const char *p = reinterpret_cast<const char *>(row) + (size_t)jn * E;
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-            const float4 q = *reinterpret_cast<const float4 *>(p + 16 * ((c + rot) & (NC - 1)));
-            if constexpr (sizeof(T) == 4) {
-                r[4 * c] = q.x; r[4 * c + 1] = q.y; r[4 * c + 2] = q.z; r[4 * c + 3] = q.w;
-            } else {
-                const double2 d = *reinterpret_cast<const double2 *>(&q);
-                r[W * c] = d.x; r[W * c + 1] = d.y;
-            }
-        }
-    } else if constexpr (E == 16) {
-        const float4 q = *reinterpret_cast<const float4 *>(row + (size_t)jn * K);
-        if constexpr (sizeof(T) == 4) {
-            r[0] = q.x; r[1] = q.y; r[2] = q.z; r[3] = q.w;
-        } else {
-            const double2 d = *reinterpret_cast<const double2 *>(&q);
-            r[0] = d.x; r[1] = d.y;
-        }
-    } else if constexpr (E == 8 && sizeof(T) == 4) {
-        const float2 q = *reinterpret_cast<const float2 *>(row + (size_t)jn * K);
-        r[0] = q.x; r[1] = q.y;
-    } else {
-        r[0] = row[jn];
-    }
-}
-
-template <typename T, int K>
-__device__ __forceinline__ int prot(int lane)
-{
-    constexpr int E = K * (int)sizeof(T);
-    return E == 32 ? (lane & 1) : E == 64 ? (lane & 3) : 0;
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void prot_fix(T (&r)[K], int rot)
-{
-    constexpr int E = K * (int)sizeof(T);
-    if constexpr (E == 32 || E == 64) {
-        constexpr int NC = E / 16, W = 16 / (int)sizeof(T);
-        T t[K];
-#pragma unroll
-        for (int i = 0; i < K; ++i) t[i] = r[i];
-#pragma unroll
-        for (int j = 0; j < NC; ++j)
-#pragma unroll
-            for (int w = 0; w < W; ++w) {
-                T v = t[w];
-#pragma unroll
-                for (int c = 1; c < NC; ++c) v = (((c + rot) & (NC - 1)) == j) ? t[W * c + w] : v;
-                r[W * j + w] = v;
-            }
-    }
-}
-
-template <typename T, int K>
-__device__ __forceinline__ void pst(T *p, const T (&r)[K])
-{
-    if constexpr (sizeof(T) * K >= 16) {
-        constexpr int W = 16 / sizeof(T);
-#pragma unroll
-        for (int c = 0; c < K; c += W) {
-            if constexpr (sizeof(T) == 4) *reinterpret_cast<float4 *>(p + c) = make_float4(r[c], r[c + 1], r[c + 2], r[c + 3]);
-            else *reinterpret_cast<double2 *>(p + c) = make_double2(r[c], r[c + 1]);
-        }
-    } else if constexpr (sizeof(T) == 4 && K == 2) {
-        *reinterpret_cast<float2 *>(p) = make_float2(r[0], r[1]);
-    } else {
-#pragma unroll
-        for (int c = 0; c < K; ++c) p[c] = r[c];
-    }
-}
 
 }  // namespace
 
@@ -183,6 +55,9 @@ struct PipeArgs {
     int row_stride;   // elements per staged row
     int wrow;         // elements per signed W row (2 * wsign)
     int slot_elems;   // elements per slot: uc rows, then uc W rows
+    int skip_pn;      // 1: pn chunks are left out (the core-grouped kernel computed them) ...
+    int nz;           // ... and these partial vectors are added at the end
+    int64_t part_stride;
 };
 
 // One step of a row's chunk sequence: nn (own row), pp chunks, pn chunks.
@@ -215,6 +90,10 @@ __device__ __forceinline__ PChunk pnext(PStream &s, const PipeArgs &A, const Dev
             s.e += cu;
             return c;
         }
+        if (A.skip_pn) {
+            s.kind = 3;
+            return PChunk{3, 0, 0, 0};
+        }
         s.kind = 2;
         s.L = D.link_begin - 1;
         s.e = s.e1 = 0;
@@ -241,7 +120,7 @@ template <typename T, int K, int NW, int CPT>
 __global__ void __launch_bounds__((NW + 1) * 32, NW <= 8 ? 2 : 1) hx_pipe_kernel(PipeArgs A, const T *__restrict__ pp_coef,
                                                                 const T *__restrict__ nn_coef,
                                                                 const T *__restrict__ ww, const T *__restrict__ x,
-                                                                T *__restrict__ y)
+                                                                T *__restrict__ y, const T *__restrict__ part)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     T *slots = reinterpret_cast<T *>(smem);
@@ -419,7 +298,15 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW <= 8 ? 2 : 1) hx_pipe_kernel
     for (int j = 0; j < CPT; ++j) {
         if (col[j] < 0) continue;
         prot_fix<T, K>(acc[j], rot);
-        pst<T, K>(y + (D.off + (int64_t)row * nN + col[j]) * K, acc[j]);
+        const int64_t at = (D.off + (int64_t)row * nN + col[j]) * K;
+        for (int t = 0; t < A.nz; ++t) {
+            // partial sums of the core-grouped pn kernel, added in a fixed order
+            T pv[K];
+            pld<T, K>(part + t * A.part_stride + at, 0, 0, pv);
+#pragma unroll
+            for (int q = 0; q < K; ++q) acc[j][q] += pv[q];
+        }
+        pst<T, K>(y + at, acc[j]);
     }
 }
 
@@ -432,7 +319,7 @@ struct PipeVariant {
 
 template <typename T, int K, int NW, int CPT>
 cudaError_t launch_pipe_t(const Device &Dv, const DevCoefs<T> &C, const T *ww, const T *nn_coef, const T *x, T *y,
-                          cudaStream_t s, int S, size_t target, bool &used)
+                          cudaStream_t s, int S, size_t target, bool &used, const T *part, int nz, int64_t dim)
 {
     const size_t es = sizeof(T);
     const int row_elems = Dv.max_nN * K;
@@ -445,7 +332,7 @@ cudaError_t launch_pipe_t(const Device &Dv, const DevCoefs<T> &C, const T *ww, c
     if (uc < 1) uc = (int)((hard > bars ? hard - bars : 0) / ((size_t)S * per_u));
     // TMA rows need 16-byte elements (k values of one basis state)
     used = uc >= 1 && (size_t)NW * CPT * 32 >= (size_t)Dv.max_nN && (K * es) % 16 == 0;
-    if (!used) return cudaSuccess;
+    if (!used || !x) return cudaSuccess;   // x == nullptr: only report whether the variant fits
     uc = std::min(uc, std::max(1, std::max(Dv.max_pu, 1)));
     uc = std::min(uc, 8);
     const int slot_elems = uc * row_stride + uc * wrow;
@@ -454,8 +341,9 @@ cudaError_t launch_pipe_t(const Device &Dv, const DevCoefs<T> &C, const T *ww, c
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     PipeArgs A{Dv.rtasks, Dv.blocks, Dv.links, Dv.pp_ptr, Dv.pp_src, Dv.p1_ptr, Dv.p1_ent, Dv.pe_perm, Dv.pe_sinfo,
-               Dv.pe_ent, Dv.pe_nn_src, Dv.pe_nn_sinfo, Dv.err, S, uc, row_stride, wrow, slot_elems};
-    kern<<<Dv.nrtasks, (NW + 1) * 32, smem, s>>>(A, C.pp_coef, nn_coef, ww, x, y);
+               Dv.pe_ent, Dv.pe_nn_src, Dv.pe_nn_sinfo, Dv.err, S, uc, row_stride, wrow, slot_elems,
+               part ? 1 : 0, part ? nz : 0, dim * K};
+    kern<<<Dv.nrtasks, (NW + 1) * 32, smem, s>>>(A, C.pp_coef, nn_coef, ww, x, y, part);
     return cudaGetLastError();
 }
 
@@ -467,19 +355,39 @@ constexpr int kNumPipe = 5;
 
 template <typename T, int K>
 cudaError_t launch_pipe_k(const Device &Dv, const DevCoefs<T> &C, const T *ww, const T *nn_coef, const T *x, T *y,
-                          cudaStream_t s, int v, bool &used)
+                          cudaStream_t s, int v, bool &used, const T *part = nullptr, int nz = 0, int64_t dim = 0)
 {
     const PipeVariant P = kPipeVariants[v];
-    if (P.nw == 8 && P.cpt == 3) return launch_pipe_t<T, K, 8, 3>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);
-    if (P.nw == 8 && P.cpt == 4) return launch_pipe_t<T, K, 8, 4>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);
-    if (P.nw == 16 && P.cpt == 2) return launch_pipe_t<T, K, 16, 2>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);
-    if (P.nw == 16 && P.cpt == 8) return launch_pipe_t<T, K, 16, 8>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);
-    return launch_pipe_t<T, K, 8, 1>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used);
+    if (P.nw == 8 && P.cpt == 3)
+        return launch_pipe_t<T, K, 8, 3>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
+    if (P.nw == 8 && P.cpt == 4)
+        return launch_pipe_t<T, K, 8, 4>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
+    if (P.nw == 16 && P.cpt == 2)
+        return launch_pipe_t<T, K, 16, 2>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
+    if (P.nw == 16 && P.cpt == 8)
+        return launch_pipe_t<T, K, 16, 8>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
+    return launch_pipe_t<T, K, 8, 1>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
 }
 
 }  // namespace
 
 int pipe_variants() { return kNumPipe; }
+
+// The pipelined kernel without its pn chunks, adding nz partial vectors
+// (FP32, k = 4 or 8) of the core-grouped pn kernel; x == nullptr only checks
+// whether variant v fits.
+cudaError_t launch_hx_pipe_combine(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
+                                   const void *part, int nz, bool &used)
+{
+    const Device &D = c->dev;
+    used = false;
+    if (dt != BS_F32 || (k != 4 && k != 8)) return cudaSuccess;
+    const float *xi = (const float *)x;
+    float *yo = (float *)y;
+    const float *pi = (const float *)part;
+    if (k == 4) return launch_pipe_k<float, 4>(D, D.c32, D.ww32, D.pe_nn_coef32, xi, yo, s, v, used, pi, nz, c->basis.dim);
+    return launch_pipe_k<float, 8>(D, D.c32, D.ww32, D.pe_nn_coef32, xi, yo, s, v, used, pi, nz, c->basis.dim);
+}
 
 // Pipelined kernel, variant v; `used` is false when it does not fit (row too
 // wide for the variant's columns or shared memory).

@@ -136,6 +136,29 @@ struct PermEll {
     std::vector<int64_t> sec_nn_ent, sec_nn_sinfo;
 };
 
+// pn term by (Z-1)-proton cores.  Every proton one-body jump a+_i a_k from
+// SD s into SD r passes through exactly one core c = a_k s (a Z-1 proton SD),
+// with r = a+_i c: a+_i a_k restricted to Z protons is sum_c a+_i|c><c|a_k.
+// A unit is one core c and a chunk of at most 4 states i of one (2m, parity)
+// key; its destination rows r_i = c + i share one proton sector, hence one
+// neutron sector and the same neutron jump lists, so one staged source row
+// c + k and one 16-byte load of the four weights W(i_p j, k l) feed four
+// destination rows.  Each destination row receives one such partial per core
+// (Z of them); they are summed in a fixed order afterwards.
+struct CoreUnit {
+    int dblock;            // destination block
+    int nsrc;              // source slots of the unit
+    int64_t src0;          // first slot in Tables::csrc
+    int drow[4];           // destination proton row (local in the sector), -1 if absent
+    int meta[4];           // rank t of i in r (0..Z-1) | 256 if the sign of a+_i on c is -1
+};
+
+struct CoreSrc {
+    int sblock, srow;      // source block and proton row c + k
+    int link;              // the pn link dst block <- src block (its neutron lists)
+    uint32_t wtab;         // W table (chunk, k) | 1 << 31 if the sign of a_k on c + k is -1
+};
+
 struct Tables {
     LikeJumps pp, nn;
     PermEll pe;                          // pipelined kernel's neutron lists
@@ -152,6 +175,11 @@ struct Tables {
     std::vector<int64_t> links_of_block; // [nblocks+1]
     int64_t n_pp = 0, n_nn = 0, n_p1 = 0, n_n1 = 0;
     double ops_per_vector = 0.0;         // multiply-adds of one H*x (structural)
+    // core-grouped pn term
+    std::vector<CoreUnit> cunits;        // sorted by work, largest first
+    std::vector<CoreSrc> csrc;
+    std::vector<double> wc;              // per (chunk, k): [2 wsign][4] weights W(i_p ., k .), +W then -W
+    int n_wtab = 0;
 };
 
 // ---------------------------------------------------------------- device mirror
@@ -219,6 +247,11 @@ struct Device {
     uint32_t *pe_ent = nullptr;
     double *pe_nn_coef64 = nullptr, *ww64 = nullptr;
     float *pe_nn_coef32 = nullptr, *ww32 = nullptr;
+    // core-grouped pn kernel
+    CoreUnit *cunits = nullptr;
+    CoreSrc *csrc = nullptr;
+    float *wc32 = nullptr;
+    int ncunits = 0, nz = 0;
     std::vector<void *> owned;   // every cudaMalloc above
 };
 
@@ -235,7 +268,10 @@ struct bs_ctx {
     // host-buffer entry point workspace
     void *hx_x = nullptr, *hx_y = nullptr;
     size_t hx_bytes = 0;
-    int hx_mode = 0;         // 0: autotuned, 1: tiled kernel, 2 + v: row kernel variant v
+    int hx_mode = 0;         // 0: autotuned, 1: tiled kernel, 2 + v: row kernel variant v, then pipelined, then core
+    // partial sums of the core-grouped pn kernel: nz x dim x k elements, grown on demand
+    mutable void *core_part = nullptr;
+    mutable size_t core_part_bytes = 0;
     int tuned[2][4] = {};    // autotuned mode per (dtype, k slot); 0 = not tuned
     // the loaded interaction as given (for the parameter derivatives of the adjoint)
     std::vector<double> spe_in;
@@ -263,4 +299,7 @@ int run_backward(bs_ctx *c, const void *x, const void *gy, void *gx, double *gth
 int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
                 bs_lanczos_report *rep);
 int pipe_variants();
+int core_variants();
+// allocates what launch_hx needs for (k, dtype) outside any stream capture
+int prepare_hx(const bs_ctx *ctx, int k, bs_dtype dt, std::string &err);
 }  // namespace bs

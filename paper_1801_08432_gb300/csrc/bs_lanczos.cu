@@ -714,6 +714,11 @@ int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o_in, const void *pivot, doubl
         cudaStream_t s;
         ~Own() { if (s) { cudaStreamSynchronize(s); cudaStreamDestroy(s); } }
     } guard{own};
+    // kernel workspace before any capture (a failure only disables that path)
+    {
+        std::string ignored;
+        (void)prepare_hx(c, o.k, o.dtype, ignored);
+    }
     if (o.dtype == BS_F64) {
         switch (o.k) {
         case 1: return lanczos_run<double, 1>(c, o, pivot, evals, evecs, rep);

@@ -333,6 +333,118 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
     }
 }
 
+
+// Units of the core-grouped pn kernel (see CoreUnit): every (Z-1)-proton core
+// c that some basis SD contains, times every chunk of <= 4 states of one
+// (2m, parity) key.  Sources of a unit: the SDs c + k for every state k not in
+// c whose block is linked to the unit's destination block, ordered by the key
+// of k so that consecutive sources share one link (one set of neutron lists).
+void build_core_units(const Basis &B, const Interaction &I, Tables &T)
+{
+    T.cunits.clear();
+    T.csrc.clear();
+    T.wc.clear();
+    T.n_wtab = 0;
+    const Species &P = B.sp[0];
+    const int ns = (int)B.st.size();
+    if (P.nparticles < 1 || T.links.empty()) return;
+    // keys and chunks
+    std::vector<std::pair<int, int>> keys;
+    std::vector<int> key_of(ns);
+    for (int s = 0; s < ns; ++s) {
+        const std::pair<int, int> kk{B.st[s].twom, B.st[s].par};
+        auto it = std::find(keys.begin(), keys.end(), kk);
+        key_of[s] = (int)(it - keys.begin());
+        if (it == keys.end()) keys.push_back(kk);
+    }
+    std::vector<std::vector<int>> chunks;
+    for (size_t q = 0; q < keys.size(); ++q) {
+        std::vector<int> st;
+        for (int s = 0; s < ns; ++s)
+            if (key_of[s] == (int)q) st.push_back(s);
+        for (size_t a = 0; a < st.size(); a += 4)
+            chunks.emplace_back(st.begin() + (long)a, st.begin() + (long)std::min(st.size(), a + 4));
+    }
+    std::vector<int> by_key(ns);
+    std::iota(by_key.begin(), by_key.end(), 0);
+    std::stable_sort(by_key.begin(), by_key.end(), [&](int a, int b) { return key_of[a] < key_of[b]; });
+    // weights per (chunk, k): row of the pre-signed W table of op a+_i a_k, + variant
+    const size_t ws2 = 2 * (size_t)T.wsign;
+    T.n_wtab = (int)(chunks.size() * (size_t)ns);
+    T.wc.assign((size_t)T.n_wtab * ws2 * 4, 0.0);
+    for (size_t q = 0; q < chunks.size(); ++q)
+        for (int k = 0; k < ns; ++k)
+            for (size_t p = 0; p < chunks[q].size(); ++p) {
+                const int op = chunks[q][p] * ns + k;
+                const int g = I.ops.group_of_op[(size_t)op];
+                if (g < 0 || I.conj_group[(size_t)g] < 0) continue;
+                const size_t row = (size_t)T.ww_off[(size_t)g] + 2 * (size_t)I.ops.local_of_op[(size_t)op] * ws2;
+                double *dst = T.wc.data() + (q * (size_t)ns + (size_t)k) * ws2 * 4;
+                for (size_t idx = 0; idx < ws2; ++idx) dst[idx * 4 + p] = T.ww[row + idx];
+            }
+    // cores
+    std::vector<uint64_t> cores;
+    cores.reserve(P.bits.size() * (size_t)P.nparticles);
+    for (uint64_t r : P.bits)
+        for (int i = 0; i < ns; ++i)
+            if (r >> i & 1) cores.push_back(r & ~(1ULL << i));
+    std::sort(cores.begin(), cores.end());
+    cores.erase(std::unique(cores.begin(), cores.end()), cores.end());
+    auto locate = [&](uint64_t m, int &blk, int &row) {
+        blk = row = -1;
+        auto it = P.index.find(m);
+        if (it == P.index.end()) return;
+        const int sec = P.sec_of_sd[(size_t)it->second];
+        blk = B.block_of_psec[(size_t)sec];
+        row = (int)(it->second - P.sec[(size_t)sec].start);
+    };
+    auto link_of = [&](int d, int s) {
+        for (int64_t l = T.links_of_block[(size_t)d]; l < T.links_of_block[(size_t)d + 1]; ++l)
+            if (T.links[(size_t)l].src_block == s) return (int)l;
+        return -1;
+    };
+    struct U { double cost; CoreUnit u; std::vector<CoreSrc> src; };
+    std::vector<U> units;
+    for (uint64_t c : cores)
+        for (size_t q = 0; q < chunks.size(); ++q) {
+            U x;
+            x.u.dblock = -1;
+            for (int p = 0; p < 4; ++p) { x.u.drow[p] = -1; x.u.meta[p] = 0; }
+            for (size_t p = 0; p < chunks[q].size(); ++p) {
+                const int i = chunks[q][p];
+                if (c >> i & 1) continue;
+                int blk, row;
+                locate(c | (1ULL << i), blk, row);
+                if (blk < 0) continue;
+                x.u.dblock = blk;
+                x.u.drow[p] = row;
+                x.u.meta[p] = __builtin_popcountll(c & ((1ULL << i) - 1ULL)) | (sign_below(c, i) < 0 ? 256 : 0);
+            }
+            if (x.u.dblock < 0) continue;
+            const int i0 = chunks[q][0];
+            for (int k : by_key) {
+                if (c >> k & 1) continue;
+                const int g = I.ops.group_of_op[(size_t)(i0 * ns + k)];
+                if (g < 0 || I.conj_group[(size_t)g] < 0) continue;
+                int blk, row;
+                locate(c | (1ULL << k), blk, row);
+                if (blk < 0) continue;
+                const int l = link_of(x.u.dblock, blk);
+                if (l < 0) continue;
+                x.src.push_back(CoreSrc{blk, row, l,
+                                        (uint32_t)(q * (size_t)ns + (size_t)k) | (sign_below(c, k) < 0 ? 0x80000000u : 0u)});
+            }
+            x.u.nsrc = (int)x.src.size();
+            x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)x.u.dblock].nN;
+            units.push_back(std::move(x));
+        }
+    std::stable_sort(units.begin(), units.end(), [](const U &a, const U &b) { return a.cost > b.cost; });
+    for (U &x : units) {
+        x.u.src0 = (int64_t)T.csrc.size();
+        T.csrc.insert(T.csrc.end(), x.src.begin(), x.src.end());
+        T.cunits.push_back(x.u);
+    }
+}
 }  // namespace
 
 int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err)
@@ -440,6 +552,7 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
         ops += (double)(T.nn.ptr[NS.start + NS.count] - T.nn.ptr[NS.start]) * (double)D.nP;
     }
     T.ops_per_vector = ops;
+    build_core_units(B, I, T);
     return BS_OK;
 }
 

@@ -163,16 +163,17 @@ def test_row_and_tiled_kernels_agree_with_oracle(case, k):
     c, o = setup(*case)
     x = I.random_block(o.dim, k, seed=30 + k)
     ref = o.spmv(x)
-    for mode in list(range(1, 11)) + [0]:
+    for mode in list(range(1, N.KERNEL_MODES + 1)) + [0]:
         c.set_kernel(mode)
         y = gpu_apply(c, x, k, N.BS_F64)
         c.sync_status()
         assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref)), mode
     c.set_kernel(0)
     xf = x.astype(np.float32)
-    for mode in range(1, 11):
+    for mode in range(1, N.KERNEL_MODES + 1):
         c.set_kernel(mode)
         yf = gpu_apply(c, xf, k, N.BS_F32)
+        c.sync_status()
         bound = abs(o.matrix()) @ np.abs(xf.astype(np.float64))
         assert np.all(np.abs(yf - ref) <= 4e-5 * bound + 1e-6 * np.max(np.abs(ref)))
     c.set_kernel(0)
@@ -183,9 +184,35 @@ def test_autotune_picks_a_valid_mode():
     s = torch.cuda.current_stream().cuda_stream
     for k, dt in ((1, N.BS_F64), (8, N.BS_F32)):
         m = c.autotune(k, dt, s)
-        assert 1 <= m <= 10
+        assert 1 <= m <= N.KERNEL_MODES
     x = I.random_block(o.dim, 8, seed=4).astype(np.float32)
     y = gpu_apply(c, x, 8, N.BS_F32)
     ref = o.spmv(x.astype(np.float64))
     assert np.max(np.abs(y - ref)) <= 1e-5 * np.max(np.abs(ref)) * 10
     c.sync_status()
+
+
+@pytest.mark.parametrize("mode", [11, 12])
+@pytest.mark.parametrize("k", [4, 8])
+def test_pf_4p4n_core_grouped_modes(mode, k):
+    """The core-grouped pn path (FP32, k = 4, 8) at the benchmark size: sampled
+    rows against the oracle, bit-identical repeats, and agreement with the
+    pipelined kernel to FP32 rounding."""
+    c, o = setup("pf", 4, 4, 0)
+    x = I.random_block(o.dim, k, seed=23).astype(np.float32)
+    c.set_kernel(mode)
+    try:
+        y = gpu_apply(c, x, k, N.BS_F32)
+        y2 = gpu_apply(c, x, k, N.BS_F32)
+        c.sync_status()
+        c.set_kernel(6)
+        yp = gpu_apply(c, x, k, N.BS_F32)
+    finally:
+        c.set_kernel(0)
+    assert np.array_equal(y, y2)
+    rows = _sample_rows(o, 4000, 3)
+    x64 = x.astype(np.float64)
+    ref = o.apply_rows(rows, x64)
+    bound = o.apply_rows(rows, np.abs(x64), absval=True)
+    assert np.all(np.abs(y[rows] - ref) <= 4e-5 * bound + 1e-30)
+    assert np.max(np.abs(y - yp)) <= 1e-5 * np.max(np.abs(yp))

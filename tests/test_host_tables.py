@@ -335,3 +335,143 @@ def test_pipe_tables_reproduce_oracle_matrix(name, Z, Nn, twoM):
     y_ref = o.spmv(x)
     y = pipe_tables_matvec(c, x)
     assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
+
+
+CORE_UNIT = np.dtype([("dblock", np.int32), ("nsrc", np.int32), ("src0", np.int64),
+                      ("drow", np.int32, 4), ("meta", np.int32, 4)])
+CORE_SRC = np.dtype([("sblock", np.int32), ("srow", np.int32), ("link", np.int32), ("wtab", np.uint32)])
+
+
+def core_tables_matvec(c, x, Z):
+    """y = H x with the pn term taken from the core-grouped tables: one partial
+    vector per rank t of the removed proton state, summed at the end; the
+    like-particle terms from the pipelined kernel's tables.  Test-side numpy.
+    Also returns how often each (row, t) slot of the partial vectors was written."""
+    B = c.export_basis()
+    blocks = B["blocks"]
+    nsec = len(B["n_sec"])
+    ws = int(c.table("stats", np.int64)[7])
+    base = c.table("pe_base", np.int64)
+    sec_base = base[:3 * nsec].reshape(-1, 3)
+    cls_base = base[3 * nsec:].reshape(-1, 2)
+    perm = c.table("pe_perm", np.int32)
+    sinfo = c.table("pe_sinfo", np.int32)
+    ent = c.table("pe_ent", np.uint32)
+    links = c.table("links", np.int64).reshape(-1, 6)
+    units = np.frombuffer(c.table("core_units", np.uint8).tobytes(), dtype=CORE_UNIT)
+    srcs = np.frombuffer(c.table("core_src", np.uint8).tobytes(), dtype=CORE_SRC)
+    wc = c.table("wc", np.float64).reshape(-1, 2 * ws, 4)
+    dim = len(x)
+    part = np.zeros((Z, dim))
+    written = np.zeros((Z, dim), dtype=np.int64)
+
+    def blk(b):
+        ps, ns_, off = blocks[b]
+        return int(off), int(B["p_sec"][ps][3]), int(ns_), int(B["n_sec"][ns_][3])
+
+    for u in units:
+        offd, nPd, nsd, nNd = blk(u["dblock"])
+        acc = np.zeros((4, nNd))
+        po = sec_base[nsd][0]
+        for q in range(u["nsrc"]):
+            sb, srow, link, wt = srcs[u["src0"] + q]
+            offs, _, _, nNs = blk(sb)
+            xs = x[offs + srow * nNs: offs + (srow + 1) * nNs]
+            flip = ws if int(wt) >> 31 else 0
+            W = wc[int(wt) & 0x7FFFFFFF]
+            ce, cs = cls_base[links[link][3]]
+            for p in range(nNd):
+                col = perm[po + p]
+                o, lmax = sinfo[cs + 2 * (p // 32)], sinfo[cs + 2 * (p // 32) + 1]
+                es = ent[ce + o + 32 * np.arange(lmax) + p % 32].astype(np.int64)
+                acc[:, col] += W[(es >> 16) ^ flip].T @ xs[es & 0xFFFF]
+        for p4 in range(4):
+            r = u["drow"][p4]
+            if r < 0:
+                continue
+            t, sg = u["meta"][p4] & 255, (-1.0 if u["meta"][p4] & 256 else 1.0)
+            part[t, offd + r * nNd: offd + (r + 1) * nNd] = sg * acc[p4]
+            written[t, offd + r * nNd: offd + (r + 1) * nNd] += 1
+    # like-particle terms (pp by rows, nn by the sector's lists)
+    y = np.zeros_like(x)
+    pp_ptr, pp_src, pp_c = c.table("pp_ptr", np.int64), c.table("pp_src", np.int32), c.table("pp_coef", np.float64)
+    nsrc_, ncoef, nsinfo = c.table("pe_nn_src", np.int32), c.table("pe_nn_coef", np.float64), c.table("pe_nn_sinfo", np.int32)
+    for b in range(len(blocks)):
+        ps, ns_, off = blocks[b]
+        p0, nP, nN = int(B["p_sec"][ps][2]), int(B["p_sec"][ps][3]), int(B["n_sec"][ns_][3])
+        X = x[off:off + nP * nN].reshape(nP, nN)
+        Y = y[off:off + nP * nN].reshape(nP, nN)
+        for r in range(nP):
+            for e in range(pp_ptr[p0 + r], pp_ptr[p0 + r + 1]):
+                Y[r] += pp_c[e] * X[pp_src[e]]
+        po, ne0, ns0 = sec_base[ns_]
+        for p in range(nN):
+            col = perm[po + p]
+            o, lmax = nsinfo[ns0 + 2 * (p // 32)], nsinfo[ns0 + 2 * (p // 32) + 1]
+            idx = ne0 + o + 32 * np.arange(lmax) + p % 32
+            Y[:, col] += X[:, nsrc_[idx]] @ ncoef[idx]
+    for t in range(Z):
+        y += part[t]
+    return y, written
+
+
+@pytest.mark.parametrize("name,Z,Nn,twoM", [("sd", 2, 2, 0), ("sd", 3, 2, 1), ("sd", 1, 1, 0), ("sd", 1, 3, 0),
+                                            ("pf", 2, 2, 2), ("p", 2, 2, 2), ("p", 3, 3, 0)])
+def test_core_tables_reproduce_oracle_matrix(name, Z, Nn, twoM):
+    """The pn term regrouped by (Z-1)-proton cores: every proton one-body jump
+    belongs to exactly one core, every destination row gets exactly one partial
+    per rank t, and the sum reproduces the oracle's H x."""
+    orbits, spe, tb = I.space(name)
+    o = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
+    c = host_ctx(name, Z, Nn, twoM)
+    x = I.random_block(o.dim, 1, seed=11)[:, 0]
+    y_ref = o.spmv(x)
+    y, written = core_tables_matvec(c, x, Z)
+    assert np.all(written == 1)
+    assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
+
+
+def test_core_units_structure():
+    """Each unit: one core c (Z-1 states) shared by its destination rows and
+    sources; destination states of one (2m, parity); the stored rank t and the
+    fermion signs of a+_i on c and of a_k on c + k, recomputed from bitmasks."""
+    name, Z, Nn = "sd", 3, 3
+    c = host_ctx(name, Z, Nn, 2)
+    B = c.export_basis()
+    pbits = B["p_bits"]
+    units = np.frombuffer(c.table("core_units", np.uint8).tobytes(), dtype=CORE_UNIT)
+    srcs = np.frombuffer(c.table("core_src", np.uint8).tobytes(), dtype=CORE_SRC)
+    orbits, _, _ = I.space(name)
+    twom = [tm for o_ in orbits for tm in range(-o_.twoj, o_.twoj + 1, 2)]
+    ns = len(twom)
+
+    def sd_bits(blk, row):
+        ps = B["blocks"][blk][0]
+        return int(pbits[B["p_sec"][ps][2] + row])
+
+    def below(m, s):
+        return -1 if bin(m & ((1 << s) - 1)).count("1") % 2 else 1
+
+    for u in units:
+        cores, keys = set(), set()
+        for p in range(4):
+            if u["drow"][p] < 0:
+                continue
+            r = sd_bits(u["dblock"], u["drow"][p])
+            t = u["meta"][p] & 255
+            i = [s for s in range(ns) if r >> s & 1][t]
+            core = r & ~(1 << i)
+            cores.add(core)
+            keys.add(twom[i])
+            assert (u["meta"][p] & 256 != 0) == (below(core, i) < 0)
+        assert len(cores) == 1 and len(keys) == 1
+        core = cores.pop()
+        assert bin(core).count("1") == Z - 1
+        for q in range(u["nsrc"]):
+            sb, srow, link, wt = srcs[u["src0"] + q]
+            s = sd_bits(sb, srow)
+            k_bits = s & ~core
+            assert s & core == core and bin(k_bits).count("1") == 1
+            k = k_bits.bit_length() - 1
+            assert (int(wt) & 0x7FFFFFFF) % ns == k
+            assert ((int(wt) >> 31) != 0) == (below(core, k) < 0)
