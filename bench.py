@@ -193,6 +193,13 @@ KERNEL_SOURCES = {1: "bs_hx.cu", 2: "bs_hx_row.cu", 3: "bs_hx_row.cu", 4: "bs_hx
 PROFILES = {1: "hx_fused_pf4p4n_k8.md", 2: "hx_row_pf4p4n_k8.md", 6: "hx_pipe_pf4p4n_k8.md"}
 
 
+def launches_per_product(mode):
+    """Kernels one H x launches in a kernel mode: the core-grouped modes run the
+    pn kernel (and in 13, 14 the pp kernel), the like-particle kernel and the
+    ordered sum of the partial vectors; every other mode is one kernel."""
+    return {11: 3, 12: 3, 13: 4, 14: 4}.get(mode, 1)
+
+
 def traffic_from_profile(k, mode):
     """DRAM bytes per launch from the committed ncu summary of the kernel mode
     the bench timed, if it was taken on the current kernel source; else None."""
@@ -349,7 +356,7 @@ def ours(args):
                         "ms_per_mode_f32": {str(k): v for k, v in mode_ms.items()}, "ms_per_mode_f64_k1": ms64modes},
         "e2e": {"value": world * args.steps * kbest / e2e_max, "unit": UNIT,
                 "h2d_bytes_per_step": dim * kbest * 4, "d2h_bytes_per_step": dim * kbest * 4},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_product(args.mode or modes.get(kbest, 0)),
         "clocks": clocks,
     }
     if not args.no_lanczos:

@@ -257,14 +257,18 @@ int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, do
  * warps, columns per thread, ring depth, shared-memory budget) of the
  * pipelined kernel (a producer warp fills a ring of shared-memory slots by
  * TMA, consumer warps keep their columns' sums in registers; needs k values
- * of 16 bytes or more per basis state); 11..12 = variants (consumer warps,
- * CTAs per SM) of the core-grouped path for FP32 with k = 4 or 8: a
- * persistent kernel computes the pn term per (Z-1)-proton core (up to four
- * destination rows per staged source row) into Z partial vectors, then the
- * pipelined kernel adds the like-particle terms and the partials in a fixed
- * order (workspace: Z x dim x k floats, allocated on first use, or by
- * bs_lanczos before it captures a graph; a first call inside a stream capture
- * without it falls back to the pipelined kernel).  A mode that does not fit
+ * of 16 bytes or more per basis state); 11..14 = the core-grouped path for
+ * FP32 with k = 4 or 8: a persistent kernel computes the pn term per
+ * (Z-1)-proton core (up to four destination rows per staged source row) into
+ * Z partial vectors (11: 18 consumer warps, 12: 10); in 11, 12 the pipelined
+ * kernel computes the like-particle terms into one more; in 13, 14 a second
+ * persistent kernel computes the pp two-body term per (Z-2)-proton core into
+ * C(Z,2) more and a row-tile kernel (13: 4 rows, 14: 2 rows per CTA) the nn
+ * term and the proton single-particle energies into one more; a last kernel
+ * sums the partial vectors in a fixed order (workspace: up to
+ * (Z + C(Z,2) + 1) x dim x k floats, allocated on first use, or by
+ * bs_lanczos before it captures a graph; a first call inside a stream
+ * capture without it falls back to the pipelined kernel).  A mode that does not fit
  * the basis falls back to the tiled kernel.  0 (default) = the mode bs_autotune picked
  * for the call's (k, dtype), else the first pipelined variant, else the first
  * row variant.  All modes give the same result up to summation order.
@@ -272,7 +276,7 @@ int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, do
 int bs_set_kernel(bs_ctx *ctx, int mode);
 
 /* Number of selectable H x kernel modes (1..BS_KERNEL_MODES). */
-#define BS_KERNEL_MODES 12
+#define BS_KERNEL_MODES 14
 
 /* Times every kernel mode 1..BS_KERNEL_MODES for (k, dtype) on `stream` on
  * scratch vectors it allocates and frees (2 x dim x k elements), and records

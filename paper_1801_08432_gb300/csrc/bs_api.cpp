@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <numeric>
 #include <cstring>
 #include <new>
 
@@ -231,6 +232,27 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
     if ((rc = put(D, D.csrc, T.csrc.data(), T.csrc.size(), err))) return rc;
     f = cast<float>(T.wc);
     if ((rc = put(D, D.wc32, f.data(), f.size(), err))) return rc;
+    // core-grouped pp kernel
+    D.nppunits = (int)T.ppunits.size();
+    D.nzpp = D.nppunits ? B.sp[0].nparticles * (B.sp[0].nparticles - 1) / 2 : 0;
+    if ((rc = put(D, D.ppunits, T.ppunits.data(), T.ppunits.size(), err))) return rc;
+    if ((rc = put(D, D.pps_row, T.pps_row.data(), T.pps_row.size(), err))) return rc;
+    f = cast<float>(T.pps_w);
+    if ((rc = put(D, D.pps_w32, f.data(), f.size(), err))) return rc;
+    f = cast<float>(T.pdiag);
+    if ((rc = put(D, D.pdiag32, f.data(), f.size(), err))) return rc;
+    for (int R : {2, 4}) {
+        // row tiles of the neutron like-particle kernel, widest sectors first
+        std::vector<int2> nt;
+        std::vector<size_t> ord(B.blocks.size());
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](size_t a, size_t b2) { return B.blocks[a].nN > B.blocks[b2].nN; });
+        for (size_t b2 : ord)
+            for (int64_t r = 0; r < B.blocks[b2].nP; r += R) nt.push_back(make_int2((int)b2, (int)r));
+        int2 *&dst = R == 2 ? D.nntasks2 : D.nntasks4;
+        (R == 2 ? D.nnntasks2 : D.nnntasks4) = (int)nt.size();
+        if ((rc = put(D, dst, nt.data(), nt.size(), err))) return rc;
+    }
     f = cast<float>(T.ww);
     if ((rc = put(D, D.ww32, f.data(), f.size(), err))) return rc;
     return BS_OK;
@@ -568,6 +590,10 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
         else if (s == "core_units") use(T.cunits.data(), T.cunits.size() * sizeof(CoreUnit));
         else if (s == "core_src") use(T.csrc.data(), T.csrc.size() * sizeof(CoreSrc));
         else if (s == "wc") use(T.wc.data(), T.wc.size() * 8);
+        else if (s == "pp_units") use(T.ppunits.data(), T.ppunits.size() * sizeof(PPUnit));
+        else if (s == "pps_row") use(T.pps_row.data(), T.pps_row.size() * 4);
+        else if (s == "pps_w") use(T.pps_w.data(), T.pps_w.size() * 8);
+        else if (s == "pdiag") use(T.pdiag.data(), T.pdiag.size() * 8);
         else if (s == "n1e_base") {
             for (size_t k = 0; k < T.n1e_col.size(); ++k) { tmp.push_back(T.n1e_col[k]); tmp.push_back(T.n1e_slice[k]); }
             use(tmp.data(), tmp.size() * 8);

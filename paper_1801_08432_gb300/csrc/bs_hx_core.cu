@@ -34,7 +34,7 @@ namespace bs {
 using namespace tma;
 
 cudaError_t launch_hx_pipe_combine(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
-                                   const void *part, int nz, bool &used);
+                                   const void *part, int nz, bool skip_pp, bool &used);
 
 namespace {
 
@@ -208,13 +208,264 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     }
 }
 
+struct PPArgs {
+    const PPUnit *units;
+    const int32_t *srow;
+    const float4 *w;
+    const DevBlock *blocks;
+    int *err;
+    int nunits;
+    int S;
+    int row_stride;
+    int64_t part_stride;
+};
+
+// pp term by (Z-2)-proton cores.  The same ring as above, one source row per
+// slot; each thread owns one destination column in natural order (so a
+// quarter warp reads eight consecutive 32-byte elements: conflict-free with
+// the lane rotation (lane >> 2) & 1) and applies the slot's four CTA-uniform
+// weights: 4 k multiply-adds per element read.
+template <int K, int NW, int MINB>
+__global__ void __launch_bounds__((NW + 1) * 32, MINB)
+    hx_ppcore_kernel(PPArgs A, const float *__restrict__ x, float *__restrict__ part)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *slots = reinterpret_cast<float *>(smem);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(slots + (size_t)A.S * A.row_stride);
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + A.S);
+    constexpr int C = NW * 32;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < A.S; ++s) {
+            bar_init(full0 + 8u * s, 1);
+            bar_init(empty0 + 8u * s, NW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    if (warp == NW) {
+        if (lane != 0) return;
+        int c = 0;
+        for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
+            const PPUnit U = A.units[u];
+            const DevBlock D = A.blocks[U.dblock];
+            const int ntile = (D.nN + C - 1) / C;
+            const uint32_t bytes = (uint32_t)(D.nN * K * (int)sizeof(float));
+            for (int tile = 0; tile < ntile; ++tile)
+                for (int q = 0; q < U.nsrc; ++q, ++c) {
+                    const int s = c % A.S;
+                    const int round = c / A.S;
+                    if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) {
+                        atomicExch(A.err, BS_ETIMEOUT);
+                        return;
+                    }
+                    const uint32_t fb = full0 + 8u * s;
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_expect_tx(fb, bytes);
+                    bulk_copy(su32(slots + (size_t)s * A.row_stride),
+                              x + (D.off + (int64_t)A.srow[U.src0 + q] * D.nN) * K, bytes, fb);
+                }
+        }
+        return;
+    }
+
+    constexpr int E = K * (int)sizeof(float);
+    const int rot = E == 32 ? ((lane >> 2) & 1) : 0;
+    int c = 0;
+    for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
+        const PPUnit U = A.units[u];
+        const DevBlock D = A.blocks[U.dblock];
+        const int nN = D.nN;
+        const int ntile = (nN + C - 1) / C;
+        for (int tile = 0; tile < ntile; ++tile) {
+            const int col = tile * C + warp * 32 + lane;
+            const bool active = tile * C + warp * 32 < nN;
+            const int cl = col < nN ? col : nN - 1;
+            float acc[4][K];
+#pragma unroll
+            for (int p = 0; p < 4; ++p)
+#pragma unroll
+                for (int q = 0; q < K; ++q) acc[p][q] = 0.0f;
+            for (int q = 0; q < U.nsrc; ++q, ++c) {
+                const int s = c % A.S;
+                const int round = c / A.S;
+                if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)round & 1u))) {
+                    if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
+                    return;
+                }
+                if (active) {
+                    const float4 w = __ldg(A.w + U.src0 + q);
+                    float xv[K];
+                    pld<float, K>(slots + (size_t)s * A.row_stride, cl, rot, xv);
+#pragma unroll
+                    for (int qq = 0; qq < K; ++qq) {
+                        acc[0][qq] = fmaf(w.x, xv[qq], acc[0][qq]);
+                        acc[1][qq] = fmaf(w.y, xv[qq], acc[1][qq]);
+                        acc[2][qq] = fmaf(w.z, xv[qq], acc[2][qq]);
+                        acc[3][qq] = fmaf(w.w, xv[qq], acc[3][qq]);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) bar_arrive(empty0 + 8u * s);
+            }
+            if (col < nN) {
+#pragma unroll
+                for (int p = 0; p < 4; ++p) {
+                    if (U.drow[p] < 0) continue;
+                    prot_fix<float, K>(acc[p], rot);
+                    pst<float, K>(part + (int64_t)U.part[p] * A.part_stride + (D.off + (int64_t)U.drow[p] * nN + col) * K,
+                                  acc[p]);
+                }
+            }
+        }
+    }
+}
+
+struct NNArgs {
+    const int2 *tasks;
+    const DevBlock *blocks;
+    const int32_t *perm;
+    const int32_t *src;
+    const float *coef;
+    const int32_t *sinfo;
+    const float *pdiag;
+    int *err;
+    int row_stride;
+};
+
+// Neutron like-particle term plus the proton single-particle diagonal over a
+// tile of R consecutive proton rows of one block: y[r][n'] = e_p(r) x[r][n'] +
+// sum_v c_v x[r][n_v].  The neutron lists are the same for every proton row,
+// so each thread (one destination column, in the sector's list order) loads
+// an entry once and applies it to the R staged rows.  The R rows arrive by
+// TMA bulk copies on one mbarrier (bounded wait).  Output: partial vector.
+template <int K, int R, int NW, int MINB>
+__global__ void __launch_bounds__(NW * 32, MINB)
+    hx_nn_rows_kernel(NNArgs A, const float *__restrict__ x, float *__restrict__ out)
+{
+    extern __shared__ __align__(128) unsigned char smem[];
+    float *rows = reinterpret_cast<float *>(smem);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(rows + (size_t)R * A.row_stride);
+    const uint32_t b0 = su32(bar);
+    const int2 task = A.tasks[blockIdx.x];
+    const DevBlock D = A.blocks[task.x];
+    const int nN = D.nN;
+    const int r0 = task.y;
+    const int nr = min(R, D.nP - r0);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (threadIdx.x == 0) {
+        bar_init(b0, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const uint32_t bytes = (uint32_t)(nN * K * (int)sizeof(float));
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        bar_expect_tx(b0, bytes * (uint32_t)nr);
+        for (int r = 0; r < nr; ++r)
+            bulk_copy(su32(rows + (size_t)r * A.row_stride), x + (D.off + (int64_t)(r0 + r) * nN) * K, bytes, b0);
+    }
+    float pd[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) pd[r] = r < nr ? A.pdiag[D.p_start + r0 + r] : 0.0f;
+    const int p = warp * 32 + lane;
+    const int sl = warp;
+    const bool active = sl * 32 < nN;   // warp-uniform
+    const int col = p < nN ? A.perm[D.perm_off + p] : -1;
+    int off = 0, lmax = 0;
+    if (active) {
+        off = A.sinfo[D.pe_nn_sinfo + 2 * sl];
+        lmax = A.sinfo[D.pe_nn_sinfo + 2 * sl + 1];
+    }
+    if (__any_sync(0xffffffffu, bar_wait(b0, 0u))) {
+        if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
+        return;
+    }
+    if (!active) return;
+    const int rot = prot<float, K>(lane);
+    float acc[R][K], xv[K];
+    const int cc = col >= 0 ? col : 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        pld<float, K>(rows + (size_t)r * A.row_stride, cc, rot, xv);
+#pragma unroll
+        for (int q = 0; q < K; ++q) acc[r][q] = pd[r] * xv[q];
+    }
+    const int64_t base = D.pe_nn_ent + off + lane;
+#pragma unroll 2
+    for (int v = 0; v < lmax; ++v) {
+        const float c = A.coef[base + 32 * (int64_t)v];
+        const int s = A.src[base + 32 * (int64_t)v];
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            pld<float, K>(rows + (size_t)r * A.row_stride, s, rot, xv);
+#pragma unroll
+            for (int q = 0; q < K; ++q) acc[r][q] = fmaf(c, xv[q], acc[r][q]);
+        }
+    }
+    if (col < 0) return;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        if (r >= nr) break;
+        prot_fix<float, K>(acc[r], rot);
+        pst<float, K>(out + (D.off + (int64_t)(r0 + r) * nN + col) * K, acc[r]);
+    }
+}
+
+// y = sum_t part[t], t = 0..n-1 in order, float4 at a time (the fixed order
+// keeps the product bit-reproducible).
+__global__ void __launch_bounds__(256) hx_sum_partials(const float4 *__restrict__ part, int n, int64_t n4,
+                                                       float4 *__restrict__ y)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n4; e += (int64_t)gridDim.x * blockDim.x) {
+        float4 a = part[e];
+        for (int t = 1; t < n; ++t) {
+            const float4 b = part[t * n4 + e];
+            a.x += b.x;
+            a.y += b.y;
+            a.z += b.z;
+            a.w += b.w;
+        }
+        y[e] = a;
+    }
+}
+
 struct CoreVariant {
     int nw, minb;
     size_t target;   // shared-memory budget per CTA
+    bool pp;         // pp term by (Z-2)-proton cores, nn by row tiles of nn_rows rows
+    int nn_rows;
 };
 
-constexpr CoreVariant kCoreVariants[] = {{18, 1, 200 * 1024}, {10, 2, 105 * 1024}};
-constexpr int kNumCore = 2;
+constexpr CoreVariant kCoreVariants[] = {
+    {18, 1, 200 * 1024, false, 0}, {10, 2, 105 * 1024, false, 0}, {18, 1, 200 * 1024, true, 4}, {18, 1, 200 * 1024, true, 2}};
+constexpr int kNumCore = 4;
+
+template <int K, int R, int MINB>
+cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, bool &used)
+{
+    const Device &Dv = ctx->dev;
+    constexpr int NW = 18;
+    const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
+    const size_t smem = (size_t)R * row_stride * sizeof(float) + 16;
+    used = Dv.max_nN <= NW * 32 && smem <= 200 * 1024;
+    if (!used || !x) return cudaSuccess;
+    auto kern = hx_nn_rows_kernel<K, R, NW, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    NNArgs A{R == 2 ? Dv.nntasks2 : Dv.nntasks4, Dv.blocks, Dv.pe_perm, Dv.pe_nn_src, Dv.pe_nn_coef32, Dv.pe_nn_sinfo,
+             Dv.pdiag32, Dv.err, row_stride};
+    kern<<<R == 2 ? Dv.nnntasks2 : Dv.nnntasks4, NW * 32, smem, s>>>(A, x, out);
+    return cudaGetLastError();
+}
+
+template <int K>
+cudaError_t launch_nn_k(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, int R, bool &used)
+{
+    return R == 2 ? launch_nn_t<K, 2, 2>(ctx, x, out, s, used) : launch_nn_t<K, 4, 1>(ctx, x, out, s, used);
+}
 
 template <int K, int NW, int MINB>
 cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaStream_t s, size_t target, bool &used)
@@ -241,6 +492,29 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     return cudaGetLastError();
 }
 
+template <int K, int NW, int MINB>
+cudaError_t launch_pp_t(const bs_ctx *ctx, const float *x, float *part, cudaStream_t s, size_t target, bool &used)
+{
+    const Device &Dv = ctx->dev;
+    const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
+    const size_t slot_bytes = (size_t)row_stride * sizeof(float) + 16;
+    const int S = (int)std::min<size_t>(8, target / slot_bytes);
+    used = S >= 2;
+    if (!used) return cudaSuccess;
+    const size_t smem = (size_t)S * row_stride * sizeof(float) + 16 * (size_t)S;
+    auto kern = hx_ppcore_kernel<K, NW, MINB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int nsm = 0, per = 0;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, Dv.dev)) != cudaSuccess) return e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (NW + 1) * 32, smem)) != cudaSuccess) return e;
+    const int grid = std::max(1, std::min(Dv.nppunits, nsm * std::max(per, 1)));
+    PPArgs A{Dv.ppunits, Dv.pps_row, reinterpret_cast<const float4 *>(Dv.pps_w32), Dv.blocks, Dv.err,
+             Dv.nppunits, S, row_stride, (int64_t)ctx->basis.dim * K};
+    kern<<<grid, (NW + 1) * 32, smem, s>>>(A, x, part);
+    return cudaGetLastError();
+}
+
 template <int K>
 cudaError_t launch_core_k(const bs_ctx *ctx, const float *x, float *part, cudaStream_t s, int v, bool &used)
 {
@@ -249,7 +523,12 @@ cudaError_t launch_core_k(const bs_ctx *ctx, const float *x, float *part, cudaSt
     return launch_core_t<K, 10, 2>(ctx, x, part, s, P.target, used);
 }
 
-size_t part_bytes(const bs_ctx *c, int k) { return (size_t)c->dev.nz * (size_t)c->basis.dim * (size_t)k * sizeof(float); }
+// partial vectors: Z of the pn kernel, C(Z,2) of the pp kernel, one of the
+// like-particle kernel
+size_t part_bytes(const bs_ctx *c, int k)
+{
+    return (size_t)(c->dev.nz + c->dev.nzpp + 1) * (size_t)c->basis.dim * (size_t)k * sizeof(float);
+}
 
 bool core_applies(const bs_ctx *c, int k, bs_dtype dt)
 {
@@ -294,14 +573,38 @@ cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dt
         std::string err;
         if (cap != cudaStreamCaptureStatusNone || prepare_hx(c, k, dt, err) != BS_OK) return cudaSuccess;
     }
+    const bool pp = kCoreVariants[v].pp;
+    const int R = kCoreVariants[v].nn_rows;
     bool fits = false;
-    cudaError_t e = launch_hx_pipe_combine(c, nullptr, nullptr, k, dt, s, 0, nullptr, c->dev.nz, fits);
+    cudaError_t e = R ? (k == 8 ? launch_nn_k<8>(c, nullptr, nullptr, s, R, fits) : launch_nn_k<4>(c, nullptr, nullptr, s, R, fits))
+                      : launch_hx_pipe_combine(c, nullptr, nullptr, k, dt, s, 0, nullptr, 0, pp, fits);
     if (e != cudaSuccess || !fits) return e;
     float *part = (float *)c->core_part;
-    e = k == 8 ? launch_core_k<8>(c, (const float *)x, part, s, v, used)
-                           : launch_core_k<4>(c, (const float *)x, part, s, v, used);
+    const float *xf = (const float *)x;
+    e = k == 8 ? launch_core_k<8>(c, xf, part, s, v, used) : launch_core_k<4>(c, xf, part, s, v, used);
     if (e != cudaSuccess || !used) return e;
-    return launch_hx_pipe_combine(c, x, y, k, dt, s, 0, part, c->dev.nz, used);
+    int nz = c->dev.nz;
+    if (pp) {
+        if (c->dev.nppunits > 0) {
+            e = k == 8 ? launch_pp_t<8, 18, 1>(c, xf, part, s, kCoreVariants[v].target, used)
+                       : launch_pp_t<4, 18, 1>(c, xf, part, s, kCoreVariants[v].target, used);
+            if (e != cudaSuccess) return e;
+            if (!used) return cudaErrorInvalidConfiguration;   // the pn kernel with the same budget fitted
+        }
+        nz += c->dev.nzpp;
+    }
+    // remaining like-particle terms into partial vector nz, then the ordered sum
+    float *last = part + (size_t)nz * (size_t)c->basis.dim * (size_t)k;
+    e = R ? (k == 8 ? launch_nn_k<8>(c, xf, last, s, R, used) : launch_nn_k<4>(c, xf, last, s, R, used))
+          : launch_hx_pipe_combine(c, x, y, k, dt, s, 0, part, -1 - nz, pp, used);
+    if (e != cudaSuccess || !used) return e;
+    const int64_t n4 = c->basis.dim * k / 4;
+    int nsm = 0;
+    if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->dev.dev)) != cudaSuccess) return e;
+    const int64_t want = (n4 + 255) / 256;
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)nsm * 8));
+    hx_sum_partials<<<grid, 256, 0, s>>>(reinterpret_cast<const float4 *>(part), nz + 1, n4, reinterpret_cast<float4 *>(y));
+    return cudaGetLastError();
 }
 
 }  // namespace bs

@@ -56,7 +56,9 @@ struct PipeArgs {
     int wrow;         // elements per signed W row (2 * wsign)
     int slot_elems;   // elements per slot: uc rows, then uc W rows
     int skip_pn;      // 1: pn chunks are left out (the core-grouped kernel computed them) ...
-    int nz;           // ... and these partial vectors are added at the end
+    int skip_pp;      // 1: pp chunks are left out, the proton single-particle diagonal is added instead ...
+    int nz;           // ... and these partial vectors are added at the end, or
+    int out_slot;     // (>= 0) the row is written to this partial vector instead of y
     int64_t part_stride;
 };
 
@@ -80,7 +82,7 @@ __device__ __forceinline__ PChunk pnext(PStream &s, const PipeArgs &A, const Dev
         s.kind = 1;
         const int g = D.p_start + row;
         s.e = A.pp_ptr[g];
-        s.e1 = A.pp_ptr[g + 1];
+        s.e1 = A.skip_pp ? s.e : A.pp_ptr[g + 1];
         return PChunk{0, -1, 0, 1};
     }
     if (s.kind == 1) {
@@ -120,7 +122,8 @@ template <typename T, int K, int NW, int CPT>
 __global__ void __launch_bounds__((NW + 1) * 32, NW <= 8 ? 2 : 1) hx_pipe_kernel(PipeArgs A, const T *__restrict__ pp_coef,
                                                                 const T *__restrict__ nn_coef,
                                                                 const T *__restrict__ ww, const T *__restrict__ x,
-                                                                T *__restrict__ y, const T *__restrict__ part)
+                                                                T *__restrict__ y, const T *__restrict__ part,
+                                                                const T *__restrict__ pdiag)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     T *slots = reinterpret_cast<T *>(smem);
@@ -212,6 +215,18 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW <= 8 ? 2 : 1) hx_pipe_kernel
         }
         const T *Xs = slots + (size_t)s * A.slot_elems;
         if (ch.kind == 0) {
+            if (A.skip_pp) {
+                // proton single-particle energies of this row (the pp two-body
+                // terms come as partial vectors)
+                const T pd = pdiag[D.p_start + row];
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    if (col[j] < 0) continue;
+                    pld<T, K>(Xs, col[j], rot, xv);
+#pragma unroll
+                    for (int q = 0; q < K; ++q) acc[j][q] = fma(pd, xv[q], acc[j][q]);
+                }
+            }
             // nn: lists in the sector's column order, sliced by 32
 #pragma unroll
             for (int j = 0; j < CPT; ++j) {
@@ -300,13 +315,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW <= 8 ? 2 : 1) hx_pipe_kernel
         prot_fix<T, K>(acc[j], rot);
         const int64_t at = (D.off + (int64_t)row * nN + col[j]) * K;
         for (int t = 0; t < A.nz; ++t) {
-            // partial sums of the core-grouped pn kernel, added in a fixed order
+            // partial sums of the core-grouped kernels, added in a fixed order
             T pv[K];
             pld<T, K>(part + t * A.part_stride + at, 0, 0, pv);
 #pragma unroll
             for (int q = 0; q < K; ++q) acc[j][q] += pv[q];
         }
-        pst<T, K>(y + at, acc[j]);
+        pst<T, K>((A.out_slot >= 0 ? const_cast<T *>(part) + A.out_slot * A.part_stride : y) + at, acc[j]);
     }
 }
 
@@ -319,7 +334,8 @@ struct PipeVariant {
 
 template <typename T, int K, int NW, int CPT>
 cudaError_t launch_pipe_t(const Device &Dv, const DevCoefs<T> &C, const T *ww, const T *nn_coef, const T *x, T *y,
-                          cudaStream_t s, int S, size_t target, bool &used, const T *part, int nz, int64_t dim)
+                          cudaStream_t s, int S, size_t target, bool &used, const T *part, int nz, int64_t dim,
+                          const T *pdiag)
 {
     const size_t es = sizeof(T);
     const int row_elems = Dv.max_nN * K;
@@ -342,8 +358,8 @@ cudaError_t launch_pipe_t(const Device &Dv, const DevCoefs<T> &C, const T *ww, c
     if (e != cudaSuccess) return e;
     PipeArgs A{Dv.rtasks, Dv.blocks, Dv.links, Dv.pp_ptr, Dv.pp_src, Dv.p1_ptr, Dv.p1_ent, Dv.pe_perm, Dv.pe_sinfo,
                Dv.pe_ent, Dv.pe_nn_src, Dv.pe_nn_sinfo, Dv.err, S, uc, row_stride, wrow, slot_elems,
-               part ? 1 : 0, part ? nz : 0, dim * K};
-    kern<<<Dv.nrtasks, (NW + 1) * 32, smem, s>>>(A, C.pp_coef, nn_coef, ww, x, y, part);
+               part ? 1 : 0, pdiag ? 1 : 0, part && nz < 0 ? 0 : (part ? nz : 0), part && nz < 0 ? -nz - 1 : -1, dim * K};
+    kern<<<Dv.nrtasks, (NW + 1) * 32, smem, s>>>(A, C.pp_coef, nn_coef, ww, x, y, part, pdiag);
     return cudaGetLastError();
 }
 
@@ -355,29 +371,32 @@ constexpr int kNumPipe = 5;
 
 template <typename T, int K>
 cudaError_t launch_pipe_k(const Device &Dv, const DevCoefs<T> &C, const T *ww, const T *nn_coef, const T *x, T *y,
-                          cudaStream_t s, int v, bool &used, const T *part = nullptr, int nz = 0, int64_t dim = 0)
+                          cudaStream_t s, int v, bool &used, const T *part = nullptr, int nz = 0, int64_t dim = 0,
+                          const T *pdiag = nullptr)
 {
     const PipeVariant P = kPipeVariants[v];
     if (P.nw == 8 && P.cpt == 3)
-        return launch_pipe_t<T, K, 8, 3>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
+        return launch_pipe_t<T, K, 8, 3>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim, pdiag);
     if (P.nw == 8 && P.cpt == 4)
-        return launch_pipe_t<T, K, 8, 4>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
+        return launch_pipe_t<T, K, 8, 4>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim, pdiag);
     if (P.nw == 16 && P.cpt == 2)
-        return launch_pipe_t<T, K, 16, 2>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
+        return launch_pipe_t<T, K, 16, 2>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim, pdiag);
     if (P.nw == 16 && P.cpt == 8)
-        return launch_pipe_t<T, K, 16, 8>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
-    return launch_pipe_t<T, K, 8, 1>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim);
+        return launch_pipe_t<T, K, 16, 8>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim, pdiag);
+    return launch_pipe_t<T, K, 8, 1>(Dv, C, ww, nn_coef, x, y, s, P.S, P.target, used, part, nz, dim, pdiag);
 }
 
 }  // namespace
 
 int pipe_variants() { return kNumPipe; }
 
-// The pipelined kernel without its pn chunks, adding nz partial vectors
-// (FP32, k = 4 or 8) of the core-grouped pn kernel; x == nullptr only checks
-// whether variant v fits.
+// The pipelined kernel without its pn chunks (and, with skip_pp, without its
+// pp chunks but with the proton single-particle diagonal), adding nz partial
+// vectors (FP32, k = 4 or 8) of the core-grouped kernels; with nz = -1 - t it
+// adds none and writes its rows to partial vector t instead of y.  x ==
+// nullptr only checks whether variant v fits.
 cudaError_t launch_hx_pipe_combine(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
-                                   const void *part, int nz, bool &used)
+                                   const void *part, int nz, bool skip_pp, bool &used)
 {
     const Device &D = c->dev;
     used = false;
@@ -385,8 +404,10 @@ cudaError_t launch_hx_pipe_combine(const bs_ctx *c, const void *x, void *y, int 
     const float *xi = (const float *)x;
     float *yo = (float *)y;
     const float *pi = (const float *)part;
-    if (k == 4) return launch_pipe_k<float, 4>(D, D.c32, D.ww32, D.pe_nn_coef32, xi, yo, s, v, used, pi, nz, c->basis.dim);
-    return launch_pipe_k<float, 8>(D, D.c32, D.ww32, D.pe_nn_coef32, xi, yo, s, v, used, pi, nz, c->basis.dim);
+    const float *pd = skip_pp ? D.pdiag32 : nullptr;
+    if (k == 4)
+        return launch_pipe_k<float, 4>(D, D.c32, D.ww32, D.pe_nn_coef32, xi, yo, s, v, used, pi, nz, c->basis.dim, pd);
+    return launch_pipe_k<float, 8>(D, D.c32, D.ww32, D.pe_nn_coef32, xi, yo, s, v, used, pi, nz, c->basis.dim, pd);
 }
 
 // Pipelined kernel, variant v; `used` is false when it does not fit (row too

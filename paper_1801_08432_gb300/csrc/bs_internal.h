@@ -2,6 +2,8 @@
 // tables, and the device mirror the kernels read.
 #pragma once
 
+#include <vector_types.h>
+
 #include <cstdint>
 #include <string>
 #include <unordered_map>
@@ -159,6 +161,22 @@ struct CoreSrc {
     uint32_t wtab;         // W table (chunk, k) | 1 << 31 if the sign of a_k on c + k is -1
 };
 
+// pp term by (Z-2)-proton cores: a two-body term a+_i a+_j a_l a_k taking
+// SD s to r belongs to exactly one core c2 = s - {k,l} = r - {i,j}.  A unit is
+// one core, one (2M, parity) key of pairs and up to four destination pairs
+// (i,j); its destination rows r_p = c2 + {i_p,j_p} and its sources
+// c2 + {k,l} all lie in one proton sector, so a staged source row serves four
+// destination rows with four CTA-uniform weights (the fermion sign folded in).
+// Row r gets one partial per pair of its states (C(Z,2) of them); the proton
+// single-particle energies are left to a per-row diagonal.
+struct PPUnit {
+    int dblock;
+    int nsrc;
+    int64_t src0;          // first source in Tables::pps_row / pps_w
+    int drow[4];           // destination proton row, -1 if absent
+    int part[4];           // partial vector of the destination row (Z + pair rank)
+};
+
 struct Tables {
     LikeJumps pp, nn;
     PermEll pe;                          // pipelined kernel's neutron lists
@@ -180,6 +198,11 @@ struct Tables {
     std::vector<CoreSrc> csrc;
     std::vector<double> wc;              // per (chunk, k): [2 wsign][4] weights W(i_p ., k .), +W then -W
     int n_wtab = 0;
+    // core-grouped pp term
+    std::vector<PPUnit> ppunits;         // sorted by work, largest first
+    std::vector<int32_t> pps_row;        // per source: proton row c2 + {k,l}
+    std::vector<double> pps_w;           // per source: 4 signed weights
+    std::vector<double> pdiag;           // per proton SD: sum of its single-particle energies
 };
 
 // ---------------------------------------------------------------- device mirror
@@ -252,6 +275,13 @@ struct Device {
     CoreSrc *csrc = nullptr;
     float *wc32 = nullptr;
     int ncunits = 0, nz = 0;
+    PPUnit *ppunits = nullptr;
+    int32_t *pps_row = nullptr;
+    float *pps_w32 = nullptr, *pdiag32 = nullptr;
+    int nppunits = 0, nzpp = 0;
+    // neutron like-particle kernel over tiles of R proton rows (R = 2, 4): (block, first row)
+    int2 *nntasks2 = nullptr, *nntasks4 = nullptr;
+    int nnntasks2 = 0, nnntasks4 = 0;
     std::vector<void *> owned;   // every cudaMalloc above
 };
 

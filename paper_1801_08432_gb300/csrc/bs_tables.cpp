@@ -445,6 +445,108 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
         T.cunits.push_back(x.u);
     }
 }
+
+// Units of the core-grouped pp kernel (see PPUnit) and the per-SD proton
+// single-particle diagonal it leaves out.
+void build_pp_units(const Basis &B, const Interaction &I, Tables &T)
+{
+    T.ppunits.clear();
+    T.pps_row.clear();
+    T.pps_w.clear();
+    const Species &P = B.sp[0];
+    const int ns = (int)B.st.size();
+    const int Z = P.nparticles;
+    T.pdiag.assign(P.bits.size(), 0.0);
+    for (size_t g = 0; g < P.bits.size(); ++g)
+        for (int s = 0; s < ns; ++s)
+            if (P.bits[g] >> s & 1) T.pdiag[g] += I.spe_state[(size_t)s];
+    if (Z < 2) return;
+    std::vector<uint64_t> cores;
+    for (uint64_t r : P.bits)
+        for (int a = 0; a < ns; ++a)
+            if (r >> a & 1)
+                for (int b = a + 1; b < ns; ++b)
+                    if (r >> b & 1) cores.push_back(r & ~(1ULL << a) & ~(1ULL << b));
+    std::sort(cores.begin(), cores.end());
+    cores.erase(std::unique(cores.begin(), cores.end()), cores.end());
+    // rank of pair (a-th, b-th occupied state), a < b, among the C(Z,2) pairs
+    auto pair_rank = [Z](int a, int b) { return a * (2 * Z - a - 1) / 2 + (b - a - 1); };
+    struct U { double cost; PPUnit u; std::vector<int32_t> row; std::vector<double> w; };
+    std::vector<U> units;
+    for (uint64_t c2 : cores)
+        for (const std::vector<int> &keyp : I.pairs_by_key) {
+            std::vector<int> av;   // pairs of the key outside the core
+            for (int q : keyp)
+                if (!(c2 >> I.pair_i[(size_t)q] & 1) && !(c2 >> I.pair_j[(size_t)q] & 1)) av.push_back(q);
+            if (av.empty()) continue;
+            // all rows of the unit share one proton sector
+            int blk = -1, sec = -1;
+            std::vector<int> rowof(av.size(), -1);
+            for (size_t t = 0; t < av.size(); ++t) {
+                const uint64_t m = c2 | (1ULL << I.pair_i[(size_t)av[t]]) | (1ULL << I.pair_j[(size_t)av[t]]);
+                auto it = P.index.find(m);
+                if (it == P.index.end()) continue;
+                sec = P.sec_of_sd[(size_t)it->second];
+                blk = B.block_of_psec[(size_t)sec];
+                rowof[t] = (int)(it->second - P.sec[(size_t)sec].start);
+            }
+            if (blk < 0) continue;
+            for (size_t d0 = 0; d0 < av.size(); d0 += 4) {
+                U x;
+                x.u.dblock = blk;
+                bool any = false;
+                for (int p = 0; p < 4; ++p) {
+                    x.u.drow[p] = -1;
+                    x.u.part[p] = 0;
+                    const size_t t = d0 + (size_t)p;
+                    if (t >= av.size() || rowof[t] < 0) continue;
+                    const int i = I.pair_i[(size_t)av[t]], j = I.pair_j[(size_t)av[t]];
+                    const uint64_t r = c2 | (1ULL << i) | (1ULL << j);
+                    const int ra = __builtin_popcountll(r & ((1ULL << i) - 1ULL));
+                    const int rb = __builtin_popcountll(r & ((1ULL << j) - 1ULL));
+                    x.u.drow[p] = rowof[t];
+                    x.u.part[p] = Z + pair_rank(ra, rb);
+                    any = true;
+                }
+                if (!any) continue;
+                for (size_t t = 0; t < av.size(); ++t) {
+                    if (rowof[t] < 0) continue;
+                    const int k = I.pair_i[(size_t)av[t]], l = I.pair_j[(size_t)av[t]];
+                    const uint64_t X = c2 | (1ULL << k) | (1ULL << l);
+                    // a_l a_k on the source, then a+_j a+_i (i < j, k < l)
+                    int sg = sign_below(X, k);
+                    uint64_t m1 = X & ~(1ULL << k);
+                    sg *= sign_below(m1, l);
+                    m1 &= ~(1ULL << l);
+                    double w[4] = {0.0, 0.0, 0.0, 0.0};
+                    bool nz = false;
+                    for (int p = 0; p < 4; ++p) {
+                        if (x.u.drow[p] < 0) continue;
+                        const int q = av[d0 + (size_t)p];
+                        const int i = I.pair_i[(size_t)q], j = I.pair_j[(size_t)q];
+                        int s2 = sign_below(m1, j);
+                        const uint64_t m2 = m1 | (1ULL << j);
+                        s2 *= sign_below(m2, i);
+                        w[p] = sg * s2 * I.Wpp[(size_t)q * I.npairs + (size_t)av[t]];
+                        nz = nz || w[p] != 0.0;
+                    }
+                    if (!nz) continue;
+                    x.row.push_back(rowof[t]);
+                    x.w.insert(x.w.end(), w, w + 4);
+                }
+                x.u.nsrc = (int)x.row.size();
+                x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)blk].nN;
+                units.push_back(std::move(x));
+            }
+        }
+    std::stable_sort(units.begin(), units.end(), [](const U &a, const U &b) { return a.cost > b.cost; });
+    for (U &x : units) {
+        x.u.src0 = (int64_t)T.pps_row.size();
+        T.pps_row.insert(T.pps_row.end(), x.row.begin(), x.row.end());
+        T.pps_w.insert(T.pps_w.end(), x.w.begin(), x.w.end());
+        T.ppunits.push_back(x.u);
+    }
+}
 }  // namespace
 
 int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err)
@@ -553,6 +655,7 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
     }
     T.ops_per_vector = ops;
     build_core_units(B, I, T);
+    build_pp_units(B, I, T);
     return BS_OK;
 }
 

@@ -192,7 +192,7 @@ def test_autotune_picks_a_valid_mode():
     c.sync_status()
 
 
-@pytest.mark.parametrize("mode", [11, 12])
+@pytest.mark.parametrize("mode", [11, 12, 13, 14])
 @pytest.mark.parametrize("k", [4, 8])
 def test_pf_4p4n_core_grouped_modes(mode, k):
     """The core-grouped pn path (FP32, k = 4, 8) at the benchmark size: sampled

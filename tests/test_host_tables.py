@@ -342,7 +342,11 @@ CORE_UNIT = np.dtype([("dblock", np.int32), ("nsrc", np.int32), ("src0", np.int6
 CORE_SRC = np.dtype([("sblock", np.int32), ("srow", np.int32), ("link", np.int32), ("wtab", np.uint32)])
 
 
-def core_tables_matvec(c, x, Z):
+PP_UNIT = np.dtype([("dblock", np.int32), ("nsrc", np.int32), ("src0", np.int64),
+                    ("drow", np.int32, 4), ("part", np.int32, 4)])
+
+
+def core_tables_matvec(c, x, Z, pp_core=False):
     """y = H x with the pn term taken from the core-grouped tables: one partial
     vector per rank t of the removed proton state, summed at the end; the
     like-particle terms from the pipelined kernel's tables.  Test-side numpy.
@@ -362,8 +366,9 @@ def core_tables_matvec(c, x, Z):
     srcs = np.frombuffer(c.table("core_src", np.uint8).tobytes(), dtype=CORE_SRC)
     wc = c.table("wc", np.float64).reshape(-1, 2 * ws, 4)
     dim = len(x)
-    part = np.zeros((Z, dim))
-    written = np.zeros((Z, dim), dtype=np.int64)
+    nz = Z + (Z * (Z - 1) // 2 if pp_core else 0)
+    part = np.zeros((nz, dim))
+    written = np.zeros((nz, dim), dtype=np.int64)
 
     def blk(b):
         ps, ns_, off = blocks[b]
@@ -392,9 +397,26 @@ def core_tables_matvec(c, x, Z):
             t, sg = u["meta"][p4] & 255, (-1.0 if u["meta"][p4] & 256 else 1.0)
             part[t, offd + r * nNd: offd + (r + 1) * nNd] = sg * acc[p4]
             written[t, offd + r * nNd: offd + (r + 1) * nNd] += 1
+    if pp_core:
+        ppu = np.frombuffer(c.table("pp_units", np.uint8).tobytes(), dtype=PP_UNIT)
+        prow = c.table("pps_row", np.int32)
+        pw = c.table("pps_w", np.float64).reshape(-1, 4)
+        for u in ppu:
+            offd, nPd, nsd, nNd = blk(u["dblock"])
+            acc = np.zeros((4, nNd))
+            for q in range(u["nsrc"]):
+                sr = prow[u["src0"] + q]
+                acc += np.outer(pw[u["src0"] + q], x[offd + sr * nNd: offd + (sr + 1) * nNd])
+            for p4 in range(4):
+                r = u["drow"][p4]
+                if r < 0:
+                    continue
+                part[u["part"][p4], offd + r * nNd: offd + (r + 1) * nNd] = acc[p4]
+                written[u["part"][p4], offd + r * nNd: offd + (r + 1) * nNd] += 1
     # like-particle terms (pp by rows, nn by the sector's lists)
     y = np.zeros_like(x)
     pp_ptr, pp_src, pp_c = c.table("pp_ptr", np.int64), c.table("pp_src", np.int32), c.table("pp_coef", np.float64)
+    pdiag = c.table("pdiag", np.float64)
     nsrc_, ncoef, nsinfo = c.table("pe_nn_src", np.int32), c.table("pe_nn_coef", np.float64), c.table("pe_nn_sinfo", np.int32)
     for b in range(len(blocks)):
         ps, ns_, off = blocks[b]
@@ -402,31 +424,36 @@ def core_tables_matvec(c, x, Z):
         X = x[off:off + nP * nN].reshape(nP, nN)
         Y = y[off:off + nP * nN].reshape(nP, nN)
         for r in range(nP):
-            for e in range(pp_ptr[p0 + r], pp_ptr[p0 + r + 1]):
-                Y[r] += pp_c[e] * X[pp_src[e]]
+            if pp_core:
+                Y[r] += pdiag[p0 + r] * X[r]
+            else:
+                for e in range(pp_ptr[p0 + r], pp_ptr[p0 + r + 1]):
+                    Y[r] += pp_c[e] * X[pp_src[e]]
         po, ne0, ns0 = sec_base[ns_]
         for p in range(nN):
             col = perm[po + p]
             o, lmax = nsinfo[ns0 + 2 * (p // 32)], nsinfo[ns0 + 2 * (p // 32) + 1]
             idx = ne0 + o + 32 * np.arange(lmax) + p % 32
             Y[:, col] += X[:, nsrc_[idx]] @ ncoef[idx]
-    for t in range(Z):
+    for t in range(nz):
         y += part[t]
     return y, written
 
 
 @pytest.mark.parametrize("name,Z,Nn,twoM", [("sd", 2, 2, 0), ("sd", 3, 2, 1), ("sd", 1, 1, 0), ("sd", 1, 3, 0),
                                             ("pf", 2, 2, 2), ("p", 2, 2, 2), ("p", 3, 3, 0)])
-def test_core_tables_reproduce_oracle_matrix(name, Z, Nn, twoM):
-    """The pn term regrouped by (Z-1)-proton cores: every proton one-body jump
-    belongs to exactly one core, every destination row gets exactly one partial
-    per rank t, and the sum reproduces the oracle's H x."""
+@pytest.mark.parametrize("pp_core", [False, True])
+def test_core_tables_reproduce_oracle_matrix(name, Z, Nn, twoM, pp_core):
+    """The pn term regrouped by (Z-1)-proton cores and (optionally) the pp term
+    by (Z-2)-proton cores: every proton jump belongs to exactly one core, every
+    destination row gets exactly one partial per rank t (and per pair of its
+    states), and the sum reproduces the oracle's H x."""
     orbits, spe, tb = I.space(name)
     o = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
     c = host_ctx(name, Z, Nn, twoM)
     x = I.random_block(o.dim, 1, seed=11)[:, 0]
     y_ref = o.spmv(x)
-    y, written = core_tables_matvec(c, x, Z)
+    y, written = core_tables_matvec(c, x, Z, pp_core)
     assert np.all(written == 1)
     assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
 
