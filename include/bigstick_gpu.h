@@ -292,9 +292,26 @@ int bs_autotune(bs_ctx *ctx, int k, bs_dtype dtype, void *stream, int *mode_out,
  * an expiry leave their output rows unwritten.  Errors: BS_ECUDA. */
 int bs_sync_status(bs_ctx *ctx, void *stream);
 
+/* Most products bs_time_kernel records. */
+#define BS_TIME_MAX 4096
+
+/* Kernel timing: records a pair of CUDA events, on the product's stream,
+ * around the dominant kernel of each of the next n (<= BS_TIME_MAX) products
+ * y = H x (the pn kernel in the core-grouped modes 11..14, else the one
+ * kernel); n = 0 stops.  Discards earlier records.  Errors: BS_EINVAL,
+ * BS_ECUDA. */
+int bs_time_kernel(bs_ctx *ctx, int n);
+
+/* Waits for the recorded events and writes the elapsed milliseconds of each
+ * recorded launch to ms (may be NULL; else room for the count), the count to
+ * *n.  Errors: BS_EINVAL, BS_ECUDA. */
+int bs_kernel_times(bs_ctx *ctx, float *ms, int *n);
+
 /* Test aid: copies a host-side table of the built interaction by name
  * ("pp_ptr", "pp_src", "pp_coef", "nn_*", "p1_ptr", "p1_ent", "p1_cls",
- * "n1_*", "wpn", "links", "ops", "op_lists", "stats") into `out` (HOST,
+ * "n1_*", "wpn", "links", "ops", "op_lists", "stats", the pipelined and
+ * core-grouped kernels' tables "pe_*", "ww", "ww_off", "core_units",
+ * "core_src", "wc", "pp_units", "pps_row", "pps_w", "pdiag") into `out` (HOST,
  * caller-allocated; NULL to query the size).  *nbytes receives the size in
  * bytes.  Works on host-only contexts (bs_create with cuda_device = -1),
  * so the host builders can be checked on a machine without a GPU.

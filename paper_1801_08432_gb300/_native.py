@@ -24,7 +24,7 @@ EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_ba
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_lanczos",
             "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_dots_noalloc",
-            "bs_debug_eigh_banded"]
+            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -92,6 +92,8 @@ def load():
     L.bs_block_dots.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
     L.bs_block_dots_noalloc.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, vp]
     L.bs_sync_status.argtypes = [vp, vp]
+    L.bs_time_kernel.argtypes = [vp, ctypes.c_int]
+    L.bs_kernel_times.argtypes = [vp, vp, ctypes.POINTER(ctypes.c_int)]
     L.bs_autotune.argtypes = [vp, ctypes.c_int, ctypes.c_int, vp, ctypes.POINTER(ctypes.c_int),
                               ctypes.POINTER(ctypes.c_float)]
     for name in EXPORTED:
@@ -203,6 +205,18 @@ class Context:
         if times:
             return m.value, {i + 1: round(float(ms[i]), 4) for i in range(KERNEL_MODES)}
         return m.value
+
+    def time_kernel(self, n):
+        """Record CUDA events around the dominant kernel of the next n products."""
+        self._check(load().bs_time_kernel(self.h, n))
+
+    def kernel_times(self):
+        """Milliseconds of the recorded launches (waits for them)."""
+        n = ctypes.c_int()
+        self._check(load().bs_kernel_times(self.h, None, ctypes.byref(n)))
+        ms = np.zeros(max(n.value, 1), dtype=np.float32)
+        self._check(load().bs_kernel_times(self.h, ms.ctypes.data_as(vp), ctypes.byref(n)))
+        return ms[:n.value]
 
     def sync_status(self, stream=None):
         self._check(load().bs_sync_status(self.h, vp(stream or 0)))

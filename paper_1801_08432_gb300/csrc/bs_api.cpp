@@ -294,6 +294,7 @@ void bs_destroy(bs_ctx *c)
         if (c->hx_x) cudaFree(c->hx_x);
         if (c->hx_y) cudaFree(c->hx_y);
         if (c->core_part) cudaFree(c->core_part);
+        for (cudaEvent_t ev : c->tev) cudaEventDestroy(ev);
     }
     delete c;
 }
@@ -542,6 +543,43 @@ int bs_sync_status(bs_ctx *c, void *stream)
     });
 }
 
+int bs_time_kernel(bs_ctx *c, int n)
+{
+    return guarded(c, [&]() -> int {
+        if (n < 0 || n > BS_TIME_MAX) { c->err = "bs_time_kernel: n out of range"; return BS_EINVAL; }
+        if (c->device < 0) { c->err = "bs_time_kernel: host-only context"; return BS_EINVAL; }
+        cudaError_t e = cudaSetDevice(c->device);
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+        for (cudaEvent_t ev : c->tev) cudaEventDestroy(ev);
+        c->tev.clear();
+        c->tev_used = 0;
+        for (int i = 0; i < 2 * n; ++i) {
+            cudaEvent_t ev;
+            if ((e = cudaEventCreate(&ev)) != cudaSuccess) return cuda_fail(c, e, "cudaEventCreate");
+            c->tev.push_back(ev);
+        }
+        return BS_OK;
+    });
+}
+
+int bs_kernel_times(bs_ctx *c, float *ms, int *n)
+{
+    return guarded(c, [&]() -> int {
+        if (!n) { c->err = "bs_kernel_times: null count"; return BS_EINVAL; }
+        const int m = c->tev_used;
+        *n = m;
+        for (int i = 0; i < m; ++i) {
+            cudaError_t e = cudaEventSynchronize(c->tev[2 * i + 1]);
+            if (e != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+            float t = 0.f;
+            if ((e = cudaEventElapsedTime(&t, c->tev[2 * i], c->tev[2 * i + 1])) != cudaSuccess)
+                return cuda_fail(c, e, "cudaEventElapsedTime");
+            if (ms) ms[i] = t;
+        }
+        return BS_OK;
+    });
+}
+
 // Host copies of the built tables, by name, for tests that check the host
 // builders without a GPU.  With out == NULL only *nbytes is set.
 int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
@@ -622,7 +660,7 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
             use(tmp.data(), tmp.size() * 8);
         } else if (s == "stats") {
             tmp = {T.n_pp, T.n_nn, T.n_p1, T.n_n1, (int64_t)T.links.size(), (int64_t)T.ops_per_vector, (int64_t)c->dev.ntasks,
-                   (int64_t)T.wsign};
+                   (int64_t)T.wsign, (int64_t)T.ops_pn, (int64_t)T.ops_pp, (int64_t)T.ops_nn};
             use(tmp.data(), tmp.size() * 8);
         } else {
             c->err = "unknown table " + s;

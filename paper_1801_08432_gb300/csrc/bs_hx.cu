@@ -170,7 +170,7 @@ cudaError_t launch_hx_row(const bs_ctx *c, const void *x, void *y, int k, bs_dty
 cudaError_t launch_hx_pipe(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
                            bool &used);
 cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
-                           bool &used);
+                           bool &used, cudaEvent_t t0, cudaEvent_t t1);
 
 static int kslot(int k)
 {
@@ -188,6 +188,12 @@ int launch_hx(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, void 
     cudaError_t e = cudaSetDevice(c->device);
     bool used = false;
     int mode = c->hx_mode;
+    // bs_time_kernel: events around the dominant kernel of this product
+    const bool timing = c->tev_used < (int)c->tev.size() / 2;
+    cudaEvent_t t0 = timing ? c->tev[2 * (size_t)c->tev_used] : nullptr;
+    cudaEvent_t t1 = timing ? c->tev[2 * (size_t)c->tev_used + 1] : nullptr;
+    bool core_used = false;
+    if (timing && e == cudaSuccess) e = cudaEventRecord(t0, s);
     const int R = row_variants();
     if (mode == 0) mode = c->tuned[dt == BS_F64 ? 0 : 1][kslot(k)];
     if (mode == 0 && e == cudaSuccess) {
@@ -195,7 +201,10 @@ int launch_hx(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, void 
         if (!used) mode = 2;
     }
     const int P = pipe_variants();
-    if (e == cudaSuccess && !used && mode >= 2 + R + P) e = launch_hx_core(c, x, y, k, dt, s, mode - 2 - R - P, used);
+    if (e == cudaSuccess && !used && mode >= 2 + R + P) {
+        e = launch_hx_core(c, x, y, k, dt, s, mode - 2 - R - P, used, t0, t1);
+        core_used = used;
+    }
     if (e == cudaSuccess && !used && mode >= 2 + R && mode < 2 + R + P)
         e = launch_hx_pipe(c, x, y, k, dt, s, mode - 2 - R, used);
     if (e == cudaSuccess && !used && mode >= 2 && mode < 2 + R) e = launch_hx_row(c, x, y, k, dt, s, mode - 2, used);
@@ -219,6 +228,10 @@ int launch_hx(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, void 
             default: e = launch<float, 8>(c->dev, c->dev.c32, xi, yo, s); break;
             }
         }
+    }
+    if (timing && e == cudaSuccess) {
+        if (!core_used) e = cudaEventRecord(t1, s);
+        ++c->tev_used;
     }
     if (e != cudaSuccess) {
         err = std::string("hx launch: ") + cudaGetErrorString(e);

@@ -211,27 +211,28 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
 struct PPArgs {
     const PPUnit *units;
     const int32_t *srow;
-    const float4 *w;
+    const float *w;        // kPPG weights per source
     const DevBlock *blocks;
     int *err;
     int nunits;
     int S;
     int row_stride;
+    int slot_elems;        // row_stride + kPPG
     int64_t part_stride;
 };
 
-// pp term by (Z-2)-proton cores.  The same ring as above, one source row per
-// slot; each thread owns one destination column in natural order (so a
-// quarter warp reads eight consecutive 32-byte elements: conflict-free with
-// the lane rotation (lane >> 2) & 1) and applies the slot's four CTA-uniform
-// weights: 4 k multiply-adds per element read.
+// pp term by (Z-2)-proton cores.  The same ring as above; a slot holds one
+// source row and its kPPG signed weights (CTA-uniform: read as broadcasts).
+// Each thread owns one destination column in natural order (a quarter warp
+// reads eight consecutive 32-byte elements: conflict-free with the lane
+// rotation (lane >> 2) & 1) and applies the element to kPPG destination rows.
 template <int K, int NW, int MINB>
 __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     hx_ppcore_kernel(PPArgs A, const float *__restrict__ x, float *__restrict__ part)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     float *slots = reinterpret_cast<float *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(slots + (size_t)A.S * A.row_stride);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(slots + (size_t)A.S * A.slot_elems);
     const uint32_t full0 = su32(bars), empty0 = su32(bars + A.S);
     constexpr int C = NW * 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -253,6 +254,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             const DevBlock D = A.blocks[U.dblock];
             const int ntile = (D.nN + C - 1) / C;
             const uint32_t bytes = (uint32_t)(D.nN * K * (int)sizeof(float));
+            const uint32_t wbytes = (uint32_t)(kPPG * sizeof(float));
             for (int tile = 0; tile < ntile; ++tile)
                 for (int q = 0; q < U.nsrc; ++q, ++c) {
                     const int s = c % A.S;
@@ -262,10 +264,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                         return;
                     }
                     const uint32_t fb = full0 + 8u * s;
+                    float *dst = slots + (size_t)s * A.slot_elems;
                     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bar_expect_tx(fb, bytes);
-                    bulk_copy(su32(slots + (size_t)s * A.row_stride),
-                              x + (D.off + (int64_t)A.srow[U.src0 + q] * D.nN) * K, bytes, fb);
+                    bar_expect_tx(fb, bytes + wbytes);
+                    bulk_copy(su32(dst), x + (D.off + (int64_t)A.srow[U.src0 + q] * D.nN) * K, bytes, fb);
+                    bulk_copy(su32(dst + A.row_stride), A.w + (U.src0 + q) * kPPG, wbytes, fb);
                 }
         }
         return;
@@ -283,9 +286,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             const int col = tile * C + warp * 32 + lane;
             const bool active = tile * C + warp * 32 < nN;
             const int cl = col < nN ? col : nN - 1;
-            float acc[4][K];
+            float acc[kPPG][K];
 #pragma unroll
-            for (int p = 0; p < 4; ++p)
+            for (int p = 0; p < kPPG; ++p)
 #pragma unroll
                 for (int q = 0; q < K; ++q) acc[p][q] = 0.0f;
             for (int q = 0; q < U.nsrc; ++q, ++c) {
@@ -296,23 +299,26 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                     return;
                 }
                 if (active) {
-                    const float4 w = __ldg(A.w + U.src0 + q);
-                    float xv[K];
-                    pld<float, K>(slots + (size_t)s * A.row_stride, cl, rot, xv);
+                    const float *Xs = slots + (size_t)s * A.slot_elems;
+                    float w[kPPG];
 #pragma unroll
-                    for (int qq = 0; qq < K; ++qq) {
-                        acc[0][qq] = fmaf(w.x, xv[qq], acc[0][qq]);
-                        acc[1][qq] = fmaf(w.y, xv[qq], acc[1][qq]);
-                        acc[2][qq] = fmaf(w.z, xv[qq], acc[2][qq]);
-                        acc[3][qq] = fmaf(w.w, xv[qq], acc[3][qq]);
+                    for (int p = 0; p < kPPG; p += 4) {
+                        const float4 w4 = *reinterpret_cast<const float4 *>(Xs + A.row_stride + p);
+                        w[p] = w4.x; w[p + 1] = w4.y; w[p + 2] = w4.z; w[p + 3] = w4.w;
                     }
+                    float xv[K];
+                    pld<float, K>(Xs, cl, rot, xv);
+#pragma unroll
+                    for (int p = 0; p < kPPG; ++p)
+#pragma unroll
+                        for (int qq = 0; qq < K; ++qq) acc[p][qq] = fmaf(w[p], xv[qq], acc[p][qq]);
                 }
                 __syncwarp();
                 if (lane == 0) bar_arrive(empty0 + 8u * s);
             }
             if (col < nN) {
 #pragma unroll
-                for (int p = 0; p < 4; ++p) {
+                for (int p = 0; p < kPPG; ++p) {
                     if (U.drow[p] < 0) continue;
                     prot_fix<float, K>(acc[p], rot);
                     pst<float, K>(part + (int64_t)U.part[p] * A.part_stride + (D.off + (int64_t)U.drow[p] * nN + col) * K,
@@ -497,11 +503,12 @@ cudaError_t launch_pp_t(const bs_ctx *ctx, const float *x, float *part, cudaStre
 {
     const Device &Dv = ctx->dev;
     const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
-    const size_t slot_bytes = (size_t)row_stride * sizeof(float) + 16;
+    const int slot_elems = row_stride + 32;   // row, kPPG weights, padded to 128 bytes
+    const size_t slot_bytes = (size_t)slot_elems * sizeof(float) + 16;
     const int S = (int)std::min<size_t>(8, target / slot_bytes);
     used = S >= 2;
     if (!used) return cudaSuccess;
-    const size_t smem = (size_t)S * row_stride * sizeof(float) + 16 * (size_t)S;
+    const size_t smem = (size_t)S * slot_elems * sizeof(float) + 16 * (size_t)S;
     auto kern = hx_ppcore_kernel<K, NW, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -509,8 +516,8 @@ cudaError_t launch_pp_t(const bs_ctx *ctx, const float *x, float *part, cudaStre
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, Dv.dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (NW + 1) * 32, smem)) != cudaSuccess) return e;
     const int grid = std::max(1, std::min(Dv.nppunits, nsm * std::max(per, 1)));
-    PPArgs A{Dv.ppunits, Dv.pps_row, reinterpret_cast<const float4 *>(Dv.pps_w32), Dv.blocks, Dv.err,
-             Dv.nppunits, S, row_stride, (int64_t)ctx->basis.dim * K};
+    PPArgs A{Dv.ppunits, Dv.pps_row, Dv.pps_w32, Dv.blocks, Dv.err, Dv.nppunits, S, row_stride, slot_elems,
+             (int64_t)ctx->basis.dim * K};
     kern<<<grid, (NW + 1) * 32, smem, s>>>(A, x, part);
     return cudaGetLastError();
 }
@@ -562,7 +569,7 @@ int prepare_hx(const bs_ctx *c, int k, bs_dtype dt, std::string &err)
 // kernel (variant 0) that adds the partials; `used` is false when the path
 // does not apply (FP64, k < 4, no cores) or does not fit.
 cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, cudaStream_t s, int v,
-                           bool &used)
+                           bool &used, cudaEvent_t t0, cudaEvent_t t1)
 {
     used = false;
     if (!core_applies(c, k, dt) || v < 0 || v >= kNumCore) return cudaSuccess;
@@ -581,8 +588,10 @@ cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dt
     if (e != cudaSuccess || !fits) return e;
     float *part = (float *)c->core_part;
     const float *xf = (const float *)x;
+    if (t0 && (e = cudaEventRecord(t0, s)) != cudaSuccess) return e;
     e = k == 8 ? launch_core_k<8>(c, xf, part, s, v, used) : launch_core_k<4>(c, xf, part, s, v, used);
     if (e != cudaSuccess || !used) return e;
+    if (t1 && (e = cudaEventRecord(t1, s)) != cudaSuccess) return e;
     int nz = c->dev.nz;
     if (pp) {
         if (c->dev.nppunits > 0) {

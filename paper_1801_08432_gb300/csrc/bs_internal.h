@@ -2,6 +2,7 @@
 // tables, and the device mirror the kernels read.
 #pragma once
 
+#include <cuda_runtime.h>
 #include <vector_types.h>
 
 #include <cstdint>
@@ -163,18 +164,19 @@ struct CoreSrc {
 
 // pp term by (Z-2)-proton cores: a two-body term a+_i a+_j a_l a_k taking
 // SD s to r belongs to exactly one core c2 = s - {k,l} = r - {i,j}.  A unit is
-// one core, one (2M, parity) key of pairs and up to four destination pairs
+// one core, one (2M, parity) key of pairs and up to eight destination pairs
 // (i,j); its destination rows r_p = c2 + {i_p,j_p} and its sources
-// c2 + {k,l} all lie in one proton sector, so a staged source row serves four
-// destination rows with four CTA-uniform weights (the fermion sign folded in).
+// c2 + {k,l} all lie in one proton sector, so a staged source row serves eight
+// destination rows with eight CTA-uniform weights (the fermion sign folded in).
 // Row r gets one partial per pair of its states (C(Z,2) of them); the proton
 // single-particle energies are left to a per-row diagonal.
+constexpr int kPPG = 8;    // destination pairs per pp unit
 struct PPUnit {
     int dblock;
     int nsrc;
     int64_t src0;          // first source in Tables::pps_row / pps_w
-    int drow[4];           // destination proton row, -1 if absent
-    int part[4];           // partial vector of the destination row (Z + pair rank)
+    int drow[kPPG];        // destination proton row, -1 if absent
+    int part[kPPG];        // partial vector of the destination row (Z + pair rank)
 };
 
 struct Tables {
@@ -193,6 +195,7 @@ struct Tables {
     std::vector<int64_t> links_of_block; // [nblocks+1]
     int64_t n_pp = 0, n_nn = 0, n_p1 = 0, n_n1 = 0;
     double ops_per_vector = 0.0;         // multiply-adds of one H*x (structural)
+    double ops_pn = 0.0, ops_pp = 0.0, ops_nn = 0.0;   // its split by term
     // core-grouped pn term
     std::vector<CoreUnit> cunits;        // sorted by work, largest first
     std::vector<CoreSrc> csrc;
@@ -201,7 +204,7 @@ struct Tables {
     // core-grouped pp term
     std::vector<PPUnit> ppunits;         // sorted by work, largest first
     std::vector<int32_t> pps_row;        // per source: proton row c2 + {k,l}
-    std::vector<double> pps_w;           // per source: 4 signed weights
+    std::vector<double> pps_w;           // per source: kPPG signed weights
     std::vector<double> pdiag;           // per proton SD: sum of its single-particle energies
 };
 
@@ -302,6 +305,9 @@ struct bs_ctx {
     // partial sums of the core-grouped pn kernel: nz x dim x k elements, grown on demand
     mutable void *core_part = nullptr;
     mutable size_t core_part_bytes = 0;
+    // event pairs around the dominant kernel of each product (bs_time_kernel)
+    std::vector<cudaEvent_t> tev;
+    mutable int tev_used = 0;
     int tuned[2][4] = {};    // autotuned mode per (dtype, k slot); 0 = not tuned
     // the loaded interaction as given (for the parameter derivatives of the adjoint)
     std::vector<double> spe_in;

@@ -491,11 +491,11 @@ void build_pp_units(const Basis &B, const Interaction &I, Tables &T)
                 rowof[t] = (int)(it->second - P.sec[(size_t)sec].start);
             }
             if (blk < 0) continue;
-            for (size_t d0 = 0; d0 < av.size(); d0 += 4) {
+            for (size_t d0 = 0; d0 < av.size(); d0 += kPPG) {
                 U x;
                 x.u.dblock = blk;
                 bool any = false;
-                for (int p = 0; p < 4; ++p) {
+                for (int p = 0; p < kPPG; ++p) {
                     x.u.drow[p] = -1;
                     x.u.part[p] = 0;
                     const size_t t = d0 + (size_t)p;
@@ -518,9 +518,9 @@ void build_pp_units(const Basis &B, const Interaction &I, Tables &T)
                     uint64_t m1 = X & ~(1ULL << k);
                     sg *= sign_below(m1, l);
                     m1 &= ~(1ULL << l);
-                    double w[4] = {0.0, 0.0, 0.0, 0.0};
+                    double w[kPPG] = {};
                     bool nz = false;
-                    for (int p = 0; p < 4; ++p) {
+                    for (int p = 0; p < kPPG; ++p) {
                         if (x.u.drow[p] < 0) continue;
                         const int q = av[d0 + (size_t)p];
                         const int i = I.pair_i[(size_t)q], j = I.pair_j[(size_t)q];
@@ -532,7 +532,7 @@ void build_pp_units(const Basis &B, const Interaction &I, Tables &T)
                     }
                     if (!nz) continue;
                     x.row.push_back(rowof[t]);
-                    x.w.insert(x.w.end(), w, w + 4);
+                    x.w.insert(x.w.end(), w, w + kPPG);
                 }
                 x.u.nsrc = (int)x.row.size();
                 x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)blk].nN;
@@ -646,12 +646,16 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
             double np_ = (double)(T.p1.ptr[P.ptr_off + D.nP] - T.p1.ptr[P.ptr_off]);
             double nn_ = (double)(T.n1.ptr[N.ptr_off + D.nN] - T.n1.ptr[N.ptr_off]);
             ops += np_ * nn_;
+            T.ops_pn += np_ * nn_;
         }
         T.links_of_block[(size_t)d + 1] = (int64_t)T.links.size();
         // like-particle work of this block
         const Sector &PS = B.sp[0].sec[D.ps], &NS = B.sp[1].sec[D.ns];
-        ops += (double)(T.pp.ptr[PS.start + PS.count] - T.pp.ptr[PS.start]) * (double)D.nN;
-        ops += (double)(T.nn.ptr[NS.start + NS.count] - T.nn.ptr[NS.start]) * (double)D.nP;
+        const double opp = (double)(T.pp.ptr[PS.start + PS.count] - T.pp.ptr[PS.start]) * (double)D.nN;
+        const double onn = (double)(T.nn.ptr[NS.start + NS.count] - T.nn.ptr[NS.start]) * (double)D.nP;
+        ops += opp + onn;
+        T.ops_pp += opp;
+        T.ops_nn += onn;
     }
     T.ops_per_vector = ops;
     build_core_units(B, I, T);

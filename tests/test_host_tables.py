@@ -342,8 +342,9 @@ CORE_UNIT = np.dtype([("dblock", np.int32), ("nsrc", np.int32), ("src0", np.int6
 CORE_SRC = np.dtype([("sblock", np.int32), ("srow", np.int32), ("link", np.int32), ("wtab", np.uint32)])
 
 
+PPG = 8
 PP_UNIT = np.dtype([("dblock", np.int32), ("nsrc", np.int32), ("src0", np.int64),
-                    ("drow", np.int32, 4), ("part", np.int32, 4)])
+                    ("drow", np.int32, PPG), ("part", np.int32, PPG)])
 
 
 def core_tables_matvec(c, x, Z, pp_core=False):
@@ -400,19 +401,19 @@ def core_tables_matvec(c, x, Z, pp_core=False):
     if pp_core:
         ppu = np.frombuffer(c.table("pp_units", np.uint8).tobytes(), dtype=PP_UNIT)
         prow = c.table("pps_row", np.int32)
-        pw = c.table("pps_w", np.float64).reshape(-1, 4)
+        pw = c.table("pps_w", np.float64).reshape(-1, PPG)
         for u in ppu:
             offd, nPd, nsd, nNd = blk(u["dblock"])
-            acc = np.zeros((4, nNd))
+            acc = np.zeros((PPG, nNd))
             for q in range(u["nsrc"]):
                 sr = prow[u["src0"] + q]
                 acc += np.outer(pw[u["src0"] + q], x[offd + sr * nNd: offd + (sr + 1) * nNd])
-            for p4 in range(4):
-                r = u["drow"][p4]
+            for p8 in range(PPG):
+                r = u["drow"][p8]
                 if r < 0:
                     continue
-                part[u["part"][p4], offd + r * nNd: offd + (r + 1) * nNd] = acc[p4]
-                written[u["part"][p4], offd + r * nNd: offd + (r + 1) * nNd] += 1
+                part[u["part"][p8], offd + r * nNd: offd + (r + 1) * nNd] = acc[p8]
+                written[u["part"][p8], offd + r * nNd: offd + (r + 1) * nNd] += 1
     # like-particle terms (pp by rows, nn by the sector's lists)
     y = np.zeros_like(x)
     pp_ptr, pp_src, pp_c = c.table("pp_ptr", np.int64), c.table("pp_src", np.int32), c.table("pp_coef", np.float64)
