@@ -232,6 +232,21 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
     if ((rc = put(D, D.csrc, T.csrc.data(), T.csrc.size(), err))) return rc;
     f = cast<float>(T.wc);
     if ((rc = put(D, D.wc32, f.data(), f.size(), err))) return rc;
+    // largest list block one column tile of the pn-core kernel stages (18 or 10 warps of 32 columns)
+    for (int vi = 0; vi < 2; ++vi) {
+        const int nw = vi == 0 ? 18 : 10;
+        int64_t mx = 0;
+        for (size_t cl = 0; cl < T.n1.cls.size(); ++cl) {
+            const int64_t n = B.sp[1].sec[(size_t)T.n1.cls[cl].s_dst].count;
+            const int64_t nsl = (n + 31) / 32;
+            const int32_t *si = T.pe.sinfo.data() + T.pe.cls_sinfo[cl];
+            for (int64_t s0 = 0; s0 < nsl; s0 += nw) {
+                const int64_t s1 = std::min(nsl, s0 + nw) - 1;
+                mx = std::max<int64_t>(mx, (int64_t)si[2 * s1] + 32 * (int64_t)si[2 * s1 + 1] - si[2 * s0]);
+            }
+        }
+        D.core_list_max[vi] = mx;
+    }
     // core-grouped pp kernel
     D.nppunits = (int)T.ppunits.size();
     D.nzpp = D.nppunits ? B.sp[0].nparticles * (B.sp[0].nparticles - 1) / 2 : 0;

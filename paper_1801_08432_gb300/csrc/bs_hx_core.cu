@@ -38,13 +38,50 @@ cudaError_t launch_hx_pipe_combine(const bs_ctx *c, const void *x, void *y, int 
 
 namespace {
 
-constexpr int kCoreMaxList = 16;
+// K values of element `jn` of a staged row.  For K = 8 (two 16-byte chunks)
+// the chunk loaded first is the entry's rotation bit r (chosen at build time
+// to spread a quarter warp's loads over the bank groups); the values are put
+// back in order with selects.
+// The same as float2 pairs (v[j] = components 2j, 2j+1) for the packed FMA.
+template <int K>
+__device__ __forceinline__ void ldx2(const float *row, uint32_t en, float2 (&v)[K / 2])
+{
+    const float *e = row + (size_t)(en & 0xFFFFu) * K;
+    if constexpr (K == 8) {
+        const uint32_t r = en >> 31;
+        const float4 a = *reinterpret_cast<const float4 *>(e + 4 * r);
+        const float4 b = *reinterpret_cast<const float4 *>(e + 4 * (1u - r));
+        v[0] = make_float2(r ? b.x : a.x, r ? b.y : a.y);
+        v[1] = make_float2(r ? b.z : a.z, r ? b.w : a.w);
+        v[2] = make_float2(r ? a.x : b.x, r ? a.y : b.y);
+        v[3] = make_float2(r ? a.z : b.z, r ? a.w : b.w);
+    } else {
+        const float4 a = *reinterpret_cast<const float4 *>(e);
+        v[0] = make_float2(a.x, a.y);
+        v[1] = make_float2(a.z, a.w);
+    }
+}
+
+template <int K>
+__device__ __forceinline__ void ldx(const float *row, uint32_t en, float (&v)[K])
+{
+    const float *e = row + (size_t)(en & 0xFFFFu) * K;
+    if constexpr (K == 8) {
+        const uint32_t r = en >> 31;
+        const float4 a = *reinterpret_cast<const float4 *>(e + 4 * r);
+        const float4 b = *reinterpret_cast<const float4 *>(e + 4 * (1u - r));
+        v[0] = r ? b.x : a.x; v[1] = r ? b.y : a.y; v[2] = r ? b.z : a.z; v[3] = r ? b.w : a.w;
+        v[4] = r ? a.x : b.x; v[5] = r ? a.y : b.y; v[6] = r ? a.z : b.z; v[7] = r ? a.w : b.w;
+    } else {
+        const float4 a = *reinterpret_cast<const float4 *>(e);
+        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
+    }
+}
 
 struct CoreArgs {
     const CoreUnit *units;
     const CoreSrc *src;
     const DevBlock *blocks;
-    const DevLink *links;
     const int32_t *perm;
     const int32_t *sinfo;
     const uint32_t *ent;
@@ -53,20 +90,30 @@ struct CoreArgs {
     int S;             // ring slots
     int row_stride;    // floats per staged row (multiple of 32)
     int wtab;          // floats per weight table (2 wsign x 4)
-    int slot_elems;    // row_stride + wtab
+    int slot_elems;    // row_stride + wtab + 8 (the slot's CoreSrc)
+    int list_elems;    // entries per list buffer (multiple of 32)
     uint32_t ws;       // wsign
     int64_t part_stride;   // dim * K
 };
 
+// Shared memory: S slots [source row | weight table | CoreSrc], two list
+// buffers (one link's neutron lists for the tile's slices) with their slice
+// info, then the barriers: full[S], empty[S], list_empty[2].  A "group" is a
+// run of slots of one tile that share a link; its lists arrive with its first
+// slot, in buffer (group & 1), and each consumer warp releases the buffer when
+// it starts the next group.
 template <int K, int NW, int MINB>
 __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     hx_core_kernel(CoreArgs A, const float *__restrict__ wc, const float *__restrict__ x, float *__restrict__ part)
 {
     extern __shared__ __align__(128) unsigned char smem[];
+    constexpr int C = NW * 32;                        // columns per tile
+    constexpr int SI = ((2 * NW + 3) / 4) * 4;        // slice-info ints per buffer
     float *slots = reinterpret_cast<float *>(smem);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(slots + (size_t)A.S * A.slot_elems);
-    const uint32_t full0 = su32(bars), empty0 = su32(bars + A.S);
-    constexpr int C = NW * 32;   // columns per tile
+    uint32_t *lists = reinterpret_cast<uint32_t *>(slots + (size_t)A.S * A.slot_elems);
+    int32_t *sinf = reinterpret_cast<int32_t *>(lists + 2 * (size_t)A.list_elems);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sinf + 2 * SI);
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + A.S), lempty0 = su32(bars + 2 * A.S);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
     if (threadIdx.x == 0) {
@@ -74,117 +121,160 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             bar_init(full0 + 8u * s, 1);
             bar_init(empty0 + 8u * s, NW);
         }
+        bar_init(lempty0, NW);
+        bar_init(lempty0 + 8u, NW);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
     if (warp == NW) {
-        // ---------------- producer: one lane streams every unit's sources, tile by tile
-        if (lane != 0) return;
-        int c = 0;
+        // ---------------- producer: lane 0 streams every unit's sources, tile by tile;
+        // the warp's 32 lanes fetch the metadata of 32 sources at a time
+        int c = 0, g = -1;
         for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
-            const CoreUnit U = A.units[u];
-            const int ntile = (A.blocks[U.dblock].nN + C - 1) / C;
-            for (int tile = 0; tile < ntile; ++tile)
-                for (int q = 0; q < U.nsrc; ++q, ++c) {
-                    const int s = c % A.S;
-                    const int round = c / A.S;
-                    if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) {
-                        atomicExch(A.err, BS_ETIMEOUT);
-                        return;
+            const int nsrc = A.units[u].nsrc;
+            const int64_t src0 = A.units[u].src0;
+            const int nN = A.blocks[A.units[u].dblock].nN;
+            const int nsl = (nN + 31) / 32;
+            const int ntile = (nN + C - 1) / C;
+            for (int tile = 0; tile < ntile; ++tile) {
+                const int sl0 = tile * NW, sl1 = min(nsl, sl0 + NW);
+                int64_t prev = -1;
+                for (int q0 = 0; q0 < nsrc; q0 += 32) {
+                    const int qm = q0 + lane;
+                    int64_t mx = 0, msb = -1, mof = 0, mol = 0;
+                    int mn = 0, mlm = 0;
+                    uint32_t mw = 0;
+                    if (qm < nsrc) {
+                        const CoreSrc cs = A.src[src0 + qm];
+                        mx = cs.x_elem;
+                        mn = cs.nN;
+                        mw = cs.wtab;
+                        msb = cs.sinfo_base;
+                        mof = cs.ent_base + A.sinfo[cs.sinfo_base + 2 * sl0];
+                        mol = A.sinfo[cs.sinfo_base + 2 * sl0];
+                        mlm = A.sinfo[cs.sinfo_base + 2 * (sl1 - 1)] + 32 * A.sinfo[cs.sinfo_base + 2 * (sl1 - 1) + 1];
                     }
-                    const CoreSrc cs = A.src[U.src0 + q];
-                    const DevBlock Sb = A.blocks[cs.sblock];
-                    const uint32_t bytes = (uint32_t)(Sb.nN * K * (int)sizeof(float));
-                    const uint32_t wbytes = (uint32_t)(A.wtab * (int)sizeof(float));
-                    float *dst = slots + (size_t)s * A.slot_elems;
-                    const uint32_t fb = full0 + 8u * s;
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bar_expect_tx(fb, bytes + wbytes);
-                    bulk_copy(su32(dst), x + (Sb.off + (int64_t)cs.srow * Sb.nN) * K, bytes, fb);
-                    bulk_copy(su32(dst + A.row_stride), wc + (size_t)(cs.wtab & 0x7FFFFFFFu) * A.wtab, wbytes, fb);
+                    const int cnt = min(32, nsrc - q0);
+                    for (int j = 0; j < cnt; ++j, ++c) {
+                        const int64_t xe = __shfl_sync(0xffffffffu, mx, j);
+                        const int sn = __shfl_sync(0xffffffffu, mn, j);
+                        const uint32_t wt = __shfl_sync(0xffffffffu, mw, j);
+                        const int64_t sb = __shfl_sync(0xffffffffu, msb, j);
+                        const int64_t lsrc = __shfl_sync(0xffffffffu, mof, j);   // first list entry of the tile
+                        const int64_t o0 = __shfl_sync(0xffffffffu, mol, j);
+                        const int lend = __shfl_sync(0xffffffffu, mlm, j);        // end of the tile's list block
+                        const bool newg = sb != prev;
+                        int bad = 0;
+                        if (lane == 0) {
+                            const int s = c % A.S;
+                            const int round = c / A.S;
+                            if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) bad = 1;
+                            uint32_t lbytes = 0, sbytes = 0;
+                            const int b = (g + (newg ? 1 : 0)) & 1;
+                            if (!bad && newg) {
+                                const int gn = g + 1;
+                                if (gn >= 2 && bar_wait(lempty0 + 8u * b, (uint32_t)((gn >> 1) - 1) & 1u)) bad = 1;
+                                lbytes = (uint32_t)((lend - o0) * 4);
+                                sbytes = (uint32_t)(((2 * (sl1 - sl0) + 3) / 4) * 16);
+                            }
+                            if (!bad) {
+                                const uint32_t bytes = (uint32_t)(sn * K * (int)sizeof(float));
+                                const uint32_t wbytes = (uint32_t)(A.wtab * (int)sizeof(float));
+                                float *dst = slots + (size_t)s * A.slot_elems;
+                                const uint32_t fb = full0 + 8u * s;
+                                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                                bar_expect_tx(fb, bytes + wbytes + 32u + lbytes + sbytes);
+                                bulk_copy(su32(dst), x + xe * K, bytes, fb);
+                                bulk_copy(su32(dst + A.row_stride), wc + (size_t)(wt & 0x7FFFFFFFu) * A.wtab, wbytes, fb);
+                                bulk_copy(su32(dst + A.row_stride + A.wtab), A.src + src0 + q0 + j, 32u, fb);
+                                if (newg) {
+                                    if (lbytes) bulk_copy(su32(lists + (size_t)b * A.list_elems), A.ent + lsrc, lbytes, fb);
+                                    bulk_copy(su32(sinf + b * SI), A.sinfo + sb + 2 * sl0, sbytes, fb);
+                                }
+                            }
+                        }
+                        if (__shfl_sync(0xffffffffu, bad, 0)) {
+                            if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
+                            return;
+                        }
+                        if (newg) {
+                            prev = sb;
+                            ++g;
+                        }
+                    }
                 }
+            }
         }
         return;
     }
 
     // ---------------- consumers
-    const int rot = prot<float, K>(lane);
-    int c = 0;
+    int c = 0, g = -1;
     for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
-        const CoreUnit U = A.units[u];
-        const DevBlock D = A.blocks[U.dblock];
+        const int nsrc = A.units[u].nsrc;
+        const DevBlock D = A.blocks[A.units[u].dblock];
         const int nN = D.nN;
+        const int64_t doff = D.off;
         const int ntile = (nN + C - 1) / C;
         for (int tile = 0; tile < ntile; ++tile) {
             const int pos0 = tile * C + warp * 32;   // warp-uniform
             const bool active = pos0 < nN;
             const int pos = pos0 + lane;
-            const int sl = pos0 >> 5;
             const int col = pos < nN ? A.perm[D.perm_off + pos] : -1;
-            float acc[4][K];
+            // packed accumulators: acc[p][j] holds components 2j, 2j+1 of destination row p
+            float2 acc[4][K / 2];
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-                for (int q = 0; q < K; ++q) acc[p][q] = 0.0f;
-            int prev = -1, lmax = 0;
-            int64_t base = 0;
-            uint32_t ev[kCoreMaxList];
-#pragma unroll
-            for (int v = 0; v < kCoreMaxList; ++v) ev[v] = 0;
-            for (int q = 0; q < U.nsrc; ++q, ++c) {
+                for (int q = 0; q < K / 2; ++q) acc[p][q] = make_float2(0.0f, 0.0f);
+            int64_t prev = -1;
+            int lmax = 0;
+            const uint32_t *lst = lists;
+            for (int q = 0; q < nsrc; ++q, ++c) {
                 const int s = c % A.S;
                 const int round = c / A.S;
                 if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)round & 1u))) {
                     if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
                     return;
                 }
-                if (active) {
-                    const CoreSrc cs = A.src[U.src0 + q];
-                    if (cs.link != prev) {
-                        // a new link: this warp's slice of its neutron lists
-                        prev = cs.link;
-                        const DevLink lk = A.links[cs.link];
-                        const int off = A.sinfo[lk.pe_sinfo + 2 * sl];
-                        lmax = A.sinfo[lk.pe_sinfo + 2 * sl + 1];
-                        base = lk.pe_ent + off + lane;
-                        if (lmax <= kCoreMaxList) {
-                            const uint32_t pad = (A.ws - 1u) << 16;   // a zero weight, source column 0
-#pragma unroll
-                            for (int v = 0; v < kCoreMaxList; ++v) ev[v] = v < lmax ? A.ent[base + 32 * v] : pad;
-                        }
+                const float *Xs = slots + (size_t)s * A.slot_elems;
+                const float *Wt = Xs + A.row_stride;
+                const CoreSrc *cs = reinterpret_cast<const CoreSrc *>(Wt + A.wtab);
+                const int64_t sb = cs->sinfo_base;
+                const uint32_t wtab = cs->wtab;
+                if (sb != prev) {
+                    // a new group: release the previous group's list buffer, read this one
+                    __syncwarp();
+                    if (g >= 0 && lane == 0) bar_arrive(lempty0 + 8u * (g & 1));
+                    ++g;
+                    prev = sb;
+                    const int b = g & 1;
+                    lst = lists + (size_t)b * A.list_elems;
+                    if (active) {
+                        const int32_t *si = sinf + b * SI;
+                        lmax = si[2 * warp + 1];
+                        lst += si[2 * warp] - si[0] + lane;
                     }
-                    const float *Xs = slots + (size_t)s * A.slot_elems;
-                    const float *Wt = Xs + A.row_stride;
-                    const uint32_t flip = (cs.wtab >> 31) ? A.ws : 0u;   // sign of a_k on c + k: swap the +W / -W halves
-                    float xv[K];
-                    if (lmax <= kCoreMaxList) {
+                }
+                if (active) {
+                    // entries straight from the staged list (32 lanes, 128 contiguous bytes per step)
+                    const uint32_t flip = (wtab >> 31) ? A.ws : 0u;   // sign of a_k on c + k: swap the +W / -W halves
+                    float2 xv[K / 2];
+#pragma unroll 2
+                    for (int v = 0; v < lmax; ++v) {
+                        const uint32_t en = lst[32 * v];
+                        const float4 w = *reinterpret_cast<const float4 *>(Wt + 4 * (((en >> 16) & 0x7FFFu) ^ flip));
+                        ldx2<K>(Xs, en, xv);
+                        const float2 w0 = make_float2(w.x, w.x), w1 = make_float2(w.y, w.y);
+                        const float2 w2 = make_float2(w.z, w.z), w3 = make_float2(w.w, w.w);
 #pragma unroll
-                        for (int v = 0; v < kCoreMaxList; ++v) {
-                            if (v >= lmax) break;
-                            const uint32_t en = ev[v];
-                            const float4 w = *reinterpret_cast<const float4 *>(Wt + 4 * ((en >> 16) ^ flip));
-                            pld<float, K>(Xs, (int)(en & 0xFFFFu), rot, xv);
-#pragma unroll
-                            for (int qq = 0; qq < K; ++qq) {
-                                acc[0][qq] = fmaf(w.x, xv[qq], acc[0][qq]);
-                                acc[1][qq] = fmaf(w.y, xv[qq], acc[1][qq]);
-                                acc[2][qq] = fmaf(w.z, xv[qq], acc[2][qq]);
-                                acc[3][qq] = fmaf(w.w, xv[qq], acc[3][qq]);
-                            }
-                        }
-                    } else {
-                        for (int v = 0; v < lmax; ++v) {
-                            const uint32_t en = A.ent[base + 32 * (int64_t)v];
-                            const float4 w = *reinterpret_cast<const float4 *>(Wt + 4 * ((en >> 16) ^ flip));
-                            pld<float, K>(Xs, (int)(en & 0xFFFFu), rot, xv);
-#pragma unroll
-                            for (int qq = 0; qq < K; ++qq) {
-                                acc[0][qq] = fmaf(w.x, xv[qq], acc[0][qq]);
-                                acc[1][qq] = fmaf(w.y, xv[qq], acc[1][qq]);
-                                acc[2][qq] = fmaf(w.z, xv[qq], acc[2][qq]);
-                                acc[3][qq] = fmaf(w.w, xv[qq], acc[3][qq]);
-                            }
+                        for (int qq = 0; qq < K / 2; ++qq) {
+                            // two correctly rounded fused multiply-adds per instruction
+                            acc[0][qq] = __ffma2_rn(w0, xv[qq], acc[0][qq]);
+                            acc[1][qq] = __ffma2_rn(w1, xv[qq], acc[1][qq]);
+                            acc[2][qq] = __ffma2_rn(w2, xv[qq], acc[2][qq]);
+                            acc[3][qq] = __ffma2_rn(w3, xv[qq], acc[3][qq]);
                         }
                     }
                 }
@@ -192,16 +282,19 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 if (lane == 0) bar_arrive(empty0 + 8u * s);
             }
             if (col >= 0) {
+                const CoreUnit *U = A.units + u;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
-                    if (U.drow[p] < 0) continue;
-                    prot_fix<float, K>(acc[p], rot);
-                    if (U.meta[p] & 256)
+                    const int drow = U->drow[p], meta = U->meta[p];
+                    if (drow < 0) continue;
+                    const float sg = (meta & 256) ? -1.0f : 1.0f;
+                    float o[K];
 #pragma unroll
-                        for (int qq = 0; qq < K; ++qq) acc[p][qq] = -acc[p][qq];
-                    pst<float, K>(part + (int64_t)(U.meta[p] & 255) * A.part_stride +
-                                      (D.off + (int64_t)U.drow[p] * nN + col) * K,
-                                  acc[p]);
+                    for (int qq = 0; qq < K / 2; ++qq) {
+                        o[2 * qq] = sg * acc[p][qq].x;
+                        o[2 * qq + 1] = sg * acc[p][qq].y;
+                    }
+                    pst<float, K>(part + (int64_t)(meta & 255) * A.part_stride + (doff + (int64_t)drow * nN + col) * K, o);
                 }
             }
         }
@@ -286,11 +379,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             const int col = tile * C + warp * 32 + lane;
             const bool active = tile * C + warp * 32 < nN;
             const int cl = col < nN ? col : nN - 1;
-            float acc[kPPG][K];
+            float2 acc[kPPG][K / 2];   // packed: components 2j, 2j+1 (in the lane's rotated order)
 #pragma unroll
             for (int p = 0; p < kPPG; ++p)
 #pragma unroll
-                for (int q = 0; q < K; ++q) acc[p][q] = 0.0f;
+                for (int q = 0; q < K / 2; ++q) acc[p][q] = make_float2(0.0f, 0.0f);
             for (int q = 0; q < U.nsrc; ++q, ++c) {
                 const int s = c % A.S;
                 const int round = c / A.S;
@@ -309,9 +402,12 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                     float xv[K];
                     pld<float, K>(Xs, cl, rot, xv);
 #pragma unroll
-                    for (int p = 0; p < kPPG; ++p)
+                    for (int p = 0; p < kPPG; ++p) {
+                        const float2 wp = make_float2(w[p], w[p]);
 #pragma unroll
-                        for (int qq = 0; qq < K; ++qq) acc[p][qq] = fmaf(w[p], xv[qq], acc[p][qq]);
+                        for (int qq = 0; qq < K / 2; ++qq)
+                            acc[p][qq] = __ffma2_rn(wp, make_float2(xv[2 * qq], xv[2 * qq + 1]), acc[p][qq]);
+                    }
                 }
                 __syncwarp();
                 if (lane == 0) bar_arrive(empty0 + 8u * s);
@@ -320,9 +416,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
 #pragma unroll
                 for (int p = 0; p < kPPG; ++p) {
                     if (U.drow[p] < 0) continue;
-                    prot_fix<float, K>(acc[p], rot);
-                    pst<float, K>(part + (int64_t)U.part[p] * A.part_stride + (D.off + (int64_t)U.drow[p] * nN + col) * K,
-                                  acc[p]);
+                    float o[K];
+#pragma unroll
+                    for (int qq = 0; qq < K / 2; ++qq) {
+                        o[2 * qq] = acc[p][qq].x;
+                        o[2 * qq + 1] = acc[p][qq].y;
+                    }
+                    prot_fix<float, K>(o, rot);
+                    pst<float, K>(part + (int64_t)U.part[p] * A.part_stride + (D.off + (int64_t)U.drow[p] * nN + col) * K, o);
                 }
             }
         }
@@ -391,32 +492,40 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     }
     if (!active) return;
     const int rot = prot<float, K>(lane);
-    float acc[R][K], xv[K];
+    float2 acc[R][K / 2];   // packed, in the lane's rotated component order
+    float xv[K];
     const int cc = col >= 0 ? col : 0;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         pld<float, K>(rows + (size_t)r * A.row_stride, cc, rot, xv);
 #pragma unroll
-        for (int q = 0; q < K; ++q) acc[r][q] = pd[r] * xv[q];
+        for (int q = 0; q < K / 2; ++q) acc[r][q] = make_float2(pd[r] * xv[2 * q], pd[r] * xv[2 * q + 1]);
     }
     const int64_t base = D.pe_nn_ent + off + lane;
 #pragma unroll 2
     for (int v = 0; v < lmax; ++v) {
         const float c = A.coef[base + 32 * (int64_t)v];
         const int s = A.src[base + 32 * (int64_t)v];
+        const float2 c2 = make_float2(c, c);
 #pragma unroll
         for (int r = 0; r < R; ++r) {
             pld<float, K>(rows + (size_t)r * A.row_stride, s, rot, xv);
 #pragma unroll
-            for (int q = 0; q < K; ++q) acc[r][q] = fmaf(c, xv[q], acc[r][q]);
+            for (int q = 0; q < K / 2; ++q) acc[r][q] = __ffma2_rn(c2, make_float2(xv[2 * q], xv[2 * q + 1]), acc[r][q]);
         }
     }
     if (col < 0) return;
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         if (r >= nr) break;
-        prot_fix<float, K>(acc[r], rot);
-        pst<float, K>(out + (D.off + (int64_t)(r0 + r) * nN + col) * K, acc[r]);
+        float o[K];
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) {
+            o[2 * q] = acc[r][q].x;
+            o[2 * q + 1] = acc[r][q].y;
+        }
+        prot_fix<float, K>(o, rot);
+        pst<float, K>(out + (D.off + (int64_t)(r0 + r) * nN + col) * K, o);
     }
 }
 
@@ -479,12 +588,16 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     const Device &Dv = ctx->dev;
     const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
     const int wtab = 8 * Dv.wsign;
-    const int slot_elems = row_stride + wtab;
+    const int slot_elems = row_stride + wtab + 8;
     const size_t slot_bytes = (size_t)slot_elems * sizeof(float) + 16;
-    int S = (int)std::min<size_t>(8, target / slot_bytes);
-    used = S >= 2;
+    const int64_t lmaxe = Dv.core_list_max[NW == 18 ? 0 : 1];
+    const int list_elems = (int)(((std::max<int64_t>(lmaxe, 32) + 31) / 32) * 32);
+    constexpr int SI = ((2 * NW + 3) / 4) * 4;
+    const size_t fixed = 2 * (size_t)list_elems * 4 + 2 * SI * 4 + 16;
+    int S = target > fixed ? (int)std::min<size_t>(8, (target - fixed) / slot_bytes) : 0;
+    used = S >= 2 && NW * 32 >= 32;
     if (!used) return cudaSuccess;
-    const size_t smem = (size_t)S * slot_elems * sizeof(float) + 16 * (size_t)S;
+    const size_t smem = (size_t)S * slot_elems * sizeof(float) + fixed + 16 * (size_t)S;
     auto kern = hx_core_kernel<K, NW, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -492,8 +605,8 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, Dv.dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (NW + 1) * 32, smem)) != cudaSuccess) return e;
     const int grid = std::max(1, std::min(Dv.ncunits, nsm * std::max(per, 1)));
-    CoreArgs A{Dv.cunits, Dv.csrc, Dv.blocks, Dv.links, Dv.pe_perm, Dv.pe_sinfo, Dv.pe_ent, Dv.err,
-               Dv.ncunits, S, row_stride, wtab, slot_elems, (uint32_t)Dv.wsign, (int64_t)ctx->basis.dim * K};
+    CoreArgs A{Dv.cunits, Dv.csrc, Dv.blocks, Dv.pe_perm, Dv.pe_sinfo, Dv.pe_ent, Dv.err, Dv.ncunits, S,
+               row_stride, wtab, slot_elems, list_elems, (uint32_t)Dv.wsign, (int64_t)ctx->basis.dim * K};
     kern<<<grid, (NW + 1) * 32, smem, s>>>(A, Dv.wc32, x, part);
     return cudaGetLastError();
 }

@@ -282,7 +282,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW <= 8 ? 2 : 1) hx_pipe_kernel
 #pragma unroll
                             for (int dv = 0; dv < 2; ++dv) {
                                 const uint32_t en = ev[v0 + dv];
-                                const T w = Wu[en >> 16];
+                                const T w = Wu[(en >> 16) & 0x7FFFu];
                                 pld<T, K>(Xu, (int)(en & 0xFFFFu), rot, xv);
 #pragma unroll
                                 for (int q = 0; q < K; ++q) acc[j][q] = fma(w, xv[q], acc[j][q]);
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW <= 8 ? 2 : 1) hx_pipe_kernel
                     for (int v = 0; v < lmax; ++v) {
                         const uint32_t en = A.ent[base + 32 * (int64_t)v];
                         for (int u = 0; u < cu; ++u) {
-                            const T w = W0[(size_t)u * A.wrow + (en >> 16)];
+                            const T w = W0[(size_t)u * A.wrow + ((en >> 16) & 0x7FFFu)];
                             pld<T, K>(Xs + (size_t)u * A.row_stride, (int)(en & 0xFFFFu), rot, xv);
 #pragma unroll
                             for (int q = 0; q < K; ++q) acc[j][q] = fma(w, xv[q], acc[j][q]);

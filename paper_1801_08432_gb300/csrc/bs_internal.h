@@ -130,7 +130,7 @@ struct Ell {
 struct PermEll {
     std::vector<int32_t> perm;          // per sector: position -> column (sector offset in perm_off)
     std::vector<int64_t> perm_off;      // per neutron sector
-    std::vector<uint32_t> ent;          // one-body entries, packed like Tables::n1e
+    std::vector<uint32_t> ent;          // one-body entries, packed like Tables::n1e, plus a rotation bit (31)
     std::vector<int32_t> sinfo;         // per class and slice: (entry offset from class base, lmax)
     std::vector<int64_t> cls_ent, cls_sinfo;   // per one-body class: base of its entries / slice info
     std::vector<int32_t> nn_src;        // like-particle lists in the same order
@@ -156,10 +156,12 @@ struct CoreUnit {
     int meta[4];           // rank t of i in r (0..Z-1) | 256 if the sign of a+_i on c is -1
 };
 
-struct CoreSrc {
-    int sblock, srow;      // source block and proton row c + k
-    int link;              // the pn link dst block <- src block (its neutron lists)
+struct CoreSrc {           // 32 bytes: staged with its source row
+    int64_t x_elem;        // first basis index of the source row c + k (block offset + row * nN)
+    int32_t nN;            // its length (the source block's neutron sector)
     uint32_t wtab;         // W table (chunk, k) | 1 << 31 if the sign of a_k on c + k is -1
+    int64_t ent_base;      // neutron lists of the link dst block <- src block: first entry of the
+    int64_t sinfo_base;    // class in PermEll::ent and its per-slice (offset, longest list)
 };
 
 // pp term by (Z-2)-proton cores: a two-body term a+_i a+_j a_l a_k taking
@@ -278,6 +280,7 @@ struct Device {
     CoreSrc *csrc = nullptr;
     float *wc32 = nullptr;
     int ncunits = 0, nz = 0;
+    int64_t core_list_max[2] = {0, 0};   // largest list block of one column tile (18, 10 warps), entries
     PPUnit *ppunits = nullptr;
     int32_t *pps_row = nullptr;
     float *pps_w32 = nullptr, *pdiag32 = nullptr;

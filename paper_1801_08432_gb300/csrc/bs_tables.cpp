@@ -179,6 +179,57 @@ void bank_order(std::vector<std::vector<Entry>> &lists, Key key)
     lists.swap(out);
 }
 
+// Step order of the neutron one-body lists of one 32-column slice for the
+// kernels that read a 32-byte element (k = 8 floats) as two 16-byte chunks
+// and a 16-byte weight quadruple per entry.  Every entry also gets a rotation
+// bit (bit 31): which chunk its lane loads first.  At every step and in every
+// quarter warp (the lanes one 16-byte shared-memory load serves together) the
+// greedy picks, lane by lane (longest remaining list first), the entry and
+// rotation that add the fewest bank conflicts: a new chunk address in an
+// occupied residue mod 8 costs its occupancy + 1, a new weight row
+// (index (e >> 16) & 0x7FFF, residue mod 8) half as much.  Lists shorter than
+// the slice's longest are padded with `pad` (a zero weight), which also gets a
+// rotation.  Output: lists[lane] of length lmax, in step order.
+void bank_schedule_rot(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
+{
+    size_t lmax = 0;
+    for (auto &l : lists) lmax = std::max(lmax, l.size());
+    std::vector<std::vector<uint32_t>> rem = lists, out(lists.size());
+    for (size_t v = 0; v < lmax; ++v)
+        for (size_t q = 0; q * 8 < lists.size(); ++q) {
+            std::vector<size_t> lanes;
+            for (size_t l = q * 8; l < std::min(lists.size(), q * 8 + 8); ++l) lanes.push_back(l);
+            std::stable_sort(lanes.begin(), lanes.end(), [&](size_t a, size_t b) { return rem[a].size() > rem[b].size(); });
+            int ares[8] = {}, wres[8] = {};
+            std::vector<uint32_t> used_a, used_w;
+            for (size_t l : lanes) {
+                const bool has = !rem[l].empty();
+                const size_t nc = has ? rem[l].size() : 1;
+                double best = 1e30;
+                size_t bt = 0;
+                uint32_t br = 0;
+                for (size_t t = 0; t < nc; ++t) {
+                    const uint32_t e = has ? rem[l][t] : pad;
+                    const uint32_t w = (e >> 16) & 0x7FFFu;
+                    for (uint32_t r = 0; r < 2; ++r) {
+                        const uint32_t a = 2 * (e & 0xFFFFu) + r;
+                        const bool na = std::find(used_a.begin(), used_a.end(), a) == used_a.end();
+                        const bool nw = std::find(used_w.begin(), used_w.end(), w) == used_w.end();
+                        const double c = (na ? ares[a & 7] + 1 : 0) + 0.5 * (nw ? wres[w & 7] + 1 : 0);
+                        if (c < best) { best = c; bt = t; br = r; }
+                    }
+                }
+                const uint32_t e = has ? rem[l][bt] : pad;
+                if (has) rem[l].erase(rem[l].begin() + (long)bt);
+                const uint32_t a = 2 * (e & 0xFFFFu) + br, w = (e >> 16) & 0x7FFFu;
+                if (std::find(used_a.begin(), used_a.end(), a) == used_a.end()) { used_a.push_back(a); ares[a & 7]++; }
+                if (std::find(used_w.begin(), used_w.end(), w) == used_w.end()) { used_w.push_back(w); wres[w & 7]++; }
+                out[l].push_back(e | (br << 31));
+            }
+        }
+    lists.swap(out);
+}
+
 // Length-sorted, 32-column-sliced ELL of packed one-body lists given as a CSR
 // (ptr[0..ncols]).  put(csr_index) returns one entry.
 template <typename Put>
@@ -271,11 +322,11 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
                         lists.back().push_back(repack(T.n1.ent[(size_t)e]));
                     lmax = std::max(lmax, lists.back().size());
                 }
-                bank_order(lists, [](uint32_t e, int ln) { return 2 * (int)(e & 0xFFFFu) + (ln & 1); });
+                bank_schedule_rot(lists, (ws - 1u) << 16);   // padding: a zero W entry, source column 0
                 P.sinfo.push_back((int32_t)((int64_t)P.ent.size() - P.cls_ent[(size_t)cls]));
                 P.sinfo.push_back((int32_t)lmax);
                 const size_t base = P.ent.size();
-                P.ent.resize(base + lmax * 32, (ws - 1u) << 16);   // padding: a zero W entry, source column 0
+                P.ent.resize(base + lmax * 32, (ws - 1u) << 16);
                 for (size_t lane = 0; lane < 32; ++lane)
                     for (size_t v = 0; v < lists[lane].size(); ++v) P.ent[base + v * 32 + lane] = lists[lane][v];
             }
@@ -310,6 +361,9 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
                 }
         }
     }
+    // whole 16-byte groups at the end: kernels copy slice info in 16-byte pieces
+    while (P.sinfo.size() % 4) P.sinfo.push_back(0);
+    while (P.ent.size() % 4) P.ent.push_back((ws - 1u) << 16);
     // pre-signed W rows: group g, operator a, proton sign sp -> [ sp W[a][.] | -sp W[a][.] ]
     const size_t ng = I.ops.ops.size();
     T.ww_off.assign(ng, 0);
@@ -431,8 +485,11 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
                 if (blk < 0) continue;
                 const int l = link_of(x.u.dblock, blk);
                 if (l < 0) continue;
-                x.src.push_back(CoreSrc{blk, row, l,
-                                        (uint32_t)(q * (size_t)ns + (size_t)k) | (sign_below(c, k) < 0 ? 0x80000000u : 0u)});
+                const Block &Sb = B.blocks[(size_t)blk];
+                const int ncl = T.links[(size_t)l].ncls;
+                x.src.push_back(CoreSrc{Sb.off + (int64_t)row * Sb.nN, (int32_t)Sb.nN,
+                                        (uint32_t)(q * (size_t)ns + (size_t)k) | (sign_below(c, k) < 0 ? 0x80000000u : 0u),
+                                        T.pe.cls_ent[(size_t)ncl], T.pe.cls_sinfo[(size_t)ncl]});
             }
             x.u.nsrc = (int)x.src.size();
             x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)x.u.dblock].nN;

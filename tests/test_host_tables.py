@@ -321,7 +321,7 @@ def pipe_tables_matvec(c, x):
                     col = perm[po + p]
                     o, lmax = sinfo[cs + 2 * (p // 32)], sinfo[cs + 2 * (p // 32) + 1]
                     es = ent[ce + o + 32 * np.arange(lmax) + p % 32]
-                    Yd[r, col] += np.dot(wrow[es >> 16], Xs[ip, es & 0xFFFF])
+                    Yd[r, col] += np.dot(wrow[(es >> 16) & 0x7FFF], Xs[ip, es & 0xFFFF])
     return y
 
 
@@ -339,7 +339,8 @@ def test_pipe_tables_reproduce_oracle_matrix(name, Z, Nn, twoM):
 
 CORE_UNIT = np.dtype([("dblock", np.int32), ("nsrc", np.int32), ("src0", np.int64),
                       ("drow", np.int32, 4), ("meta", np.int32, 4)])
-CORE_SRC = np.dtype([("sblock", np.int32), ("srow", np.int32), ("link", np.int32), ("wtab", np.uint32)])
+CORE_SRC = np.dtype([("x_elem", np.int64), ("nN", np.int32), ("wtab", np.uint32),
+                     ("ent_base", np.int64), ("sinfo_base", np.int64)])
 
 
 PPG = 8
@@ -380,17 +381,15 @@ def core_tables_matvec(c, x, Z, pp_core=False):
         acc = np.zeros((4, nNd))
         po = sec_base[nsd][0]
         for q in range(u["nsrc"]):
-            sb, srow, link, wt = srcs[u["src0"] + q]
-            offs, _, _, nNs = blk(sb)
-            xs = x[offs + srow * nNs: offs + (srow + 1) * nNs]
+            xe, nNs, wt, ce, cs = srcs[u["src0"] + q]
+            xs = x[xe: xe + nNs]
             flip = ws if int(wt) >> 31 else 0
             W = wc[int(wt) & 0x7FFFFFFF]
-            ce, cs = cls_base[links[link][3]]
             for p in range(nNd):
                 col = perm[po + p]
                 o, lmax = sinfo[cs + 2 * (p // 32)], sinfo[cs + 2 * (p // 32) + 1]
                 es = ent[ce + o + 32 * np.arange(lmax) + p % 32].astype(np.int64)
-                acc[:, col] += W[(es >> 16) ^ flip].T @ xs[es & 0xFFFF]
+                acc[:, col] += W[((es >> 16) & 0x7FFF) ^ flip].T @ xs[es & 0xFFFF]
         for p4 in range(4):
             r = u["drow"][p4]
             if r < 0:
@@ -480,6 +479,16 @@ def test_core_units_structure():
     def below(m, s):
         return -1 if bin(m & ((1 << s) - 1)).count("1") % 2 else 1
 
+    def sd_of_elem(xe):
+        # the proton SD of the source row starting at basis index xe
+        for b_, (ps, ns_, off) in enumerate(B["blocks"]):
+            nN = int(B["n_sec"][ns_][3])
+            nP = int(B["p_sec"][ps][3])
+            if off <= xe < off + nP * nN:
+                assert (xe - off) % nN == 0
+                return sd_bits(b_, (xe - off) // nN)
+        raise AssertionError(xe)
+
     for u in units:
         cores, keys = set(), set()
         for p in range(4):
@@ -496,8 +505,8 @@ def test_core_units_structure():
         core = cores.pop()
         assert bin(core).count("1") == Z - 1
         for q in range(u["nsrc"]):
-            sb, srow, link, wt = srcs[u["src0"] + q]
-            s = sd_bits(sb, srow)
+            xe, nNs, wt, _, _ = srcs[u["src0"] + q]
+            s = sd_of_elem(int(xe))
             k_bits = s & ~core
             assert s & core == core and bin(k_bits).count("1") == 1
             k = k_bits.bit_length() - 1
