@@ -270,8 +270,8 @@ int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, do
  * bs_lanczos before it captures a graph; a first call inside a stream
  * capture without it falls back to the pipelined kernel).  A mode that does not fit
  * the basis falls back to the tiled kernel.  0 (default) = the mode bs_autotune picked
- * for the call's (k, dtype), else the first pipelined variant, else the first
- * row variant.  All modes give the same result up to summation order.
+ * for the call's (k, dtype), else mode 13 where it applies (FP32, k = 4, 8),
+ * else the first pipelined variant, else the first row variant.  All modes give the same result up to summation order.
  * Errors: BS_EINVAL. */
 int bs_set_kernel(bs_ctx *ctx, int mode);
 

@@ -197,7 +197,11 @@ int launch_hx(const bs_ctx *c, const void *x, void *y, int k, bs_dtype dt, void 
     const int R = row_variants();
     if (mode == 0) mode = c->tuned[dt == BS_F64 ? 0 : 1][kslot(k)];
     if (mode == 0 && e == cudaSuccess) {
-        e = launch_hx_pipe(c, x, y, k, dt, s, 0, used);
+        // not tuned: the core-grouped path where it applies, else the first
+        // pipelined variant, else the first row variant
+        e = launch_hx_core(c, x, y, k, dt, s, 2, used, t0, t1);
+        core_used = used;
+        if (e == cudaSuccess && !used) e = launch_hx_pipe(c, x, y, k, dt, s, 0, used);
         if (!used) mode = 2;
     }
     const int P = pipe_variants();

@@ -52,40 +52,97 @@ struct DF {   // double-float: value = hi + lo
     float hi, lo;
 };
 
+__device__ __forceinline__ double df_value(const DF &a) { return (double)a.hi + (double)a.lo; }
+
+// hi + lo += a * b exactly up to the final rounding of lo: the product is
+// split as p + e (fma) and p added by a two-sum
 __device__ __forceinline__ void df_add_prod(DF &acc, float a, float b)
 {
     const float p = a * b;
-    const float e = fmaf(a, b, -p);           // a*b = p + e exactly
-    const float s = acc.hi + p;               // two-sum of hi and p
+    const float e = fmaf(a, b, -p);
+    const float s = acc.hi + p;
     const float bb = s - acc.hi;
     const float err = (acc.hi - (s - bb)) + (p - bb);
     acc.hi = s;
     acc.lo += err + e;
 }
 
-__device__ __forceinline__ double df_value(const DF &a) { return (double)a.hi + (double)a.lo; }
+// hi + lo += s (two-sum: the rounding error of the addition is kept in lo)
+__device__ __forceinline__ void df_add(DF &acc, float s)
+{
+    const float t = acc.hi + s;
+    const float bb = t - acc.hi;
+    const float err = (acc.hi - (t - bb)) + (s - bb);
+    acc.hi = t;
+    acc.lo += err;
+}
 
-template <typename T>
+// Extended-precision sums of products.  FP32, EXACT: every product exactly
+// (p + e) into a double-float accumulator (~48 bits), for the entries of T and
+// for bs_block_dots.  FP32, not EXACT (the Gram-Schmidt coefficients):
+// products summed in FP32 over chunks of kChunk rows, each chunk sum added to
+// a double-float accumulator; a chunk's rounding error is at most
+// kChunk * 2^-24 of its sum of |products|, below the 2^-24 relative rounding
+// of the FP32 vectors, and the second Gram-Schmidt pass removes what the
+// first leaves.  FP64: FP64 FMAs.
+constexpr int kChunk = 16;
+template <typename T, bool EXACT>
 struct Accum;
 template <>
-struct Accum<float> {
+struct Accum<float, true> {
     DF v{0.f, 0.f};
     __device__ __forceinline__ void add(float a, float b) { df_add_prod(v, a, b); }
+    __device__ __forceinline__ void flush() {}
     __device__ __forceinline__ double get() const { return df_value(v); }
 };
 template <>
-struct Accum<double> {
+struct Accum<float, false> {
+    DF v{0.f, 0.f};
+    float c = 0.f;
+    __device__ __forceinline__ void add(float a, float b) { c = fmaf(a, b, c); }
+    __device__ __forceinline__ void flush()
+    {
+        df_add(v, c);
+        c = 0.f;
+    }
+    __device__ __forceinline__ double get() const { return df_value(v) + (double)c; }
+};
+template <bool EXACT>
+struct Accum<double, EXACT> {
     double v = 0.0;
     __device__ __forceinline__ void add(double a, double b) { v = fma(a, b, v); }
+    __device__ __forceinline__ void flush() {}
     __device__ __forceinline__ double get() const { return v; }
 };
+
+// K consecutive values (one basis state of a [dim][K] block), vector loads
+template <typename T, int K>
+__device__ __forceinline__ void ldrow(const T *p, T (&v)[K])
+{
+    if constexpr (sizeof(T) * K >= 16) {
+        constexpr int W = 16 / sizeof(T);
+#pragma unroll
+        for (int c = 0; c < K; c += W) {
+            if constexpr (sizeof(T) == 4) {
+                const float4 q = *reinterpret_cast<const float4 *>(p + c);
+                v[c] = q.x; v[c + 1] = q.y; v[c + 2] = q.z; v[c + 3] = q.w;
+            } else {
+                const double2 q = *reinterpret_cast<const double2 *>(p + c);
+                v[c] = q.x; v[c + 1] = q.y;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int c = 0; c < K; ++c) v[c] = p[c];
+    }
+}
 
 // partial[cta][b][i][j] = sum over this CTA's rows alpha of V_b[alpha][i] * W[alpha][j]
 // for the nb blocks V_b of the stored basis (stride `bstride` elements).
 // Thread (row slot r, column j): K threads share a row, one W column each.
 // Blocks are taken BG = 16 / K at a time, so W is read once per group and a
 // thread carries BG x K extended-precision sums.
-template <typename T, int K>
+template <typename T, int K, bool EXACT = true>
 __global__ void __launch_bounds__(kDotThreads) blk_dots(const T *__restrict__ V, int64_t bstride, int nb,
                                                         const T *__restrict__ W, int64_t dim,
                                                         double *__restrict__ partial, const int *__restrict__ nb_iter)
@@ -98,16 +155,25 @@ __global__ void __launch_bounds__(kDotThreads) blk_dots(const T *__restrict__ V,
     const int warp = tid >> 5, lane = tid & 31;
     for (int b0 = 0; b0 < nb; b0 += BG) {
         const int nbg = min(BG, nb - b0);
-        Accum<T> acc[BG][K];
+        Accum<T, EXACT> acc[BG][K];
+        int cnt = 0;
         for (int64_t a = (int64_t)blockIdx.x * RPS + r; a < dim; a += (int64_t)gridDim.x * RPS) {
             const T w = W[a * K + j];
 #pragma unroll
             for (int g = 0; g < BG; ++g) {
                 if (g < nbg) {
-                    const T *v = V + (int64_t)(b0 + g) * bstride + a * K;
+                    T v[K];
+                    ldrow<T, K>(V + (int64_t)(b0 + g) * bstride + a * K, v);
 #pragma unroll
                     for (int i = 0; i < K; ++i) acc[g][i].add(v[i], w);
                 }
+            }
+            if (++cnt == kChunk) {
+                cnt = 0;
+#pragma unroll
+                for (int g = 0; g < BG; ++g)
+#pragma unroll
+                    for (int i = 0; i < K; ++i) acc[g][i].flush();
             }
         }
         // reduce over the rows of the warp (lanes with equal j), then over warps
@@ -158,16 +224,17 @@ __global__ void blk_update(const T *__restrict__ V, int64_t bstride, int nb, con
     __syncthreads();
     for (int64_t a = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; a < dim; a += (int64_t)gridDim.x * blockDim.x) {
         T w[K];
-#pragma unroll
-        for (int j = 0; j < K; ++j) w[j] = W[a * K + j];
+        ldrow<T, K>(W + a * K, w);
         for (int b = 0; b < nb; ++b) {
-            const T *v = V + (int64_t)b * bstride + a * K;
+            T v[K];
+            ldrow<T, K>(V + (int64_t)b * bstride + a * K, v);
             const T *c = Cs + b * K * K;
 #pragma unroll
             for (int i = 0; i < K; ++i) {
-                const T vi = v[i];
+                T ci[K];
+                ldrow<T, K>(c + i * K, ci);
 #pragma unroll
-                for (int j = 0; j < K; ++j) w[j] = fma(-vi, c[i * K + j], w[j]);
+                for (int j = 0; j < K; ++j) w[j] = fma(-v[i], ci[j], w[j]);
             }
         }
 #pragma unroll
@@ -236,79 +303,133 @@ __global__ void resid_inplace(double *__restrict__ R, const double *__restrict__
         for (int m = 0; m < nm; ++m) R[a * ld + m] -= e[m] * X[a * ld + m];
 }
 
-// One thread: symmetric Jacobi on the K x K Gram matrix O (FP64).  Writes
-// M = U Lambda^(-1/2) (to normalize) and B = Lambda^(1/2) U^T; columns whose
+// One warp: symmetric Jacobi on the K x K Gram matrix O (FP64), K = 1, 2, 4
+// or 8.  Each round applies K/2 disjoint rotations at once (round-robin pair
+// schedule: state 0 fixed, the others cycled), one (pair, index) per lane,
+// so a sweep of all K(K-1)/2 pairs takes K-1 rounds.  Writes M = U
+// Lambda^(-1/2) (to normalize) and B = Lambda^(1/2) U^T; columns whose
 // eigenvalue is below rel * max are flagged (bit i of *flags) and get a zero
 // column in M and a zero row in B.  Also symmetrizes A in place when given.
-__global__ void small_gram(int K, const double *__restrict__ O, double rel, double *__restrict__ M,
-                           double *__restrict__ B, int *__restrict__ flags, double *__restrict__ A,
-                           const int *__restrict__ iter)
+__global__ void __launch_bounds__(32) small_gram(int K, const double *__restrict__ O, double rel,
+                                                 double *__restrict__ M, double *__restrict__ B,
+                                                 int *__restrict__ flags, double *__restrict__ A,
+                                                 const int *__restrict__ iter)
 {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    __shared__ double a[64], u[64], cs[4][2];
+    __shared__ int pq[4][2];
+    const int lane = threadIdx.x;
     if (iter) {   // graph replay: B_n and A_n of iteration n
         B += (int64_t)(*iter) * K * K;
         if (A) A += (int64_t)(*iter) * K * K;
     }
-    double a[64], u[64];
-    for (int i = 0; i < K; ++i)
-        for (int j = 0; j < K; ++j) {
-            a[i * K + j] = 0.5 * (O[i * K + j] + O[j * K + i]);
-            u[i * K + j] = i == j ? 1.0 : 0.0;
-        }
-    if (A) {
+    for (int e = lane; e < K * K; e += 32) {
+        const int i = e / K, jj = e % K;
+        a[e] = 0.5 * (O[i * K + jj] + O[jj * K + i]);
+        u[e] = i == jj ? 1.0 : 0.0;
+    }
+    if (A && lane == 0) {
         for (int i = 0; i < K; ++i)
-            for (int j = i + 1; j < K; ++j) {
-                const double s = 0.5 * (A[i * K + j] + A[j * K + i]);
-                A[i * K + j] = A[j * K + i] = s;
+            for (int jj = i + 1; jj < K; ++jj) {
+                const double sv = 0.5 * (A[i * K + jj] + A[jj * K + i]);
+                A[i * K + jj] = A[jj * K + i] = sv;
             }
     }
-    for (int sweep = 0; sweep < 30; ++sweep) {
+    __syncwarp();
+    const int np = K / 2;                  // rotations per round
+    const int m = lane / K, r = lane % K;  // this lane: rotation m, index r (m < np)
+    for (int sweep = 0; sweep < 30 && K > 1; ++sweep) {
         double off = 0.0, tot = 0.0;
-        for (int i = 0; i < K; ++i)
-            for (int j = 0; j < K; ++j) {
-                tot += a[i * K + j] * a[i * K + j];
-                if (i != j) off += a[i * K + j] * a[i * K + j];
-            }
+        for (int e = lane; e < K * K; e += 32) {
+            const double v2 = a[e] * a[e];
+            tot += v2;
+            if (e / K != e % K) off += v2;
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            off += __shfl_xor_sync(0xffffffffu, off, o);
+            tot += __shfl_xor_sync(0xffffffffu, tot, o);
+        }
         if (off <= 1e-32 * tot) break;
-        for (int p = 0; p < K; ++p)
-            for (int q = p + 1; q < K; ++q) {
+        for (int t = 0; t < K - 1; ++t) {
+            if (lane < np) {
+                // circle method: position i holds state 0 (i = 0) or 1 + (i - 1 + t) mod (K - 1)
+                auto st = [&](int i) { return i == 0 ? 0 : 1 + (i - 1 + t) % (K - 1); };
+                int p = st(lane), q = st(K - 1 - lane);
+                if (p > q) { const int x = p; p = q; q = x; }
+                pq[lane][0] = p;
+                pq[lane][1] = q;
                 const double apq = a[p * K + q];
-                if (apq == 0.0) continue;
-                // rotation angle that zeroes a[p][q]
-                const double theta = 0.5 * (a[q * K + q] - a[p * K + p]) / apq;
-                const double t = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                const double c = 1.0 / sqrt(t * t + 1.0), s = t * c;
-                for (int r = 0; r < K; ++r) {   // columns p, q
-                    const double arp = a[r * K + p], arq = a[r * K + q];
-                    a[r * K + p] = c * arp - s * arq;
-                    a[r * K + q] = s * arp + c * arq;
+                double c = 1.0, sn = 0.0;
+                if (apq != 0.0) {
+                    // rotation angle that zeroes a[p][q]
+                    const double theta = 0.5 * (a[q * K + q] - a[p * K + p]) / apq;
+                    const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    c = 1.0 / sqrt(tt * tt + 1.0);
+                    sn = tt * c;
                 }
-                for (int r = 0; r < K; ++r) {   // rows p, q
-                    const double apr = a[p * K + r], aqr = a[q * K + r];
-                    a[p * K + r] = c * apr - s * aqr;
-                    a[q * K + r] = s * apr + c * aqr;
-                }
-                for (int r = 0; r < K; ++r) {
-                    const double urp = u[r * K + p], urq = u[r * K + q];
-                    u[r * K + p] = c * urp - s * urq;
-                    u[r * K + q] = s * urp + c * urq;
-                }
+                cs[lane][0] = c;
+                cs[lane][1] = sn;
             }
-    }
-    double lmax = 0.0;
-    for (int i = 0; i < K; ++i) lmax = fmax(lmax, a[i * K + i]);
-    int fl = 0;
-    for (int i = 0; i < K; ++i) {
-        const double lam = a[i * K + i];
-        const bool bad = !(lam > rel * lmax) || !(lam > 0.0);
-        if (bad) fl |= 1 << i;
-        const double sq = bad ? 0.0 : sqrt(lam), isq = bad ? 0.0 : 1.0 / sqrt(lam);
-        for (int r = 0; r < K; ++r) {
-            M[r * K + i] = u[r * K + i] * isq;
-            B[i * K + r] = sq * u[r * K + i];
+            __syncwarp();
+            const bool on = m < np;
+            int p = 0, q = 0;
+            double c = 1.0, sn = 0.0;
+            if (on) {
+                p = pq[m][0];
+                q = pq[m][1];
+                c = cs[m][0];
+                sn = cs[m][1];
+            }
+            // columns p, q of A and U (row r)
+            double arp = 0, arq = 0, urp = 0, urq = 0;
+            if (on) {
+                arp = a[r * K + p]; arq = a[r * K + q];
+                urp = u[r * K + p]; urq = u[r * K + q];
+            }
+            __syncwarp();
+            if (on) {
+                a[r * K + p] = c * arp - sn * arq;
+                a[r * K + q] = sn * arp + c * arq;
+                u[r * K + p] = c * urp - sn * urq;
+                u[r * K + q] = sn * urp + c * urq;
+            }
+            __syncwarp();
+            // rows p, q of A (column r)
+            double apr = 0, aqr = 0;
+            if (on) {
+                apr = a[p * K + r];
+                aqr = a[q * K + r];
+            }
+            __syncwarp();
+            if (on) {
+                a[p * K + r] = c * apr - sn * aqr;
+                a[q * K + r] = sn * apr + c * aqr;
+            }
+            __syncwarp();
         }
     }
-    *flags = fl;
+    if (lane == 0) {
+        double lmax = 0.0;
+        for (int i = 0; i < K; ++i) lmax = fmax(lmax, a[i * K + i]);
+        int fl = 0;
+        for (int i = 0; i < K; ++i) {
+            const double lam = a[i * K + i];
+            const bool bad = !(lam > rel * lmax) || !(lam > 0.0);
+            if (bad) fl |= 1 << i;
+        }
+        *flags = fl;
+        pq[0][0] = fl;
+    }
+    __syncwarp();
+    const int fl = pq[0][0];
+    for (int e = lane; e < K * K; e += 32) {
+        const int rr = e / K, i = e % K;   // M[rr][i], B[i][rr]
+        const double lam = a[i * K + i];
+        const bool bad = (fl >> i) & 1;
+        const double sq = bad ? 0.0 : sqrt(lam), isq = bad ? 0.0 : 1.0 / sqrt(lam);
+        M[rr * K + i] = u[rr * K + i] * isq;
+        B[i * K + rr] = sq * u[rr * K + i];
+    }
 }
 
 // Column `col` of the [dim][K] block X <- Gaussian numbers from a SplitMix64
@@ -341,11 +462,11 @@ struct LState {
 // nb_iter / out_iter (device, may be null): take the block count n+1 or the
 // output slot n from the iteration counter, for graph replay.  nb_max bounds
 // the launch when the count comes from the device.
-template <typename T, int K>
+template <typename T, int K, bool EXACT = true>
 void dots(LState &L, const T *V, int nb, const T *W, double *out, const int *nb_iter = nullptr,
           const int *out_iter = nullptr, int nb_max = 0)
 {
-    blk_dots<T, K><<<L.ncta, kDotThreads, 0, L.s>>>(V, L.bstride, nb, W, L.dim, L.partial, nb_iter);
+    blk_dots<T, K, EXACT><<<L.ncta, kDotThreads, 0, L.s>>>(V, L.bstride, nb, W, L.dim, L.partial, nb_iter);
     const int n = (nb_iter ? nb_max : nb) * K * K;
     dots_reduce<<<(n + 255) / 256, 256, 0, L.s>>>(L.partial, L.ncta, nb * K * K, out, nb_iter, out_iter, K * K);
 }
@@ -421,7 +542,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
     // orthonormalize the pivot block (FP64 Gram, one reorthogonalization-free QR)
     cudaMemcpyAsync(W, pivot, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
     dots<T, K>(L, W, 1, W, L.C);
-    small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bn, L.flags, nullptr, nullptr);
+    small_gram<<<1, 32, 0, L.s>>>(K, L.C, rel, L.M, L.Bn, L.flags, nullptr, nullptr);
     blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V, L.dim, nullptr, 0, nullptr);
 
     // Graph mode: the whole block iteration (H X, alpha, reorthogonalization,
@@ -447,11 +568,11 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
             dots<T, K>(L, Xcur, 1, W, L.Ahist, nullptr, d_iter, 1);
             update<T, K>(L, Xcur, 1, L.Ahist, W, nullptr, d_iter, 1);
             for (int p = 0; p < passes; ++p) {
-                dots<T, K>(L, V, 1, W, L.C, d_iter, nullptr, niter + 1);
+                dots<T, K, false>(L, V, 1, W, L.C, d_iter, nullptr, niter + 1);
                 update<T, K>(L, V, 1, L.C, W, d_iter, nullptr, niter + 1);
             }
             dots<T, K>(L, W, 1, W, L.C);
-            small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist, L.flags, L.Ahist, d_iter);
+            small_gram<<<1, 32, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist, L.flags, L.Ahist, d_iter);
             blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V, L.dim, d_iter, L.bstride, Xcur);
             iter_advance<<<1, 1, 0, L.s>>>(d_iter);
             cudaEventRecord(ev[2], L.s);
@@ -480,11 +601,11 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         dots<T, K>(L, Vn, 1, W, An);
         update<T, K>(L, Vn, 1, An, W);
         for (int p = 0; p < passes; ++p) {
-            dots<T, K>(L, V, n + 1, W, L.C);
+            dots<T, K, false>(L, V, n + 1, W, L.C);
             update<T, K>(L, V, n + 1, L.C, W);
         }
         dots<T, K>(L, W, 1, W, L.C);
-        small_gram<<<1, 1, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist + (size_t)n * K * K, L.flags, An, nullptr);
+        small_gram<<<1, 32, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist + (size_t)n * K * K, L.flags, An, nullptr);
         blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V + (int64_t)(n + 1) * L.bstride, L.dim, nullptr, 0, nullptr);
         cudaEventRecord(ev[2], L.s);
         }
@@ -508,12 +629,12 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
                 if (flags >> i & 1)
                     fill_random_col<T, K><<<L.ncta, 256, 0, L.s>>>(Vn1, i, 0xB5297A4D3F84D5B5ull + 7919ull * (uint64_t)(n * K + i), L.dim);
             for (int p = 0; p < 2; ++p) {
-                dots<T, K>(L, V, n + 1, Vn1, L.C);
+                dots<T, K, false>(L, V, n + 1, Vn1, L.C);
                 update<T, K>(L, V, n + 1, L.C, Vn1);
             }
             cudaMemcpyAsync(W, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
             dots<T, K>(L, W, 1, W, L.C);
-            small_gram<<<1, 1, 0, L.s>>>(K, L.C, 1e-20, L.M, L.Bn, L.flags, nullptr, nullptr);
+            small_gram<<<1, 32, 0, L.s>>>(K, L.C, 1e-20, L.M, L.Bn, L.flags, nullptr, nullptr);
             blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, Vn1, L.dim, nullptr, 0, nullptr);
             // B_n <- G B_n with G = Bn (the Gram factor of the refilled block: W = Vnew G)
             std::vector<double> G(K * K), Bn(K * K), out(K * K, 0.0);
