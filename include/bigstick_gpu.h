@@ -260,11 +260,12 @@ int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, do
  * of 16 bytes or more per basis state); 11..14 = the core-grouped path for
  * FP32 with k = 4 or 8: a persistent kernel computes the pn term per
  * (Z-1)-proton core (up to four destination rows per staged source row) into
- * Z partial vectors (11: 18 consumer warps, 12: 10); in 11, 12 the pipelined
- * kernel computes the like-particle terms into one more; in 13, 14 a second
- * persistent kernel computes the pp two-body term per (Z-2)-proton core into
- * C(Z,2) more and a row-tile kernel (13: 4 rows, 14: 2 rows per CTA) the nn
- * term and the proton single-particle energies into one more; a last kernel
+ * Z partial vectors (11, 13: 18 consumer warps with one 32-column slice each;
+ * 12, 14: 9 warps with two slices each, a long and a short list); in 11, 12
+ * the pipelined kernel computes the like-particle terms into one more; in
+ * 13, 14 a second persistent kernel computes the pp two-body term per
+ * (Z-2)-proton core into C(Z,2) more and a row-tile kernel (4 rows per CTA)
+ * the nn term and the proton single-particle energies into one more; a last kernel
  * sums the partial vectors in a fixed order (workspace: up to
  * (Z + C(Z,2) + 1) x dim x k floats, allocated on first use, or by
  * bs_lanczos before it captures a graph; a first call inside a stream

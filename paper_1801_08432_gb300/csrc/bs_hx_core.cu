@@ -78,6 +78,27 @@ __device__ __forceinline__ void ldx(const float *row, uint32_t en, float (&v)[K]
     }
 }
 
+// One list entry of one destination column: the gathered element of the
+// staged source row times the four weights of the entry's weight row.
+template <int K>
+__device__ __forceinline__ void core_step(const float *Xs, const float *Wt, uint32_t en, uint32_t flip,
+                                          float2 (&acc)[4][K / 2])
+{
+    const float4 w = *reinterpret_cast<const float4 *>(Wt + 4 * (((en >> 16) & 0x7FFFu) ^ flip));
+    float2 xv[K / 2];
+    ldx2<K>(Xs, en, xv);
+    const float2 w0 = make_float2(w.x, w.x), w1 = make_float2(w.y, w.y);
+    const float2 w2 = make_float2(w.z, w.z), w3 = make_float2(w.w, w.w);
+#pragma unroll
+    for (int qq = 0; qq < K / 2; ++qq) {
+        // two correctly rounded fused multiply-adds per instruction
+        acc[0][qq] = __ffma2_rn(w0, xv[qq], acc[0][qq]);
+        acc[1][qq] = __ffma2_rn(w1, xv[qq], acc[1][qq]);
+        acc[2][qq] = __ffma2_rn(w2, xv[qq], acc[2][qq]);
+        acc[3][qq] = __ffma2_rn(w3, xv[qq], acc[3][qq]);
+    }
+}
+
 struct CoreArgs {
     const CoreUnit *units;
     const CoreSrc *src;
@@ -92,27 +113,32 @@ struct CoreArgs {
     int wtab;          // floats per weight table (2 wsign x 4)
     int slot_elems;    // row_stride + wtab + 8 (the slot's CoreSrc)
     int list_elems;    // entries per list buffer (multiple of 32)
+    int nlb;           // list buffers (2..4)
     uint32_t ws;       // wsign
     int64_t part_stride;   // dim * K
 };
 
-// Shared memory: S slots [source row | weight table | CoreSrc], two list
+// Shared memory: S slots [source row | weight table | CoreSrc], nlb list
 // buffers (one link's neutron lists for the tile's slices) with their slice
-// info, then the barriers: full[S], empty[S], list_empty[2].  A "group" is a
+// info, then the barriers: full[S], empty[S], list_empty[nlb].  A "group" is a
 // run of slots of one tile that share a link; its lists arrive with its first
-// slot, in buffer (group & 1), and each consumer warp releases the buffer when
-// it starts the next group.
-template <int K, int NW, int MINB>
+// slot, in buffer (group % nlb), and each consumer warp releases the buffer
+// when it starts the next group, so the producer can run nlb - 1 groups ahead.
+// CPT = 1: consumer warp w owns 32-column slice w of the tile; CPT = 2: it
+// owns slices w and ns - 1 - w (ns slices in the tile), a long and a short
+// list in the sector's list-length order, which balances the warps' work.
+template <int K, int NW, int MINB, int CPT>
 __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     hx_core_kernel(CoreArgs A, const float *__restrict__ wc, const float *__restrict__ x, float *__restrict__ part)
 {
     extern __shared__ __align__(128) unsigned char smem[];
-    constexpr int C = NW * 32;                        // columns per tile
-    constexpr int SI = ((2 * NW + 3) / 4) * 4;        // slice-info ints per buffer
+    constexpr int SL = NW * CPT;                      // slices per tile
+    constexpr int C = SL * 32;                        // columns per tile
+    constexpr int SI = ((2 * SL + 3) / 4) * 4;        // slice-info ints per buffer
     float *slots = reinterpret_cast<float *>(smem);
     uint32_t *lists = reinterpret_cast<uint32_t *>(slots + (size_t)A.S * A.slot_elems);
-    int32_t *sinf = reinterpret_cast<int32_t *>(lists + 2 * (size_t)A.list_elems);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sinf + 2 * SI);
+    int32_t *sinf = reinterpret_cast<int32_t *>(lists + (size_t)A.nlb * A.list_elems);
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sinf + A.nlb * SI);
     const uint32_t full0 = su32(bars), empty0 = su32(bars + A.S), lempty0 = su32(bars + 2 * A.S);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -121,8 +147,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             bar_init(full0 + 8u * s, 1);
             bar_init(empty0 + 8u * s, NW);
         }
-        bar_init(lempty0, NW);
-        bar_init(lempty0 + 8u, NW);
+        for (int b = 0; b < A.nlb; ++b) bar_init(lempty0 + 8u * b, NW);
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
@@ -138,7 +163,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             const int nsl = (nN + 31) / 32;
             const int ntile = (nN + C - 1) / C;
             for (int tile = 0; tile < ntile; ++tile) {
-                const int sl0 = tile * NW, sl1 = min(nsl, sl0 + NW);
+                const int sl0 = tile * SL, sl1 = min(nsl, sl0 + SL);
                 int64_t prev = -1;
                 for (int q0 = 0; q0 < nsrc; q0 += 32) {
                     const int qm = q0 + lane;
@@ -171,10 +196,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                             const int round = c / A.S;
                             if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) bad = 1;
                             uint32_t lbytes = 0, sbytes = 0;
-                            const int b = (g + (newg ? 1 : 0)) & 1;
+                            const int b = (g + (newg ? 1 : 0)) % A.nlb;
                             if (!bad && newg) {
-                                const int gn = g + 1;
-                                if (gn >= 2 && bar_wait(lempty0 + 8u * b, (uint32_t)((gn >> 1) - 1) & 1u)) bad = 1;
+                                const int gn = g + 1;   // its use n = gn / nlb of buffer b waits for release n - 1
+                                if (gn >= A.nlb && bar_wait(lempty0 + 8u * b, (uint32_t)(gn / A.nlb - 1) & 1u)) bad = 1;
                                 lbytes = (uint32_t)((lend - o0) * 4);
                                 sbytes = (uint32_t)(((2 * (sl1 - sl0) + 3) / 4) * 16);
                             }
@@ -216,21 +241,26 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
         const DevBlock D = A.blocks[A.units[u].dblock];
         const int nN = D.nN;
         const int64_t doff = D.off;
+        const int nsl = (nN + 31) / 32;
         const int ntile = (nN + C - 1) / C;
         for (int tile = 0; tile < ntile; ++tile) {
-            const int pos0 = tile * C + warp * 32;   // warp-uniform
-            const bool active = pos0 < nN;
-            const int pos = pos0 + lane;
-            const int col = pos < nN ? A.perm[D.perm_off + pos] : -1;
+            const int nst = min(SL, nsl - tile * SL);   // slices in this tile
+            // this warp's slices (warp-uniform): sa always, sb only when CPT = 2
+            const int sa = warp, sb = CPT == 2 ? nst - 1 - warp : -1;
+            const bool hasA = CPT == 2 ? sa <= sb : sa < nst;
+            const bool hasB = CPT == 2 && sa < sb;
+            const int posA = tile * C + sa * 32 + lane, posB = tile * C + sb * 32 + lane;
+            const int colA = hasA && posA < nN ? A.perm[D.perm_off + posA] : -1;
+            const int colB = hasB && posB < nN ? A.perm[D.perm_off + posB] : -1;
             // packed accumulators: acc[p][j] holds components 2j, 2j+1 of destination row p
-            float2 acc[4][K / 2];
+            float2 accA[4][K / 2], accB[4][K / 2];
 #pragma unroll
             for (int p = 0; p < 4; ++p)
 #pragma unroll
-                for (int q = 0; q < K / 2; ++q) acc[p][q] = make_float2(0.0f, 0.0f);
+                for (int q = 0; q < K / 2; ++q) accA[p][q] = accB[p][q] = make_float2(0.0f, 0.0f);
             int64_t prev = -1;
-            int lmax = 0;
-            const uint32_t *lst = lists;
+            int la = 0, lb = 0;
+            const uint32_t *lstA = lists, *lstB = lists;
             for (int q = 0; q < nsrc; ++q, ++c) {
                 const int s = c % A.S;
                 const int round = c / A.S;
@@ -241,48 +271,40 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 const float *Xs = slots + (size_t)s * A.slot_elems;
                 const float *Wt = Xs + A.row_stride;
                 const CoreSrc *cs = reinterpret_cast<const CoreSrc *>(Wt + A.wtab);
-                const int64_t sb = cs->sinfo_base;
+                const int64_t sbase = cs->sinfo_base;
                 const uint32_t wtab = cs->wtab;
-                if (sb != prev) {
+                if (sbase != prev) {
                     // a new group: release the previous group's list buffer, read this one
                     __syncwarp();
-                    if (g >= 0 && lane == 0) bar_arrive(lempty0 + 8u * (g & 1));
+                    if (g >= 0 && lane == 0) bar_arrive(lempty0 + 8u * (g % A.nlb));
                     ++g;
-                    prev = sb;
-                    const int b = g & 1;
-                    lst = lists + (size_t)b * A.list_elems;
-                    if (active) {
-                        const int32_t *si = sinf + b * SI;
-                        lmax = si[2 * warp + 1];
-                        lst += si[2 * warp] - si[0] + lane;
-                    }
+                    prev = sbase;
+                    const int b = g % A.nlb;
+                    const int32_t *si = sinf + b * SI;
+                    const uint32_t *lb0 = lists + (size_t)b * A.list_elems - si[0] + lane;
+                    la = hasA ? si[2 * sa + 1] : 0;
+                    lb = hasB ? si[2 * sb + 1] : 0;
+                    lstA = lb0 + (hasA ? si[2 * sa] : 0);
+                    lstB = lb0 + (hasB ? si[2 * sb] : 0);
                 }
-                if (active) {
-                    // entries straight from the staged list (32 lanes, 128 contiguous bytes per step)
-                    const uint32_t flip = (wtab >> 31) ? A.ws : 0u;   // sign of a_k on c + k: swap the +W / -W halves
-                    float2 xv[K / 2];
+                // entries straight from the staged lists (32 lanes, 128 contiguous bytes per step)
+                const uint32_t flip = (wtab >> 31) ? A.ws : 0u;   // sign of a_k on c + k: swap the +W / -W halves
+                const int lm = min(la, lb);
+                int v = 0;
+                for (; v < lm; ++v) {
+                    core_step<K>(Xs, Wt, lstA[32 * v], flip, accA);
+                    core_step<K>(Xs, Wt, lstB[32 * v], flip, accB);
+                }
 #pragma unroll 2
-                    for (int v = 0; v < lmax; ++v) {
-                        const uint32_t en = lst[32 * v];
-                        const float4 w = *reinterpret_cast<const float4 *>(Wt + 4 * (((en >> 16) & 0x7FFFu) ^ flip));
-                        ldx2<K>(Xs, en, xv);
-                        const float2 w0 = make_float2(w.x, w.x), w1 = make_float2(w.y, w.y);
-                        const float2 w2 = make_float2(w.z, w.z), w3 = make_float2(w.w, w.w);
-#pragma unroll
-                        for (int qq = 0; qq < K / 2; ++qq) {
-                            // two correctly rounded fused multiply-adds per instruction
-                            acc[0][qq] = __ffma2_rn(w0, xv[qq], acc[0][qq]);
-                            acc[1][qq] = __ffma2_rn(w1, xv[qq], acc[1][qq]);
-                            acc[2][qq] = __ffma2_rn(w2, xv[qq], acc[2][qq]);
-                            acc[3][qq] = __ffma2_rn(w3, xv[qq], acc[3][qq]);
-                        }
-                    }
-                }
+                for (int va = v; va < la; ++va) core_step<K>(Xs, Wt, lstA[32 * va], flip, accA);
+#pragma unroll 2
+                for (int vb = v; vb < lb; ++vb) core_step<K>(Xs, Wt, lstB[32 * vb], flip, accB);
                 __syncwarp();
                 if (lane == 0) bar_arrive(empty0 + 8u * s);
             }
-            if (col >= 0) {
-                const CoreUnit *U = A.units + u;
+            const CoreUnit *U = A.units + u;
+            auto store = [&](int col, float2 (&acc)[4][K / 2]) {
+                if (col < 0) return;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
                     const int drow = U->drow[p], meta = U->meta[p];
@@ -296,7 +318,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                     }
                     pst<float, K>(part + (int64_t)(meta & 255) * A.part_stride + (doff + (int64_t)drow * nN + col) * K, o);
                 }
-            }
+            };
+            store(colA, accA);
+            if (CPT == 2) store(colB, accB);
         }
     }
 }
@@ -548,14 +572,14 @@ __global__ void __launch_bounds__(256) hx_sum_partials(const float4 *__restrict_
 }
 
 struct CoreVariant {
-    int nw, minb;
+    int nw, cpt;     // consumer warps, 32-column slices per warp
     size_t target;   // shared-memory budget per CTA
     bool pp;         // pp term by (Z-2)-proton cores, nn by row tiles of nn_rows rows
     int nn_rows;
 };
 
 constexpr CoreVariant kCoreVariants[] = {
-    {18, 1, 200 * 1024, false, 0}, {10, 2, 105 * 1024, false, 0}, {18, 1, 200 * 1024, true, 4}, {18, 1, 200 * 1024, true, 2}};
+    {18, 1, 200 * 1024, false, 0}, {9, 2, 200 * 1024, false, 0}, {18, 1, 200 * 1024, true, 4}, {9, 2, 200 * 1024, true, 4}};
 constexpr int kNumCore = 4;
 
 template <int K, int R, int MINB>
@@ -582,7 +606,7 @@ cudaError_t launch_nn_k(const bs_ctx *ctx, const float *x, float *out, cudaStrea
     return R == 2 ? launch_nn_t<K, 2, 2>(ctx, x, out, s, used) : launch_nn_t<K, 4, 1>(ctx, x, out, s, used);
 }
 
-template <int K, int NW, int MINB>
+template <int K, int NW, int MINB, int CPT>
 cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaStream_t s, size_t target, bool &used)
 {
     const Device &Dv = ctx->dev;
@@ -590,15 +614,23 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     const int wtab = 8 * Dv.wsign;
     const int slot_elems = row_stride + wtab + 8;
     const size_t slot_bytes = (size_t)slot_elems * sizeof(float) + 16;
-    const int64_t lmaxe = Dv.core_list_max[NW == 18 ? 0 : 1];
+    static_assert(NW * CPT == 18 || NW * CPT == 10, "list bounds are built for tiles of 18 or 10 slices");
+    const int64_t lmaxe = Dv.core_list_max[NW * CPT == 18 ? 0 : 1];
     const int list_elems = (int)(((std::max<int64_t>(lmaxe, 32) + 31) / 32) * 32);
-    constexpr int SI = ((2 * NW + 3) / 4) * 4;
-    const size_t fixed = 2 * (size_t)list_elems * 4 + 2 * SI * 4 + 16;
-    int S = target > fixed ? (int)std::min<size_t>(8, (target - fixed) / slot_bytes) : 0;
-    used = S >= 2 && NW * 32 >= 32;
+    constexpr int SI = ((2 * NW * CPT + 3) / 4) * 4;
+    // list buffers: three when the ring still keeps seven slots, else two (a
+    // deeper ring pays more than a third buffer)
+    int nlb = 3, S = 0;
+    for (; nlb >= 2; --nlb) {
+        const size_t fixed = (size_t)nlb * list_elems * 4 + (size_t)nlb * SI * 4 + 8 * (size_t)nlb;
+        S = target > fixed ? (int)std::min<size_t>(8, (target - fixed) / slot_bytes) : 0;
+        if (S >= 7 || nlb == 2) break;
+    }
+    const size_t fixed = (size_t)nlb * list_elems * 4 + (size_t)nlb * SI * 4 + 8 * (size_t)nlb;
+    used = S >= 2;
     if (!used) return cudaSuccess;
     const size_t smem = (size_t)S * slot_elems * sizeof(float) + fixed + 16 * (size_t)S;
-    auto kern = hx_core_kernel<K, NW, MINB>;
+    auto kern = hx_core_kernel<K, NW, MINB, CPT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int nsm = 0, per = 0;
@@ -606,7 +638,7 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (NW + 1) * 32, smem)) != cudaSuccess) return e;
     const int grid = std::max(1, std::min(Dv.ncunits, nsm * std::max(per, 1)));
     CoreArgs A{Dv.cunits, Dv.csrc, Dv.blocks, Dv.pe_perm, Dv.pe_sinfo, Dv.pe_ent, Dv.err, Dv.ncunits, S,
-               row_stride, wtab, slot_elems, list_elems, (uint32_t)Dv.wsign, (int64_t)ctx->basis.dim * K};
+               row_stride, wtab, slot_elems, list_elems, nlb, (uint32_t)Dv.wsign, (int64_t)ctx->basis.dim * K};
     kern<<<grid, (NW + 1) * 32, smem, s>>>(A, Dv.wc32, x, part);
     return cudaGetLastError();
 }
@@ -639,8 +671,8 @@ template <int K>
 cudaError_t launch_core_k(const bs_ctx *ctx, const float *x, float *part, cudaStream_t s, int v, bool &used)
 {
     const CoreVariant P = kCoreVariants[v];
-    if (P.nw == 18) return launch_core_t<K, 18, 1>(ctx, x, part, s, P.target, used);
-    return launch_core_t<K, 10, 2>(ctx, x, part, s, P.target, used);
+    if (P.cpt == 2) return launch_core_t<K, 9, 1, 2>(ctx, x, part, s, P.target, used);
+    return launch_core_t<K, 18, 1, 1>(ctx, x, part, s, P.target, used);
 }
 
 // partial vectors: Z of the pn kernel, C(Z,2) of the pp kernel, one of the
