@@ -162,20 +162,37 @@ def aggregate_max(values, dist=None):
     return [float(v) for v in t.cpu()]
 
 
+def reorth_bytes(dim, k, s, n_iter, passes):
+    """Compulsory HBM bytes of the vector work between H X and the next
+    block in n_iter block-Lanczos iterations (blocks of dim * k * s bytes):
+    alpha (V_n^T W reads 2 blocks; W -= V_n A_n reads 2, writes 1), each
+    Gram-Schmidt pass against the n + 1 stored blocks (dots read n + 2
+    blocks; the update reads n + 2 and writes 1), the Gram matrix W^T W (1)
+    and the normalization (read 1, write 1): 8 + passes (2 n + 5) blocks in
+    iteration n."""
+    blocks = sum(8 + passes * (2 * n + 5) for n in range(n_iter))
+    return float(blocks) * dim * k * s
+
+
 def lanczos_check(ctx, N, I, torch, stream):
     """FP32-mixed block Lanczos (k=8) against FP64 single-vector Lanczos on the
     same space: lowest 5 eigenvalues after the FP64 refinement, residuals and
     the time split."""
     out = {}
+    hbm_gbs = (peaks() or {}).get("hbm_gbs", 6800.0)
     runs = {"fp64_k1": (1, N.BS_F64, 300), "fp32_k8": (8, N.BS_F32, 80)}
     for name, (k, dt, niter) in runs.items():
         p = torch.from_numpy(I.random_block(ctx.dim, k, seed=I.PIVOT_SEED)).to(
             "cuda", torch.float64 if dt == N.BS_F64 else torch.float32)
         ev, rep = ctx.lanczos(p, k, dt, niter, 5, refine=True, stream=stream)
-        out[name] = {"k": k, "block_iterations": rep["iterations"], "vector_matvecs": rep["iterations"] * k,
+        nit = rep["iterations"]
+        rb = reorth_bytes(ctx.dim, k, 8 if dt == N.BS_F64 else 4, nit, 2)
+        out[name] = {"k": k, "block_iterations": nit, "vector_matvecs": nit * k,
                      "evals_mev": [round(float(e), 9) for e in ev], "residual_mev": rep["residual"],
                      "ms_total": round(rep["ms_total"], 1), "ms_matvec": round(rep["ms_matvec"], 1),
-                     "ms_reorth_alpha_gram": round(rep["ms_reorth"], 1), "delta_conv": rep["delta_conv"]}
+                     "ms_reorth_alpha_gram": round(rep["ms_reorth"], 1), "delta_conv": rep["delta_conv"],
+                     "reorth_alg_bytes": rb, "reorth_gbs": round(rb / (rep["ms_reorth"] / 1000.0) / 1e9, 1),
+                     "reorth_hbm_frac": round(rb / (rep["ms_reorth"] / 1000.0) / 1e9 / hbm_gbs, 3)}
     # compare the pairs both runs converged (FP64 residual <= 1e-3 MeV bounds the
     # eigenvalue error by r^2/gap)
     a, b = out["fp32_k8"], out["fp64_k1"]
@@ -289,6 +306,20 @@ def ours(args):
     mode_ms = {}
     if args.mode:
         ctx.set_kernel(args.mode)
+    if args.profile_lanczos:
+        # only an FP32 block Lanczos of that many block iterations (for ncu of the reorthogonalization kernels)
+        k = args.k or 8
+        if args.mode:
+            ctx.set_kernel(args.mode)
+        p = torch.from_numpy(I.random_block(dim, k, seed=I.PIVOT_SEED)).to("cuda", torch.float32)
+        ev, rep = ctx.lanczos(p, k, N.BS_F32, args.profile_lanczos, 5, refine=False, stream=sp)
+        rb = reorth_bytes(dim, k, 4, rep["iterations"], 2)
+        if rank == 0:
+            print(json.dumps({"profile_lanczos": True, "k": k, "iterations": rep["iterations"],
+                              "ms_reorth_alpha_gram": rep["ms_reorth"], "ms_matvec": rep["ms_matvec"],
+                              "reorth_gbs": rb / (rep["ms_reorth"] / 1000.0) / 1e9}), flush=True)
+        ctx.close()
+        return 0
     if args.profile_only:
         # a fixed kernel mode and k, warm-up launches then the timed ones, nothing else (for ncu)
         ms, _, _ = timed(args.k or 8, N.BS_F32, args.steps, args.warmup)
@@ -403,6 +434,8 @@ def main():
     ap.add_argument("--no-lanczos", action="store_true", help="skip the Lanczos accuracy check")
     ap.add_argument("--mode", type=int, default=0, help="fix the H x kernel mode (bs_set_kernel) instead of autotuning")
     ap.add_argument("--profile-only", action="store_true", help="only the FP32 H*X launches (for ncu)")
+    ap.add_argument("--profile-lanczos", type=int, default=0,
+                    help="only an FP32 block Lanczos of this many block iterations (for ncu)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

@@ -289,16 +289,22 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 }
                 // entries straight from the staged lists (32 lanes, 128 contiguous bytes per step)
                 const uint32_t flip = (wtab >> 31) ? A.ws : 0u;   // sign of a_k on c + k: swap the +W / -W halves
-                const int lm = min(la, lb);
-                int v = 0;
-                for (; v < lm; ++v) {
-                    core_step<K>(Xs, Wt, lstA[32 * v], flip, accA);
-                    core_step<K>(Xs, Wt, lstB[32 * v], flip, accB);
+                if constexpr (CPT == 1) {
+                    // one slice: the plain loop (the two-slice form costs ~7 % more instructions here)
+#pragma unroll 2
+                    for (int v = 0; v < la; ++v) core_step<K>(Xs, Wt, lstA[32 * v], flip, accA);
+                } else {
+                    const int lm = min(la, lb);
+                    int v = 0;
+                    for (; v < lm; ++v) {
+                        core_step<K>(Xs, Wt, lstA[32 * v], flip, accA);
+                        core_step<K>(Xs, Wt, lstB[32 * v], flip, accB);
+                    }
+#pragma unroll 2
+                    for (int va = v; va < la; ++va) core_step<K>(Xs, Wt, lstA[32 * va], flip, accA);
+#pragma unroll 2
+                    for (int vb = v; vb < lb; ++vb) core_step<K>(Xs, Wt, lstB[32 * vb], flip, accB);
                 }
-#pragma unroll 2
-                for (int va = v; va < la; ++va) core_step<K>(Xs, Wt, lstA[32 * va], flip, accA);
-#pragma unroll 2
-                for (int vb = v; vb < lb; ++vb) core_step<K>(Xs, Wt, lstB[32 * vb], flip, accB);
                 __syncwarp();
                 if (lane == 0) bar_arrive(empty0 + 8u * s);
             }

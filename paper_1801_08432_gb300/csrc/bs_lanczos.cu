@@ -34,9 +34,11 @@
 #include <cmath>
 #include <cstring>
 #include <mutex>
+#include <type_traits>
 #include <vector>
 
 #include "bs_internal.h"
+#include "bs_tma.cuh"
 
 namespace bs {
 
@@ -198,7 +200,11 @@ __global__ void __launch_bounds__(kDotThreads) blk_dots(const T *__restrict__ V,
 }
 
 // out[e] = sum over CTAs of partial[cta][e], e < n (fixed order)
-__global__ void dots_reduce(const double *__restrict__ partial, int ncta, int n, double *__restrict__ out,
+__device__ __forceinline__ double part_value(double p) { return p; }
+__device__ __forceinline__ double part_value(float2 p) { return (double)p.x + (double)p.y; }
+
+template <typename P>
+__global__ void dots_reduce(const P *__restrict__ partial, int ncta, int n, double *__restrict__ out,
                             const int *__restrict__ nb_iter, const int *__restrict__ out_iter, int kk)
 {
     if (nb_iter) n = (*nb_iter + 1) * kk;       // graph replay: n+1 blocks of k x k
@@ -206,7 +212,7 @@ __global__ void dots_reduce(const double *__restrict__ partial, int ncta, int n,
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= n) return;
     double t = 0.0;
-    for (int c = 0; c < ncta; ++c) t += partial[(int64_t)c * n + e];
+    for (int c = 0; c < ncta; ++c) t += part_value(partial[(int64_t)c * n + e]);
     out[e] = t;
 }
 
@@ -456,8 +462,497 @@ struct LState {
     void *V = nullptr, *W = nullptr;      // basis blocks and work block
     double *partial = nullptr, *C = nullptr, *M = nullptr, *Bn = nullptr, *Ahist = nullptr, *Bhist = nullptr;
     int *flags = nullptr;
+    int *err = nullptr;                   // device status word (bounded waits of the streamed kernels)
+    bool padded = false;                  // V, W blocks readable up to the next 16 bytes past dim * K
     cudaStream_t s = 0;
 };
+
+// ---- streamed block products (the HBM-bound part of every Lanczos step)
+//
+// V_b^T W and W -= sum_b V_b C_b read the whole stored basis once per call.
+// A CTA takes chunks of kRsCE consecutive elements (kRsCE / K rows) in turn;
+// per chunk it streams the tile of W and then the matching tile of every
+// block V_b through a ring of S shared-memory stages that one producer
+// thread fills with TMA bulk copies (S x 8 KB in flight per CTA at FP32, no
+// registers held by outstanding loads).  W is thus read once per call, not
+// once per group of blocks.  Consumer thread (r, j), r < 256 / K, owns
+// column j of the rows r + (256 / K) m, m < kRsRT, of each tile.
+//
+// Dot products: each thread sums its kRsRT rows (FP32 FMAs unless EXACT),
+// the lanes of a warp with equal j are combined (the first two steps in
+// FP32, so a plain FP32 sum never spans more than 4 kRsRT = 32 products;
+// then double-float), the 8 warps in a fixed order, and the tile's K x K
+// result is added to the CTA's double-float partial in global memory, which
+// dots_reduce sums over CTAs in FP64 in a fixed order: deterministic.
+// EXACT forms every product exactly (p + fma residual) in double-float, as
+// the row-slot kernel does.  FP64 vectors use FP64 throughout.
+// The update applies, per output element, the blocks in order and within a
+// block i = 0..K-1, the order of blk_update, so both give identical W.
+// Applicability: 16-byte aligned V, W and block stride (the TMA rule) and
+// either dim * K * sizeof(T) a multiple of 16 or blocks padded to 16 bytes
+// (the Lanczos driver's own buffers); anything else runs the row-slot
+// kernels above.
+constexpr int kRsCons = 256;     // consumer threads (8 warps) + one producer warp
+constexpr int kRsCE = 2048;      // elements per tile
+constexpr int kRsRT = 8;         // rows per consumer thread per tile = kRsCE / kRsCons
+
+__device__ __forceinline__ float2 df_sum(float2 a, float2 b)
+{
+    const float s = a.x + b.x;
+    const float bb = s - a.x;
+    const float e = (a.x - (s - bb)) + (b.x - bb);
+    const float t = e + a.y + b.y;
+    const float hi = s + t;
+    return make_float2(hi, t - (hi - s));
+}
+
+template <typename T>
+struct RsRed;
+template <>
+struct RsRed<float> {   // double-float (hi, lo)
+    using S = float2;
+    static __device__ __forceinline__ S zero() { return make_float2(0.f, 0.f); }
+    static __device__ __forceinline__ S add(S a, S b) { return df_sum(a, b); }
+    static __device__ __forceinline__ S shfl(S a, int o)
+    {
+        return make_float2(__shfl_xor_sync(0xffffffffu, a.x, o), __shfl_xor_sync(0xffffffffu, a.y, o));
+    }
+    static __device__ __forceinline__ double value(S a) { return (double)a.x + (double)a.y; }
+};
+template <>
+struct RsRed<double> {
+    using S = double;
+    static __device__ __forceinline__ S zero() { return 0.0; }
+    static __device__ __forceinline__ S add(S a, S b) { return a + b; }
+    static __device__ __forceinline__ S shfl(S a, int o) { return __shfl_xor_sync(0xffffffffu, a, o); }
+    static __device__ __forceinline__ double value(S a) { return a; }
+};
+
+// Stage and phase of the tile sequence (S stages, used in turn).
+template <int S>
+struct RsRing {
+    int s = 0;
+    uint32_t ph = 0;   // parity of the current use of stage s
+    int uses = 0;      // tiles so far
+    __device__ __forceinline__ void next()
+    {
+        ++uses;
+        if (++s == S) {
+            s = 0;
+            ph ^= 1u;
+        }
+    }
+};
+
+// Producer of both kernels: for each chunk of this CTA, the W tile then the
+// tiles of blocks 0..nb-1 into the stages in turn.  Returns false on a wait
+// timeout.
+template <typename T, int S>
+__device__ __forceinline__ bool rs_produce(const T *V, int64_t bstride, int nb, const T *W, int64_t nel, T *ring,
+                                           uint32_t full0, uint32_t empty0)
+{
+    using namespace tma;
+    const int64_t nch = (nel + kRsCE - 1) / kRsCE;
+    RsRing<S> q;
+    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int64_t e0 = ch * kRsCE;
+        // a multiple of 16 bytes: exact unless the caller's blocks are padded
+        const uint32_t bytes = (uint32_t)((min((int64_t)kRsCE, nel - e0) * (int64_t)sizeof(T) + 15) / 16 * 16);
+        for (int b = -1; b < nb; ++b, q.next()) {
+            // stage s was used S tiles ago: wait until every consumer warp released it
+            if (q.uses >= S && bar_wait(empty0 + 8u * q.s, q.ph ^ 1u)) return false;
+            bar_expect_tx(full0 + 8u * q.s, bytes);
+            bulk_copy(su32(ring + (size_t)q.s * kRsCE), (b < 0 ? W : V + (int64_t)b * bstride) + e0, bytes,
+                      full0 + 8u * q.s);
+        }
+    }
+    return true;
+}
+
+// partial[cta][b][i][j] (RsRed<T>::S) = this CTA's share of sum_alpha V_b[alpha][i] W[alpha][j].
+// Warps 0-7 consume tiles: thread (r, i), r < 256 / K, takes element i of
+// rows r + (256 / K) m, m < kRsRT, with the W rows of those elements in
+// registers for the whole chunk (one conflict-free scalar shared-memory read
+// per V element).  Each warp sums its tile over its rows and lanes and hands
+// the K x K result to warp 9 through a ring of SR staging slots; warp 9 adds
+// the 8 warps' results in a fixed order to the CTA's running sums and, at the
+// end, writes them out.  So no consumer waits on a CTA-wide barrier.  The
+// running sums stay in shared memory when nb K^2 of them fit (acc_in_smem),
+// else in `partial` itself.
+constexpr int kRsSR = 4;   // staging slots of warp results
+// FP32, K = 8: the consumer lanes hand over their raw sums (lane (rl, i), 8
+// values j each) instead of reducing across lanes themselves; per warp the
+// slot holds [i][j][rl] with an i-stride of 36 floats (conflict-free stores:
+// bank 4 i + rl + 4 j), read back by the reducer as one 16-byte load per
+// (warp, i, j).
+constexpr int kRsLaneIS = 36;
+constexpr int kRsLaneSR = 3;
+
+template <typename T, int K, bool EXACT>
+__host__ __device__ constexpr bool rs_lane_staging()
+{
+    return std::is_same<T, float>::value && !EXACT && K == 8;
+}
+
+template <typename T, int K, bool EXACT, int S>
+__global__ void __launch_bounds__(kRsCons + 64, sizeof(T) == 4 ? 2 : 1)
+    rs_dots(const T *__restrict__ V, int64_t bstride, int nb, const T *__restrict__ W, int64_t nel,
+            typename RsRed<T>::S *__restrict__ partial, int acc_in_smem, const int *__restrict__ nb_iter, int *err)
+{
+    using namespace tma;
+    using R = RsRed<T>;
+    using Sv = typename R::S;
+    constexpr int NR = kRsCons / K;
+    constexpr int NCW = kRsCons / 32;   // consumer warps
+    constexpr bool PACKED = std::is_same<T, float>::value && !EXACT && K >= 2;   // two-wide FP32 FMAs
+    constexpr bool LANES = rs_lane_staging<T, K, EXACT>();
+    constexpr int SR = LANES ? kRsLaneSR : kRsSR;
+    constexpr int SLOT = LANES ? NCW * K * kRsLaneIS * 4 : NCW * K * K * (int)sizeof(Sv);   // bytes per staging slot
+    if (nb_iter) nb = *nb_iter + 1;   // graph replay: blocks 0..n of iteration n
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // full[S], empty[S], pfull[SR], pempty[SR] (256 bytes)
+    T *ring = reinterpret_cast<T *>(smem + 256);
+    unsigned char *stage = reinterpret_cast<unsigned char *>(ring + (size_t)S * kRsCE);   // [SR][SLOT]
+    Sv *red = reinterpret_cast<Sv *>(stage);
+    Sv *cacc = acc_in_smem ? reinterpret_cast<Sv *>(stage + (size_t)SR * SLOT)
+                           : partial + (int64_t)blockIdx.x * nb * K * K;   // [nb][K * K]
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + S);
+    const uint32_t pfull0 = su32(bars + 2 * S), pempty0 = su32(bars + 2 * S + SR);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            bar_init(full0 + 8u * s, 1);
+            bar_init(empty0 + 8u * s, NCW);
+        }
+        for (int s = 0; s < SR; ++s) {
+            bar_init(pfull0 + 8u * s, NCW);
+            bar_init(pempty0 + 8u * s, 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    const int64_t nch = (nel + kRsCE - 1) / kRsCE;
+    if (warp == NCW) {   // producer
+        if (lane == 0 && !rs_produce<T, S>(V, bstride, nb, W, nel, ring, full0, empty0)) atomicExch(err, BS_ETIMEOUT);
+        return;
+    }
+    if (warp == NCW + 1) {   // reducer: the 8 warps' tile results, in warp order, into the running sums
+        RsRing<SR> sr;
+        bool bad = false, first = true;
+        for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x, first = false) {
+            for (int b = 0; b < nb; ++b, sr.next()) {
+                if (!bad && __any_sync(0xffffffffu, bar_wait(pfull0 + 8u * sr.s, sr.ph))) {
+                    bad = true;
+                    if (lane == 0) atomicExch(err, BS_ETIMEOUT);
+                }
+                if constexpr (LANES) {
+                    // per (warp, i, j): the 4 lanes' sums in FP32 (32 products), then warps in double-float
+                    const float *sb = reinterpret_cast<const float *>(stage + (size_t)sr.s * SLOT);
+#pragma unroll
+                    for (int h = 0; h < 2; ++h) {
+                        const int e = lane + 32 * h, ii = e / K, jj = e % K;
+                        DF tot{0.f, 0.f};
+#pragma unroll
+                        for (int w2 = 0; w2 < NCW; ++w2) {
+                            const float4 v4 = *reinterpret_cast<const float4 *>(sb + ((size_t)w2 * K + ii) * kRsLaneIS + jj * 4);
+                            const float sw = (v4.x + v4.y) + (v4.z + v4.w);
+                            if (w2 == 0) tot = DF{sw, 0.f};
+                            else df_add(tot, sw);
+                        }
+                        const float2 t2 = make_float2(tot.hi, tot.lo);
+                        Sv *p = cacc + (int64_t)b * K * K + e;
+                        *p = first ? t2 : R::add(*p, t2);
+                    }
+                } else {
+                    const Sv *rb = red + (size_t)sr.s * NCW * K * K;
+                    for (int e = lane; e < K * K; e += 32) {
+                        Sv tot = rb[e];
+#pragma unroll
+                        for (int w2 = 1; w2 < NCW; ++w2) tot = R::add(tot, rb[(size_t)w2 * K * K + e]);
+                        Sv *p = cacc + (int64_t)b * K * K + e;
+                        *p = first ? tot : R::add(*p, tot);
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) bar_arrive(pempty0 + 8u * sr.s);
+            }
+        }
+        __syncwarp();
+        if (acc_in_smem) {
+            for (int e = lane; e < nb * K * K; e += 32)
+                partial[(int64_t)blockIdx.x * nb * K * K + e] = first ? R::zero() : cacc[e];
+        } else if (first) {   // no chunk for this CTA: its partials are zero
+            for (int e = lane; e < nb * K * K; e += 32) partial[(int64_t)blockIdx.x * nb * K * K + e] = R::zero();
+        }
+        return;
+    }
+    const int i = tid % K, r = tid / K;
+    RsRing<S> q;
+    RsRing<SR> sr;
+    bool bad = false;
+    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int rows = (int)(min((int64_t)kRsCE, nel - ch * kRsCE) / K);
+        T w[kRsRT][K];
+        {
+            if (!bad && __any_sync(0xffffffffu, bar_wait(full0 + 8u * q.s, q.ph))) {
+                bad = true;
+                if (lane == 0) atomicExch(err, BS_ETIMEOUT);
+            }
+            const T *tile = ring + (size_t)q.s * kRsCE;
+#pragma unroll
+            for (int m = 0; m < kRsRT; ++m) {
+                const int a = r + NR * m;
+                if (!bad && a < rows) {
+                    ldrow<T, K>(tile + a * K, w[m]);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < K; ++j) w[m][j] = T(0);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) bar_arrive(empty0 + 8u * q.s);
+            q.next();
+        }
+        for (int b = 0; b < nb; ++b, q.next(), sr.next()) {
+            if (!bad && __any_sync(0xffffffffu, bar_wait(full0 + 8u * q.s, q.ph))) {
+                bad = true;
+                if (lane == 0) atomicExch(err, BS_ETIMEOUT);
+            }
+            const T *tile = ring + (size_t)q.s * kRsCE;
+            Sv sum[K];
+            float2 acc[PACKED ? K / 2 : 1];
+            if constexpr (PACKED) {
+#pragma unroll
+                for (int j = 0; j < K / 2; ++j) acc[j] = make_float2(0.f, 0.f);
+                if (!bad) {
+#pragma unroll
+                    for (int m = 0; m < kRsRT; ++m) {
+                        const int a = r + NR * m;
+                        if (a < rows) {
+                            const float v = tile[a * K + i];
+                            const float2 v2 = make_float2(v, v);
+#pragma unroll
+                            for (int j = 0; j < K / 2; ++j)
+                                acc[j] = __ffma2_rn(v2, make_float2(w[m][2 * j], w[m][2 * j + 1]), acc[j]);
+                        }
+                    }
+                }
+            }
+            if constexpr (LANES) {
+                // raw lane sums go to the reducer
+            } else if constexpr (PACKED) {
+                // the first two lane steps in FP32 (at most 4 kRsRT products per plain sum)
+                const float2 one = make_float2(1.f, 1.f);
+#pragma unroll
+                for (int o = K; o < 32 && o <= 2 * K; o <<= 1)
+#pragma unroll
+                    for (int j = 0; j < K / 2; ++j) {
+                        const float2 t2 = make_float2(__shfl_xor_sync(0xffffffffu, acc[j].x, o),
+                                                      __shfl_xor_sync(0xffffffffu, acc[j].y, o));
+                        acc[j] = __ffma2_rn(t2, one, acc[j]);
+                    }
+#pragma unroll
+                for (int j = 0; j < K / 2; ++j) {
+                    sum[2 * j] = make_float2(acc[j].x, 0.f);
+                    sum[2 * j + 1] = make_float2(acc[j].y, 0.f);
+                }
+#pragma unroll
+                for (int o = 4 * K; o < 32; o <<= 1)
+#pragma unroll
+                    for (int j = 0; j < K; ++j) sum[j] = R::add(sum[j], R::shfl(sum[j], o));
+            } else if constexpr (std::is_same<T, float>::value && !EXACT) {   // K = 1
+                float acc = 0.f;
+                if (!bad) {
+#pragma unroll
+                    for (int m = 0; m < kRsRT; ++m) {
+                        const int a = r + NR * m;
+                        if (a < rows) acc = fmaf(tile[a], w[m][0], acc);
+                    }
+                }
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                sum[0] = make_float2(acc, 0.f);
+#pragma unroll
+                for (int o = 4; o < 32; o <<= 1) sum[0] = R::add(sum[0], R::shfl(sum[0], o));
+            } else {
+                if constexpr (std::is_same<T, float>::value) {
+                    DF acc[K];
+#pragma unroll
+                    for (int j = 0; j < K; ++j) acc[j] = DF{0.f, 0.f};
+                    if (!bad) {
+#pragma unroll
+                        for (int m = 0; m < kRsRT; ++m) {
+                            const int a = r + NR * m;
+                            if (a < rows) {
+                                const float v = tile[a * K + i];
+#pragma unroll
+                                for (int j = 0; j < K; ++j) df_add_prod(acc[j], v, w[m][j]);
+                            }
+                        }
+                    }
+#pragma unroll
+                    for (int j = 0; j < K; ++j) sum[j] = make_float2(acc[j].hi, acc[j].lo);
+                } else {
+#pragma unroll
+                    for (int j = 0; j < K; ++j) sum[j] = 0.0;
+                    if (!bad) {
+#pragma unroll
+                        for (int m = 0; m < kRsRT; ++m) {
+                            const int a = r + NR * m;
+                            if (a < rows) {
+                                const double v = (double)tile[a * K + i];
+#pragma unroll
+                                for (int j = 0; j < K; ++j) sum[j] = fma(v, (double)w[m][j], sum[j]);
+                            }
+                        }
+                    }
+                }
+#pragma unroll
+                for (int o = K; o < 32; o <<= 1)
+#pragma unroll
+                    for (int j = 0; j < K; ++j) sum[j] = R::add(sum[j], R::shfl(sum[j], o));
+            }
+            __syncwarp();
+            if (lane == 0) bar_arrive(empty0 + 8u * q.s);
+            // hand the warp's result to the reducer (staging slot free once it read it)
+            if (!bad && sr.uses >= SR && __any_sync(0xffffffffu, bar_wait(pempty0 + 8u * sr.s, sr.ph ^ 1u))) {
+                bad = true;
+                if (lane == 0) atomicExch(err, BS_ETIMEOUT);
+            }
+            if constexpr (LANES) {
+                float *sb = reinterpret_cast<float *>(stage + (size_t)sr.s * SLOT) + ((size_t)warp * K + i) * kRsLaneIS + lane / K;
+#pragma unroll
+                for (int j = 0; j < K / 2; ++j) {
+                    sb[(2 * j) * 4] = acc[j].x;
+                    sb[(2 * j + 1) * 4] = acc[j].y;
+                }
+            } else if (lane < K) {   // lane = i here: the warp's sums of row i
+                Sv *rb = red + ((size_t)sr.s * NCW + warp) * K * K;
+#pragma unroll
+                for (int j = 0; j < K; ++j) rb[i * K + j] = sum[j];
+            }
+            __syncwarp();
+            if (lane == 0) bar_arrive(pfull0 + 8u * sr.s);
+        }
+    }
+}
+
+// W[alpha][j] -= sum_b sum_i V_b[alpha][i] C[b][i][j]  (C: FP64, used in the vectors' precision).
+// Thread t owns the whole rows t + 256 m, m < 8 / K, of each chunk (its W
+// values in registers), reads each of its V rows once (consecutive lanes,
+// consecutive rows) and C_b as warp-uniform broadcasts.  FP32 pairs of
+// columns go through two-wide FMAs, each component rounded as fmaf would.
+template <typename T, int K, int S>
+__global__ void __launch_bounds__(kRsCons + 32) rs_update(const T *__restrict__ V, int64_t bstride, int nb,
+                                                          const double *__restrict__ C, T *__restrict__ W,
+                                                          int64_t nel, const int *__restrict__ nb_iter,
+                                                          const int *__restrict__ c_iter, int *err)
+{
+    using namespace tma;
+    constexpr int RU = kRsCE / K / kRsCons;   // rows per thread per tile
+    constexpr bool PACKED = std::is_same<T, float>::value && K >= 2;
+    if (nb_iter) nb = *nb_iter + 1;
+    if (c_iter) C += (int64_t)(*c_iter) * K * K;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
+    T *ring = reinterpret_cast<T *>(smem + 128);
+    T *Cs = ring + (size_t)S * kRsCE;   // [nb][i][j]
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + S);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < S; ++s) {
+            bar_init(full0 + 8u * s, 1);
+            bar_init(empty0 + 8u * s, kRsCons / 32);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    for (int e = tid; e < nb * K * K; e += blockDim.x) Cs[e] = (T)C[e];
+    __syncthreads();
+    if (warp == kRsCons / 32) {
+        if (lane == 0 && !rs_produce<T, S>(V, bstride, nb, W, nel, ring, full0, empty0)) atomicExch(err, BS_ETIMEOUT);
+        return;
+    }
+    const int64_t nch = (nel + kRsCE - 1) / kRsCE;
+    RsRing<S> q;
+    bool bad = false;
+    for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
+        const int64_t e0 = ch * kRsCE;
+        const int rows = (int)(min((int64_t)kRsCE, nel - e0) / K);
+        T w[RU][K];
+        for (int b = -1; b < nb; ++b, q.next()) {
+            if (!bad && __any_sync(0xffffffffu, bar_wait(full0 + 8u * q.s, q.ph))) {
+                bad = true;
+                if (lane == 0) atomicExch(err, BS_ETIMEOUT);
+            }
+            const T *tile = ring + (size_t)q.s * kRsCE;
+            if (b < 0) {
+#pragma unroll
+                for (int m = 0; m < RU; ++m) {
+                    const int a = tid + kRsCons * m;
+                    if (!bad && a < rows) {
+                        ldrow<T, K>(tile + a * K, w[m]);
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < K; ++j) w[m][j] = T(0);
+                    }
+                }
+            } else if (!bad) {
+                T v[RU][K];
+#pragma unroll
+                for (int m = 0; m < RU; ++m) {
+                    const int a = tid + kRsCons * m;
+                    if (a < rows) {
+                        ldrow<T, K>(tile + a * K, v[m]);
+                    } else {
+#pragma unroll
+                        for (int ii = 0; ii < K; ++ii) v[m][ii] = T(0);
+                    }
+                }
+                const T *cb = Cs + (size_t)b * K * K;
+#pragma unroll
+                for (int ii = 0; ii < K; ++ii) {
+                    T ci[K];
+                    ldrow<T, K>(cb + ii * K, ci);
+#pragma unroll
+                    for (int m = 0; m < RU; ++m) {
+                        if constexpr (PACKED) {
+                            const float2 nv2 = make_float2(-v[m][ii], -v[m][ii]);
+#pragma unroll
+                            for (int j = 0; j < K / 2; ++j) {
+                                const float2 o2 = __ffma2_rn(nv2, make_float2(ci[2 * j], ci[2 * j + 1]),
+                                                             make_float2(w[m][2 * j], w[m][2 * j + 1]));
+                                w[m][2 * j] = o2.x;
+                                w[m][2 * j + 1] = o2.y;
+                            }
+                        } else {
+#pragma unroll
+                            for (int j = 0; j < K; ++j) w[m][j] = fma(-v[m][ii], ci[j], w[m][j]);
+                        }
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) bar_arrive(empty0 + 8u * q.s);
+        }
+        if (!bad) {
+#pragma unroll
+            for (int m = 0; m < RU; ++m) {
+                const int a = tid + kRsCons * m;
+                if (a < rows) pst<T, K>(W + e0 + (int64_t)a * K, w[m]);
+            }
+        }
+    }
+}
+
+template <typename T>
+constexpr int rs_stages() { return sizeof(T) == 4 ? 6 : 4; }
+
+template <typename T, int K>
+bool rs_applies(const LState &L, const void *V, const void *W)
+{
+    return L.err && ((uintptr_t)V % 16 == 0) && ((uintptr_t)W % 16 == 0) &&
+           ((L.bstride * (int64_t)sizeof(T)) % 16 == 0) && (L.padded || (L.dim * K * (int64_t)sizeof(T)) % 16 == 0);
+}
 
 // nb_iter / out_iter (device, may be null): take the block count n+1 or the
 // output slot n from the iteration counter, for graph replay.  nb_max bounds
@@ -466,17 +961,54 @@ template <typename T, int K, bool EXACT = true>
 void dots(LState &L, const T *V, int nb, const T *W, double *out, const int *nb_iter = nullptr,
           const int *out_iter = nullptr, int nb_max = 0)
 {
-    blk_dots<T, K, EXACT><<<L.ncta, kDotThreads, 0, L.s>>>(V, L.bstride, nb, W, L.dim, L.partial, nb_iter);
     const int n = (nb_iter ? nb_max : nb) * K * K;
-    dots_reduce<<<(n + 255) / 256, 256, 0, L.s>>>(L.partial, L.ncta, nb * K * K, out, nb_iter, out_iter, K * K);
+    if (rs_applies<T, K>(L, V, W)) {
+        using Sv = typename RsRed<T>::S;
+        constexpr int S = rs_lane_staging<T, K, EXACT>() ? 5 : rs_stages<T>();   // lane staging needs the room
+        const size_t acc = (size_t)(nb_iter ? nb_max : nb) * K * K * sizeof(Sv);
+        constexpr bool LANES = rs_lane_staging<T, K, EXACT>();
+        const size_t slots = LANES ? (size_t)kRsLaneSR * 8 * K * kRsLaneIS * 4 : (size_t)kRsSR * 8 * K * K * sizeof(Sv);
+        const size_t fixed = 256 + (size_t)S * kRsCE * sizeof(T) + slots;
+        const int acc_in_smem = fixed + acc <= 113 * 1024;
+        const size_t smem = fixed + (acc_in_smem ? acc : 0);
+        static unsigned long long attr = 0;   // per instantiation: devices already configured
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && !(attr >> dev & 1ull)) {
+            cudaFuncSetAttribute(rs_dots<T, K, EXACT, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 113 * 1024);
+            attr |= 1ull << dev;
+        }
+        rs_dots<T, K, EXACT, S><<<L.ncta, kRsCons + 64, smem, L.s>>>(V, L.bstride, nb, W, L.dim * K,
+                                                                     reinterpret_cast<Sv *>(L.partial), acc_in_smem,
+                                                                     nb_iter, L.err);
+        dots_reduce<Sv><<<(n + 255) / 256, 256, 0, L.s>>>(reinterpret_cast<const Sv *>(L.partial), L.ncta, nb * K * K,
+                                                          out, nb_iter, out_iter, K * K);
+        return;
+    }
+    blk_dots<T, K, EXACT><<<L.ncta, kDotThreads, 0, L.s>>>(V, L.bstride, nb, W, L.dim, L.partial, nb_iter);
+    dots_reduce<double><<<(n + 255) / 256, 256, 0, L.s>>>(L.partial, L.ncta, nb * K * K, out, nb_iter, out_iter, K * K);
 }
 
 template <typename T, int K>
 void update(LState &L, const T *V, int nb, const double *C, T *W, const int *nb_iter = nullptr,
             const int *c_iter = nullptr, int nb_max = 0)
 {
-    const size_t smem = (size_t)(nb_iter ? nb_max : nb) * K * K * sizeof(T);
-    blk_update<T, K><<<L.ncta, 256, smem, L.s>>>(V, L.bstride, nb, C, W, L.dim, nb_iter, c_iter);
+    const int nbm = nb_iter ? nb_max : nb;
+    const size_t csm = (size_t)nbm * K * K * sizeof(T);
+    constexpr int S = rs_stages<T>();
+    const size_t rsm = 128 + (size_t)S * kRsCE * sizeof(T) + csm;
+    if (rs_applies<T, K>(L, V, W) && rsm <= 112 * 1024) {
+        static unsigned long long attr = 0;   // per instantiation: devices already configured
+        int dev = 0;
+        cudaGetDevice(&dev);
+        if (dev < 64 && !(attr >> dev & 1ull)) {
+            cudaFuncSetAttribute(rs_update<T, K, S>, cudaFuncAttributeMaxDynamicSharedMemorySize, 112 * 1024);
+            attr |= 1ull << dev;
+        }
+        rs_update<T, K, S><<<L.ncta, kRsCons + 32, rsm, L.s>>>(V, L.bstride, nb, C, W, L.dim * K, nb_iter, c_iter, L.err);
+        return;
+    }
+    blk_update<T, K><<<L.ncta, 256, csm, L.s>>>(V, L.bstride, nb, C, W, L.dim, nb_iter, c_iter);
 }
 
 }  // namespace
@@ -488,13 +1020,17 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
     LState L;
     L.k = K;
     L.dim = c->basis.dim;
-    L.bstride = L.dim * K;
+    // block stride rounded up to 16 bytes: every block starts on a TMA
+    // boundary, and the streamed kernels may copy up to the next 16 bytes
+    L.bstride = (L.dim * K + (int64_t)(16 / sizeof(T)) - 1) / (int64_t)(16 / sizeof(T)) * (int64_t)(16 / sizeof(T));
+    L.padded = true;
     L.s = (cudaStream_t)o.stream;
     int dev = 0;
     cudaGetDevice(&dev);
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     L.ncta = 2 * nsm;
+    L.err = c->dev.err;
     int niter = std::max(1, o.niter);
     niter = (int)std::min<int64_t>(niter, std::max<int64_t>(1, L.dim / K));
     const size_t es = sizeof(T);
@@ -540,7 +1076,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
     const int passes = std::max(1, o.reorth_passes);
 
     // orthonormalize the pivot block (FP64 Gram, one reorthogonalization-free QR)
-    cudaMemcpyAsync(W, pivot, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
+    cudaMemcpyAsync(W, pivot, (size_t)L.dim * K * es, cudaMemcpyDeviceToDevice, L.s);
     dots<T, K>(L, W, 1, W, L.C);
     small_gram<<<1, 32, 0, L.s>>>(K, L.C, rel, L.M, L.Bn, L.flags, nullptr, nullptr);
     blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V, L.dim, nullptr, 0, nullptr);
@@ -731,6 +1267,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
             if ((rc = launch_hx(c, Xown, HX, kref, BS_F64, L.s, c->err)) == BS_OK) {
                 LState L2 = L;
                 L2.bstride = L.dim * kref;
+                L2.padded = false;
                 std::vector<double> xx(kref * kref), xh(kref * kref), hh(kref * kref);
                 auto dots64 = [&](const double *A, const double *Bm, double *out) {
                     switch (kref) {
@@ -791,6 +1328,7 @@ static int block_dots_run(bs_ctx *c, const void *V, int nb, const void *W, doubl
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     L.ncta = 2 * nsm;
+    L.err = c->dev.err;
     cudaError_t e = cudaMallocAsync((void **)&L.partial, (size_t)L.ncta * nb * K * K * sizeof(double), s);
     if (e != cudaSuccess) { c->err = std::string("block dots: ") + cudaGetErrorString(e); return BS_ENOMEM; }
     dots<T, K>(L, (const T *)V, nb, (const T *)W, C);
@@ -890,7 +1428,7 @@ int noalloc_dots_run(const void *V, int nb, const void *W, int64_t dim, double *
     // as many CTAs as the fixed array holds partial blocks for, at most 2 per SM
     const int ncta = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)nsm, BS_BLOCK_DOTS_NOALLOC_MAX / per));
     blk_dots<T, K><<<ncta, kDotThreads, 0, s>>>((const T *)V, dim * K, nb, (const T *)W, dim, scratch, nullptr);
-    dots_reduce<<<(int)((per + 255) / 256), 256, 0, s>>>(scratch, ncta, (int)per, C, nullptr, nullptr, K * K);
+    dots_reduce<double><<<(int)((per + 255) / 256), 256, 0, s>>>(scratch, ncta, (int)per, C, nullptr, nullptr, K * K);
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA;
 }
 

@@ -140,6 +140,33 @@ def test_block_dots_match_fp64_numpy(k, dtype):
 
 
 @pytest.mark.gpu
+@pytest.mark.parametrize("k,dtype", [(8, N.BS_F32), (4, N.BS_F32), (2, N.BS_F32), (1, N.BS_F32),
+                                     (1, N.BS_F64), (2, N.BS_F64), (8, N.BS_F64)])
+def test_block_dots_streamed_sizes(k, dtype):
+    """Block inner products on sd 6p6n (dim 93,710): for k >= 2, or FP64, a
+    block is a multiple of 16 bytes and the TMA-streamed kernel runs, with
+    chunks of 2,048 elements spread over the CTAs (some get two, some none)
+    and a ragged last chunk; FP32 k = 1 (374,840 bytes per block) takes the
+    row-slot kernel.  Against FP64 numpy, and bit-identical when repeated."""
+    c, _ = ctx_oracle("sd", 6, 6, 0, with_oracle=False)
+    assert c.dim == 93710
+    nb = 7
+    rng = np.random.default_rng(40 + k)
+    tdt = torch.float64 if dtype == N.BS_F64 else torch.float32
+    V = torch.from_numpy(rng.standard_normal((nb, c.dim, k))).to("cuda", tdt)
+    W = torch.from_numpy(rng.standard_normal((c.dim, k))).to("cuda", tdt)
+    C = torch.zeros(nb * k * k, device="cuda", dtype=torch.float64)
+    c.block_dots(V, nb, W, k, dtype, C)
+    ref = np.einsum("bai,aj->bij", V.double().cpu().numpy(), W.double().cpu().numpy()).reshape(-1)
+    got = C.cpu().numpy()
+    assert np.max(np.abs(got - ref)) <= 1e-12 * np.max(np.abs(ref))
+    C2 = torch.zeros_like(C)
+    c.block_dots(V, nb, W, k, dtype, C2)
+    assert torch.equal(C, C2)
+    c.sync_status()   # raises on a recorded wait timeout
+
+
+@pytest.mark.gpu
 @pytest.mark.parametrize("k,dtype", [(1, N.BS_F64), (8, N.BS_F32)])
 def test_graph_captured_iteration_equals_plain_loop(k, dtype):
     c, _ = ctx_oracle("sd", 4, 4, 0, with_oracle=False)
