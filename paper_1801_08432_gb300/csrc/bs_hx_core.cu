@@ -99,6 +99,19 @@ __device__ __forceinline__ void core_step(const float *Xs, const float *Wt, uint
     }
 }
 
+// Stage c % S and round c / S of a running slot counter c, kept up to date
+// without integer divisions (S is a launch parameter).
+struct SlotRing {
+    int s = 0, round = 0;
+    __device__ __forceinline__ void next(int S)
+    {
+        if (++s == S) {
+            s = 0;
+            ++round;
+        }
+    }
+};
+
 struct CoreArgs {
     const CoreUnit *units;
     const CoreSrc *src;
@@ -155,7 +168,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     if (warp == NW) {
         // ---------------- producer: lane 0 streams every unit's sources, tile by tile;
         // the warp's 32 lanes fetch the metadata of 32 sources at a time
-        int c = 0, g = -1;
+        SlotRing rg;
+        int gb = 0, ground = 0;   // list buffer and its use number for the next group (g + 1)
         for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
             const int nsrc = A.units[u].nsrc;
             const int64_t src0 = A.units[u].src0;
@@ -181,7 +195,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                         mlm = A.sinfo[cs.sinfo_base + 2 * (sl1 - 1)] + 32 * A.sinfo[cs.sinfo_base + 2 * (sl1 - 1) + 1];
                     }
                     const int cnt = min(32, nsrc - q0);
-                    for (int j = 0; j < cnt; ++j, ++c) {
+                    for (int j = 0; j < cnt; ++j, rg.next(A.S)) {
                         const int64_t xe = __shfl_sync(0xffffffffu, mx, j);
                         const int sn = __shfl_sync(0xffffffffu, mn, j);
                         const uint32_t wt = __shfl_sync(0xffffffffu, mw, j);
@@ -192,14 +206,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                         const bool newg = sb != prev;
                         int bad = 0;
                         if (lane == 0) {
-                            const int s = c % A.S;
-                            const int round = c / A.S;
+                            const int s = rg.s;
+                            const int round = rg.round;
                             if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) bad = 1;
                             uint32_t lbytes = 0, sbytes = 0;
-                            const int b = (g + (newg ? 1 : 0)) % A.nlb;
+                            const int b = gb;
                             if (!bad && newg) {
-                                const int gn = g + 1;   // its use n = gn / nlb of buffer b waits for release n - 1
-                                if (gn >= A.nlb && bar_wait(lempty0 + 8u * b, (uint32_t)(gn / A.nlb - 1) & 1u)) bad = 1;
+                                // use `ground` of buffer b waits for the consumers' release of use ground - 1
+                                if (ground > 0 && bar_wait(lempty0 + 8u * b, (uint32_t)(ground - 1) & 1u)) bad = 1;
                                 lbytes = (uint32_t)((lend - o0) * 4);
                                 sbytes = (uint32_t)(((2 * (sl1 - sl0) + 3) / 4) * 16);
                             }
@@ -225,7 +239,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                         }
                         if (newg) {
                             prev = sb;
-                            ++g;
+                            if (++gb == A.nlb) {
+                                gb = 0;
+                                ++ground;
+                            }
                         }
                     }
                 }
@@ -235,7 +252,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     }
 
     // ---------------- consumers
-    int c = 0, g = -1;
+    SlotRing rg;
+    int cb = -1;   // list buffer of the current group (none yet)
     for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
         const int nsrc = A.units[u].nsrc;
         const DevBlock D = A.blocks[A.units[u].dblock];
@@ -261,10 +279,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             int64_t prev = -1;
             int la = 0, lb = 0;
             const uint32_t *lstA = lists, *lstB = lists;
-            for (int q = 0; q < nsrc; ++q, ++c) {
-                const int s = c % A.S;
-                const int round = c / A.S;
-                if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)round & 1u))) {
+            for (int q = 0; q < nsrc; ++q, rg.next(A.S)) {
+                const int s = rg.s;
+                if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)rg.round & 1u))) {
                     if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
                     return;
                 }
@@ -276,10 +293,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 if (sbase != prev) {
                     // a new group: release the previous group's list buffer, read this one
                     __syncwarp();
-                    if (g >= 0 && lane == 0) bar_arrive(lempty0 + 8u * (g % A.nlb));
-                    ++g;
+                    if (cb >= 0 && lane == 0) bar_arrive(lempty0 + 8u * cb);
+                    cb = cb + 1 == A.nlb ? 0 : cb + 1;
                     prev = sbase;
-                    const int b = g % A.nlb;
+                    const int b = cb;
                     const int32_t *si = sinf + b * SI;
                     const uint32_t *lb0 = lists + (size_t)b * A.list_elems - si[0] + lane;
                     la = hasA ? si[2 * sa + 1] : 0;
@@ -371,7 +388,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
 
     if (warp == NW) {
         if (lane != 0) return;
-        int c = 0;
+        SlotRing rg;
         for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
             const PPUnit U = A.units[u];
             const DevBlock D = A.blocks[U.dblock];
@@ -379,9 +396,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             const uint32_t bytes = (uint32_t)(D.nN * K * (int)sizeof(float));
             const uint32_t wbytes = (uint32_t)(kPPG * sizeof(float));
             for (int tile = 0; tile < ntile; ++tile)
-                for (int q = 0; q < U.nsrc; ++q, ++c) {
-                    const int s = c % A.S;
-                    const int round = c / A.S;
+                for (int q = 0; q < U.nsrc; ++q, rg.next(A.S)) {
+                    const int s = rg.s;
+                    const int round = rg.round;
                     if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) {
                         atomicExch(A.err, BS_ETIMEOUT);
                         return;
@@ -399,7 +416,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
 
     constexpr int E = K * (int)sizeof(float);
     const int rot = E == 32 ? ((lane >> 2) & 1) : 0;
-    int c = 0;
+    SlotRing rg;
     for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
         const PPUnit U = A.units[u];
         const DevBlock D = A.blocks[U.dblock];
@@ -414,10 +431,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             for (int p = 0; p < kPPG; ++p)
 #pragma unroll
                 for (int q = 0; q < K / 2; ++q) acc[p][q] = make_float2(0.0f, 0.0f);
-            for (int q = 0; q < U.nsrc; ++q, ++c) {
-                const int s = c % A.S;
-                const int round = c / A.S;
-                if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)round & 1u))) {
+            for (int q = 0; q < U.nsrc; ++q, rg.next(A.S)) {
+                const int s = rg.s;
+                if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)rg.round & 1u))) {
                     if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
                     return;
                 }
