@@ -207,18 +207,19 @@ def lanczos_check(ctx, N, I, torch, stream):
 
 KERNEL_SOURCES = {1: "bs_hx.cu", 2: "bs_hx_row.cu", 3: "bs_hx_row.cu", 4: "bs_hx_row.cu", 5: "bs_hx_row.cu",
                   6: "bs_hx_pipe.cu", 7: "bs_hx_pipe.cu", 8: "bs_hx_pipe.cu", 9: "bs_hx_pipe.cu", 10: "bs_hx_pipe.cu",
-                  11: "bs_hx_core.cu", 12: "bs_hx_core.cu", 13: "bs_hx_core.cu", 14: "bs_hx_core.cu"}
-# ncu summaries of the dominant kernel per mode (the pn-core kernel in 11..14)
+                  11: "bs_hx_core.cu", 12: "bs_hx_core.cu", 13: "bs_hx_core.cu", 14: "bs_hx_core.cu",
+                  15: "bs_hx_core.cu", 16: "bs_hx_core.cu"}
+# ncu summaries of the dominant kernel per mode (the pn-core kernel in 11..16)
 PROFILES = {1: "hx_fused_pf4p4n_k8.md", 2: "hx_row_pf4p4n_k8.md", 6: "hx_pipe_pf4p4n_k8.md",
             11: "hx_core_pf4p4n_k8.md", 12: "hx_core_pf4p4n_k8.md", 13: "hx_core_pf4p4n_k8.md",
-            14: "hx_core_pf4p4n_k8.md"}
+            14: "hx_core_pf4p4n_k8.md", 15: "hx_core_pf4p4n_k8.md", 16: "hx_core_pf4p4n_k8.md"}
 
 
 def launches_per_product(mode):
     """Kernels one H x launches in a kernel mode: the core-grouped modes run the
-    pn kernel (and in 13, 14 the pp kernel), the like-particle kernel and the
+    pn kernel (and in 13 to 16 the pp kernel), the like-particle kernel and the
     ordered sum of the partial vectors; every other mode is one kernel."""
-    return {11: 3, 12: 3, 13: 4, 14: 4}.get(mode, 1)
+    return {11: 3, 12: 3, 13: 4, 14: 4, 15: 4, 16: 4}.get(mode, 1)
 
 
 def traffic_from_profile(k, mode):
@@ -327,18 +328,36 @@ def ours(args):
             print(json.dumps({"profile_only": True, "mode": args.mode, "k": args.k or 8, "ms": ms}), flush=True)
         ctx.close()
         return 0
-    if args.k:
-        kbest = args.k
-        modes[kbest], mode_ms[kbest] = ctx.autotune(kbest, N.BS_F32, sp, times=True)
-        if args.mode:
-            ctx.set_kernel(args.mode)
+    if args.tune_load:
+        # replay a recorded tuning: the same kernel choices, no timing (so that a
+        # profiled run, whose serialized launches would skew the autotuner, runs
+        # the kernels the plain run chose)
+        rec = json.load(open(args.tune_load))
+        kbest = int(rec["kbest"])
+        modes = {int(k): int(m) for k, m in rec["f32"].items()}
+        mode_ms = {int(k): v for k, v in rec["ms_per_mode_f32"].items()}
+        tune = {int(k): v for k, v in rec["autotune_k"].items()}
+        mode64, ms64modes = int(rec["f64_k1"]), rec["ms_per_mode_f64_k1"]
+        for k, m in modes.items():
+            ctx.set_tuned(k, N.BS_F32, m)
+        ctx.set_tuned(1, N.BS_F64, mode64)
     else:
-        for k in (1, 2, 4, 8):
-            modes[k], mode_ms[k] = ctx.autotune(k, N.BS_F32, sp, times=True)
-            ms, _, _ = timed(k, N.BS_F32, 3, 2)
-            tune[k] = k / (min(ms) / 1000.0)
-        kbest = max(tune, key=tune.get)
-    mode64, ms64modes = ctx.autotune(1, N.BS_F64, sp, times=True)
+        if args.k:
+            kbest = args.k
+            modes[kbest], mode_ms[kbest] = ctx.autotune(kbest, N.BS_F32, sp, times=True)
+            if args.mode:
+                ctx.set_kernel(args.mode)
+        else:
+            for k in (1, 2, 4, 8):
+                modes[k], mode_ms[k] = ctx.autotune(k, N.BS_F32, sp, times=True)
+                ms, _, _ = timed(k, N.BS_F32, 3, 2)
+                tune[k] = k / (min(ms) / 1000.0)
+            kbest = max(tune, key=tune.get)
+        mode64, ms64modes = ctx.autotune(1, N.BS_F64, sp, times=True)
+    if args.tune_save and rank == 0:
+        json.dump({"workload": WORKLOAD_NAME, "kbest": kbest, "f32": modes, "ms_per_mode_f32": mode_ms,
+                   "autotune_k": tune, "f64_k1": mode64, "ms_per_mode_f64_k1": ms64modes},
+                  open(args.tune_save, "w"), indent=1)
 
     sampler = ClockSampler(local)
     sampler.start()
@@ -372,7 +391,7 @@ def ours(args):
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = nsm * 128 * 2 * sm_mhz_max * 1e6 / 1e12       # TFLOP/s, FMA = 2 FLOP
     mode_used = args.mode or modes.get(kbest, 0)
-    core = mode_used in (11, 12, 13, 14)
+    core = mode_used in (11, 12, 13, 14, 15, 16)
     # dominant kernel: the pn-core kernel of the core-grouped modes (its own
     # multiply-adds), else the one kernel of the product (all of them)
     dom_ops = float(stats[8]) if core else ops
@@ -434,6 +453,8 @@ def main():
     ap.add_argument("--no-lanczos", action="store_true", help="skip the Lanczos accuracy check")
     ap.add_argument("--mode", type=int, default=0, help="fix the H x kernel mode (bs_set_kernel) instead of autotuning")
     ap.add_argument("--profile-only", action="store_true", help="only the FP32 H*X launches (for ncu)")
+    ap.add_argument("--tune-save", default="", help="write the autotuned kernel modes and k to this JSON file")
+    ap.add_argument("--tune-load", default="", help="replay kernel modes and k from a --tune-save file instead of autotuning")
     ap.add_argument("--profile-lanczos", type=int, default=0,
                     help="only an FP32 block Lanczos of this many block iterations (for ncu)")
     args = ap.parse_args()

@@ -257,13 +257,15 @@ int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, do
  * warps, columns per thread, ring depth, shared-memory budget) of the
  * pipelined kernel (a producer warp fills a ring of shared-memory slots by
  * TMA, consumer warps keep their columns' sums in registers; needs k values
- * of 16 bytes or more per basis state); 11..14 = the core-grouped path for
+ * of 16 bytes or more per basis state); 11..16 = the core-grouped path for
  * FP32 with k = 4 or 8: a persistent kernel computes the pn term per
  * (Z-1)-proton core (up to four destination rows per staged source row) into
- * Z partial vectors (11, 13: 18 consumer warps with one 32-column slice each;
- * 12, 14: 9 warps with two slices each, a long and a short list); in 11, 12
+ * Z partial vectors (11, 13, 15, 16: 18 consumer warps with one 32-column
+ * slice each; 12, 14: 9 warps with two slices each, a long and a short list;
+ * 15, 16: as 13 with the whole 227 KB of shared memory and three or four
+ * neutron-list buffers); in 11, 12
  * the pipelined kernel computes the like-particle terms into one more; in
- * 13, 14 a second persistent kernel computes the pp two-body term per
+ * 13..16 a second persistent kernel computes the pp two-body term per
  * (Z-2)-proton core into C(Z,2) more and a row-tile kernel (4 rows per CTA)
  * the nn term and the proton single-particle energies into one more; a last kernel
  * sums the partial vectors in a fixed order (workspace: up to
@@ -277,7 +279,7 @@ int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, do
 int bs_set_kernel(bs_ctx *ctx, int mode);
 
 /* Number of selectable H x kernel modes (1..BS_KERNEL_MODES). */
-#define BS_KERNEL_MODES 14
+#define BS_KERNEL_MODES 16
 
 /* Times every kernel mode 1..BS_KERNEL_MODES for (k, dtype) on `stream` on
  * scratch vectors it allocates and frees (2 x dim x k elements), and records
@@ -286,6 +288,13 @@ int bs_set_kernel(bs_ctx *ctx, int mode);
  * mode.
  * Synchronizes `stream`.  Errors: as bs_apply_H, BS_ENOMEM. */
 int bs_autotune(bs_ctx *ctx, int k, bs_dtype dtype, void *stream, int *mode_out, float *ms_out);
+
+/* Records `mode` (1..BS_KERNEL_MODES) as the autotuned mode for (k, dtype),
+ * as bs_autotune would after timing, so that a tuning measured once (for
+ * example by a previous process on the same GPU and basis) is replayed
+ * without re-timing; calls with mode 0 then take it.  No device work.
+ * Errors: BS_EINVAL (k not 1, 2, 4, 8; unknown dtype; mode out of range). */
+int bs_set_tuned(bs_ctx *ctx, int k, bs_dtype dtype, int mode);
 
 /* Synchronizes `stream` and reads the context's device status word: returns
  * BS_ETIMEOUT (and clears the word) if a kernel's bounded wait on an
@@ -298,7 +307,7 @@ int bs_sync_status(bs_ctx *ctx, void *stream);
 
 /* Kernel timing: records a pair of CUDA events, on the product's stream,
  * around the dominant kernel of each of the next n (<= BS_TIME_MAX) products
- * y = H x (the pn kernel in the core-grouped modes 11..14, else the one
+ * y = H x (the pn kernel in the core-grouped modes 11..16, else the one
  * kernel); n = 0 stops.  Discards earlier records.  Errors: BS_EINVAL,
  * BS_ECUDA. */
 int bs_time_kernel(bs_ctx *ctx, int n);

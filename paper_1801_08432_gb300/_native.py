@@ -15,14 +15,14 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbsgpu.so")
 
 BS_F64, BS_F32 = 0, 1
-KERNEL_MODES = 14          # BS_KERNEL_MODES: selectable H x kernel modes 1..14
+KERNEL_MODES = 16          # BS_KERNEL_MODES: selectable H x kernel modes 1..16
 ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "BS_ENOMEM",
           -5: "BS_ECUDA", -6: "BS_EBREAKDOWN", -7: "BS_ETIMEOUT"}
 
 # every symbol include/bigstick_gpu.h declares
 EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
-            "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_lanczos",
+            "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_set_tuned", "bs_lanczos",
             "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_dots_noalloc",
             "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times"]
 
@@ -85,6 +85,7 @@ def load():
     L.bs_apply_H_host.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     L.bs_debug_table.argtypes = [vp, ctypes.c_char_p, vp, i64p]
     L.bs_set_kernel.argtypes = [vp, ctypes.c_int]
+    L.bs_set_tuned.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bs_lanczos.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, f64p, vp, ctypes.POINTER(bs_lanczos_report)]
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.bs_debug_eigh_banded.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
@@ -205,6 +206,10 @@ class Context:
         if times:
             return m.value, {i + 1: round(float(ms[i]), 4) for i in range(KERNEL_MODES)}
         return m.value
+
+    def set_tuned(self, k, dtype, mode):
+        """Record `mode` as the autotuned kernel mode for (k, dtype) (no timing)."""
+        self._check(load().bs_set_tuned(self.h, k, dtype, mode))
 
     def time_kernel(self, n):
         """Record CUDA events around the dominant kernel of the next n products."""

@@ -540,6 +540,19 @@ int bs_autotune(bs_ctx *c, int k, bs_dtype dt, void *stream, int *mode_out, floa
     });
 }
 
+int bs_set_tuned(bs_ctx *c, int k, bs_dtype dt, int mode)
+{
+    return guarded(c, [&]() -> int {
+        if ((k != 1 && k != 2 && k != 4 && k != 8) || (dt != BS_F64 && dt != BS_F32) || mode < 1 ||
+            mode > BS_KERNEL_MODES) {
+            c->err = "set_tuned: need k in {1, 2, 4, 8}, a known dtype and a mode in 1..BS_KERNEL_MODES";
+            return BS_EINVAL;
+        }
+        c->tuned[dt == BS_F64 ? 0 : 1][k == 1 ? 0 : k == 2 ? 1 : k == 4 ? 2 : 3] = mode;
+        return BS_OK;
+    });
+}
+
 int bs_sync_status(bs_ctx *c, void *stream)
 {
     return guarded(c, [&]() -> int {

@@ -598,11 +598,16 @@ struct CoreVariant {
     size_t target;   // shared-memory budget per CTA
     bool pp;         // pp term by (Z-2)-proton cores, nn by row tiles of nn_rows rows
     int nn_rows;
+    int nlb;         // neutron-list buffers (0: three if the ring keeps seven slots, else two)
 };
 
-constexpr CoreVariant kCoreVariants[] = {
-    {18, 1, 200 * 1024, false, 0}, {9, 2, 200 * 1024, false, 0}, {18, 1, 200 * 1024, true, 4}, {9, 2, 200 * 1024, true, 4}};
-constexpr int kNumCore = 4;
+// Modes 11.. in this order.  The last two spend the whole 227 KB on three or
+// four list buffers: the producer can then run two or three link groups
+// ahead of the slowest consumer warp instead of one.
+constexpr CoreVariant kCoreVariants[] = {{18, 1, 200 * 1024, false, 0, 0}, {9, 2, 200 * 1024, false, 0, 0},
+                                         {18, 1, 200 * 1024, true, 4, 0},  {9, 2, 200 * 1024, true, 4, 0},
+                                         {18, 1, 227 * 1024, true, 4, 3},  {18, 1, 227 * 1024, true, 4, 4}};
+constexpr int kNumCore = 6;
 
 template <int K, int R, int MINB>
 cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, bool &used)
@@ -629,7 +634,8 @@ cudaError_t launch_nn_k(const bs_ctx *ctx, const float *x, float *out, cudaStrea
 }
 
 template <int K, int NW, int MINB, int CPT>
-cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaStream_t s, size_t target, bool &used)
+cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaStream_t s, size_t target, int nlb_req,
+                          bool &used)
 {
     const Device &Dv = ctx->dev;
     const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
@@ -642,11 +648,11 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     constexpr int SI = ((2 * NW * CPT + 3) / 4) * 4;
     // list buffers: three when the ring still keeps seven slots, else two (a
     // deeper ring pays more than a third buffer)
-    int nlb = 3, S = 0;
+    int nlb = nlb_req > 0 ? nlb_req : 3, S = 0;
     for (; nlb >= 2; --nlb) {
         const size_t fixed = (size_t)nlb * list_elems * 4 + (size_t)nlb * SI * 4 + 8 * (size_t)nlb;
         S = target > fixed ? (int)std::min<size_t>(8, (target - fixed) / slot_bytes) : 0;
-        if (S >= 7 || nlb == 2) break;
+        if (nlb_req > 0 || S >= 7 || nlb == 2) break;
     }
     const size_t fixed = (size_t)nlb * list_elems * 4 + (size_t)nlb * SI * 4 + 8 * (size_t)nlb;
     used = S >= 2;
@@ -693,8 +699,8 @@ template <int K>
 cudaError_t launch_core_k(const bs_ctx *ctx, const float *x, float *part, cudaStream_t s, int v, bool &used)
 {
     const CoreVariant P = kCoreVariants[v];
-    if (P.cpt == 2) return launch_core_t<K, 9, 1, 2>(ctx, x, part, s, P.target, used);
-    return launch_core_t<K, 18, 1, 1>(ctx, x, part, s, P.target, used);
+    if (P.cpt == 2) return launch_core_t<K, 9, 1, 2>(ctx, x, part, s, P.target, P.nlb, used);
+    return launch_core_t<K, 18, 1, 1>(ctx, x, part, s, P.target, P.nlb, used);
 }
 
 // partial vectors: Z of the pn kernel, C(Z,2) of the pp kernel, one of the

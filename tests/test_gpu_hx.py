@@ -192,7 +192,7 @@ def test_autotune_picks_a_valid_mode():
     c.sync_status()
 
 
-@pytest.mark.parametrize("mode", [11, 12, 13, 14])
+@pytest.mark.parametrize("mode", [11, 12, 13, 14, 15, 16])
 @pytest.mark.parametrize("k", [4, 8])
 def test_pf_4p4n_core_grouped_modes(mode, k):
     """The core-grouped pn path (FP32, k = 4, 8) at the benchmark size: sampled
@@ -216,3 +216,24 @@ def test_pf_4p4n_core_grouped_modes(mode, k):
     bound = o.apply_rows(rows, np.abs(x64), absval=True)
     assert np.all(np.abs(y[rows] - ref) <= 4e-5 * bound + 1e-30)
     assert np.max(np.abs(y - yp)) <= 1e-5 * np.max(np.abs(yp))
+
+
+@pytest.mark.gpu
+def test_set_tuned_replays_a_mode_and_rejects_bad_arguments():
+    """bs_set_tuned records a mode for (k, dtype) without timing; mode-0 calls
+    then run it (the product equals the one with the mode forced)."""
+    orbits, spe, tb = I.space("sd")
+    c = N.make(orbits, spe, tb, 4, 4, 0, +1, device=0)
+    x = torch.from_numpy(I.random_block(c.dim, 8, seed=3)).to("cuda", torch.float32)
+    y_set, y_forced = torch.empty_like(x), torch.empty_like(x)
+    c.set_tuned(8, N.BS_F32, 13)
+    c.apply_H(x, y_set, 8, N.BS_F32)
+    c.set_kernel(13)
+    c.apply_H(x, y_forced, 8, N.BS_F32)
+    c.set_kernel(0)
+    torch.cuda.synchronize()
+    assert torch.equal(y_set, y_forced)
+    for bad in ((3, N.BS_F32, 13), (8, 7, 13), (8, N.BS_F32, 0), (8, N.BS_F32, N.KERNEL_MODES + 1)):
+        with pytest.raises(Exception):
+            c.set_tuned(*bad)
+    c.close()
