@@ -495,6 +495,7 @@ struct LState {
 constexpr int kRsCons = 256;     // consumer threads (8 warps) + one producer warp
 constexpr int kRsCE = 2048;      // elements per tile
 constexpr int kRsRT = 8;         // rows per consumer thread per tile = kRsCE / kRsCons
+constexpr int kRsCEU = 4096;     // elements per tile of the update kernel
 
 __device__ __forceinline__ float2 df_sum(float2 a, float2 b)
 {
@@ -547,22 +548,22 @@ struct RsRing {
 // Producer of both kernels: for each chunk of this CTA, the W tile then the
 // tiles of blocks 0..nb-1 into the stages in turn.  Returns false on a wait
 // timeout.
-template <typename T, int S>
+template <typename T, int S, int CE = kRsCE>
 __device__ __forceinline__ bool rs_produce(const T *V, int64_t bstride, int nb, const T *W, int64_t nel, T *ring,
                                            uint32_t full0, uint32_t empty0)
 {
     using namespace tma;
-    const int64_t nch = (nel + kRsCE - 1) / kRsCE;
+    const int64_t nch = (nel + CE - 1) / CE;
     RsRing<S> q;
     for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-        const int64_t e0 = ch * kRsCE;
+        const int64_t e0 = ch * CE;
         // a multiple of 16 bytes: exact unless the caller's blocks are padded
-        const uint32_t bytes = (uint32_t)((min((int64_t)kRsCE, nel - e0) * (int64_t)sizeof(T) + 15) / 16 * 16);
+        const uint32_t bytes = (uint32_t)((min((int64_t)CE, nel - e0) * (int64_t)sizeof(T) + 15) / 16 * 16);
         for (int b = -1; b < nb; ++b, q.next()) {
             // stage s was used S tiles ago: wait until every consumer warp released it
             if (q.uses >= S && bar_wait(empty0 + 8u * q.s, q.ph ^ 1u)) return false;
             bar_expect_tx(full0 + 8u * q.s, bytes);
-            bulk_copy(su32(ring + (size_t)q.s * kRsCE), (b < 0 ? W : V + (int64_t)b * bstride) + e0, bytes,
+            bulk_copy(su32(ring + (size_t)q.s * CE), (b < 0 ? W : V + (int64_t)b * bstride) + e0, bytes,
                       full0 + 8u * q.s);
         }
     }
@@ -586,7 +587,7 @@ constexpr int kRsSR = 4;   // staging slots of warp results
 // bank 4 i + rl + 4 j), read back by the reducer as one 16-byte load per
 // (warp, i, j).
 constexpr int kRsLaneIS = 36;
-constexpr int kRsLaneSR = 3;
+constexpr int kRsLaneSR = 2;
 
 template <typename T, int K, bool EXACT>
 __host__ __device__ constexpr bool rs_lane_staging()
@@ -838,9 +839,11 @@ __global__ void __launch_bounds__(kRsCons + 64, sizeof(T) == 4 ? 2 : 1)
 }
 
 // W[alpha][j] -= sum_b sum_i V_b[alpha][i] C[b][i][j]  (C: FP64, used in the vectors' precision).
-// Thread t owns the whole rows t + 256 m, m < 8 / K, of each chunk (its W
-// values in registers), reads each of its V rows once (consecutive lanes,
-// consecutive rows) and C_b as warp-uniform broadcasts.  FP32 pairs of
+// Tiles of kRsCEU elements: thread t owns the whole rows t + 256 m, m <
+// kRsCEU / (256 K), of each chunk (its W values in registers), reads each of
+// its V rows once (consecutive lanes, consecutive rows) and C_b as
+// warp-uniform broadcasts, each C_b row serving all of its rows (the C reads
+// bound shared memory at one row per thread).  FP32 pairs of
 // columns go through two-wide FMAs, each component rounded as fmaf would.
 template <typename T, int K, int S>
 __global__ void __launch_bounds__(kRsCons + 32) rs_update(const T *__restrict__ V, int64_t bstride, int nb,
@@ -849,14 +852,14 @@ __global__ void __launch_bounds__(kRsCons + 32) rs_update(const T *__restrict__ 
                                                           const int *__restrict__ c_iter, int *err)
 {
     using namespace tma;
-    constexpr int RU = kRsCE / K / kRsCons;   // rows per thread per tile
+    constexpr int RU = kRsCEU / K / kRsCons;   // rows per thread per tile
     constexpr bool PACKED = std::is_same<T, float>::value && K >= 2;
     if (nb_iter) nb = *nb_iter + 1;
     if (c_iter) C += (int64_t)(*c_iter) * K * K;
     extern __shared__ __align__(128) unsigned char smem[];
     uint64_t *bars = reinterpret_cast<uint64_t *>(smem);
     T *ring = reinterpret_cast<T *>(smem + 128);
-    T *Cs = ring + (size_t)S * kRsCE;   // [nb][i][j]
+    T *Cs = ring + (size_t)S * kRsCEU;   // [nb][i][j]
     const uint32_t full0 = su32(bars), empty0 = su32(bars + S);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     if (tid == 0) {
@@ -869,22 +872,22 @@ __global__ void __launch_bounds__(kRsCons + 32) rs_update(const T *__restrict__ 
     for (int e = tid; e < nb * K * K; e += blockDim.x) Cs[e] = (T)C[e];
     __syncthreads();
     if (warp == kRsCons / 32) {
-        if (lane == 0 && !rs_produce<T, S>(V, bstride, nb, W, nel, ring, full0, empty0)) atomicExch(err, BS_ETIMEOUT);
+        if (lane == 0 && !rs_produce<T, S, kRsCEU>(V, bstride, nb, W, nel, ring, full0, empty0)) atomicExch(err, BS_ETIMEOUT);
         return;
     }
-    const int64_t nch = (nel + kRsCE - 1) / kRsCE;
+    const int64_t nch = (nel + kRsCEU - 1) / kRsCEU;
     RsRing<S> q;
     bool bad = false;
     for (int64_t ch = blockIdx.x; ch < nch; ch += gridDim.x) {
-        const int64_t e0 = ch * kRsCE;
-        const int rows = (int)(min((int64_t)kRsCE, nel - e0) / K);
+        const int64_t e0 = ch * kRsCEU;
+        const int rows = (int)(min((int64_t)kRsCEU, nel - e0) / K);
         T w[RU][K];
         for (int b = -1; b < nb; ++b, q.next()) {
             if (!bad && __any_sync(0xffffffffu, bar_wait(full0 + 8u * q.s, q.ph))) {
                 bad = true;
                 if (lane == 0) atomicExch(err, BS_ETIMEOUT);
             }
-            const T *tile = ring + (size_t)q.s * kRsCE;
+            const T *tile = ring + (size_t)q.s * kRsCEU;
             if (b < 0) {
 #pragma unroll
                 for (int m = 0; m < RU; ++m) {
@@ -964,7 +967,7 @@ void dots(LState &L, const T *V, int nb, const T *W, double *out, const int *nb_
     const int n = (nb_iter ? nb_max : nb) * K * K;
     if (rs_applies<T, K>(L, V, W)) {
         using Sv = typename RsRed<T>::S;
-        constexpr int S = rs_lane_staging<T, K, EXACT>() ? 5 : rs_stages<T>();   // lane staging needs the room
+        constexpr int S = rs_stages<T>();
         const size_t acc = (size_t)(nb_iter ? nb_max : nb) * K * K * sizeof(Sv);
         constexpr bool LANES = rs_lane_staging<T, K, EXACT>();
         const size_t slots = LANES ? (size_t)kRsLaneSR * 8 * K * kRsLaneIS * 4 : (size_t)kRsSR * 8 * K * K * sizeof(Sv);
@@ -995,8 +998,8 @@ void update(LState &L, const T *V, int nb, const double *C, T *W, const int *nb_
 {
     const int nbm = nb_iter ? nb_max : nb;
     const size_t csm = (size_t)nbm * K * K * sizeof(T);
-    constexpr int S = rs_stages<T>();
-    const size_t rsm = 128 + (size_t)S * kRsCE * sizeof(T) + csm;
+    constexpr int S = sizeof(T) == 4 ? 3 : 2;   // 16 KB (FP32) or 32 KB (FP64) tiles
+    const size_t rsm = 128 + (size_t)S * kRsCEU * sizeof(T) + csm;
     if (rs_applies<T, K>(L, V, W) && rsm <= 112 * 1024) {
         static unsigned long long attr = 0;   // per instantiation: devices already configured
         int dev = 0;
