@@ -79,23 +79,41 @@ __device__ __forceinline__ void ldx(const float *row, uint32_t en, float (&v)[K]
 }
 
 // One list entry of one destination column: the gathered element of the
-// staged source row times the four weights of the entry's weight row.
-template <int K>
+// staged source row times the weights of the entry's weight row, for the
+// unit's first R destination rows (its rows are packed to the front; R = 4
+// also serves units with three).
+template <int K, int R = 4>
 __device__ __forceinline__ void core_step(const float *Xs, const float *Wt, uint32_t en, uint32_t flip,
                                           float2 (&acc)[4][K / 2])
 {
-    const float4 w = *reinterpret_cast<const float4 *>(Wt + 4 * (((en >> 16) & 0x7FFFu) ^ flip));
+    const float *wr = Wt + 4 * (((en >> 16) & 0x7FFFu) ^ flip);
     float2 xv[K / 2];
     ldx2<K>(Xs, en, xv);
-    const float2 w0 = make_float2(w.x, w.x), w1 = make_float2(w.y, w.y);
-    const float2 w2 = make_float2(w.z, w.z), w3 = make_float2(w.w, w.w);
+    // two correctly rounded fused multiply-adds per instruction
+    if constexpr (R == 1) {
+        const float w = *wr;
+        const float2 w0 = make_float2(w, w);
 #pragma unroll
-    for (int qq = 0; qq < K / 2; ++qq) {
-        // two correctly rounded fused multiply-adds per instruction
-        acc[0][qq] = __ffma2_rn(w0, xv[qq], acc[0][qq]);
-        acc[1][qq] = __ffma2_rn(w1, xv[qq], acc[1][qq]);
-        acc[2][qq] = __ffma2_rn(w2, xv[qq], acc[2][qq]);
-        acc[3][qq] = __ffma2_rn(w3, xv[qq], acc[3][qq]);
+        for (int qq = 0; qq < K / 2; ++qq) acc[0][qq] = __ffma2_rn(w0, xv[qq], acc[0][qq]);
+    } else if constexpr (R == 2) {
+        const float2 w = *reinterpret_cast<const float2 *>(wr);
+        const float2 w0 = make_float2(w.x, w.x), w1 = make_float2(w.y, w.y);
+#pragma unroll
+        for (int qq = 0; qq < K / 2; ++qq) {
+            acc[0][qq] = __ffma2_rn(w0, xv[qq], acc[0][qq]);
+            acc[1][qq] = __ffma2_rn(w1, xv[qq], acc[1][qq]);
+        }
+    } else {
+        const float4 w = *reinterpret_cast<const float4 *>(wr);
+        const float2 w0 = make_float2(w.x, w.x), w1 = make_float2(w.y, w.y);
+        const float2 w2 = make_float2(w.z, w.z), w3 = make_float2(w.w, w.w);
+#pragma unroll
+        for (int qq = 0; qq < K / 2; ++qq) {
+            acc[0][qq] = __ffma2_rn(w0, xv[qq], acc[0][qq]);
+            acc[1][qq] = __ffma2_rn(w1, xv[qq], acc[1][qq]);
+            acc[2][qq] = __ffma2_rn(w2, xv[qq], acc[2][qq]);
+            acc[3][qq] = __ffma2_rn(w3, xv[qq], acc[3][qq]);
+        }
     }
 }
 
@@ -257,6 +275,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
         const int nsrc = A.units[u].nsrc;
         const DevBlock D = A.blocks[A.units[u].dblock];
+        // destination rows of the unit (packed to the front): 1, 2 or more
+        const int nrow = A.units[u].drow[1] < 0 ? 1 : A.units[u].drow[2] < 0 ? 2 : 4;
         const int nN = D.nN;
         const int64_t doff = D.off;
         const int nsl = (nN + 31) / 32;
@@ -307,9 +327,17 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 // entries straight from the staged lists (32 lanes, 128 contiguous bytes per step)
                 const uint32_t flip = (wtab >> 31) ? A.ws : 0u;   // sign of a_k on c + k: swap the +W / -W halves
                 if constexpr (CPT == 1) {
-                    // one slice: the plain loop (the two-slice form costs ~7 % more instructions here)
+                    // one slice: the plain loop, for the unit's number of rows
+                    if (nrow == 1) {
 #pragma unroll 2
-                    for (int v = 0; v < la; ++v) core_step<K>(Xs, Wt, lstA[32 * v], flip, accA);
+                        for (int v = 0; v < la; ++v) core_step<K, 1>(Xs, Wt, lstA[32 * v], flip, accA);
+                    } else if (nrow == 2) {
+#pragma unroll 2
+                        for (int v = 0; v < la; ++v) core_step<K, 2>(Xs, Wt, lstA[32 * v], flip, accA);
+                    } else {
+#pragma unroll 2
+                        for (int v = 0; v < la; ++v) core_step<K, 4>(Xs, Wt, lstA[32 * v], flip, accA);
+                    }
                 } else {
                     const int lm = min(la, lb);
                     int v = 0;

@@ -8,6 +8,7 @@
 // applies its transpose for the "back" half; here both directions are kept so
 // that every output element has one owner and no atomics are needed).
 #include <algorithm>
+#include <map>
 #include <numeric>
 
 #include "bs_internal.h"
@@ -422,20 +423,36 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
     std::vector<int> by_key(ns);
     std::iota(by_key.begin(), by_key.end(), 0);
     std::stable_sort(by_key.begin(), by_key.end(), [&](int a, int b) { return key_of[a] < key_of[b]; });
-    // weights per (chunk, k): row of the pre-signed W table of op a+_i a_k, + variant
+    // Weights per (chunk, subset of its states, k): column j of table row idx is
+    // the pre-signed W row of op a+_i a_k (+ variant, then - variant) for the
+    // j-th state i of the subset.  A unit's destination rows are the chunk
+    // states its core leaves free, packed to the front, so that the kernel
+    // can skip the padded rows of units with one or two of them.  Tables are
+    // made on first use, ns of them (one per k) per (chunk, subset).
     const size_t ws2 = 2 * (size_t)T.wsign;
-    T.n_wtab = (int)(chunks.size() * (size_t)ns);
-    T.wc.assign((size_t)T.n_wtab * ws2 * 4, 0.0);
-    for (size_t q = 0; q < chunks.size(); ++q)
-        for (int k = 0; k < ns; ++k)
+    std::map<std::pair<size_t, int>, int> tab_of;   // (chunk, subset mask) -> first table
+    auto tables_for = [&](size_t q, int mask) -> int {
+        auto it = tab_of.find({q, mask});
+        if (it != tab_of.end()) return it->second;
+        const int t0 = T.n_wtab;
+        T.n_wtab += ns;
+        T.wc.resize((size_t)T.n_wtab * ws2 * 4, 0.0);
+        for (int k = 0; k < ns; ++k) {
+            int j = 0;
             for (size_t p = 0; p < chunks[q].size(); ++p) {
+                if (!(mask >> p & 1)) continue;
+                const int col = j++;
                 const int op = chunks[q][p] * ns + k;
                 const int g = I.ops.group_of_op[(size_t)op];
                 if (g < 0 || I.conj_group[(size_t)g] < 0) continue;
                 const size_t row = (size_t)T.ww_off[(size_t)g] + 2 * (size_t)I.ops.local_of_op[(size_t)op] * ws2;
-                double *dst = T.wc.data() + (q * (size_t)ns + (size_t)k) * ws2 * 4;
-                for (size_t idx = 0; idx < ws2; ++idx) dst[idx * 4 + p] = T.ww[row + idx];
+                double *dst = T.wc.data() + ((size_t)t0 + (size_t)k) * ws2 * 4;
+                for (size_t idx = 0; idx < ws2; ++idx) dst[idx * 4 + col] = T.ww[row + idx];
             }
+        }
+        tab_of[{q, mask}] = t0;
+        return t0;
+    };
     // cores
     std::vector<uint64_t> cores;
     cores.reserve(P.bits.size() * (size_t)P.nparticles);
@@ -464,6 +481,7 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
             U x;
             x.u.dblock = -1;
             for (int p = 0; p < 4; ++p) { x.u.drow[p] = -1; x.u.meta[p] = 0; }
+            int mask = 0, nr = 0;
             for (size_t p = 0; p < chunks[q].size(); ++p) {
                 const int i = chunks[q][p];
                 if (c >> i & 1) continue;
@@ -471,10 +489,13 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
                 locate(c | (1ULL << i), blk, row);
                 if (blk < 0) continue;
                 x.u.dblock = blk;
-                x.u.drow[p] = row;
-                x.u.meta[p] = __builtin_popcountll(c & ((1ULL << i) - 1ULL)) | (sign_below(c, i) < 0 ? 256 : 0);
+                x.u.drow[nr] = row;
+                x.u.meta[nr] = __builtin_popcountll(c & ((1ULL << i) - 1ULL)) | (sign_below(c, i) < 0 ? 256 : 0);
+                mask |= 1 << p;
+                ++nr;
             }
             if (x.u.dblock < 0) continue;
+            const int tq = tables_for(q, mask);
             const int i0 = chunks[q][0];
             for (int k : by_key) {
                 if (c >> k & 1) continue;
@@ -488,7 +509,7 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
                 const Block &Sb = B.blocks[(size_t)blk];
                 const int ncl = T.links[(size_t)l].ncls;
                 x.src.push_back(CoreSrc{Sb.off + (int64_t)row * Sb.nN, (int32_t)Sb.nN,
-                                        (uint32_t)(q * (size_t)ns + (size_t)k) | (sign_below(c, k) < 0 ? 0x80000000u : 0u),
+                                        (uint32_t)(tq + k) | (sign_below(c, k) < 0 ? 0x80000000u : 0u),
                                         T.pe.cls_ent[(size_t)ncl], T.pe.cls_sinfo[(size_t)ncl]});
             }
             x.u.nsrc = (int)x.src.size();

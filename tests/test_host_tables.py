@@ -491,6 +491,8 @@ def test_core_units_structure():
 
     for u in units:
         cores, keys = set(), set()
+        nr = int(np.sum(u["drow"] >= 0))
+        assert nr >= 1 and np.all(u["drow"][:nr] >= 0) and np.all(u["drow"][nr:] < 0)   # rows packed to the front
         for p in range(4):
             if u["drow"][p] < 0:
                 continue
