@@ -92,6 +92,25 @@ def test_host_buffer_entry_point():
     assert np.array_equal(y, gpu_apply(c, x, 2, N.BS_F64))
 
 
+def test_host_buffer_entry_point_pinned_and_pageable():
+    """sd 6p6n, k = 8 FP32 (3.0 MB per vector block), page-locked and pageable
+    host buffers, twice in a row: the same y as the device-buffer call."""
+    orbits, spe, tb = I.space("sd")
+    c = N.make(orbits, spe, tb, 6, 6, 0, +1, device=0)
+    x = I.random_block(c.dim, 8, seed=7).astype(np.float32)
+    ref = gpu_apply(c, x, 8, N.BS_F32)
+    xp = torch.from_numpy(x).pin_memory()
+    yp = torch.zeros_like(xp).pin_memory()
+    for _ in range(2):
+        y = np.full_like(x, np.nan)
+        c.apply_H_host(x, y, 8, N.BS_F32)            # pageable
+        assert np.array_equal(y, ref)
+        yp.fill_(float("nan"))
+        c.apply_H_host(xp.numpy(), yp.numpy(), 8, N.BS_F32)   # page-locked
+        assert np.array_equal(yp.numpy(), ref)
+    c.close()
+
+
 def test_rejects_bad_calls():
     c, o = setup("sd", 2, 2, 0)
     xd = torch.zeros((o.dim, 3), device="cuda", dtype=torch.float64)
