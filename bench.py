@@ -208,18 +208,19 @@ def lanczos_check(ctx, N, I, torch, stream):
 KERNEL_SOURCES = {1: "bs_hx.cu", 2: "bs_hx_row.cu", 3: "bs_hx_row.cu", 4: "bs_hx_row.cu", 5: "bs_hx_row.cu",
                   6: "bs_hx_pipe.cu", 7: "bs_hx_pipe.cu", 8: "bs_hx_pipe.cu", 9: "bs_hx_pipe.cu", 10: "bs_hx_pipe.cu",
                   11: "bs_hx_core.cu", 12: "bs_hx_core.cu", 13: "bs_hx_core.cu", 14: "bs_hx_core.cu",
-                  15: "bs_hx_core.cu", 16: "bs_hx_core.cu"}
-# ncu summaries of the dominant kernel per mode (the pn-core kernel in 11..16)
+                  15: "bs_hx_core.cu", 16: "bs_hx_core.cu", 17: "bs_hx_core.cu", 18: "bs_hx_core.cu"}
+# ncu summaries of the dominant kernel per mode (the pn-core kernel in 11..18)
 PROFILES = {1: "hx_fused_pf4p4n_k8.md", 2: "hx_row_pf4p4n_k8.md", 6: "hx_pipe_pf4p4n_k8.md",
             11: "hx_core_pf4p4n_k8.md", 12: "hx_core_pf4p4n_k8.md", 13: "hx_core_pf4p4n_k8.md",
-            14: "hx_core_pf4p4n_k8.md", 15: "hx_core_pf4p4n_k8.md", 16: "hx_core_pf4p4n_k8.md"}
+            14: "hx_core_pf4p4n_k8.md", 15: "hx_core_pf4p4n_k8.md", 16: "hx_core_pf4p4n_k8.md",
+            17: "hx_core_pf4p4n_k8.md", 18: "hx_core_pf4p4n_k8.md"}
 
 
 def launches_per_product(mode):
     """Kernels one H x launches in a kernel mode: the core-grouped modes run the
-    pn kernel (and in 13 to 16 the pp kernel), the like-particle kernel and the
+    pn kernel (and in 13 to 16 and 18 the pp kernel), the like-particle kernel and the
     ordered sum of the partial vectors; every other mode is one kernel."""
-    return {11: 3, 12: 3, 13: 4, 14: 4, 15: 4, 16: 4}.get(mode, 1)
+    return {11: 3, 12: 3, 13: 4, 14: 4, 15: 4, 16: 4, 17: 3, 18: 4}.get(mode, 1)
 
 
 def traffic_from_profile(k, mode):
@@ -238,6 +239,69 @@ def traffic_from_profile(k, mode):
         if len(f) == 4 and f[0] == "traffic" and f[1] == "k=%d" % k and f[2] == "src=" + sha:
             return int(f[3].split("=")[1])
     return None
+
+
+def fe52_run(args):
+    """The pf 6p6n space (52Fe, M=0, dim 109,954,620): FP32 block Lanczos with
+    k = 4 interleaved vectors, 50 block iterations kept on the device, FP64
+    refinement of the 5 lowest pairs.  Its eigenvalues have no feasible
+    oracle (the explicit H would be ~1.4 TB): the FP64 residuals are reported
+    instead.  One JSON line."""
+    import torch
+    from paper_1801_08432_gb300 import _native as N
+    from paper_1801_08432_gb300 import build as B
+    from paper_1801_08432_gb300 import inputs as I
+
+    torch.cuda.set_device(0)
+    B.build()
+    orbits, spe, tb = I.space("pf")
+    t0 = time.time()
+    ctx = N.make(orbits, spe, tb, 6, 6, 0, +1, device=0)
+    setup_s = time.time() - t0
+    dim, k = ctx.dim, 4
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    mode, mode_ms = ctx.autotune(k, N.BS_F32, sp, times=True)
+    g = torch.Generator(device="cuda").manual_seed(52)
+    x = torch.randn((dim, k), device="cuda", dtype=torch.float32, generator=g)
+    y = torch.empty_like(x)
+    with torch.cuda.stream(stream):
+        for _ in range(2):
+            ctx.apply_H(x, y, k, N.BS_F32, sp)
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+    nrep = 5
+    ctx.time_kernel(nrep)
+    ev[0].record(stream)
+    with torch.cuda.stream(stream):
+        for _ in range(nrep):
+            ctx.apply_H(x, y, k, N.BS_F32, sp)
+    ev[1].record(stream)
+    stream.synchronize()
+    hx_ms = ev[0].elapsed_time(ev[1]) / nrep
+    kern_ms = float(np.mean(ctx.kernel_times()))
+    ctx.time_kernel(0)
+    del x, y
+    torch.cuda.empty_cache()
+    stats = ctx.table("stats", np.int64)
+    p = torch.from_numpy(I.random_block(dim, k, seed=I.PIVOT_SEED)).to("cuda", torch.float32)
+    ev5, rep = ctx.lanczos(p, k, N.BS_F32, 50, 5, refine=True, stream=sp)
+    nit = rep["iterations"]
+    rb = reorth_bytes(dim, k, 4, nit, 2)
+    hbm_gbs = (peaks() or {}).get("hbm_gbs", 6800.0)
+    line = {"workload": "pf shell 6p6n M=0 (52Fe), dim %d, 195 seeded random TBMEs" % dim, "k": k,
+            "set_up_s": round(setup_s, 1), "kernel_mode": mode, "ms_per_mode_f32": mode_ms,
+            "hx_ms_per_block_product": round(hx_ms, 2), "vector_matvecs_per_s": k / (hx_ms / 1000.0),
+            "dominant_kernel_ms": round(kern_ms, 2),
+            "dominant_kernel_tflops": 2.0 * float(stats[8]) * k / (kern_ms / 1000.0) / 1e12,
+            "lanczos": {"block_iterations": nit, "ms_total": round(rep["ms_total"], 1),
+                        "ms_matvec": round(rep["ms_matvec"], 1), "ms_reorth_alpha_gram": round(rep["ms_reorth"], 1),
+                        "reorth_alg_bytes": rb, "reorth_gbs": round(rb / (rep["ms_reorth"] / 1000.0) / 1e9, 1),
+                        "reorth_hbm_frac": round(rb / (rep["ms_reorth"] / 1000.0) / 1e9 / hbm_gbs, 3),
+                        "evals_mev": [round(float(e), 6) for e in ev5], "residual_mev": rep["residual"],
+                        "delta_conv": rep["delta_conv"]}}
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
 
 
 def ours(args):
@@ -391,7 +455,7 @@ def ours(args):
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = nsm * 128 * 2 * sm_mhz_max * 1e6 / 1e12       # TFLOP/s, FMA = 2 FLOP
     mode_used = args.mode or modes.get(kbest, 0)
-    core = mode_used in (11, 12, 13, 14, 15, 16)
+    core = mode_used in (11, 12, 13, 14, 15, 16, 17, 18)
     # dominant kernel: the pn-core kernel of the core-grouped modes (its own
     # multiply-adds), else the one kernel of the product (all of them)
     dom_ops = float(stats[8]) if core else ops
@@ -453,6 +517,7 @@ def main():
     ap.add_argument("--no-lanczos", action="store_true", help="skip the Lanczos accuracy check")
     ap.add_argument("--mode", type=int, default=0, help="fix the H x kernel mode (bs_set_kernel) instead of autotuning")
     ap.add_argument("--profile-only", action="store_true", help="only the FP32 H*X launches (for ncu)")
+    ap.add_argument("--fe52", action="store_true", help="only the pf 6p6n (52Fe) block Lanczos, k = 4, 50 iterations")
     ap.add_argument("--tune-save", default="", help="write the autotuned kernel modes and k to this JSON file")
     ap.add_argument("--tune-load", default="", help="replay kernel modes and k from a --tune-save file instead of autotuning")
     ap.add_argument("--profile-lanczos", type=int, default=0,
@@ -462,6 +527,8 @@ def main():
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.fe52:
+        return fe52_run(args)
     return ours(args)
 
 

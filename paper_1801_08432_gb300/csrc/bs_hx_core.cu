@@ -632,10 +632,16 @@ struct CoreVariant {
 // Modes 11.. in this order.  The last two spend the whole 227 KB on three or
 // four list buffers: the producer can then run two or three link groups
 // ahead of the slowest consumer warp instead of one.
+// Modes 17, 18 also spend 227 KB, with two list buffers, and leave the
+// like-particle terms (17: pp and nn; 18: nn, after the pp-core kernel) to
+// the first pipelined variant that fits the basis: for neutron sectors wider
+// than the row-tile kernel's 576 columns (pf 6p6n: 3,952) and source rows of
+// up to ~64 KB.
 constexpr CoreVariant kCoreVariants[] = {{18, 1, 200 * 1024, false, 0, 0}, {9, 2, 200 * 1024, false, 0, 0},
                                          {18, 1, 200 * 1024, true, 4, 0},  {9, 2, 200 * 1024, true, 4, 0},
-                                         {18, 1, 227 * 1024, true, 4, 3},  {18, 1, 227 * 1024, true, 4, 4}};
-constexpr int kNumCore = 6;
+                                         {18, 1, 227 * 1024, true, 4, 3},  {18, 1, 227 * 1024, true, 4, 4},
+                                         {18, 1, 227 * 1024, false, 0, 2}, {18, 1, 227 * 1024, true, 0, 2}};
+constexpr int kNumCore = 8;
 
 template <int K, int R, int MINB>
 cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, bool &used)
@@ -784,8 +790,16 @@ cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dt
     const bool pp = kCoreVariants[v].pp;
     const int R = kCoreVariants[v].nn_rows;
     bool fits = false;
-    cudaError_t e = R ? (k == 8 ? launch_nn_k<8>(c, nullptr, nullptr, s, R, fits) : launch_nn_k<4>(c, nullptr, nullptr, s, R, fits))
-                      : launch_hx_pipe_combine(c, nullptr, nullptr, k, dt, s, 0, nullptr, 0, pp, fits);
+    cudaError_t e = cudaSuccess;
+    int pv = 0;   // pipelined variant for the like-particle terms: the first that fits
+    if (R) {
+        e = k == 8 ? launch_nn_k<8>(c, nullptr, nullptr, s, R, fits) : launch_nn_k<4>(c, nullptr, nullptr, s, R, fits);
+    } else {
+        for (; pv < pipe_variants() && e == cudaSuccess; ++pv) {
+            e = launch_hx_pipe_combine(c, nullptr, nullptr, k, dt, s, pv, nullptr, 0, pp, fits);
+            if (fits) break;
+        }
+    }
     if (e != cudaSuccess || !fits) return e;
     float *part = (float *)c->core_part;
     const float *xf = (const float *)x;
@@ -806,7 +820,7 @@ cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dt
     // remaining like-particle terms into partial vector nz, then the ordered sum
     float *last = part + (size_t)nz * (size_t)c->basis.dim * (size_t)k;
     e = R ? (k == 8 ? launch_nn_k<8>(c, xf, last, s, R, used) : launch_nn_k<4>(c, xf, last, s, R, used))
-          : launch_hx_pipe_combine(c, x, y, k, dt, s, 0, part, -1 - nz, pp, used);
+          : launch_hx_pipe_combine(c, x, y, k, dt, s, pv, part, -1 - nz, pp, used);
     if (e != cudaSuccess || !used) return e;
     const int64_t n4 = c->basis.dim * k / 4;
     int nsm = 0;

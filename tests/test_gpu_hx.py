@@ -153,6 +153,35 @@ def test_pf_4p4n_sampled_rows(k, dtype):
     assert np.all(np.isfinite(y))
 
 
+@pytest.mark.parametrize("mode", [17, 18])
+def test_pf_6p6n_core_grouped_modes(mode):
+    """The core-grouped pn path at the pf 6p6n size (neutron sectors up to
+    3,952 columns, source rows of 63 KB at k = 4), with the like-particle terms
+    on the first pipelined variant that fits: sampled rows against the oracle
+    and a bit-identical repeat."""
+    c, o = setup("pf", 6, 6, 0)
+    k = 4
+    g = torch.Generator(device="cuda").manual_seed(11)
+    xd = torch.randn((o.dim, k), device="cuda", dtype=torch.float32, generator=g)
+    yd, yd2 = torch.empty_like(xd), torch.empty_like(xd)
+    s = torch.cuda.current_stream().cuda_stream
+    c.set_kernel(mode)
+    try:
+        c.apply_H(xd, yd, k, N.BS_F32, s)
+        c.apply_H(xd, yd2, k, N.BS_F32, s)
+        torch.cuda.synchronize()
+        c.sync_status()
+    finally:
+        c.set_kernel(0)
+    assert torch.equal(yd, yd2)
+    rows = _sample_rows(o, 1500, 4)
+    x = xd.double().cpu().numpy()
+    ref = o.apply_rows(rows, x)
+    bound = o.apply_rows(rows, np.abs(x), absval=True)
+    y = yd[torch.from_numpy(rows).cuda()].double().cpu().numpy()
+    assert np.all(np.abs(y - ref) <= 4e-5 * bound + 1e-30)
+
+
 @pytest.mark.parametrize("k,dtype", [(4, N.BS_F32), (1, N.BS_F64)])
 def test_pf_6p6n_sampled_rows(k, dtype):
     c, o = setup("pf", 6, 6, 0)
@@ -211,7 +240,7 @@ def test_autotune_picks_a_valid_mode():
     c.sync_status()
 
 
-@pytest.mark.parametrize("mode", [11, 12, 13, 14, 15, 16])
+@pytest.mark.parametrize("mode", [11, 12, 13, 14, 15, 16, 17, 18])
 @pytest.mark.parametrize("k", [4, 8])
 def test_pf_4p4n_core_grouped_modes(mode, k):
     """The core-grouped pn path (FP32, k = 4, 8) at the benchmark size: sampled
