@@ -208,19 +208,20 @@ def lanczos_check(ctx, N, I, torch, stream):
 KERNEL_SOURCES = {1: "bs_hx.cu", 2: "bs_hx_row.cu", 3: "bs_hx_row.cu", 4: "bs_hx_row.cu", 5: "bs_hx_row.cu",
                   6: "bs_hx_pipe.cu", 7: "bs_hx_pipe.cu", 8: "bs_hx_pipe.cu", 9: "bs_hx_pipe.cu", 10: "bs_hx_pipe.cu",
                   11: "bs_hx_core.cu", 12: "bs_hx_core.cu", 13: "bs_hx_core.cu", 14: "bs_hx_core.cu",
-                  15: "bs_hx_core.cu", 16: "bs_hx_core.cu", 17: "bs_hx_core.cu", 18: "bs_hx_core.cu"}
-# ncu summaries of the dominant kernel per mode (the pn-core kernel in 11..18)
+                  15: "bs_hx_core.cu", 16: "bs_hx_core.cu", 17: "bs_hx_core.cu", 18: "bs_hx_core.cu",
+                  19: "bs_hx_core.cu"}
+# ncu summaries of the dominant kernel per mode (the pn-core kernel in 11..19)
 PROFILES = {1: "hx_fused_pf4p4n_k8.md", 2: "hx_row_pf4p4n_k8.md", 6: "hx_pipe_pf4p4n_k8.md",
             11: "hx_core_pf4p4n_k8.md", 12: "hx_core_pf4p4n_k8.md", 13: "hx_core_pf4p4n_k8.md",
             14: "hx_core_pf4p4n_k8.md", 15: "hx_core_pf4p4n_k8.md", 16: "hx_core_pf4p4n_k8.md",
-            17: "hx_core_pf4p4n_k8.md", 18: "hx_core_pf4p4n_k8.md"}
+            17: "hx_core_pf4p4n_k8.md", 18: "hx_core_pf4p4n_k8.md", 19: "hx_core_pf4p4n_k8.md"}
 
 
 def launches_per_product(mode):
     """Kernels one H x launches in a kernel mode: the core-grouped modes run the
-    pn kernel (and in 13 to 16 and 18 the pp kernel), the like-particle kernel and the
+    pn kernel (and in 13 to 16, 18 and 19 the pp kernel), the like-particle kernel and the
     ordered sum of the partial vectors; every other mode is one kernel."""
-    return {11: 3, 12: 3, 13: 4, 14: 4, 15: 4, 16: 4, 17: 3, 18: 4}.get(mode, 1)
+    return {11: 3, 12: 3, 13: 4, 14: 4, 15: 4, 16: 4, 17: 3, 18: 4, 19: 4}.get(mode, 1)
 
 
 def traffic_from_profile(k, mode):
@@ -455,7 +456,7 @@ def ours(args):
     nsm = torch.cuda.get_device_properties(local).multi_processor_count
     fp32_peak = nsm * 128 * 2 * sm_mhz_max * 1e6 / 1e12       # TFLOP/s, FMA = 2 FLOP
     mode_used = args.mode or modes.get(kbest, 0)
-    core = mode_used in (11, 12, 13, 14, 15, 16, 17, 18)
+    core = 11 <= mode_used <= 19
     # dominant kernel: the pn-core kernel of the core-grouped modes (its own
     # multiply-adds), else the one kernel of the product (all of them)
     dom_ops = float(stats[8]) if core else ops

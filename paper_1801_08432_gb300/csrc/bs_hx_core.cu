@@ -551,55 +551,54 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     float pd[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) pd[r] = r < nr ? A.pdiag[D.p_start + r0 + r] : 0.0f;
-    const int p = warp * 32 + lane;
-    const int sl = warp;
-    const bool active = sl * 32 < nN;   // warp-uniform
-    const int col = p < nN ? A.perm[D.perm_off + p] : -1;
-    int off = 0, lmax = 0;
-    if (active) {
-        off = A.sinfo[D.pe_nn_sinfo + 2 * sl];
-        lmax = A.sinfo[D.pe_nn_sinfo + 2 * sl + 1];
-    }
     if (__any_sync(0xffffffffu, bar_wait(b0, 0u))) {
         if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
         return;
     }
-    if (!active) return;
     const int rot = prot<float, K>(lane);
-    float2 acc[R][K / 2];   // packed, in the lane's rotated component order
-    float xv[K];
-    const int cc = col >= 0 ? col : 0;
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        pld<float, K>(rows + (size_t)r * A.row_stride, cc, rot, xv);
-#pragma unroll
-        for (int q = 0; q < K / 2; ++q) acc[r][q] = make_float2(pd[r] * xv[2 * q], pd[r] * xv[2 * q + 1]);
-    }
-    const int64_t base = D.pe_nn_ent + off + lane;
-#pragma unroll 2
-    for (int v = 0; v < lmax; ++v) {
-        const float c = A.coef[base + 32 * (int64_t)v];
-        const int s = A.src[base + 32 * (int64_t)v];
-        const float2 c2 = make_float2(c, c);
+    // column tiles of NW * 32 (one column per thread) over the staged rows
+    for (int c0 = 0; c0 < nN; c0 += NW * 32) {
+        const int p = c0 + warp * 32 + lane;
+        const int sl = c0 / 32 + warp;
+        if (sl * 32 >= nN) break;   // warp-uniform
+        const int col = p < nN ? A.perm[D.perm_off + p] : -1;
+        const int off = A.sinfo[D.pe_nn_sinfo + 2 * sl];
+        const int lmax = A.sinfo[D.pe_nn_sinfo + 2 * sl + 1];
+        float2 acc[R][K / 2];   // packed, in the lane's rotated component order
+        float xv[K];
+        const int cc = col >= 0 ? col : 0;
 #pragma unroll
         for (int r = 0; r < R; ++r) {
-            pld<float, K>(rows + (size_t)r * A.row_stride, s, rot, xv);
+            pld<float, K>(rows + (size_t)r * A.row_stride, cc, rot, xv);
 #pragma unroll
-            for (int q = 0; q < K / 2; ++q) acc[r][q] = __ffma2_rn(c2, make_float2(xv[2 * q], xv[2 * q + 1]), acc[r][q]);
+            for (int q = 0; q < K / 2; ++q) acc[r][q] = make_float2(pd[r] * xv[2 * q], pd[r] * xv[2 * q + 1]);
         }
-    }
-    if (col < 0) return;
+        const int64_t base = D.pe_nn_ent + off + lane;
+#pragma unroll 2
+        for (int v = 0; v < lmax; ++v) {
+            const float c = A.coef[base + 32 * (int64_t)v];
+            const int s = A.src[base + 32 * (int64_t)v];
+            const float2 c2 = make_float2(c, c);
 #pragma unroll
-    for (int r = 0; r < R; ++r) {
-        if (r >= nr) break;
-        float o[K];
+            for (int r = 0; r < R; ++r) {
+                pld<float, K>(rows + (size_t)r * A.row_stride, s, rot, xv);
 #pragma unroll
-        for (int q = 0; q < K / 2; ++q) {
-            o[2 * q] = acc[r][q].x;
-            o[2 * q + 1] = acc[r][q].y;
+                for (int q = 0; q < K / 2; ++q) acc[r][q] = __ffma2_rn(c2, make_float2(xv[2 * q], xv[2 * q + 1]), acc[r][q]);
+            }
         }
-        prot_fix<float, K>(o, rot);
-        pst<float, K>(out + (D.off + (int64_t)(r0 + r) * nN + col) * K, o);
+        if (col < 0) continue;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (r >= nr) break;
+            float o[K];
+#pragma unroll
+            for (int q = 0; q < K / 2; ++q) {
+                o[2 * q] = acc[r][q].x;
+                o[2 * q + 1] = acc[r][q].y;
+            }
+            prot_fix<float, K>(o, rot);
+            pst<float, K>(out + (D.off + (int64_t)(r0 + r) * nN + col) * K, o);
+        }
     }
 }
 
@@ -634,14 +633,15 @@ struct CoreVariant {
 // ahead of the slowest consumer warp instead of one.
 // Modes 17, 18 also spend 227 KB, with two list buffers, and leave the
 // like-particle terms (17: pp and nn; 18: nn, after the pp-core kernel) to
-// the first pipelined variant that fits the basis: for neutron sectors wider
-// than the row-tile kernel's 576 columns (pf 6p6n: 3,952) and source rows of
-// up to ~64 KB.
+// the first pipelined variant that fits the basis: for source rows of up to
+// ~64 KB (pf 6p6n: 3,952 columns of 16 bytes at k = 4).  Mode 19 is 18 with
+// the nn term in row tiles of 2 rows.
 constexpr CoreVariant kCoreVariants[] = {{18, 1, 200 * 1024, false, 0, 0}, {9, 2, 200 * 1024, false, 0, 0},
                                          {18, 1, 200 * 1024, true, 4, 0},  {9, 2, 200 * 1024, true, 4, 0},
                                          {18, 1, 227 * 1024, true, 4, 3},  {18, 1, 227 * 1024, true, 4, 4},
-                                         {18, 1, 227 * 1024, false, 0, 2}, {18, 1, 227 * 1024, true, 0, 2}};
-constexpr int kNumCore = 8;
+                                         {18, 1, 227 * 1024, false, 0, 2}, {18, 1, 227 * 1024, true, 0, 2},
+                                         {18, 1, 227 * 1024, true, 2, 2}};
+constexpr int kNumCore = 9;
 
 template <int K, int R, int MINB>
 cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, bool &used)
@@ -650,7 +650,7 @@ cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStrea
     constexpr int NW = 18;
     const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
     const size_t smem = (size_t)R * row_stride * sizeof(float) + 16;
-    used = Dv.max_nN <= NW * 32 && smem <= 200 * 1024;
+    used = smem <= 200 * 1024;   // wider sectors than NW * 32 columns run in column tiles
     if (!used || !x) return cudaSuccess;
     auto kern = hx_nn_rows_kernel<K, R, NW, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
