@@ -148,6 +148,19 @@ int bs_apply_H_host(bs_ctx *ctx, const void *x_host, void *y_host, int k,
 int bs_apply_H_backward(bs_ctx *ctx, const void *x, const void *gy, void *gx, double *gtheta, int k,
                         bs_dtype dtype, void *stream);
 
+/* The update half of a block Gram-Schmidt pass (Sec. "Block Lanczos": the
+ * reorthogonalization of bs_lanczos): W[alpha][j] -= sum_b sum_i
+ * V_b[alpha][i] C[b][i][j] for b < nb, with V nb consecutive [dim][k] blocks,
+ * W one [dim][k] block not overlapping V (device, dtype) and C nb*k*k FP64
+ * coefficients (device, e.g. from bs_block_dots), used in the vectors'
+ * precision; per element the blocks are applied in order and within a
+ * block i = 0..k-1, each as one fused multiply-add.  nb*k*k coefficients
+ * must fit shared memory (227 KB).  Runs on `stream`.  Errors: BS_ENOBASIS,
+ * BS_ENOINT, BS_EINVAL (null pointer, nb < 1, overlap, too many
+ * coefficients, k, dtype), BS_ECUDA. */
+int bs_block_update(bs_ctx *ctx, const void *V, int nb, const double *C, void *W, int k, bs_dtype dtype,
+                    void *stream);
+
 /* Inner products of basis vectors with FP64-grade accumulation (overlaps of
  * wave functions; the alpha, Gram and reorthogonalization products of
  * bs_lanczos): for b < nb, C[b][i][j] = sum_alpha V_b[alpha][i] W[alpha][j],

@@ -23,7 +23,7 @@ ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "
 EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_basis_info",
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_set_tuned", "bs_lanczos",
-            "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_dots_noalloc",
+            "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_update", "bs_block_dots_noalloc",
             "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times"]
 
 
@@ -91,6 +91,7 @@ def load():
     L.bs_debug_eigh_banded.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]
     L.bs_block_dots.argtypes = [vp, vp, ctypes.c_int, vp, ctypes.c_int, ctypes.c_int, vp, vp]
+    L.bs_block_update.argtypes = [vp, vp, ctypes.c_int, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     L.bs_block_dots_noalloc.argtypes = [vp, ctypes.c_int, vp, ctypes.c_int64, ctypes.c_int, ctypes.c_int, vp, vp]
     L.bs_sync_status.argtypes = [vp, vp]
     L.bs_time_kernel.argtypes = [vp, ctypes.c_int]
@@ -248,6 +249,11 @@ class Context:
         (C float64 with nb*k*k elements)."""
         ptr = lambda t: vp(t if isinstance(t, int) else t.data_ptr())
         self._check(load().bs_block_dots(self.h, ptr(V), nb, ptr(W), k, dtype, ptr(C), vp(stream or 0)))
+
+    def block_update(self, V, nb, C, W, k, dtype, stream=None):
+        """W -= sum_b V_b C_b; V, C (float64, nb*k*k), W device tensors."""
+        ptr = lambda t: vp(t if isinstance(t, int) else t.data_ptr())
+        self._check(load().bs_block_update(self.h, ptr(V), nb, ptr(C), ptr(W), k, dtype, vp(stream or 0)))
 
     def apply_H_host(self, x, y, k, dtype, stream=None):
         """y = H x with host numpy buffers (copies inside)."""

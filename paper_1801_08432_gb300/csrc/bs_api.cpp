@@ -459,6 +459,19 @@ int bs_block_dots(bs_ctx *c, const void *V, int nb, const void *W, int k, bs_dty
     });
 }
 
+int bs_block_update(bs_ctx *c, const void *V, int nb, const double *C, void *W, int k, bs_dtype dt, void *stream)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, k, dt);
+        if (rc) return rc;
+        if (!V || !W || !C || nb < 1) { c->err = "block update: need V, C, W and nb >= 1"; return BS_EINVAL; }
+        const size_t es = dt == BS_F64 ? 8 : 4, blk = (size_t)c->basis.dim * (size_t)k * es;
+        const uintptr_t v0 = (uintptr_t)V, v1 = v0 + (size_t)nb * blk, w0 = (uintptr_t)W, w1 = w0 + blk;
+        if (w0 < v1 && v0 < w1) { c->err = "block update: W overlaps V"; return BS_EINVAL; }
+        return run_block_update(c, V, nb, C, W, k, dt, stream);
+    });
+}
+
 int bs_apply_H_backward(bs_ctx *c, const void *x, const void *gy, void *gx, double *gtheta, int k, bs_dtype dt,
                         void *stream)
 {

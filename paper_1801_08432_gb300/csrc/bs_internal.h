@@ -333,6 +333,7 @@ void release(Device &D);
 int launch_hx(const bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err);
 int row_variants();
 int run_block_dots(bs_ctx *c, const void *V, int nb, const void *W, int k, bs_dtype dt, double *C, void *stream);
+int run_block_update(bs_ctx *c, const void *V, int nb, const double *C, void *W, int k, bs_dtype dt, void *stream);
 int run_backward(bs_ctx *c, const void *x, const void *gy, void *gx, double *gtheta, int k, bs_dtype dt,
                  void *stream);
 int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,

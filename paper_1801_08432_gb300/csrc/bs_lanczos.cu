@@ -562,6 +562,10 @@ __device__ __forceinline__ bool rs_produce(const T *V, int64_t bstride, int nb, 
         for (int b = -1; b < nb; ++b, q.next()) {
             // stage s was used S tiles ago: wait until every consumer warp released it
             if (q.uses >= S && bar_wait(empty0 + 8u * q.s, q.ph ^ 1u)) return false;
+            // order the consumers' reads of the stage (generic proxy, observed
+            // through the empty barrier) before the bulk copy's writes (async
+            // proxy); without it the copy can overwrite data still being read
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
             bar_expect_tx(full0 + 8u * q.s, bytes);
             bulk_copy(su32(ring + (size_t)q.s * CE), (b < 0 ? W : V + (int64_t)b * bstride) + e0, bytes,
                       full0 + 8u * q.s);
@@ -1338,6 +1342,48 @@ static int block_dots_run(bs_ctx *c, const void *V, int nb, const void *W, doubl
     cudaFreeAsync(L.partial, s);
     if ((e = cudaGetLastError()) != cudaSuccess) { c->err = std::string("block dots: ") + cudaGetErrorString(e); return BS_ECUDA; }
     return BS_OK;
+}
+
+template <typename T, int K>
+static int block_update_run(bs_ctx *c, const void *V, int nb, const double *C, void *W, cudaStream_t s)
+{
+    LState L;
+    L.dim = c->basis.dim;
+    L.bstride = L.dim * K;
+    L.s = s;
+    int dev = 0, nsm = 152;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    L.ncta = 2 * nsm;
+    L.err = c->dev.err;
+    if ((size_t)nb * K * K * sizeof(T) > 227 * 1024) { c->err = "block update: nb * k * k coefficients exceed shared memory"; return BS_EINVAL; }
+    cudaError_t e = cudaFuncSetAttribute(blk_update<T, K>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)((size_t)nb * K * K * sizeof(T)));
+    if (e != cudaSuccess) { c->err = std::string("block update: ") + cudaGetErrorString(e); return BS_ECUDA; }
+    update<T, K>(L, (const T *)V, nb, C, (T *)W);
+    if ((e = cudaGetLastError()) != cudaSuccess) { c->err = std::string("block update: ") + cudaGetErrorString(e); return BS_ECUDA; }
+    return BS_OK;
+}
+
+int run_block_update(bs_ctx *c, const void *V, int nb, const double *C, void *W, int k, bs_dtype dt, void *stream)
+{
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return BS_ECUDA; }
+    cudaStream_t s = (cudaStream_t)stream;
+    if (dt == BS_F64) {
+        switch (k) {
+        case 1: return block_update_run<double, 1>(c, V, nb, C, W, s);
+        case 2: return block_update_run<double, 2>(c, V, nb, C, W, s);
+        case 4: return block_update_run<double, 4>(c, V, nb, C, W, s);
+        default: return block_update_run<double, 8>(c, V, nb, C, W, s);
+        }
+    }
+    switch (k) {
+    case 1: return block_update_run<float, 1>(c, V, nb, C, W, s);
+    case 2: return block_update_run<float, 2>(c, V, nb, C, W, s);
+    case 4: return block_update_run<float, 4>(c, V, nb, C, W, s);
+    default: return block_update_run<float, 8>(c, V, nb, C, W, s);
+    }
 }
 
 int run_block_dots(bs_ctx *c, const void *V, int nb, const void *W, int k, bs_dtype dt, double *C, void *stream)

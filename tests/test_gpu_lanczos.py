@@ -98,6 +98,25 @@ def test_fp32_mixed_block_lanczos_within_1e4_mev(k):
 
 
 @pytest.mark.gpu
+def test_fp32_block_lanczos_48cr_reproducible_and_within_1e4_mev():
+    """48Cr (pf 4p4n, dim 1,963,461), FP32 k = 8, 80 block iterations: two runs
+    give bit-identical eigenvalues (the streamed block products keep a fixed
+    order and no stage of their rings is overwritten while read), the lowest
+    three levels converge (FP64 residual <= 1e-3 MeV) and agree with FP64
+    k = 1 Lanczos within 1e-4 MeV."""
+    c, _ = ctx_oracle("pf", 4, 4, 0, with_oracle=False)
+    p = pivot(c.dim, 8, N.BS_F32)
+    ev_a, rep_a = c.lanczos(p, 8, N.BS_F32, 80, 5, refine=True)
+    ev_b, _ = c.lanczos(p, 8, N.BS_F32, 80, 5, refine=True)
+    assert np.array_equal(ev_a, ev_b)
+    assert max(rep_a["residual"][:3]) <= 1e-3, rep_a["residual"]
+    ev64, rep64 = c.lanczos(pivot(c.dim, 1, N.BS_F64), 1, N.BS_F64, 300, 5, refine=True)
+    assert max(rep64["residual"][:3]) <= 1e-6
+    assert np.max(np.abs(ev_a[:3] - ev64[:3])) <= 1e-4, (ev_a, ev64)
+    c.sync_status()
+
+
+@pytest.mark.gpu
 def test_gpu_j_degeneracy_m1_inside_m0():
     c0, _ = ctx_oracle("sd", 4, 4, 0, with_oracle=False)
     c1, _ = ctx_oracle("sd", 4, 4, 2, with_oracle=False)
@@ -164,6 +183,35 @@ def test_block_dots_streamed_sizes(k, dtype):
     c.block_dots(V, nb, W, k, dtype, C2)
     assert torch.equal(C, C2)
     c.sync_status()   # raises on a recorded wait timeout
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("space,Z,k,dtype,nb", [("sd", 6, 8, N.BS_F32, 7), ("sd", 6, 4, N.BS_F32, 5),
+                                              ("sd", 6, 2, N.BS_F32, 3), ("sd", 6, 1, N.BS_F32, 9),
+                                              ("sd", 6, 1, N.BS_F64, 4), ("sd", 6, 8, N.BS_F64, 2),
+                                              ("pf", 4, 8, N.BS_F32, 3), ("pf", 4, 1, N.BS_F64, 2)])
+def test_block_update_matches_fp64_numpy(space, Z, k, dtype, nb):
+    """W -= sum_b V_b C_b against FP64 numpy: sd 6p6n and pf 4p4n (48Cr, ragged
+    last tile of the streamed kernel), every k, FP32 and FP64, and the
+    row-slot kernel where a block is not a multiple of 16 bytes (FP32 k = 1
+    at dim 93,710 and 1,963,461)."""
+    c, _ = ctx_oracle(space, Z, Z, 0, with_oracle=False)
+    rng = np.random.default_rng(70 + k + nb)
+    tdt = torch.float64 if dtype == N.BS_F64 else torch.float32
+    V = torch.from_numpy(rng.standard_normal((nb, c.dim, k))).to("cuda", tdt)
+    W = torch.from_numpy(rng.standard_normal((c.dim, k))).to("cuda", tdt)
+    Cm = rng.standard_normal((nb, k, k)) * 0.1
+    C = torch.from_numpy(Cm.reshape(-1)).to("cuda", torch.float64)
+    Vh, Wh = V.double().cpu().numpy(), W.double().cpu().numpy()
+    Ch = Cm.astype(np.float32).astype(np.float64) if dtype == N.BS_F32 else Cm   # used in the vectors' precision
+    ref = Wh - np.einsum("bai,bij->aj", Vh, Ch)
+    bound = np.abs(Wh) + np.einsum("bai,bij->aj", np.abs(Vh), np.abs(Ch))
+    c.block_update(V, nb, C, W, k, dtype)
+    torch.cuda.synchronize()
+    got = W.double().cpu().numpy()
+    tol = 1e-13 if dtype == N.BS_F64 else (nb * k + 1) * 2.0 ** -23
+    assert np.all(np.abs(got - ref) <= tol * bound)
+    c.sync_status()
 
 
 @pytest.mark.gpu
