@@ -263,6 +263,85 @@ class Oracle:
         X = V[:n].T @ U[:, :nk]
         return ev[:nk], X
 
+    def block_lanczos_thick(self, pivot, niter, nthick, restarts, nkeep=None, return_vectors=False,
+                            return_state=False):
+        """Thick-restart block Lanczos (FP64): Sec. "Block Lanczos", Sec.
+        "Thick-restart Lanczos" and Sec. "Thick-restart block Lanczos".
+
+        pivot: [dim][k] block.  One cycle builds blocks V_n, n0 <= n < niter,
+        each with  W = H V_n;  A_n = V_n^T W;  W -= V_n A_n;  then twice
+        W -= Q (Q^T W) over every stored block Q;  O = W^T W = U L U^T;
+        B_n = L^(1/2) U^T;  V_(n+1) = W U L^(-1/2).  T (niter k square) holds
+        A_n on the diagonal and B_n below it.  After a restart its leading
+        nthick x nthick part is the diagonal of the kept Ritz values E and
+        the block row of V_t (t = nthick / k, the restart pivot) holds
+        r = B_last U[last block rows, :nthick] against them (the arrow of the
+        thick-restart matrix).  A restart diagonalizes T, keeps the lowest
+        nthick Ritz vectors Q U[:, :nthick] as the first t blocks, and takes
+        the last Lanczos block V_niter as V_t.  ``restarts`` restarts are
+        done, so restarts + 1 cycles.
+
+        Returns the eigenvalues of the last T (the lowest nkeep, or all) and
+        per cycle the list of all Ritz values; with ``return_vectors`` also
+        the Ritz vectors of the lowest nkeep; with ``return_state`` also the
+        last cycle's stored blocks Q ([dim][niter k]) and T.
+        """
+        H = self.matrix()
+        X = np.array(pivot, dtype=np.float64).reshape(self.dim, -1)
+        k = X.shape[1]
+        if nthick % k or not 0 <= nthick // k < niter - 1:
+            raise ValueError("nthick must be a multiple of k with nthick / k + 1 < niter")
+        t = nthick // k
+
+        def orthonormal(W):
+            lam, U = np.linalg.eigh(W.T @ W)
+            if lam[0] <= 1e-24 * lam[-1]:
+                raise OracleError("block Lanczos breakdown")
+            return W @ (U / np.sqrt(lam)), (np.sqrt(lam)[:, None] * U.T)
+
+        Q = [orthonormal(X)[0]]
+        E = R = None
+        history = []
+        for cycle in range(restarts + 1):
+            n0 = 0 if cycle == 0 else t
+            A, B = {}, {}
+            for n in range(n0, niter):
+                W = H @ Q[n]
+                A[n] = Q[n].T @ W
+                W = W - Q[n] @ A[n]
+                S = np.hstack(Q)
+                for _ in range(2):
+                    W = W - S @ (S.T @ W)
+                Vn1, B[n] = orthonormal(W)
+                Q.append(Vn1)
+            nT = niter * k
+            T = np.zeros((nT, nT))
+            if cycle > 0:
+                T[:nthick, :nthick] = np.diag(E)
+                T[t * k:(t + 1) * k, :nthick] = R
+                T[:nthick, t * k:(t + 1) * k] = R.T
+            for n in range(n0, niter):
+                T[n * k:(n + 1) * k, n * k:(n + 1) * k] = 0.5 * (A[n] + A[n].T)
+                if n + 1 < niter:
+                    T[(n + 1) * k:(n + 2) * k, n * k:(n + 1) * k] = B[n]
+                    T[n * k:(n + 1) * k, (n + 1) * k:(n + 2) * k] = B[n].T
+            ev, Z = np.linalg.eigh(T)
+            history.append(ev.copy())
+            if cycle == restarts:
+                break
+            S = np.hstack(Q[:niter])
+            Y = S @ Z[:, :nthick]
+            R = B[niter - 1] @ Z[(niter - 1) * k:niter * k, :nthick]
+            E = ev[:nthick]
+            Q = [Y[:, j * k:(j + 1) * k] for j in range(t)] + [Q[niter]]
+        nk = len(ev) if nkeep is None else nkeep
+        out = [ev[:nk], history]
+        if return_vectors:
+            out.append(np.hstack(Q[:niter]) @ Z[:, :nk])
+        if return_state:
+            out += [np.hstack(Q[:niter]), T]
+        return tuple(out)
+
     def eigh(self, nkeep=None):
         ev, X = np.linalg.eigh(self.dense())
         if nkeep is None:

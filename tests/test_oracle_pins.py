@@ -302,3 +302,44 @@ def test_lanczos_ritz_vectors_are_eigenvectors(sd22):
     for n in range(3):
         r = H @ X[:, n] - ev[n] * X[:, n]
         assert np.linalg.norm(r) < 1e-8
+
+
+# ------------------------------------------------------ thick-restart block Lanczos
+@pytest.mark.parametrize("k,niter,nthick", [(1, 12, 3), (2, 8, 4), (4, 6, 8)])
+def test_thick_restart_converges_to_dense(sd22, k, niter, nthick):
+    piv = I.random_block(sd22.dim, k)
+    ev, hist = sd22.block_lanczos_thick(piv, niter, nthick, 25, nkeep=3)
+    ev_d = np.linalg.eigvalsh(sd22.dense())[:3]
+    assert np.max(np.abs(ev - ev_d)) < 1e-9
+
+
+@pytest.mark.parametrize("k,niter,nthick", [(1, 10, 3), (2, 7, 4), (4, 5, 8)])
+def test_thick_restart_matrix_is_the_projection(sd22, k, niter, nthick):
+    # the arrow-shaped T after restarts (Ritz values, coupling r = B U_last,
+    # then the block-tridiagonal part) must equal Q^T H Q over the stored
+    # orthonormal basis Q, whatever the restart formulas are
+    piv = I.random_block(sd22.dim, k)
+    for restarts in (1, 3):
+        ev, hist, Q, T = sd22.block_lanczos_thick(piv, niter, nthick, restarts, return_state=True)
+        H = sd22.matrix()
+        assert np.max(np.abs(Q.T @ Q - np.eye(Q.shape[1]))) < 1e-12
+        assert np.max(np.abs(T - Q.T @ (H @ Q))) < 1e-11
+        assert np.max(np.abs(T[:nthick, :nthick] - np.diag(np.diag(T[:nthick, :nthick])))) == 0.0
+
+
+def test_thick_restart_ritz_values_never_rise(sd22):
+    # the subspace after a restart contains the kept Ritz vectors, so by
+    # Courant-Fischer the i-th lowest Ritz value (i < nthick) cannot rise
+    piv = I.random_block(sd22.dim, 2)
+    ev, hist = sd22.block_lanczos_thick(piv, 6, 4, 12)
+    h = np.array([x[:4] for x in hist])
+    assert np.all(np.diff(h, axis=0) <= 1e-11)
+    assert np.all(h[-1] >= np.linalg.eigvalsh(sd22.dense())[:4] - 1e-11)
+
+
+def test_thick_restart_without_restart_is_lanczos(sd22):
+    # no restart, k = 1: the same Krylov space as the single-vector routine
+    piv = I.random_block(sd22.dim, 1)
+    ev_t, _ = sd22.block_lanczos_thick(piv, 15, 2, 0)
+    ev_l = sd22.lanczos(piv[:, 0], 15)
+    assert np.max(np.abs(ev_t - ev_l)) < 1e-10
