@@ -218,6 +218,12 @@ typedef struct {
                            iteration number from a device counter) and replay it */
     void *stream;       /* cudaStream_t the work runs on (not the legacy default stream
                            when use_graph = 1: capture needs a created stream) */
+    int nthick;         /* thick restart (Sec. "Thick-restart block Lanczos"): Ritz vectors
+                           kept per restart, a multiple of k with nthick / k + 1 < niter;
+                           0 = no restart */
+    int max_restarts;   /* restarts at most (ignored when nthick = 0) */
+    double tol;         /* stop restarting once the residual estimate of each of the lowest
+                           nkeep pairs is <= tol (0 = run all max_restarts restarts) */
 } bs_lanczos_opts;
 
 /* What bs_lanczos did. */
@@ -230,6 +236,10 @@ typedef struct {
     double ms_matvec;        /* GPU time in H x */
     double ms_reorth;        /* GPU time in alpha, reorthogonalization, Gram and normalization */
     double ms_total;         /* wall time of the call */
+    int restarts;            /* thick restarts done */
+    int matvec_blocks;       /* block products H X done (restarts included) */
+    double resid_est;        /* max over the lowest nkeep pairs of |B_last U_last,mu|, the
+                                Lanczos estimate of |H psi - E psi| from the last T */
 } bs_lanczos_report;
 
 /* Block Lanczos with full reorthogonalization (Sec. "Standard Lanczos
@@ -241,10 +251,17 @@ typedef struct {
  * evecs: device [dim][nkeep] FP64 Ritz vectors of the lowest min(nkeep, 8)
  * pairs, or NULL.  report may be NULL.  Inner products accumulate in
  * extended precision (FP64, or exact FP32 products summed in double-float);
- * T is diagonalized in FP64 on the host.  Allocates its workspace (about
- * (niter+2) dim k elements) for the call and frees it.  Synchronizes the
- * stream.  Errors: BS_ENOBASIS, BS_ENOINT, BS_EINVAL (k, dtype, niter,
- * nkeep), BS_ENOMEM, BS_ECUDA, BS_EBREAKDOWN (eigensolver failure). */
+ * T is diagonalized in FP64 on the host.
+ * Thick restart (opts->nthick > 0): after niter block iterations the lowest
+ * nthick Ritz vectors of T replace the first nthick / k stored blocks, the
+ * last Lanczos block becomes the next pivot, and T restarts in the arrow form
+ * of Sec. "Thick-restart Lanczos" (Ritz values on the diagonal, coupling
+ * r = B_last U[last block rows, 1:nthick] to the pivot block), so storage
+ * stays at niter + 1 blocks however many block products the run takes.
+ * Allocates its workspace (about (niter + 2 + nthick / k) dim k elements)
+ * for the call and frees it.  Synchronizes the stream.  Errors: BS_ENOBASIS, BS_ENOINT, BS_EINVAL (k, dtype, niter,
+ * nkeep, nthick, max_restarts, tol), BS_ENOMEM, BS_ECUDA, BS_EBREAKDOWN
+ * (eigensolver failure). */
 int bs_lanczos(bs_ctx *ctx, const bs_lanczos_opts *opts, const void *pivot, double *evals, double *evecs,
                bs_lanczos_report *report);
 

@@ -39,13 +39,15 @@ class bs_tbme(ctypes.Structure):
 class bs_lanczos_opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("dtype", ctypes.c_int), ("niter", ctypes.c_int), ("nkeep", ctypes.c_int),
                 ("refine", ctypes.c_int), ("reorth_passes", ctypes.c_int), ("use_graph", ctypes.c_int),
-                ("stream", ctypes.c_void_p)]
+                ("stream", ctypes.c_void_p), ("nthick", ctypes.c_int), ("max_restarts", ctypes.c_int),
+                ("tol", ctypes.c_double)]
 
 
 class bs_lanczos_report(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int), ("breakdowns", ctypes.c_int), ("n_kept", ctypes.c_int),
                 ("residual", ctypes.c_double * 64), ("delta_conv", ctypes.c_double),
-                ("ms_matvec", ctypes.c_double), ("ms_reorth", ctypes.c_double), ("ms_total", ctypes.c_double)]
+                ("ms_matvec", ctypes.c_double), ("ms_reorth", ctypes.c_double), ("ms_total", ctypes.c_double),
+                ("restarts", ctypes.c_int), ("matvec_blocks", ctypes.c_int), ("resid_est", ctypes.c_double)]
 
 
 class BSError(RuntimeError):
@@ -180,11 +182,15 @@ class Context:
         return out
 
     def lanczos(self, pivot, k, dtype, niter, nkeep, refine=True, evecs=None, stream=None, reorth_passes=2,
-                use_graph=False):
+                use_graph=False, nthick=0, max_restarts=0, tol=0.0):
         """Block Lanczos on the GPU.  pivot: device tensor [dim][k] (dtype);
-        evecs: optional device float64 tensor [dim][nkeep].  Returns
-        (eigenvalues as numpy, report dict)."""
-        o = bs_lanczos_opts(k, dtype, niter, nkeep, int(refine), reorth_passes, int(use_graph), vp(stream or 0))
+        evecs: optional device float64 tensor [dim][nkeep]; nthick > 0 turns
+        on thick restart (Ritz vectors kept, a multiple of k) with at most
+        max_restarts restarts, stopping once the residual estimates of the
+        lowest nkeep pairs are <= tol.  Returns (eigenvalues as numpy,
+        report dict)."""
+        o = bs_lanczos_opts(k, dtype, niter, nkeep, int(refine), reorth_passes, int(use_graph), vp(stream or 0),
+                            nthick, max_restarts, tol)
         ev = np.zeros(nkeep)
         rep = bs_lanczos_report()
         pp = pivot if isinstance(pivot, int) else pivot.data_ptr()
@@ -192,7 +198,8 @@ class Context:
         self._check(load().bs_lanczos(self.h, ctypes.byref(o), vp(pp), ev.ctypes.data_as(f64p), ep, ctypes.byref(rep)))
         r = {"iterations": rep.iterations, "breakdowns": rep.breakdowns, "n_kept": rep.n_kept,
              "residual": [rep.residual[i] for i in range(rep.n_kept)], "delta_conv": rep.delta_conv,
-             "ms_matvec": rep.ms_matvec, "ms_reorth": rep.ms_reorth, "ms_total": rep.ms_total}
+             "ms_matvec": rep.ms_matvec, "ms_reorth": rep.ms_reorth, "ms_total": rep.ms_total,
+             "restarts": rep.restarts, "matvec_blocks": rep.matvec_blocks, "resid_est": rep.resid_est}
         return ev, r
 
     def set_kernel(self, mode):

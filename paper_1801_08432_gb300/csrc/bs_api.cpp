@@ -495,6 +495,12 @@ int bs_lanczos(bs_ctx *c, const bs_lanczos_opts *o, const void *pivot, double *e
             c->err = "lanczos: need niter >= 1, 1 <= nkeep <= 64, a pivot and an evals array";
             return BS_EINVAL;
         }
+        if (o->nthick < 0 || o->max_restarts < 0 || !(o->tol >= 0.0) ||
+            (o->nthick > 0 && (o->nthick % o->k || o->nthick / o->k + 1 >= o->niter))) {
+            c->err = "lanczos: thick restart needs nthick a multiple of k with nthick / k + 1 < niter, "
+                     "max_restarts >= 0, tol >= 0";
+            return BS_EINVAL;
+        }
         if (rep) std::memset(rep, 0, sizeof(*rep));
         return run_lanczos(c, *o, pivot, evals, evecs, rep);
     });

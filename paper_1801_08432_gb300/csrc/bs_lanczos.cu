@@ -279,6 +279,11 @@ __global__ void iter_advance(int *iter)
     if (threadIdx.x == 0 && blockIdx.x == 0) ++*iter;
 }
 
+__global__ void iter_set(int *iter, int v)
+{
+    if (threadIdx.x == 0 && blockIdx.x == 0) *iter = v;
+}
+
 // X[alpha][m] = sum_b sum_i V_b[alpha][i] Y[b*K+i][m], m < nm, FP64 output [dim][ldx]
 template <typename T, int K>
 __global__ void blk_combine(const T *__restrict__ V, int64_t bstride, int nb, const double *__restrict__ Y, int nm,
@@ -1052,8 +1057,14 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         for (void *p : owned) cudaFree(p);
         owned.clear();
     };
-    L.V = alloc((size_t)(niter + 1) * L.bstride * es);
+    // thick restart: nthick / K blocks of Ritz vectors, formed in as many
+    // scratch blocks past V_niter
+    const int tb = o.nthick > 0 ? o.nthick / K : 0;
+    const bool thick = tb > 0;
+    if (thick && tb + 1 >= niter) { c->err = "lanczos: nthick / k + 1 must stay below niter (clamped to dim / k)"; return BS_EINVAL; }
+    L.V = alloc((size_t)(niter + 1 + tb) * L.bstride * es);
     L.W = alloc((size_t)L.bstride * es);
+    double *Ct = (double *)alloc((size_t)std::max(tb, 1) * niter * K * K * sizeof(double));
     // dot scratch: (niter+1) blocks of K x K, or one 8 x 8 block for the refinement
     const size_t ndot = std::max<size_t>((size_t)(niter + 1) * K * K, 64);
     L.partial = (double *)alloc((size_t)L.ncta * ndot * sizeof(double));
@@ -1075,6 +1086,23 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
     const double rel = 1e-24;
     cudaEvent_t ev[4];
     for (auto &e : ev) cudaEventCreate(&e);
+    // every CUDA error of the call is caught here and reported with the
+    // stage that met it, never left in the runtime's last-error state
+    std::string cuda_fail;
+    auto stage = [&](const char *where) {
+        const cudaError_t le = cudaGetLastError();
+        if (le != cudaSuccess && cuda_fail.empty()) cuda_fail = std::string(where) + ": " + cudaGetErrorString(le);
+        return cuda_fail.empty();
+    };
+    // event timings are diagnostics: an event that cannot be timed counts 0
+    auto elapsed = [&](cudaEvent_t from, cudaEvent_t to) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, from, to) != cudaSuccess) {
+            (void)cudaGetLastError();
+            ms = 0.f;
+        }
+        return ms;
+    };
     float ms_mv = 0.f, ms_or = 0.f;
     int breakdowns = 0, done = 0;
     std::vector<double> Ah((size_t)niter * K * K), Bh((size_t)niter * K * K);
@@ -1130,121 +1158,193 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         }
     }
 
-    for (int n = 0; n < niter && rc == BS_OK; ++n) {
-        T *Vn = V + (int64_t)n * L.bstride;
-        if (gexec) {
-            cudaError_t e = cudaGraphLaunch(gexec, L.s);
-            if (e != cudaSuccess) { c->err = std::string("lanczos graph launch: ") + cudaGetErrorString(e); rc = BS_ECUDA; break; }
-        } else {
-        cudaEventRecord(ev[0], L.s);
-        if ((rc = launch_hx(c, Vn, W, K, o.dtype, L.s, c->err))) break;
-        cudaEventRecord(ev[1], L.s);
-        // alpha first: A_n = V_n^T W, W -= V_n A_n
-        double *An = L.Ahist + (size_t)n * K * K;
-        dots<T, K>(L, Vn, 1, W, An);
-        update<T, K>(L, Vn, 1, An, W);
-        for (int p = 0; p < passes; ++p) {
-            dots<T, K, false>(L, V, n + 1, W, L.C);
-            update<T, K>(L, V, n + 1, L.C, W);
-        }
-        dots<T, K>(L, W, 1, W, L.C);
-        small_gram<<<1, 32, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist + (size_t)n * K * K, L.flags, An, nullptr);
-        blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V + (int64_t)(n + 1) * L.bstride, L.dim, nullptr, 0, nullptr);
-        cudaEventRecord(ev[2], L.s);
-        }
-        int flags = 0;
-        cudaError_t e = cudaMemcpyAsync(&flags, L.flags, sizeof(int), cudaMemcpyDeviceToHost, L.s);
-        if (e == cudaSuccess) e = cudaStreamSynchronize(L.s);
-        if (e != cudaSuccess) { c->err = std::string("lanczos: ") + cudaGetErrorString(e); rc = BS_ECUDA; break; }
-        float a = 0.f, b = 0.f;
-        cudaEventElapsedTime(&a, ev[0], ev[1]);
-        cudaEventElapsedTime(&b, ev[1], ev[2]);
-        ms_mv += a;
-        ms_or += b;
-        done = n + 1;
-        if (flags && n + 1 < niter) {
-            // breakdown: flagged columns of V_{n+1} are zero; refill them with
-            // random vectors, orthogonalize against V_0..V_n, renormalize the
-            // block, and fold the change of basis into B_n
-            ++breakdowns;
-            T *Vn1 = V + (int64_t)(n + 1) * L.bstride;
-            for (int i = 0; i < K; ++i)
-                if (flags >> i & 1)
-                    fill_random_col<T, K><<<L.ncta, 256, 0, L.s>>>(Vn1, i, 0xB5297A4D3F84D5B5ull + 7919ull * (uint64_t)(n * K + i), L.dim);
-            for (int p = 0; p < 2; ++p) {
-                dots<T, K, false>(L, V, n + 1, Vn1, L.C);
-                update<T, K>(L, V, n + 1, L.C, Vn1);
-            }
-            cudaMemcpyAsync(W, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
-            dots<T, K>(L, W, 1, W, L.C);
-            small_gram<<<1, 32, 0, L.s>>>(K, L.C, 1e-20, L.M, L.Bn, L.flags, nullptr, nullptr);
-            blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, Vn1, L.dim, nullptr, 0, nullptr);
-            // B_n <- G B_n with G = Bn (the Gram factor of the refilled block: W = Vnew G)
-            std::vector<double> G(K * K), Bn(K * K), out(K * K, 0.0);
-            int fl2 = 0;
-            cudaMemcpyAsync(G.data(), L.Bn, K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
-            cudaMemcpyAsync(Bn.data(), L.Bhist + (size_t)n * K * K, K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
-            cudaMemcpyAsync(&fl2, L.flags, sizeof(int), cudaMemcpyDeviceToHost, L.s);
-            cudaStreamSynchronize(L.s);
-            if (fl2) { niter = n + 1; break; }   // the Krylov space is exhausted
-            for (int i = 0; i < K; ++i)
-                for (int j = 0; j < K; ++j)
-                    for (int l = 0; l < K; ++l) out[i * K + j] += G[i * K + l] * Bn[l * K + j];
-            cudaMemcpyAsync(L.Bhist + (size_t)n * K * K, out.data(), K * K * sizeof(double), cudaMemcpyHostToDevice, L.s);
-            if (Xcur) cudaMemcpyAsync(Xcur, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
-            cudaStreamSynchronize(L.s);
-        }
-    }
-    if (rc == BS_OK) {
-        cudaMemcpyAsync(Ah.data(), L.Ahist, (size_t)done * K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
-        cudaMemcpyAsync(Bh.data(), L.Bhist, (size_t)done * K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
-        if (cudaStreamSynchronize(L.s) != cudaSuccess) { rc = BS_ECUDA; c->err = "lanczos: copy failed"; }
-    }
+    // Cycles: one without thick restart; with it, each cycle runs the block
+    // iterations n0..niter-1 (n0 = 0, then nthick / K), diagonalizes T and,
+    // unless done, restarts (Sec. "Thick-restart block Lanczos").
+    int n0 = 0, restarts = 0, matvecs = 0;
+    bool exhausted = false;
+    std::vector<double> Eth, Rth;   // arrow of the restarted T: kept Ritz values, coupling [K][nthick]
     std::vector<double> wT, Z;
     const int nkeep = std::max(1, o.nkeep);
-    int nT = done * K;
-    if (rc == BS_OK) {
-        std::vector<double> T_((size_t)nT * nT, 0.0);
-        for (int n = 0; n < done; ++n)
-            for (int i = 0; i < K; ++i)
-                for (int j = 0; j < K; ++j) {
-                    T_[(size_t)(n * K + i) * nT + n * K + j] = Ah[(size_t)n * K * K + i * K + j];
-                    if (n + 1 < done) {
-                        const double b = Bh[(size_t)n * K * K + i * K + j];   // B_n: row i of block n+1, column j of block n
-                        T_[(size_t)((n + 1) * K + i) * nT + n * K + j] = b;
-                        T_[(size_t)(n * K + j) * nT + (n + 1) * K + i] = b;
-                    }
+    int nT = 0, nv = 0;
+    double resid_est = 0.0;
+    for (;;) {
+    for (int n = n0; n < niter && rc == BS_OK && !exhausted; ++n) {
+            T *Vn = V + (int64_t)n * L.bstride;
+            if (gexec) {
+                cudaError_t e = cudaGraphLaunch(gexec, L.s);
+                if (e != cudaSuccess) { c->err = std::string("lanczos graph launch: ") + cudaGetErrorString(e); rc = BS_ECUDA; break; }
+            } else {
+            cudaEventRecord(ev[0], L.s);
+            if ((rc = launch_hx(c, Vn, W, K, o.dtype, L.s, c->err))) break;
+            cudaEventRecord(ev[1], L.s);
+            // alpha first: A_n = V_n^T W, W -= V_n A_n
+            double *An = L.Ahist + (size_t)n * K * K;
+            dots<T, K>(L, Vn, 1, W, An);
+            update<T, K>(L, Vn, 1, An, W);
+            for (int p = 0; p < passes; ++p) {
+                dots<T, K, false>(L, V, n + 1, W, L.C);
+                update<T, K>(L, V, n + 1, L.C, W);
+            }
+            dots<T, K>(L, W, 1, W, L.C);
+            small_gram<<<1, 32, 0, L.s>>>(K, L.C, rel, L.M, L.Bhist + (size_t)n * K * K, L.flags, An, nullptr);
+            blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V + (int64_t)(n + 1) * L.bstride, L.dim, nullptr, 0, nullptr);
+            cudaEventRecord(ev[2], L.s);
+            }
+            int flags = 0;
+            cudaError_t e = cudaMemcpyAsync(&flags, L.flags, sizeof(int), cudaMemcpyDeviceToHost, L.s);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(L.s);
+            if (e != cudaSuccess) { c->err = std::string("lanczos: ") + cudaGetErrorString(e); rc = BS_ECUDA; break; }
+            ms_mv += elapsed(ev[0], ev[1]);
+            ms_or += elapsed(ev[1], ev[2]);
+            if (!stage("block iteration")) { rc = BS_ECUDA; break; }
+            done = n + 1;
+            if (flags && (n + 1 < niter || thick)) {
+                // breakdown: flagged columns of V_{n+1} are zero; refill them with
+                // random vectors, orthogonalize against V_0..V_n, renormalize the
+                // block, and fold the change of basis into B_n
+                ++breakdowns;
+                T *Vn1 = V + (int64_t)(n + 1) * L.bstride;
+                for (int i = 0; i < K; ++i)
+                    if (flags >> i & 1)
+                        fill_random_col<T, K><<<L.ncta, 256, 0, L.s>>>(Vn1, i, 0xB5297A4D3F84D5B5ull + 7919ull * (uint64_t)(n * K + i), L.dim);
+                for (int p = 0; p < 2; ++p) {
+                    dots<T, K, false>(L, V, n + 1, Vn1, L.C);
+                    update<T, K>(L, V, n + 1, L.C, Vn1);
                 }
+                cudaMemcpyAsync(W, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
+                dots<T, K>(L, W, 1, W, L.C);
+                small_gram<<<1, 32, 0, L.s>>>(K, L.C, 1e-20, L.M, L.Bn, L.flags, nullptr, nullptr);
+                blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, Vn1, L.dim, nullptr, 0, nullptr);
+                // B_n <- G B_n with G = Bn (the Gram factor of the refilled block: W = Vnew G)
+                std::vector<double> G(K * K), Bn(K * K), out(K * K, 0.0);
+                int fl2 = 0;
+                cudaMemcpyAsync(G.data(), L.Bn, K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+                cudaMemcpyAsync(Bn.data(), L.Bhist + (size_t)n * K * K, K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+                cudaMemcpyAsync(&fl2, L.flags, sizeof(int), cudaMemcpyDeviceToHost, L.s);
+                cudaStreamSynchronize(L.s);
+                if (fl2) { exhausted = true; break; }   // the Krylov space is exhausted
+                for (int i = 0; i < K; ++i)
+                    for (int j = 0; j < K; ++j)
+                        for (int l = 0; l < K; ++l) out[i * K + j] += G[i * K + l] * Bn[l * K + j];
+                cudaMemcpyAsync(L.Bhist + (size_t)n * K * K, out.data(), K * K * sizeof(double), cudaMemcpyHostToDevice, L.s);
+                if (Xcur) cudaMemcpyAsync(Xcur, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
+                cudaStreamSynchronize(L.s);
+            }
+        ++matvecs;
+    }
+    if (rc != BS_OK) break;
+    cudaMemcpyAsync(Ah.data(), L.Ahist, (size_t)done * K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+    cudaMemcpyAsync(Bh.data(), L.Bhist, (size_t)done * K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+    if (cudaStreamSynchronize(L.s) != cudaSuccess) { rc = BS_ECUDA; c->err = "lanczos: copy failed"; break; }
+    nT = done * K;
+    std::vector<double> T_((size_t)nT * nT, 0.0);
+    if (restarts > 0) {
+        // arrow of the thick-restart matrix: E on the diagonal, r in the rows of block tb
+        for (int m = 0; m < o.nthick; ++m) T_[(size_t)m * nT + m] = Eth[m];
+        for (int i = 0; i < K; ++i)
+            for (int m = 0; m < o.nthick; ++m) {
+                const double r = Rth[(size_t)i * o.nthick + m];
+                T_[(size_t)(tb * K + i) * nT + m] = r;
+                T_[(size_t)m * nT + tb * K + i] = r;
+            }
+    }
+    for (int n = n0; n < done; ++n)
+        for (int i = 0; i < K; ++i)
+            for (int j = 0; j < K; ++j) {
+                T_[(size_t)(n * K + i) * nT + n * K + j] = Ah[(size_t)n * K * K + i * K + j];
+                if (n + 1 < done) {
+                    const double b = Bh[(size_t)n * K * K + i * K + j];   // B_n: row i of block n+1, column j of block n
+                    T_[(size_t)((n + 1) * K + i) * nT + n * K + j] = b;
+                    T_[(size_t)(n * K + j) * nT + (n + 1) * K + i] = b;
+                }
+            }
+    const int nwant = std::max(nkeep, thick ? o.nthick : 0);
+    const int nval = std::min(nT, std::max(nkeep + 5, nwant));
+    nv = std::min(nwant, nT);
+    wT.assign(std::max(nT, 1), 0.0);
+    Z.assign((size_t)nT * std::max(nv, 1), 0.0);
+    int bw = 0;
+    if (restarts == 0) {
         // T is banded: B_n = Lambda^1/2 Q^T from the Gram eigendecomposition
         // is a full k x k block, so the half-bandwidth is up to 2k - 1 (read
         // off T).  Eigenvalues by bisection on inertia counts, eigenvectors by
         // inverse iteration, O(nT bw^2) each.
-        int bw = 0;
         for (int i = 0; i < nT; ++i)
             for (int j = 0; j < i - bw; ++j)
                 if (T_[(size_t)i * nT + j] != 0.0) { bw = i - j; break; }
-        const int nval = std::min(nT, nkeep + 5);
-        wT.assign(std::max(nval, 1), 0.0);
-        const int nv = std::min(nkeep, nT);
-        Z.resize((size_t)nT * nv);
-        if (!host_eigh_banded(nT, bw, T_.data(), nval, wT.data(), Z.data(), nv)) { rc = BS_EBREAKDOWN; c->err = "lanczos: eigensolver failed"; }
-        // convergence measure of the paper: the lowest nkeep+5 eigenvalues of
-        // T now and one block iteration earlier
-        if (rc == BS_OK && rep) {
-            const int nprev = (done - 1) * K, m = std::min(nkeep + 5, nprev);
-            double delta = 0.0;
-            if (m > 0) {
-                std::vector<double> Tp((size_t)nprev * nprev), wp(std::max(m, 1));
-                for (int i = 0; i < nprev; ++i)
-                    for (int j = 0; j < nprev; ++j) Tp[(size_t)i * nprev + j] = T_[(size_t)i * nT + j];
-                std::vector<double> dummy(1);
-                host_eigh_banded(nprev, bw, Tp.data(), m, wp.data(), dummy.data(), 0);
-                for (int i = 0; i < m; ++i) delta += std::fabs(wT[i] - wp[i]);
-                delta /= std::sqrt((double)m);
-            }
-            rep->delta_conv = delta;
-        }
+        if (!host_eigh_banded(nT, bw, T_.data(), nval, wT.data(), Z.data(), nv)) { rc = BS_EBREAKDOWN; c->err = "lanczos: eigensolver failed"; break; }
+    } else if (!host_eigh(nT, T_.data(), wT.data(), Z.data(), nv)) {   // the arrow is not banded
+        rc = BS_EBREAKDOWN; c->err = "lanczos: eigensolver failed"; break;
     }
+    // convergence measure of the paper: the lowest nkeep+5 eigenvalues of
+    // T now and one block iteration earlier
+    if (rep) {
+        const int nprev = (done - 1) * K, m = std::min(nkeep + 5, nprev);
+        double delta = 0.0;
+        if (m > 0) {
+            std::vector<double> Tp((size_t)nprev * nprev), wp(std::max(nprev, 1));
+            for (int i = 0; i < nprev; ++i)
+                for (int j = 0; j < nprev; ++j) Tp[(size_t)i * nprev + j] = T_[(size_t)i * nT + j];
+            std::vector<double> dummy(1);
+            if (restarts == 0) host_eigh_banded(nprev, bw, Tp.data(), m, wp.data(), dummy.data(), 0);
+            else host_eigh(nprev, Tp.data(), wp.data(), dummy.data(), 0);
+            for (int i = 0; i < m; ++i) delta += std::fabs(wT[i] - wp[i]);
+            delta /= std::sqrt((double)m);
+        }
+        rep->delta_conv = delta;
+    }
+    // |H psi_mu - E_mu psi_mu| = |B_last U[last block rows, mu]| for the Ritz
+    // pairs of T (the component of H psi along the next Lanczos block)
+    auto coupling = [&](int i, int m) {
+        double r = 0.0;
+        for (int j = 0; j < K; ++j)
+            r += Bh[(size_t)(done - 1) * K * K + i * K + j] * Z[(size_t)((done - 1) * K + j) * nv + m];
+        return r;
+    };
+    resid_est = 0.0;
+    for (int m = 0; m < std::min(nkeep, nv); ++m) {
+        double r2 = 0.0;
+        for (int i = 0; i < K; ++i) r2 += coupling(i, m) * coupling(i, m);
+        resid_est = std::max(resid_est, std::sqrt(r2));
+    }
+    if (!thick || exhausted || done < niter || restarts >= o.max_restarts || (o.tol > 0.0 && resid_est <= o.tol)) break;
+    // restart: Y_j = sum_b V_b U[b rows, j cols] (j < tb) into the scratch
+    // blocks past V_niter, then V_niter -> V_tb and Y -> V_0..V_(tb-1)
+    cudaEventRecord(ev[0], L.s);
+    {
+        std::vector<double> Ch((size_t)tb * done * K * K);
+        for (int jb = 0; jb < tb; ++jb)
+            for (int b = 0; b < done; ++b)
+                for (int i = 0; i < K; ++i)
+                    for (int jj = 0; jj < K; ++jj)
+                        Ch[(((size_t)jb * done + b) * K + i) * K + jj] = -Z[(size_t)(b * K + i) * nv + jb * K + jj];
+        cudaMemcpyAsync(Ct, Ch.data(), Ch.size() * sizeof(double), cudaMemcpyHostToDevice, L.s);
+        T *scratch = V + (int64_t)(niter + 1) * L.bstride;
+        cudaMemsetAsync(scratch, 0, (size_t)tb * L.bstride * es, L.s);
+        for (int jb = 0; jb < tb; ++jb)
+            update<T, K>(L, V, done, Ct + (size_t)jb * done * K * K, scratch + (int64_t)jb * L.bstride);
+        cudaMemcpyAsync(V + (int64_t)tb * L.bstride, V + (int64_t)done * L.bstride, (size_t)L.bstride * es,
+                        cudaMemcpyDeviceToDevice, L.s);
+        cudaMemcpyAsync(V, scratch, (size_t)tb * L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
+        if (gexec) {
+            cudaMemcpyAsync(Xcur, V + (int64_t)tb * L.bstride, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
+            iter_set<<<1, 1, 0, L.s>>>(d_iter, tb);
+        }
+        Eth.assign(wT.begin(), wT.begin() + o.nthick);
+        Rth.assign((size_t)K * o.nthick, 0.0);
+        for (int i = 0; i < K; ++i)
+            for (int m = 0; m < o.nthick; ++m) Rth[(size_t)i * o.nthick + m] = coupling(i, m);
+        // Ch must outlive its (pageable, staged) copy
+        cudaEventRecord(ev[3], L.s);
+        if (cudaStreamSynchronize(L.s) != cudaSuccess) { rc = BS_ECUDA; c->err = "lanczos: restart failed"; break; }
+    }
+    ms_or += elapsed(ev[0], ev[3]);
+    if (!stage("thick restart")) { rc = BS_ECUDA; break; }
+    n0 = tb;
+    ++restarts;
+    }
+
     int nk = std::min(nkeep, nT);
     if (rc == BS_OK) {
         for (int i = 0; i < nk; ++i) evals[i] = wT[i];
@@ -1264,7 +1364,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         if (rc == BS_OK) {
             std::vector<double> Yh((size_t)nT * nk);
             for (int r = 0; r < nT; ++r)
-                for (int m = 0; m < nk; ++m) Yh[(size_t)r * nk + m] = Z[(size_t)r * std::min(nkeep, nT) + m];
+                for (int m = 0; m < nk; ++m) Yh[(size_t)r * nk + m] = Z[(size_t)r * nv + m];
             cudaMemcpyAsync(Yd, Yh.data(), Yh.size() * sizeof(double), cudaMemcpyHostToDevice, L.s);
             cudaMemsetAsync(Xown, 0, (size_t)L.dim * kref * sizeof(double), L.s);
             blk_combine<T, K><<<L.ncta, 256, 0, L.s>>>(V, L.bstride, done, Yd, nk, Xown, kref, L.dim);
@@ -1309,9 +1409,13 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         }
         cudaStreamSynchronize(L.s);
     }
+    stage("Ritz vectors and refinement");
     for (auto &e : ev) cudaEventDestroy(e);
     if (gexec) cudaGraphExecDestroy(gexec);
     cleanup();
+    if (!stage("release") && rc == BS_OK) rc = BS_ECUDA;
+    if (rc == BS_ECUDA && !cuda_fail.empty()) c->err = "lanczos: " + cuda_fail;
+    else if (rc == BS_OK && !cuda_fail.empty()) { rc = BS_ECUDA; c->err = "lanczos: " + cuda_fail; }
     const auto t1 = std::chrono::steady_clock::now();
     if (rep) {
         rep->iterations = done;
@@ -1320,6 +1424,9 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         rep->ms_reorth = ms_or;
         rep->ms_total = std::chrono::duration<double, std::milli>(t1 - t0).count();
         rep->n_kept = nk;
+        rep->restarts = restarts;
+        rep->matvec_blocks = matvecs;
+        rep->resid_est = resid_est;
     }
     return rc;
 }

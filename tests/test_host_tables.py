@@ -514,3 +514,36 @@ def test_core_units_structure():
             k = k_bits.bit_length() - 1
             assert (int(wt) & 0x7FFFFFFF) % ns == k
             assert ((int(wt) >> 31) != 0) == (below(core, k) < 0)
+
+
+def test_abi_struct_layout_matches_header(tmp_path):
+    # the ctypes structures of the binding against sizeof / offsetof of the
+    # C declarations, compiled from the public header by the host compiler
+    import os
+    import shutil
+    import subprocess
+    if not shutil.which("gcc"):
+        pytest.skip("no host C compiler")
+    inc = os.path.join(os.path.dirname(os.path.dirname(__file__)), "include")
+    structs = [N.bs_orbit, N.bs_tbme, N.bs_lanczos_opts, N.bs_lanczos_report]
+    body = []
+    for S in structs:
+        body.append('printf("%s %%zu\\n", sizeof(%s));' % (S.__name__, S.__name__))
+        for f in S._fields_:
+            body.append('printf("%s.%s %%zu\\n", offsetof(%s, %s));' % (S.__name__, f[0], S.__name__, f[0]))
+    src = tmp_path / "layout.c"
+    src.write_text("#include <stdio.h>\n#include <stddef.h>\n#include <stdint.h>\n#include \"bigstick_gpu.h\"\n"
+                   "int main(void) {\n" + "\n".join(body) + "\nreturn 0;\n}\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-I", inc, str(src), "-o", str(exe)], check=True)
+    got = dict(line.split() for line in subprocess.run([str(exe)], check=True, capture_output=True,
+                                                       text=True).stdout.splitlines())
+    for S in structs:
+        assert int(got[S.__name__]) == ctypes_sizeof(S), S.__name__
+        for f in S._fields_:
+            assert int(got[S.__name__ + "." + f[0]]) == getattr(S, f[0]).offset, (S.__name__, f[0])
+
+
+def ctypes_sizeof(S):
+    import ctypes
+    return ctypes.sizeof(S)
