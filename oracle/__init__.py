@@ -348,6 +348,27 @@ class Oracle:
             return ev, X
         return ev[:nkeep], X[:, :nkeep]
 
+    # -- occupations -----------------------------------------------------
+    def occupations(self, psi):
+        """n_a = sum_alpha psi_alpha^2 (protons + neutrons of SD alpha in
+        orbit a) / |psi|^2, per orbit a (Sec. "Occupations": the number of
+        nucleons in each orbit).  Single-particle states are numbered
+        orbit-major, 2m ascending, so orbit a owns a run of 2j_a + 1 bits."""
+        psi = np.asarray(psi, dtype=np.float64)
+        w = psi * psi / float(psi @ psi)
+        P, Nn = self.states()
+        ones = np.array([bin(v).count("1") for v in range(256)], dtype=np.int64)
+
+        def popcount(x):
+            return ones[x.view(np.uint8).reshape(-1, 8)].sum(axis=1)
+
+        out, off = [], 0
+        for o in self.orbits:
+            mask = np.uint64(((1 << (o.twoj + 1)) - 1) << off)
+            out.append(float(w @ (popcount(P & mask) + popcount(Nn & mask))))
+            off += o.twoj + 1
+        return np.array(out)
+
     # -- J^2 ------------------------------------------------------------
     def j2(self, psi, oracle_up):
         """<J^2> = |J+ psi|^2 + M(M+1), with J+ psi evaluated in the 2M+2 basis."""

@@ -172,6 +172,7 @@ class Context:
         spe = np.ascontiguousarray(spe, dtype=np.float64)
         arr = (bs_tbme * max(1, len(tbmes)))(*[bs_tbme(*t) for t in tbmes])
         self._check(load().bs_load_interaction(self.h, _p(spe, f64p), len(spe), arr, len(tbmes)))
+        self.n_spe, self.n_tbme = len(spe), len(tbmes)
         return self
 
     def table(self, name, dtype):

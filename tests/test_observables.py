@@ -1,6 +1,11 @@
-"""<J^2> as an operator in the interaction format (observables.j2_operator),
-applied by the library's kernels, pinned against the oracle's independent
-route |J+ psi|^2 + M(M+1) (J+ applied by bit operations into the 2M+2 basis).
+"""<J^2> and <T^2> as operators in the interaction format
+(observables.j2_operator, t2_operator) and orbit occupations from the adjoint
+(observables.occupations), applied by the library's kernels.  <J^2> is
+pinned against the oracle's independent route |J+ psi|^2 + M(M+1) (J+
+applied by bit operations into the 2M+2 basis); T^2 against isospin
+multiplet counting; occupations against finite differences of the
+eigenvalue in the SPEs (Hellmann-Feynman), the particle number and the
+filling of a pure one-body Hamiltonian.
 
   * CPU: the J^2 table loaded into the oracle gives, for random vectors, the
     same <J^2> as the J+ route, and its explicit matrix has the eigenvalues
@@ -62,3 +67,92 @@ def test_gpu_j2_of_lanczos_eigenvectors(twoM):
             assert abs(J - round(J)) < 1e-5 and round(J) >= twoM // 2
     c.close()
     cj.close()
+
+
+@pytest.mark.parametrize("Z,Nn", [(2, 2), (3, 2), (3, 1)])
+def test_t2_operator_spectrum_counts_isospin_multiplets(Z, Nn):
+    # every isospin multiplet with T >= t has exactly one member with
+    # Tz = t, so the number of states with isospin T in the basis of
+    # (Z, N) is dim(Tz = T) - dim(Tz = T + 1) at the same A, 2M, parity
+    orbits, spe, tb = I.space("sd")
+    A, twoM = Z + Nn, (Z + Nn) % 2
+    st, tt = OB.t2_operator(orbits)
+    ot = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(st, tt)
+    T2 = ot.dense()
+    w = np.linalg.eigvalsh(T2)
+    twoT = np.rint(2 * OB.j_from_j2(w)).astype(int)
+    assert np.max(np.abs(2 * OB.j_from_j2(w) - twoT)) < 1e-9
+
+    def dim_tz(twoTz):   # 2Tz = Z' - N' >= 0, 0 if no such nucleus in the space
+        Zp = (A + twoTz) // 2
+        if Zp > 12 or A - Zp < 0:
+            return 0
+        try:
+            return O.Oracle(orbits, Zp, A - Zp, twoM, 0).dim
+        except O.OracleError:
+            return 0
+
+    for t2 in sorted(set(twoT)):
+        assert np.sum(twoT == t2) == dim_tz(t2) - dim_tz(t2 + 2), t2
+    assert min(twoT) == abs(Z - Nn)
+    H = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb).dense()
+    assert np.max(np.abs(H @ T2 - T2 @ H)) < 1e-12 * np.max(np.abs(H))   # isospin-conserving H
+
+
+def test_oracle_occupations_pins():
+    orbits, spe, tb = I.space("sd")
+    o = O.Oracle(orbits, 2, 2, 0, 0).set_interaction(spe, tb)
+    ev, X = o.eigh(3)
+    n0 = o.occupations(X[:, 0])
+    for m in range(3):
+        assert abs(o.occupations(X[:, m]).sum() - 4.0) < 1e-12
+    # Hellmann-Feynman: n_a = dE_0 / de_a, central differences on dense eigh
+    h = 1e-4
+    for a in range(len(orbits)):
+        e = []
+        for sgn in (1, -1):
+            sp = list(spe)
+            sp[a] += sgn * h
+            e.append(O.Oracle(orbits, 2, 2, 0, 0).set_interaction(sp, tb).eigh(1)[0][0])
+        assert abs((e[0] - e[1]) / (2 * h) - n0[a]) < 1e-7, a
+    # one-body only: the lowest level fills the lowest orbit (0d5/2 takes 4)
+    o1 = O.Oracle(orbits, 2, 2, 0, 0).set_interaction(spe, [])
+    ev1, X1 = o1.eigh(1)
+    assert np.allclose(o1.occupations(X1[:, 0]), [4.0, 0.0, 0.0], atol=1e-12)
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("name,Z", [("sd", 4), ("pf", 4)])
+def test_gpu_occupations_and_t2_of_lanczos_eigenvectors(name, Z):
+    """sd 4p4n and 48Cr (pf 4p4n, dim 1,963,461), FP64 Lanczos eigenvectors:
+    occupations from the adjoint equal the oracle's bit counts on the same
+    vectors and sum to A; <T^2> through a T^2 context equals the oracle's
+    explicit T^2 (sd) and is T(T+1) with integer T >= 0 for converged levels."""
+    torch = pytest.importorskip("torch")
+    from paper_1801_08432_gb300 import _native as N
+    orbits, spe, tb = I.space(name)
+    c = N.make(orbits, spe, tb, Z, Z, 0, +1, device=0)
+    ct = OB.t2_context(orbits, Z, Z, 0, device=0)
+    nkeep = 3
+    p = torch.from_numpy(I.random_block(c.dim, 1, seed=I.PIVOT_SEED)).to("cuda", torch.float64)
+    X = torch.zeros((c.dim, nkeep), device="cuda", dtype=torch.float64)
+    ev, rep = c.lanczos(p, 1, N.BS_F64, 150, nkeep, refine=True, evecs=X)
+    occ = OB.occupations(c, X, N.BS_F64)
+    orc = O.Oracle(orbits, Z, Z, 0, 0)
+    Xh = X.cpu().numpy()
+    for m in range(nkeep):
+        ref = orc.occupations(Xh[:, m])
+        assert np.max(np.abs(occ[m] - ref)) < 1e-9, (m, occ[m], ref)
+        assert abs(occ[m].sum() - 2 * Z) < 1e-9
+    t2 = np.diag(OB.expectation(ct, X, nkeep, N.BS_F64))
+    if name == "sd":
+        st, tt = OB.t2_operator(orbits)
+        ot = O.Oracle(orbits, Z, Z, 0, 0).set_interaction(st, tt)
+        ref = np.array([Xh[:, m] @ ot.spmv(Xh[:, m]) / (Xh[:, m] @ Xh[:, m]) for m in range(nkeep)])
+        assert np.max(np.abs(t2 - ref)) < 1e-9
+    for m in range(nkeep):
+        if rep["residual"][m] <= 1e-6:
+            T = OB.j_from_j2(t2[m])
+            assert abs(T - round(T)) < 1e-5
+    c.close()
+    ct.close()
