@@ -342,6 +342,51 @@ class Oracle:
             out += [np.hstack(Q[:niter]), T]
         return tuple(out)
 
+    def strength(self, pivot, niter):
+        """Block strength function (FP64): Sec. "Generating strength function
+        distributions" and Sec. "Block strength function".
+
+        pivot: [dim][k] block W_0 of any norm.  Its overlap matrix
+        O = W_0^T W_0 = U L U^T gives the orthonormal pivot V_1 = W_0 U L^(-1/2)
+        and B_0 = L^(1/2) U^T (so W_0 = V_1 B_0); niter block Lanczos
+        iterations with full reorthogonalization follow (as in
+        ``block_lanczos_thick`` without restart).  With T = L_T E L_T^T the
+        overlaps are <w_i|E_r> = sum_j (B_0)_ji (L_T)_jr over the first block's
+        rows j.  Returns (E [n], S [k][n]) with S = |<w_i|E_r>|^2 for every
+        eigenvalue of T (n = niter k)."""
+        W0 = np.array(pivot, dtype=np.float64).reshape(self.dim, -1)
+        k = W0.shape[1]
+        lam, U = np.linalg.eigh(W0.T @ W0)
+        if lam[0] <= 1e-24 * lam[-1]:
+            raise OracleError("rank-deficient pivot block")
+        B0 = np.sqrt(lam)[:, None] * U.T
+        V1 = W0 @ (U / np.sqrt(lam))
+        H = self.matrix()
+        Q = [V1]
+        A, B = [], []
+        for n in range(niter):
+            W = H @ Q[n]
+            A.append(Q[n].T @ W)
+            W = W - Q[n] @ A[n]
+            S = np.hstack(Q)
+            for _ in range(2):
+                W = W - S @ (S.T @ W)
+            l2, U2 = np.linalg.eigh(W.T @ W)
+            if l2[0] <= 1e-24 * max(l2[-1], 1e-300):
+                raise OracleError("block Lanczos breakdown")
+            B.append(np.sqrt(l2)[:, None] * U2.T)
+            Q.append(W @ (U2 / np.sqrt(l2)))
+        nT = niter * k
+        T = np.zeros((nT, nT))
+        for n in range(niter):
+            T[n * k:(n + 1) * k, n * k:(n + 1) * k] = 0.5 * (A[n] + A[n].T)
+            if n + 1 < niter:
+                T[(n + 1) * k:(n + 2) * k, n * k:(n + 1) * k] = B[n]
+                T[n * k:(n + 1) * k, (n + 1) * k:(n + 2) * k] = B[n].T
+        E, LT = np.linalg.eigh(T)
+        ov = B0.T @ LT[:k, :]
+        return E, ov * ov
+
     def eigh(self, nkeep=None):
         ev, X = np.linalg.eigh(self.dense())
         if nkeep is None:

@@ -343,3 +343,28 @@ def test_thick_restart_without_restart_is_lanczos(sd22):
     ev_t, _ = sd22.block_lanczos_thick(piv, 15, 2, 0)
     ev_l = sd22.lanczos(piv[:, 0], 15)
     assert np.max(np.abs(ev_t - ev_l)) < 1e-10
+
+
+# ------------------------------------------------------ strength function
+@pytest.mark.parametrize("k,niter", [(1, 6), (3, 5)])
+def test_strength_moments_equal_matrix_powers(sd22, k, niter):
+    # Lanczos reproduces the moments sum_r E_r^p |<w_i|E_r>|^2 = <w_i|H^p|w_i>
+    # exactly for p < 2 niter (k = 1; block: the diagonal of the moment
+    # matrices), whatever the pivot's norm
+    W0 = I.random_block(sd22.dim, k, seed=5) * np.array([1.0, 2.5, 0.3][:k])
+    E, S = sd22.strength(W0, niter)
+    H = sd22.dense()
+    Hp = np.eye(sd22.dim)
+    for p in range(2 * niter):
+        lhs = (S * E ** p).sum(axis=1)
+        rhs = np.einsum("ai,ai->i", W0, Hp @ W0)
+        assert np.max(np.abs(lhs - rhs) / np.abs(rhs)) < 1e-12, p
+        Hp = H @ Hp
+
+
+def test_strength_converged_levels_equal_dense_overlaps(sd22):
+    W0 = I.random_block(sd22.dim, 3, seed=6) * np.array([1.0, 2.5, 0.3])
+    E, S = sd22.strength(W0, 60)
+    ev, X = np.linalg.eigh(sd22.dense())
+    assert np.max(np.abs(E[:2] - ev[:2])) < 1e-9
+    assert np.max(np.abs(S[:, 0] - (X[:, 0] @ W0) ** 2)) < 1e-12
