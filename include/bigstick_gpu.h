@@ -265,6 +265,24 @@ typedef struct {
 int bs_lanczos(bs_ctx *ctx, const bs_lanczos_opts *opts, const void *pivot, double *evals, double *evecs,
                bs_lanczos_report *report);
 
+/* Strength function (Sec. "Generating strength function distributions",
+ * Sec. "Block strength function"): block Lanczos from the caller's pivot
+ * block W_0 (device [dim][k] in opts->dtype, any norm, full rank), which is
+ * orthonormalized as V_0 = W_0 U Lambda^(-1/2) with O = W_0^T W_0 =
+ * U Lambda U^T, so W_0 = V_0 B_0, B_0 = Lambda^(1/2) U^T.  After
+ * opts->niter block iterations T = L E L^T is diagonalized (dense, FP64,
+ * host) and, for the lowest n_out eigenvalues E_r of T, energies[r] = E_r
+ * and strengths[i * n_out + r] = |<w_i|E_r>|^2 = (sum_j (B_0)_ji L_jr)^2
+ * (HOST arrays of n_out and k * n_out doubles; entries past the dimension
+ * of T, when the Krylov space is exhausted early, are NaN).  Summed over
+ * all r, the strengths of column i give |w_i|^2, and sum_r E_r^p S_ir =
+ * <w_i|H^p|w_i> for p < 2 niter.  opts->refine, nkeep and max_restarts are
+ * ignored; opts->nthick must be 0.  Errors: as bs_lanczos, and BS_EINVAL for
+ * a rank-deficient pivot block (an overlap eigenvalue below 1e-12 of the
+ * largest) or n_out < 1. */
+int bs_strength(bs_ctx *ctx, const bs_lanczos_opts *opts, const void *pivot, int n_out, double *energies,
+                double *strengths, bs_lanczos_report *report);
+
 /* Test aid: all eigenvalues (ascending, w[n]) and the eigenvectors of the
  * lowest nvec (columns of Z, n x nvec row-major) of the symmetric n x n
  * matrix A (row-major, HOST), by the host FP64 solver bs_lanczos uses for T.

@@ -24,7 +24,7 @@ EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_ba
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_set_tuned", "bs_lanczos",
             "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_update", "bs_block_dots_noalloc",
-            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times"]
+            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -89,6 +89,8 @@ def load():
     L.bs_set_kernel.argtypes = [vp, ctypes.c_int]
     L.bs_set_tuned.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bs_lanczos.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, f64p, vp, ctypes.POINTER(bs_lanczos_report)]
+    L.bs_strength.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, ctypes.c_int, f64p, f64p,
+                              ctypes.POINTER(bs_lanczos_report)]
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.bs_debug_eigh_banded.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]
@@ -202,6 +204,20 @@ class Context:
              "ms_matvec": rep.ms_matvec, "ms_reorth": rep.ms_reorth, "ms_total": rep.ms_total,
              "restarts": rep.restarts, "matvec_blocks": rep.matvec_blocks, "resid_est": rep.resid_est}
         return ev, r
+
+    def strength(self, pivot, k, dtype, niter, n_out, stream=None, use_graph=False, reorth_passes=2):
+        """Strength function from the pivot block (device tensor [dim][k], any
+        norm): (E [n_out], S [k][n_out]) as numpy, S = |<w_i|E_r>|^2, plus the
+        report dict."""
+        o = bs_lanczos_opts(k, dtype, niter, 1, 0, reorth_passes, int(use_graph), vp(stream or 0), 0, 0, 0.0)
+        E = np.zeros(n_out)
+        S = np.zeros((k, n_out))
+        rep = bs_lanczos_report()
+        pp = pivot if isinstance(pivot, int) else pivot.data_ptr()
+        self._check(load().bs_strength(self.h, ctypes.byref(o), vp(pp), n_out, E.ctypes.data_as(f64p),
+                                       S.ctypes.data_as(f64p), ctypes.byref(rep)))
+        return E, S, {"iterations": rep.iterations, "breakdowns": rep.breakdowns, "ms_total": rep.ms_total,
+                      "ms_matvec": rep.ms_matvec, "ms_reorth": rep.ms_reorth}
 
     def set_kernel(self, mode):
         self._check(load().bs_set_kernel(self.h, mode))

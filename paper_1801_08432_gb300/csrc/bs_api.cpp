@@ -506,6 +506,28 @@ int bs_lanczos(bs_ctx *c, const bs_lanczos_opts *o, const void *pivot, double *e
     });
 }
 
+int bs_strength(bs_ctx *c, const bs_lanczos_opts *o, const void *pivot, int n_out, double *energies,
+                double *strengths, bs_lanczos_report *rep)
+{
+    return guarded(c, [&]() -> int {
+        if (!o) { c->err = "null options"; return BS_EINVAL; }
+        int rc = check_apply(c, o->k, o->dtype);
+        if (rc) return rc;
+        if (o->niter < 1 || n_out < 1 || !pivot || !energies || !strengths || o->nthick != 0) {
+            c->err = "strength: need niter >= 1, n_out >= 1, a pivot, output arrays and no thick restart";
+            return BS_EINVAL;
+        }
+        bs_lanczos_opts so = *o;
+        so.refine = 0;
+        so.nkeep = 1;
+        so.max_restarts = 0;
+        double e0 = 0.0;
+        StrengthReq req{n_out, energies, strengths};
+        if (rep) std::memset(rep, 0, sizeof(*rep));
+        return run_lanczos(c, so, pivot, &e0, nullptr, rep, &req);
+    });
+}
+
 int bs_set_kernel(bs_ctx *c, int mode)
 {
     return guarded(c, [&]() -> int {

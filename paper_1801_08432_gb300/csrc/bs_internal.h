@@ -336,8 +336,15 @@ int run_block_dots(bs_ctx *c, const void *V, int nb, const void *W, int k, bs_dt
 int run_block_update(bs_ctx *c, const void *V, int nb, const double *C, void *W, int k, bs_dtype dt, void *stream);
 int run_backward(bs_ctx *c, const void *x, const void *gy, void *gx, double *gtheta, int k, bs_dtype dt,
                  void *stream);
+// strength-function outputs of a Lanczos run (host): the lowest n_out
+// eigenvalues of T and |<w_i|E_r>|^2 per pivot column i ([k][n_out])
+struct StrengthReq {
+    int n_out;
+    double *E;
+    double *S;
+};
 int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
-                bs_lanczos_report *rep);
+                bs_lanczos_report *rep, const StrengthReq *sreq = nullptr);
 int pipe_variants();
 int core_variants();
 // allocates what launch_hx needs for (k, dtype) outside any stream capture

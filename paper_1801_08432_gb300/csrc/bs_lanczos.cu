@@ -1027,7 +1027,7 @@ void update(LState &L, const T *V, int nb, const double *C, T *W, const int *nb_
 
 template <typename T, int K>
 static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
-                       bs_lanczos_report *rep)
+                       bs_lanczos_report *rep, const StrengthReq *sreq)
 {
     LState L;
     L.k = K;
@@ -1113,8 +1113,26 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
     // orthonormalize the pivot block (FP64 Gram, one reorthogonalization-free QR)
     cudaMemcpyAsync(W, pivot, (size_t)L.dim * K * es, cudaMemcpyDeviceToDevice, L.s);
     dots<T, K>(L, W, 1, W, L.C);
-    small_gram<<<1, 32, 0, L.s>>>(K, L.C, rel, L.M, L.Bn, L.flags, nullptr, nullptr);
+    // a strength pivot must be well conditioned (its overlaps go through
+    // B_0): overlap eigenvalues below 1e-12 of the largest count as rank loss
+    small_gram<<<1, 32, 0, L.s>>>(K, L.C, sreq ? 1e-12 : rel, L.M, L.Bn, L.flags, nullptr, nullptr);
     blk_scale<T, K><<<L.ncta, 256, 0, L.s>>>(W, L.M, V, L.dim, nullptr, 0, nullptr);
+    // strength function: W_0 = V_0 B_0 with B_0 = Lambda^1/2 U^T of the pivot's
+    // overlap matrix (Sec. "Block strength function"); the pivot must have full rank
+    std::vector<double> B0((size_t)K * K);
+    if (sreq) {
+        int fl = 0;
+        cudaMemcpyAsync(B0.data(), L.Bn, (size_t)K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);
+        cudaMemcpyAsync(&fl, L.flags, sizeof(int), cudaMemcpyDeviceToHost, L.s);
+        int src = BS_OK;
+        if (cudaStreamSynchronize(L.s) != cudaSuccess) { c->err = "strength: pivot copy failed"; src = BS_ECUDA; }
+        else if (fl) { c->err = "strength: the pivot block is rank deficient"; src = BS_EINVAL; }
+        if (src != BS_OK) {
+            for (auto &e : ev) cudaEventDestroy(e);
+            cleanup();
+            return src;
+        }
+    }
 
     // Graph mode: the whole block iteration (H X, alpha, reorthogonalization,
     // Gram eigen-decomposition, normalization) is captured once in a CUDA
@@ -1153,6 +1171,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         if (graph) cudaGraphDestroy(graph);
         if (e != cudaSuccess || rc != BS_OK) {
             if (rc == BS_OK) { c->err = std::string("lanczos graph: ") + cudaGetErrorString(e); rc = BS_ECUDA; }
+            for (auto &ee : ev) cudaEventDestroy(ee);
             cleanup();
             return rc;
         }
@@ -1307,6 +1326,20 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         double r2 = 0.0;
         for (int i = 0; i < K; ++i) r2 += coupling(i, m) * coupling(i, m);
         resid_est = std::max(resid_est, std::sqrt(r2));
+    }
+    if (sreq) {
+        // every eigenpair of T; overlaps <w_i|E_r> = sum_j (B_0)_ji L_jr over the
+        // first block's rows (T is dense-diagonalized: all vectors are needed)
+        std::vector<double> wa((size_t)nT), za((size_t)nT * nT);
+        if (!host_eigh(nT, T_.data(), wa.data(), za.data(), nT)) { rc = BS_EBREAKDOWN; c->err = "strength: eigensolver failed"; break; }
+        for (int r = 0; r < sreq->n_out; ++r) {
+            sreq->E[r] = r < nT ? wa[r] : NAN;
+            for (int i = 0; i < K; ++i) {
+                double ov = 0.0;
+                for (int j = 0; j < K && r < nT; ++j) ov += B0[(size_t)j * K + i] * za[(size_t)j * nT + r];
+                sreq->S[(size_t)i * sreq->n_out + r] = r < nT ? ov * ov : NAN;
+            }
+        }
     }
     if (!thick || exhausted || done < niter || restarts >= o.max_restarts || (o.tol > 0.0 && resid_est <= o.tol)) break;
     // restart: Y_j = sum_b V_b U[b rows, j cols] (j < tb) into the scratch
@@ -1515,7 +1548,7 @@ int run_block_dots(bs_ctx *c, const void *V, int nb, const void *W, int k, bs_dt
 }
 
 int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o_in, const void *pivot, double *evals, double *evecs,
-                bs_lanczos_report *rep)
+                bs_lanczos_report *rep, const StrengthReq *sreq)
 {
     cudaError_t e = cudaSetDevice(c->device);
     if (e != cudaSuccess) { c->err = cudaGetErrorString(e); return BS_ECUDA; }
@@ -1536,17 +1569,17 @@ int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o_in, const void *pivot, doubl
     }
     if (o.dtype == BS_F64) {
         switch (o.k) {
-        case 1: return lanczos_run<double, 1>(c, o, pivot, evals, evecs, rep);
-        case 2: return lanczos_run<double, 2>(c, o, pivot, evals, evecs, rep);
-        case 4: return lanczos_run<double, 4>(c, o, pivot, evals, evecs, rep);
-        default: return lanczos_run<double, 8>(c, o, pivot, evals, evecs, rep);
+        case 1: return lanczos_run<double, 1>(c, o, pivot, evals, evecs, rep, sreq);
+        case 2: return lanczos_run<double, 2>(c, o, pivot, evals, evecs, rep, sreq);
+        case 4: return lanczos_run<double, 4>(c, o, pivot, evals, evecs, rep, sreq);
+        default: return lanczos_run<double, 8>(c, o, pivot, evals, evecs, rep, sreq);
         }
     }
     switch (o.k) {
-    case 1: return lanczos_run<float, 1>(c, o, pivot, evals, evecs, rep);
-    case 2: return lanczos_run<float, 2>(c, o, pivot, evals, evecs, rep);
-    case 4: return lanczos_run<float, 4>(c, o, pivot, evals, evecs, rep);
-    default: return lanczos_run<float, 8>(c, o, pivot, evals, evecs, rep);
+    case 1: return lanczos_run<float, 1>(c, o, pivot, evals, evecs, rep, sreq);
+    case 2: return lanczos_run<float, 2>(c, o, pivot, evals, evecs, rep, sreq);
+    case 4: return lanczos_run<float, 4>(c, o, pivot, evals, evecs, rep, sreq);
+    default: return lanczos_run<float, 8>(c, o, pivot, evals, evecs, rep, sreq);
     }
 }
 
