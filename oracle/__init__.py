@@ -414,6 +414,69 @@ class Oracle:
             off += o.twoj + 1
         return np.array(out)
 
+    # -- one-body densities ----------------------------------------------
+    def sp_states(self):
+        """(orbit, 2m) of every single-particle state: orbit-major, 2m ascending."""
+        out = []
+        for a, o in enumerate(self.orbits):
+            out += [(a, tm) for tm in range(-o.twoj, o.twoj + 1, 2)]
+        return out
+
+    def density(self, F, X, other=None):
+        """M-scheme one-body transition densities (Sec. "One-body density
+        matrices and occupations", before the reduction):
+
+            rho[t][i][k] = <F| a+_i a_k |X>   (t = 0 protons, 1 neutrons)
+
+        for vectors X in this basis and F in ``other``'s (default: this one),
+        every single-particle pair (i, k).  Each term applies a_k and then
+        a+_i to the species' bitstring with the sign (-1)^(number of occupied
+        states below the acted-on state), finds the resulting state in F's
+        basis and adds sign F[dst] X[src]; a pair of operators of one species
+        passes the other species' operators without a sign."""
+        fo = self if other is None else other
+        X = np.asarray(X, dtype=np.float64)
+        F = np.asarray(F, dtype=np.float64)
+        ns = self.ns
+        P, Nn = self.states()
+        Pf, Nf = fo.states()
+        key_f = (Pf << np.uint64(ns)) | Nf
+        order = np.argsort(key_f)
+        sorted_f = key_f[order]
+        ones = np.array([bin(v).count("1") for v in range(256)], dtype=np.int64)
+
+        def popcount(x):
+            return ones[x.view(np.uint8).reshape(-1, 8)].sum(axis=1)
+
+        st = self.sp_states()
+        dtm = fo.twoM - self.twoM
+        rho = np.zeros((2, ns, ns))
+        for t in range(2):
+            bits = P if t == 0 else Nn
+            for i in range(ns):
+                for k in range(ns):
+                    if st[i][1] - st[k][1] != dtm or self.orbits[st[i][0]].l % 2 != self.orbits[st[k][0]].l % 2:
+                        continue
+                    bk, bi = np.uint64(1) << np.uint64(k), np.uint64(1) << np.uint64(i)
+                    ok = (bits & bk) != 0
+                    b1 = bits ^ bk
+                    ok &= (b1 & bi) == 0
+                    if not ok.any():
+                        continue
+                    idx = np.nonzero(ok)[0]
+                    below_k = popcount(bits[idx] & (bk - np.uint64(1)))
+                    b1 = b1[idx]
+                    below_i = popcount(b1 & (bi - np.uint64(1)))
+                    b2 = b1 | bi
+                    sign = np.where((below_k + below_i) % 2 == 0, 1.0, -1.0)
+                    key = (b2 << np.uint64(ns)) | Nn[idx] if t == 0 else (P[idx] << np.uint64(ns)) | b2
+                    pos = np.searchsorted(sorted_f, key)
+                    pos = np.minimum(pos, len(sorted_f) - 1)
+                    hit = sorted_f[pos] == key
+                    dst = order[pos[hit]]
+                    rho[t, i, k] = float(np.sum(sign[hit] * F[dst] * X[idx[hit]]))
+        return rho
+
     # -- J^2 ------------------------------------------------------------
     def j2(self, psi, oracle_up):
         """<J^2> = |J+ psi|^2 + M(M+1), with J+ psi evaluated in the 2M+2 basis."""

@@ -368,3 +368,43 @@ def test_strength_converged_levels_equal_dense_overlaps(sd22):
     ev, X = np.linalg.eigh(sd22.dense())
     assert np.max(np.abs(E[:2] - ev[:2])) < 1e-9
     assert np.max(np.abs(S[:, 0] - (X[:, 0] @ W0) ** 2)) < 1e-12
+
+
+# ------------------------------------------------------ one-body densities
+@pytest.mark.parametrize("name,Z,Nn,twoM,par", [("sd", 2, 3, 1, 0), ("sd", 2, 2, 0, 0), ("p", 2, 3, -1, 1)])
+def test_density_contracts_to_the_jplus_route(name, Z, Nn, twoM, par):
+    # <F|J+|X> = sum_ik (j+)_ik rho_FX(i, k) with (j+) = sqrt(j(j+1) - m(m+1))
+    # between neighbouring m of one orbit, J+ applied by the oracle's C code
+    orbits, spe, tb = I.space(name)
+    o = O.Oracle(orbits, Z, Nn, twoM, par)
+    up = O.Oracle(orbits, Z, Nn, twoM + 2, par)
+    rng = np.random.default_rng(17 + twoM)
+    X, F = rng.standard_normal(o.dim), rng.standard_normal(up.dim)
+    out = np.zeros(up.dim)
+    assert O.lib().orc_jplus(o.h, up.h, O._p(np.ascontiguousarray(X), O.f64p), O._p(out, O.f64p)) == 0
+    rho = o.density(F, X, other=up)
+    st = o.sp_states()
+    jp = np.zeros((o.ns, o.ns))
+    for i, (a, tm) in enumerate(st):
+        for k, (b, tm2) in enumerate(st):
+            if a == b and tm == tm2 + 2:
+                tj = orbits[a].twoj
+                jp[i, k] = 0.5 * np.sqrt((tj - tm2) * (tj + tm2 + 2.0))
+    ref = float(F @ out)
+    assert abs(np.sum(jp * (rho[0] + rho[1])) - ref) <= 1e-12 * max(1.0, abs(ref))
+
+
+def test_density_diagonal_gives_occupations_and_particle_numbers(sd22):
+    ev, X = sd22.eigh(3)
+    st = sd22.sp_states()
+    for m in range(3):
+        rho = sd22.density(X[:, m], X[:, m])
+        assert abs(np.trace(rho[0]) - 2.0) < 1e-12 and abs(np.trace(rho[1]) - 2.0) < 1e-12
+        n = np.zeros(3)
+        for i, (a, tm) in enumerate(st):
+            n[a] += rho[0, i, i] + rho[1, i, i]
+        assert np.max(np.abs(n - sd22.occupations(X[:, m]))) < 1e-12
+        assert np.max(np.abs(rho - rho.transpose(0, 2, 1))) < 1e-13   # real symmetric for F = X
+    # transition densities: rho_fi(i, k) = rho_if(k, i)
+    r01, r10 = sd22.density(X[:, 0], X[:, 1]), sd22.density(X[:, 1], X[:, 0])
+    assert np.max(np.abs(r01 - r10.transpose(0, 2, 1))) < 1e-13
