@@ -283,6 +283,21 @@ int bs_lanczos(bs_ctx *ctx, const bs_lanczos_opts *opts, const void *pivot, doub
 int bs_strength(bs_ctx *ctx, const bs_lanczos_opts *opts, const void *pivot, int n_out, double *energies,
                 double *strengths, bs_lanczos_report *report);
 
+/* One-body transition densities (Sec. "One-body density matrices and
+ * occupations", the M-scheme matrix elements under the reduced densities):
+ *   rho[((t * ns + i) * ns + l) * k * k + f * k + j] = <F_f| a+_i a_l |X_j>
+ * for species t (0 protons, 1 neutrons), single-particle states i, l
+ * (numbered orbit-major, 2m ascending; ns states) and the k columns of F and
+ * X, two FP64 device blocks [dim][k] on this context's basis.  Only pairs
+ * with 2m_i = 2m_l and equal parity can connect two states of one basis;
+ * every other entry is 0.  rho: HOST array of 2 ns^2 k^2 doubles.  The
+ * diagonal sums to the particle numbers times <F_f|X_j>.  Accumulated in
+ * FP64 with atomics (last bits may vary between runs).  Synchronizes the
+ * stream; allocates and frees a small work area.  Errors: BS_ENOBASIS,
+ * BS_ENOINT (the jump tables come with the interaction), BS_EINVAL (k not
+ * 1, 2, 4 or 8, null pointer), BS_ENOMEM, BS_ECUDA. */
+int bs_density(bs_ctx *ctx, const double *F, const double *X, int k, double *rho, void *stream);
+
 /* Test aid: all eigenvalues (ascending, w[n]) and the eigenvectors of the
  * lowest nvec (columns of Z, n x nvec row-major) of the symmetric n x n
  * matrix A (row-major, HOST), by the host FP64 solver bs_lanczos uses for T.

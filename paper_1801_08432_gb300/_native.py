@@ -24,7 +24,7 @@ EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_ba
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_set_tuned", "bs_lanczos",
             "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_update", "bs_block_dots_noalloc",
-            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength"]
+            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength", "bs_density"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -91,6 +91,7 @@ def load():
     L.bs_lanczos.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, f64p, vp, ctypes.POINTER(bs_lanczos_report)]
     L.bs_strength.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, ctypes.c_int, f64p, f64p,
                               ctypes.POINTER(bs_lanczos_report)]
+    L.bs_density.argtypes = [vp, vp, vp, ctypes.c_int, f64p, vp]
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.bs_debug_eigh_banded.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]
@@ -218,6 +219,15 @@ class Context:
                                        S.ctypes.data_as(f64p), ctypes.byref(rep)))
         return E, S, {"iterations": rep.iterations, "breakdowns": rep.breakdowns, "ms_total": rep.ms_total,
                       "ms_matvec": rep.ms_matvec, "ms_reorth": rep.ms_reorth}
+
+    def density(self, F, X, k, ns, stream=None):
+        """One-body transition densities rho[t][i][l][f][j] = <F_f| a+_i a_l |X_j>
+        (numpy, t = 0 protons, 1 neutrons) of the k columns of two FP64 CUDA
+        tensors [dim][k] on this basis; ns single-particle states."""
+        rho = np.zeros((2, ns, ns, k, k))
+        ptr = lambda t: vp(t if isinstance(t, int) else t.data_ptr())
+        self._check(load().bs_density(self.h, ptr(F), ptr(X), k, rho.ctypes.data_as(f64p), vp(stream or 0)))
+        return rho
 
     def set_kernel(self, mode):
         self._check(load().bs_set_kernel(self.h, mode))

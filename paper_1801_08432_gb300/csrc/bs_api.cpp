@@ -528,6 +528,16 @@ int bs_strength(bs_ctx *c, const bs_lanczos_opts *o, const void *pivot, int n_ou
     });
 }
 
+int bs_density(bs_ctx *c, const double *F, const double *X, int k, double *rho, void *stream)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, k, BS_F64);
+        if (rc) return rc;
+        if (!F || !X || !rho) { c->err = "density: null pointer"; return BS_EINVAL; }
+        return run_density(c, F, X, k, rho, stream);
+    });
+}
+
 int bs_set_kernel(bs_ctx *c, int mode)
 {
     return guarded(c, [&]() -> int {
