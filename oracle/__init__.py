@@ -477,6 +477,42 @@ class Oracle:
                     rho[t, i, k] = float(np.sum(sign[hit] * F[dst] * X[idx[hit]]))
         return rho
 
+    def reduced_density(self, rho, twoJf, twoJi):
+        """Reduced one-body densities in proton-neutron form (Sec. "One-body
+        density matrices and occupations"), from the M-scheme densities
+        ``rho`` (as returned by ``density`` for two states of this basis,
+        M_f = M_i = M):
+
+            rho_K(a+ b) = [K]^-1 <J_f||(a+ b~)_K||J_i>,
+            (a+ b~)_K0 = sum_m (j_a m, j_b -m | K 0) a+_{a m} b~_{b -m},
+            b~_{b -m} = (-1)^(j_b - m) b_{b m},
+            <J_f||O_K||J_i> = [J_f] <J_f M|O_K0|J_i M> / (J_i M, K 0 | J_f M)
+
+        with [x] = sqrt(2x + 1) and Edmonds' Wigner-Eckart convention.
+        Returns {(t, a, b, 2K): value}, NaN where the Clebsch-Gordan
+        coefficient vanishes at this M."""
+        st = self.sp_states()
+        tM = self.twoM
+        out = {}
+        na = len(self.orbits)
+        for t in range(2):
+            for a in range(na):
+                for b in range(na):
+                    ja, jb = self.orbits[a].twoj, self.orbits[b].twoj
+                    for twoK in range(abs(ja - jb), ja + jb + 1, 2):
+                        s = 0.0
+                        for i, (oa, tma) in enumerate(st):
+                            if oa != a:
+                                continue
+                            for l, (ob, tmb) in enumerate(st):
+                                if ob == b and tmb == tma:
+                                    ph = -1.0 if ((jb - tma) // 2) % 2 else 1.0
+                                    s += cg(ja, tma, jb, -tma, twoK, 0) * ph * rho[t, i, l]
+                        c = cg(twoJi, tM, twoK, 0, twoJf, tM)
+                        out[(t, a, b, twoK)] = (np.nan if abs(c) < 1e-12 else
+                                                np.sqrt(twoJf + 1.0) * s / c / np.sqrt(twoK + 1.0))
+        return out
+
     # -- J^2 ------------------------------------------------------------
     def j2(self, psi, oracle_up):
         """<J^2> = |J+ psi|^2 + M(M+1), with J+ psi evaluated in the 2M+2 basis."""

@@ -408,3 +408,80 @@ def test_density_diagonal_gives_occupations_and_particle_numbers(sd22):
     # transition densities: rho_fi(i, k) = rho_if(k, i)
     r01, r10 = sd22.density(X[:, 0], X[:, 1]), sd22.density(X[:, 1], X[:, 0])
     assert np.max(np.abs(r01 - r10.transpose(0, 2, 1))) < 1e-13
+
+
+# ------------------------------------------------------ reduced densities
+def _levels_with_j(o, nlev):
+    up = O.Oracle(o.orbits, o.Z, o.N, o.twoM + 2, o.parity)
+    ev, X = o.eigh(nlev)
+    J = [int(round(O.j_from_j2(o.j2(X[:, m], up)))) for m in range(nlev)]
+    return ev, X, J
+
+
+@pytest.fixture(scope="module")
+def sd22_m1():
+    orbits, spe, tb = I.space("sd")
+    return O.Oracle(orbits, 2, 2, 2, 0).set_interaction(spe, tb)
+
+
+def test_reduced_density_k0_is_scaled_occupation(sd22):
+    # (a+ a~)_00 = n_a / [j_a], so rho_0(a+ a) = [J] n_a / [j_a] per species
+    ev, X, J = _levels_with_j(sd22, 5)
+    st = sd22.sp_states()
+    for m in range(5):
+        rho = sd22.density(X[:, m], X[:, m])
+        r = sd22.reduced_density(rho, 2 * J[m], 2 * J[m])
+        for t in range(2):
+            for a, o in enumerate(sd22.orbits):
+                n = sum(rho[t, i, i] for i, (oa, _) in enumerate(st) if oa == a)
+                assert abs(r[(t, a, a, 0)] - np.sqrt(2 * J[m] + 1.0) * n / np.sqrt(o.twoj + 1.0)) < 1e-12
+
+
+def test_reduced_density_k1_gives_reduced_j(sd22_m1):
+    # <J||J||J> = sqrt(J(J+1)(2J+1)) = sum_a <a||j||a> (rho_1^p + rho_1^n)(a+ a),
+    # <a||j||a> = sqrt(j(j+1)(2j+1)) (Edmonds); M = 1, so every J >= 1 counts
+    o = sd22_m1
+    ev, X, J = _levels_with_j(o, 5)
+    for m in range(5):
+        rho = o.density(X[:, m], X[:, m])
+        r = o.reduced_density(rho, 2 * J[m], 2 * J[m])
+        s = sum(np.sqrt(orb.twoj / 2 * (orb.twoj / 2 + 1) * (orb.twoj + 1)) * (r[(0, a, a, 2)] + r[(1, a, a, 2)])
+                for a, orb in enumerate(o.orbits))
+        assert abs(s - np.sqrt(J[m] * (J[m] + 1) * (2 * J[m] + 1))) < 1e-11, (m, J[m])
+
+
+def test_reduced_density_independent_of_m(sd22, sd22_m1):
+    # Wigner-Eckart: the same levels at M = 0 and M = 1 give the same rho_K
+    ev0, X0, J0 = _levels_with_j(sd22, 6)
+    ev1, X1, J1 = _levels_with_j(sd22_m1, 5)
+    checked = 0
+    for m1 in range(5):
+        m0 = int(np.argmin(np.abs(ev0 - ev1[m1])))
+        if abs(ev0[m0] - ev1[m1]) > 1e-8 or J0[m0] != J1[m1]:
+            continue
+        r0 = sd22.reduced_density(sd22.density(X0[:, m0], X0[:, m0]), 2 * J0[m0], 2 * J0[m0])
+        r1 = sd22_m1.reduced_density(sd22_m1.density(X1[:, m1], X1[:, m1]), 2 * J1[m1], 2 * J1[m1])
+        for key, v in r0.items():
+            if np.isfinite(v) and np.isfinite(r1[key]):
+                assert abs(v - r1[key]) < 1e-11, key
+                checked += 1
+    assert checked > 50
+
+
+def test_reduced_transition_density_symmetry(sd22_m1):
+    # Edmonds' convention, real states: rho^{if}_K(b+ a) =
+    # (-1)^(J_f - J_i + j_a - j_b) rho^{fi}_K(a+ b); the other coupling order
+    # of the Wigner-Eckart theorem would scale one side by [J_i] / [J_f]
+    o = sd22_m1
+    ev, X, J = _levels_with_j(o, 6)
+    n = 0
+    for f, i in [(0, 1), (1, 3), (0, 3), (2, 4)]:
+        rfi = o.reduced_density(o.density(X[:, f], X[:, i]), 2 * J[f], 2 * J[i])
+        rif = o.reduced_density(o.density(X[:, i], X[:, f]), 2 * J[i], 2 * J[f])
+        for (t, a, b, tk), v in rfi.items():
+            w = rif[(t, b, a, tk)]
+            if np.isfinite(v) and np.isfinite(w):
+                ph = (-1) ** ((J[f] - J[i]) + (o.orbits[a].twoj - o.orbits[b].twoj) // 2)
+                assert abs(w - ph * v) < 1e-12
+                n += 1
+    assert n > 100 and len({J[0], J[1], J[3], J[4]}) > 2
