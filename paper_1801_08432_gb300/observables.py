@@ -1,5 +1,6 @@
 """Scalar observables: J^2 and T^2 as one- plus two-body operators in the
-interaction format, and orbit occupations from the adjoint.
+interaction format, orbit occupations from the adjoint, and reduced one-body
+densities from the GPU's M-scheme densities.
 
 The total angular momentum squared is J^2 = sum_i j_i^2 + sum_{i != j} j_i . j_j.
 Its single-particle part is j_a (j_a + 1) on every particle in orbit a, and
@@ -70,6 +71,69 @@ def occupations(ctx, psi, dtype, stream=None):
         g = ctx.apply_H_backward(x, x, gx, 1, dtype, n_theta=n_theta, stream=stream)
         ctx.block_dots(x, 1, x, 1, dtype, nrm, stream)
         out[m] = g[:n_spe] / float(nrm.cpu()[0])
+    return out
+
+
+def clebsch_gordan(tj1, tm1, tj2, tm2, tJ, tM):
+    """<j1 m1 j2 m2 | J M>, all arguments doubled, by Racah's closed formula
+    (a finite alternating sum of factorial ratios)."""
+    from math import factorial as fac, sqrt
+    if tm1 + tm2 != tM or abs(tm1) > tj1 or abs(tm2) > tj2 or abs(tM) > tJ:
+        return 0.0
+    if (tj1 + tm1) % 2 or (tj2 + tm2) % 2 or (tJ + tM) % 2 or (tj1 + tj2 + tJ) % 2:
+        return 0.0
+    if tJ > tj1 + tj2 or tJ < abs(tj1 - tj2):
+        return 0.0
+    a, b, c = (tj1 + tj2 - tJ) // 2, (tj1 - tj2 + tJ) // 2, (-tj1 + tj2 + tJ) // 2
+    pre = sqrt((tJ + 1) * fac(a) * fac(b) * fac(c) / fac((tj1 + tj2 + tJ) // 2 + 1))
+    pre *= sqrt(fac((tj1 + tm1) // 2) * fac((tj1 - tm1) // 2) * fac((tj2 + tm2) // 2) * fac((tj2 - tm2) // 2)
+                * fac((tJ + tM) // 2) * fac((tJ - tM) // 2))
+    s = 0.0
+    for k in range(0, a + 1):
+        d = [k, a - k, (tj1 - tm1) // 2 - k, (tj2 + tm2) // 2 - k, (tJ - tj2 + tm1) // 2 + k,
+             (tJ - tj1 - tm2) // 2 + k]
+        if min(d) < 0:
+            continue
+        den = 1
+        for x in d:
+            den *= fac(x)
+        s += (-1.0 if k % 2 else 1.0) / den
+    return pre * s
+
+
+def reduced_densities(rho, orbits, twoM, twoJf, twoJi):
+    """Reduced one-body densities in proton-neutron form (Sec. "One-body
+    density matrices and occupations") from the M-scheme densities of one
+    pair of states of one basis (rho[t][i][l] = <f| a+_i a_l |i>, species t,
+    as bs_density returns them per column pair; M_f = M_i = M):
+
+        rho_K(a+ b) = [K]^-1 [J_f] <J_f M| (a+ b~)_K0 |J_i M> / (J_i M, K 0 | J_f M),
+        (a+ b~)_K0 = sum_m (j_a m, j_b -m | K 0) (-1)^(j_b - m) a+_{a m} b_{b m},
+
+    [x] = sqrt(2x + 1), Edmonds' Wigner-Eckart convention.  Returns
+    {(t, a, b, 2K): value}; NaN where (J_i M, K 0 | J_f M) vanishes (choose
+    another M for those K)."""
+    st = []
+    for a, o in enumerate(orbits):
+        st += [(a, tm) for tm in range(-o.twoj, o.twoj + 1, 2)]
+    first = {}
+    for i, (a, tm) in enumerate(st):
+        first.setdefault(a, i)
+    out = {}
+    for t in range(2):
+        for a, oa in enumerate(orbits):
+            for b, ob in enumerate(orbits):
+                ja, jb = oa.twoj, ob.twoj
+                for twoK in range(abs(ja - jb), ja + jb + 1, 2):
+                    s = 0.0
+                    for tm in range(-min(ja, jb), min(ja, jb) + 1, 2):
+                        i = first[a] + (tm + ja) // 2
+                        l = first[b] + (tm + jb) // 2
+                        ph = -1.0 if ((jb - tm) // 2) % 2 else 1.0
+                        s += clebsch_gordan(ja, tm, jb, -tm, twoK, 0) * ph * rho[t][i][l]
+                    c = clebsch_gordan(twoJi, twoM, twoK, 0, twoJf, twoM)
+                    out[(t, a, b, twoK)] = (float("nan") if abs(c) < 1e-12 else
+                                            np.sqrt(twoJf + 1.0) * s / c / np.sqrt(twoK + 1.0))
     return out
 
 

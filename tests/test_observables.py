@@ -156,3 +156,57 @@ def test_gpu_occupations_and_t2_of_lanczos_eigenvectors(name, Z):
             assert abs(T - round(T)) < 1e-5
     c.close()
     ct.close()
+
+
+def test_product_clebsch_gordan_matches_sympy():
+    sympy = pytest.importorskip("sympy")
+    from sympy.physics.wigner import clebsch_gordan as cg_exact
+    H = sympy.Rational(1, 2)
+    worst = 0.0
+    for tj1 in range(0, 8):
+        for tj2 in range(0, 8):
+            for tJ in range(abs(tj1 - tj2), tj1 + tj2 + 1, 2):
+                for tm1 in range(-tj1, tj1 + 1, 2):
+                    for tm2 in range(-tj2, tj2 + 1, 2):
+                        if abs(tm1 + tm2) > tJ:
+                            continue
+                        ref = float(cg_exact(tj1 * H, tj2 * H, tJ * H, tm1 * H, tm2 * H, (tm1 + tm2) * H))
+                        worst = max(worst, abs(OB.clebsch_gordan(tj1, tm1, tj2, tm2, tJ, tm1 + tm2) - ref))
+    assert worst < 1e-12
+
+
+@pytest.mark.gpu
+def test_gpu_reduced_densities_of_lanczos_eigenvectors():
+    """sd 4p4n at M = 1: M-scheme densities of GPU Lanczos eigenvectors from
+    bs_density, reduced by observables.reduced_densities, equal the oracle's
+    reduction of its own densities of the same vectors (diagonal and
+    transitions); the reduced J of every converged level is sqrt(J(J+1)(2J+1))."""
+    torch = pytest.importorskip("torch")
+    from paper_1801_08432_gb300 import _native as N
+    orbits, spe, tb = I.space("sd")
+    c = N.make(orbits, spe, tb, 4, 4, 2, +1, device=0)
+    cj = OB.j2_context(orbits, 4, 4, 2, device=0)
+    nkeep = 4
+    p = torch.from_numpy(I.random_block(c.dim, 1, seed=I.PIVOT_SEED)).to("cuda", torch.float64)
+    X = torch.zeros((c.dim, nkeep), device="cuda", dtype=torch.float64)
+    ev, rep = c.lanczos(p, 1, N.BS_F64, 200, nkeep, refine=True, evecs=X)
+    assert max(rep["residual"]) < 1e-6
+    J = [int(round(float(v))) for v in OB.j_from_j2(np.diag(OB.expectation(cj, X, nkeep, N.BS_F64)))]
+    ns = sum(o.twoj + 1 for o in orbits)
+    rho = c.density(X, X, nkeep, ns)
+    Xh = X.cpu().numpy()
+    orc = O.Oracle(orbits, 4, 4, 2, 0)
+    for f, i in [(0, 0), (1, 1), (0, 1), (2, 3), (3, 0)]:
+        got = OB.reduced_densities(rho[:, :, :, f, i], orbits, 2, 2 * J[f], 2 * J[i])
+        ref = orc.reduced_density(orc.density(Xh[:, f], Xh[:, i]), 2 * J[f], 2 * J[i])
+        for key, v in ref.items():
+            assert np.isnan(v) == np.isnan(got[key])
+            if np.isfinite(v):
+                assert abs(got[key] - v) < 1e-9, (f, i, key)
+    for m in range(nkeep):
+        r = OB.reduced_densities(rho[:, :, :, m, m], orbits, 2, 2 * J[m], 2 * J[m])
+        s = sum(np.sqrt(o.twoj / 2 * (o.twoj / 2 + 1) * (o.twoj + 1)) * (r[(0, a, a, 2)] + r[(1, a, a, 2)])
+                for a, o in enumerate(orbits))
+        assert abs(s - np.sqrt(J[m] * (J[m] + 1) * (2 * J[m] + 1))) < 1e-6
+    c.close()
+    cj.close()
