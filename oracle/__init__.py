@@ -264,7 +264,7 @@ class Oracle:
         return ev[:nk], X
 
     def block_lanczos_thick(self, pivot, niter, nthick, restarts, nkeep=None, return_vectors=False,
-                            return_state=False):
+                            return_state=False, target=None):
         """Thick-restart block Lanczos (FP64): Sec. "Block Lanczos", Sec.
         "Thick-restart Lanczos" and Sec. "Thick-restart block Lanczos".
 
@@ -285,8 +285,21 @@ class Oracle:
         per cycle the list of all Ritz values; with ``return_vectors`` also
         the Ritz vectors of the lowest nkeep; with ``return_state`` also the
         last cycle's stored blocks Q ([dim][niter k]) and T.
+
+        ``target`` = E_bar runs the same iteration on (H - E_bar)^2
+        (Sec. "Targeted thick-restart Lanczos: interior eigenvalues"): the
+        levels nearest E_bar become the lowest of that operator, and T holds
+        its projection.
         """
-        H = self.matrix()
+        H0 = self.matrix()
+        if target is None:
+            H = H0
+        else:
+            class _Shifted2:   # v -> (H - E_bar)^2 v
+                def __matmul__(_, v):
+                    w = H0 @ v - target * v
+                    return H0 @ w - target * w
+            H = _Shifted2()
         X = np.array(pivot, dtype=np.float64).reshape(self.dim, -1)
         k = X.shape[1]
         if nthick % k or not 0 <= nthick // k < niter - 1:

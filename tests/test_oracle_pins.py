@@ -485,3 +485,18 @@ def test_reduced_transition_density_symmetry(sd22_m1):
                 assert abs(w - ph * v) < 1e-12
                 n += 1
     assert n > 100 and len({J[0], J[1], J[3], J[4]}) > 2
+
+
+def test_targeted_thick_restart_finds_levels_nearest_the_target(sd22):
+    # thick restart on (H - E_bar)^2: the Ritz vectors of its lowest levels
+    # are the eigenvectors of H nearest E_bar (dense diagonalization)
+    ev = np.linalg.eigvalsh(sd22.dense())
+    H = sd22.matrix()
+    for idx, niter, restarts in ((8, 40, 60), (100, 60, 100)):
+        Eb = 0.5 * (ev[idx] + ev[idx + 1]) + 0.013
+        piv = I.random_block(sd22.dim, 2)
+        e2, hist, X = sd22.block_lanczos_thick(piv, niter, 8, restarts, nkeep=3, return_vectors=True, target=Eb)
+        rq = np.sort([X[:, m] @ (H @ X[:, m]) / (X[:, m] @ X[:, m]) for m in range(3)])
+        near = np.sort(ev[np.argsort(np.abs(ev - Eb))[:3]])
+        assert np.max(np.abs(rq - near)) < 1e-9
+        assert np.max(np.abs(np.sort(e2) - np.sort((near - Eb) ** 2))) < 1e-9
