@@ -224,6 +224,12 @@ typedef struct {
     int max_restarts;   /* restarts at most (ignored when nthick = 0) */
     double tol;         /* stop restarting once the residual estimate of each of the lowest
                            nkeep pairs is <= tol (0 = run all max_restarts restarts) */
+    int targeted;       /* 1: interior levels (Sec. "Targeted thick-restart Lanczos"): the
+                           iteration runs on (H - target)^2, two products H X per block
+                           iteration, so the levels nearest target come first; needs
+                           refine = 1 and nkeep <= 8 (evals are then FP64 Rayleigh quotients
+                           of H, ordered as the levels of (H - target)^2, residuals of H) */
+    double target;      /* E_bar of the targeted operator */
 } bs_lanczos_opts;
 
 /* What bs_lanczos did. */
@@ -237,7 +243,8 @@ typedef struct {
     double ms_reorth;        /* GPU time in alpha, reorthogonalization, Gram and normalization */
     double ms_total;         /* wall time of the call */
     int restarts;            /* thick restarts done */
-    int matvec_blocks;       /* block products H X done (restarts included) */
+    int matvec_blocks;       /* block products H X done (restarts included; two per block
+                                iteration when targeted) */
     double resid_est;        /* max over the lowest nkeep pairs of |B_last U_last,mu|, the
                                 Lanczos estimate of |H psi - E psi| from the last T */
 } bs_lanczos_report;

@@ -40,7 +40,7 @@ class bs_lanczos_opts(ctypes.Structure):
     _fields_ = [("k", ctypes.c_int), ("dtype", ctypes.c_int), ("niter", ctypes.c_int), ("nkeep", ctypes.c_int),
                 ("refine", ctypes.c_int), ("reorth_passes", ctypes.c_int), ("use_graph", ctypes.c_int),
                 ("stream", ctypes.c_void_p), ("nthick", ctypes.c_int), ("max_restarts", ctypes.c_int),
-                ("tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("targeted", ctypes.c_int), ("target", ctypes.c_double)]
 
 
 class bs_lanczos_report(ctypes.Structure):
@@ -186,15 +186,17 @@ class Context:
         return out
 
     def lanczos(self, pivot, k, dtype, niter, nkeep, refine=True, evecs=None, stream=None, reorth_passes=2,
-                use_graph=False, nthick=0, max_restarts=0, tol=0.0):
+                use_graph=False, nthick=0, max_restarts=0, tol=0.0, target=None):
         """Block Lanczos on the GPU.  pivot: device tensor [dim][k] (dtype);
         evecs: optional device float64 tensor [dim][nkeep]; nthick > 0 turns
         on thick restart (Ritz vectors kept, a multiple of k) with at most
         max_restarts restarts, stopping once the residual estimates of the
-        lowest nkeep pairs are <= tol.  Returns (eigenvalues as numpy,
-        report dict)."""
+        lowest nkeep pairs are <= tol; target = E_bar runs on (H - E_bar)^2 for
+        the levels nearest E_bar.  Returns (eigenvalues as numpy, report
+        dict)."""
         o = bs_lanczos_opts(k, dtype, niter, nkeep, int(refine), reorth_passes, int(use_graph), vp(stream or 0),
-                            nthick, max_restarts, tol)
+                            nthick, max_restarts, tol, int(target is not None),
+                            0.0 if target is None else float(target))
         ev = np.zeros(nkeep)
         rep = bs_lanczos_report()
         pp = pivot if isinstance(pivot, int) else pivot.data_ptr()
@@ -210,7 +212,7 @@ class Context:
         """Strength function from the pivot block (device tensor [dim][k], any
         norm): (E [n_out], S [k][n_out]) as numpy, S = |<w_i|E_r>|^2, plus the
         report dict."""
-        o = bs_lanczos_opts(k, dtype, niter, 1, 0, reorth_passes, int(use_graph), vp(stream or 0), 0, 0, 0.0)
+        o = bs_lanczos_opts(k, dtype, niter, 1, 0, reorth_passes, int(use_graph), vp(stream or 0), 0, 0, 0.0, 0, 0.0)
         E = np.zeros(n_out)
         S = np.zeros((k, n_out))
         rep = bs_lanczos_report()

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <numeric>
 #include <cstring>
 #include <new>
@@ -501,6 +502,10 @@ int bs_lanczos(bs_ctx *c, const bs_lanczos_opts *o, const void *pivot, double *e
                      "max_restarts >= 0, tol >= 0";
             return BS_EINVAL;
         }
+        if (o->targeted && (!o->refine || o->nkeep > 8 || !std::isfinite(o->target))) {
+            c->err = "lanczos: a targeted run needs refine = 1, nkeep <= 8 and a finite target";
+            return BS_EINVAL;
+        }
         if (rep) std::memset(rep, 0, sizeof(*rep));
         return run_lanczos(c, *o, pivot, evals, evecs, rep);
     });
@@ -518,6 +523,7 @@ int bs_strength(bs_ctx *c, const bs_lanczos_opts *o, const void *pivot, int n_ou
             return BS_EINVAL;
         }
         bs_lanczos_opts so = *o;
+        so.targeted = 0;
         so.refine = 0;
         so.nkeep = 1;
         so.max_restarts = 0;

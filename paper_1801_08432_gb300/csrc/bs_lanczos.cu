@@ -284,6 +284,14 @@ __global__ void iter_set(int *iter, int v)
     if (threadIdx.x == 0 && blockIdx.x == 0) *iter = v;
 }
 
+// y[e] += a x[e], e < n (the shift of the targeted operator (H - E_bar)^2)
+template <typename T>
+__global__ void vec_axpy(T *__restrict__ y, const T *__restrict__ x, T a, int64_t n)
+{
+    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] = fma(a, x[e], y[e]);
+}
+
 // X[alpha][m] = sum_b sum_i V_b[alpha][i] Y[b*K+i][m], m < nm, FP64 output [dim][ldx]
 template <typename T, int K>
 __global__ void blk_combine(const T *__restrict__ V, int64_t bstride, int nb, const double *__restrict__ Y, int nm,
@@ -1064,6 +1072,20 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
     if (thick && tb + 1 >= niter) { c->err = "lanczos: nthick / k + 1 must stay below niter (clamped to dim / k)"; return BS_EINVAL; }
     L.V = alloc((size_t)(niter + 1 + tb) * L.bstride * es);
     L.W = alloc((size_t)L.bstride * es);
+    // targeted restart (Sec. "Targeted thick-restart Lanczos"): the operator is
+    // (H - E_bar)^2, applied as two products with the shift in between
+    const bool targeted = o.targeted != 0;
+    T *W1 = targeted ? (T *)alloc((size_t)L.bstride * es) : nullptr;
+    const T tshift = (T)(-o.target);
+    auto apply_op = [&](const T *x, T *y) -> int {
+        if (!targeted) return launch_hx(c, x, y, K, o.dtype, L.s, c->err);
+        int r = launch_hx(c, x, W1, K, o.dtype, L.s, c->err);
+        if (r) return r;
+        vec_axpy<T><<<L.ncta, 256, 0, L.s>>>(W1, x, tshift, L.dim * K);
+        if ((r = launch_hx(c, W1, y, K, o.dtype, L.s, c->err))) return r;
+        vec_axpy<T><<<L.ncta, 256, 0, L.s>>>(y, W1, tshift, L.dim * K);
+        return BS_OK;
+    };
     double *Ct = (double *)alloc((size_t)std::max(tb, 1) * niter * K * K * sizeof(double));
     // dot scratch: (niter+1) blocks of K x K, or one 8 x 8 block for the refinement
     const size_t ndot = std::max<size_t>((size_t)(niter + 1) * K * K, 64);
@@ -1152,7 +1174,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         cudaError_t e = cudaStreamBeginCapture(L.s, cudaStreamCaptureModeThreadLocal);
         if (e == cudaSuccess) {
             cudaEventRecord(ev[0], L.s);
-            rc = launch_hx(c, Xcur, W, K, o.dtype, L.s, c->err);
+            rc = apply_op(Xcur, W);
             cudaEventRecord(ev[1], L.s);
             dots<T, K>(L, Xcur, 1, W, L.Ahist, nullptr, d_iter, 1);
             update<T, K>(L, Xcur, 1, L.Ahist, W, nullptr, d_iter, 1);
@@ -1195,7 +1217,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
                 if (e != cudaSuccess) { c->err = std::string("lanczos graph launch: ") + cudaGetErrorString(e); rc = BS_ECUDA; break; }
             } else {
             cudaEventRecord(ev[0], L.s);
-            if ((rc = launch_hx(c, Vn, W, K, o.dtype, L.s, c->err))) break;
+            if ((rc = apply_op(Vn, W))) break;
             cudaEventRecord(ev[1], L.s);
             // alpha first: A_n = V_n^T W, W -= V_n A_n
             double *An = L.Ahist + (size_t)n * K * K;
@@ -1250,7 +1272,7 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
                 if (Xcur) cudaMemcpyAsync(Xcur, Vn1, (size_t)L.bstride * es, cudaMemcpyDeviceToDevice, L.s);
                 cudaStreamSynchronize(L.s);
             }
-        ++matvecs;
+        matvecs += targeted ? 2 : 1;
     }
     if (rc != BS_OK) break;
     cudaMemcpyAsync(Ah.data(), L.Ahist, (size_t)done * K * K * sizeof(double), cudaMemcpyDeviceToHost, L.s);

@@ -94,3 +94,45 @@ def test_thick_restart_argument_checks(sd44):
         with pytest.raises(N.BSError) as e:
             c.lanczos(pd, 4, N.BS_F64, niter, 3, refine=False, **kw)
         assert e.value.code == -1, kw
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("idx,niter,restarts", [(8, 40, 60), (100, 60, 100)])
+def test_targeted_thick_restart_finds_levels_nearest_target(idx, niter, restarts):
+    """sd 2p2n (dim 640), FP64 k = 2: thick restart on (H - E_bar)^2 returns the
+    three levels of H nearest E_bar (dense diagonalization of the oracle's
+    H), as FP64 Rayleigh quotients with small residuals, like the oracle's
+    targeted run; the graph-captured iteration gives the same levels."""
+    orbits, spe, tb = I.space("sd")
+    c = N.make(orbits, spe, tb, 2, 2, 0, +1, device=0)
+    o = O.Oracle(orbits, 2, 2, 0, 0).set_interaction(spe, tb)
+    ev = np.linalg.eigvalsh(o.dense())
+    Eb = 0.5 * (ev[idx] + ev[idx + 1]) + 0.013
+    near = np.sort(ev[np.argsort(np.abs(ev - Eb))[:3]])
+    ph, pd = pivot(o.dim, 2, N.BS_F64)
+    e, rep = c.lanczos(pd, 2, N.BS_F64, niter, 3, refine=True, nthick=8, max_restarts=restarts, target=Eb)
+    assert np.max(np.abs(np.sort(e) - near)) < 1e-8, (e, near)
+    assert max(rep["residual"]) < 1e-6
+    assert rep["matvec_blocks"] == 2 * (niter + rep["restarts"] * (niter - 4))
+    e_o, _, X_o = o.block_lanczos_thick(ph, niter, 8, restarts, nkeep=3, return_vectors=True, target=Eb)
+    H = o.matrix()
+    rq = np.sort([X_o[:, m] @ (H @ X_o[:, m]) / (X_o[:, m] @ X_o[:, m]) for m in range(3)])
+    assert np.max(np.abs(np.sort(e) - rq)) < 1e-8
+    s = torch.cuda.Stream()
+    e_g, _ = c.lanczos(pd, 2, N.BS_F64, niter, 3, refine=True, nthick=8, max_restarts=restarts, target=Eb,
+                       use_graph=True, stream=s.cuda_stream)
+    assert np.max(np.abs(np.sort(e_g) - np.sort(e))) < 1e-9
+    c.sync_status()
+
+
+@pytest.mark.gpu
+def test_targeted_argument_checks(sd44):
+    c, o = sd44
+    _, pd = pivot(o.dim, 4, N.BS_F64)
+    for kw in [dict(refine=False), dict(nkeep=9), dict(target=float("nan"))]:
+        args = dict(refine=True, nkeep=3, target=-30.0)
+        args.update(kw)
+        nk = args.pop("nkeep")
+        with pytest.raises(N.BSError) as e:
+            c.lanczos(pd, 4, N.BS_F64, 8, nk, nthick=8, max_restarts=2, **args)
+        assert e.value.code == -1, kw
