@@ -254,9 +254,11 @@ PROFILES = {1: "hx_fused_pf4p4n_k8.md", 2: "hx_row_pf4p4n_k8.md", 6: "hx_pipe_pf
 
 def launches_per_product(mode):
     """Kernels one H x launches in a kernel mode: the core-grouped modes run the
-    pn kernel (and in 13 to 16, 18 and 19 the pp kernel), the like-particle kernel and the
-    ordered sum of the partial vectors; every other mode is one kernel."""
-    return {11: 3, 12: 3, 13: 4, 14: 4, 15: 4, 16: 4, 17: 3, 18: 4, 19: 4}.get(mode, 1)
+    pn kernel (and in 13 to 16, 18 and 19 the pp kernel) and the like-particle
+    kernel; the row-tile like-particle kernel of 13 to 16 and 19 also adds the
+    partial vectors, the pipelined one of 11, 12, 17 and 18 is followed by the
+    ordered sum; every other mode is one kernel."""
+    return {11: 3, 12: 3, 13: 3, 14: 3, 15: 3, 16: 3, 17: 3, 18: 4, 19: 3}.get(mode, 1)
 
 
 def traffic_from_profile(k, mode):

@@ -514,6 +514,9 @@ struct NNArgs {
     const float *pdiag;
     int *err;
     int row_stride;
+    const float *part;   // the other terms' partial vectors (nz of them, pstride apart), summed in, or null
+    int nz;
+    int64_t pstride;
 };
 
 // Neutron like-particle term plus the proton single-particle diagonal over a
@@ -521,7 +524,10 @@ struct NNArgs {
 // sum_v c_v x[r][n_v].  The neutron lists are the same for every proton row,
 // so each thread (one destination column, in the sector's list order) loads
 // an entry once and applies it to the R staged rows.  The R rows arrive by
-// TMA bulk copies on one mbarrier (bounded wait).  Output: partial vector.
+// TMA bulk copies on one mbarrier (bounded wait).  Output: y itself when the
+// other terms' partial vectors are given (their ordered sum, then this term:
+// the order of hx_sum_partials, so the result is bit-identical to a separate
+// summation pass), else a partial vector.
 template <int K, int R, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB)
     hx_nn_rows_kernel(NNArgs A, const float *__restrict__ x, float *__restrict__ out)
@@ -597,7 +603,22 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 o[2 * q + 1] = acc[r][q].y;
             }
             prot_fix<float, K>(o, rot);
-            pst<float, K>(out + (D.off + (int64_t)(r0 + r) * nN + col) * K, o);
+            const int64_t e = (D.off + (int64_t)(r0 + r) * nN + col) * K;
+            if (A.nz > 0) {
+#pragma unroll
+                for (int q = 0; q < K; q += 4) {   // four components at a time: few live registers
+                    float4 a = __ldg(reinterpret_cast<const float4 *>(A.part + e + q));
+                    for (int t = 1; t < A.nz; ++t) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(A.part + (int64_t)t * A.pstride + e + q));
+                        a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+                    }
+                    o[q] = a.x + o[q];
+                    o[q + 1] = a.y + o[q + 1];
+                    o[q + 2] = a.z + o[q + 2];
+                    o[q + 3] = a.w + o[q + 3];
+                }
+            }
+            pst<float, K>(out + e, o);
         }
     }
 }
@@ -644,7 +665,8 @@ constexpr CoreVariant kCoreVariants[] = {{18, 1, 200 * 1024, false, 0, 0}, {9, 2
 constexpr int kNumCore = 9;
 
 template <int K, int R, int MINB>
-cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, bool &used)
+cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, bool &used,
+                        const float *part = nullptr, int nz = 0)
 {
     const Device &Dv = ctx->dev;
     constexpr int NW = 18;
@@ -656,15 +678,17 @@ cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStrea
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     NNArgs A{R == 2 ? Dv.nntasks2 : Dv.nntasks4, Dv.blocks, Dv.pe_perm, Dv.pe_nn_src, Dv.pe_nn_coef32, Dv.pe_nn_sinfo,
-             Dv.pdiag32, Dv.err, row_stride};
+             Dv.pdiag32, Dv.err, row_stride, part, part ? nz : 0, ctx->basis.dim * K};
     kern<<<R == 2 ? Dv.nnntasks2 : Dv.nnntasks4, NW * 32, smem, s>>>(A, x, out);
     return cudaGetLastError();
 }
 
 template <int K>
-cudaError_t launch_nn_k(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, int R, bool &used)
+cudaError_t launch_nn_k(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, int R, bool &used,
+                       const float *part = nullptr, int nz = 0)
 {
-    return R == 2 ? launch_nn_t<K, 2, 2>(ctx, x, out, s, used) : launch_nn_t<K, 4, 1>(ctx, x, out, s, used);
+    return R == 2 ? launch_nn_t<K, 2, 2>(ctx, x, out, s, used, part, nz)
+                  : launch_nn_t<K, 4, 1>(ctx, x, out, s, used, part, nz);
 }
 
 template <int K, int NW, int MINB, int CPT>
@@ -817,10 +841,16 @@ cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dt
         }
         nz += c->dev.nzpp;
     }
-    // remaining like-particle terms into partial vector nz, then the ordered sum
-    float *last = part + (size_t)nz * (size_t)c->basis.dim * (size_t)k;
-    e = R ? (k == 8 ? launch_nn_k<8>(c, xf, last, s, R, used) : launch_nn_k<4>(c, xf, last, s, R, used))
-          : launch_hx_pipe_combine(c, x, y, k, dt, s, pv, part, -1 - nz, pp, used);
+    // remaining like-particle terms: the row-tile kernel adds the nz partial
+    // vectors in order and writes y itself; else they go into partial
+    // vector nz, followed by the ordered sum
+    if (R) {
+        float *yf = (float *)y;
+        e = k == 8 ? launch_nn_k<8>(c, xf, yf, s, R, used, part, nz) : launch_nn_k<4>(c, xf, yf, s, R, used, part, nz);
+        if (e != cudaSuccess) return e;
+        return used ? cudaGetLastError() : cudaSuccess;
+    }
+    e = launch_hx_pipe_combine(c, x, y, k, dt, s, pv, part, -1 - nz, pp, used);
     if (e != cudaSuccess || !used) return e;
     const int64_t n4 = c->basis.dim * k / 4;
     int nsm = 0;
