@@ -541,6 +541,18 @@ def ours(args):
         "gpu_launches": args.steps * launches_per_product(mode_used),
         "clocks": clocks,
     }
+    if kbest in (4, 8):
+        # measured on-chip ceiling of the product's inner step (bs_gather_ceiling:
+        # random k-float gathers from shared memory or L2, each applied to 1, 2
+        # or 4 rows by packed FP32 FMAs), outside the timed region
+        ceil = {}
+        for where, name in ((0, "smem"), (1, "l2")):
+            for rows in (1, 2, 4):
+                ceil["%s_rows%d" % (name, rows)] = ctx.gather_ceiling(where, kbest, rows, sp) / 1e3
+        line["roofline"]["gather_ceiling"] = dict(
+            unit="TFLOP/s", **ceil,
+            frac_vs_smem_rows4=achieved / ceil["smem_rows4"], frac_vs_smem_rows2=achieved / ceil["smem_rows2"],
+            note="the pn-core kernel applies each gathered element to 1, 2 or 4 rows (2.2 on average at 48Cr)")
     if not args.no_lanczos:
         line["lanczos"] = lanczos_check(ctx, N, I, torch, sp)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

@@ -305,6 +305,18 @@ int bs_strength(bs_ctx *ctx, const bs_lanczos_opts *opts, const void *pivot, int
  * 1, 2, 4 or 8, null pointer), BS_ENOMEM, BS_ECUDA. */
 int bs_density(bs_ctx *ctx, const double *F, const double *X, int k, double *rho, void *stream);
 
+/* Measurement aid: the measured on-chip ceiling of the H x kernels' inner
+ * step.  Every multiply-add of the product gathers one k-float element of a
+ * source vector at an index read from a list and applies it to one or more
+ * destination rows.  This times that step alone: one CTA of 576 threads per
+ * SM walks a list of 8,192 seeded random indices, gathers the element at
+ * each (where = 0: from a 96 KB table in shared memory; 1: from a 64 MB table
+ * in global memory, L2-resident) and applies it to `rows` (1, 2 or 4)
+ * accumulator rows with packed FP32 FMAs.  *gflops = 2 x multiply-adds / s
+ * (k = 4 or 8).  Uses the context's device; allocates and frees ~64 MB;
+ * synchronizes the stream.  Errors: BS_EINVAL, BS_ENOMEM, BS_ECUDA. */
+int bs_gather_ceiling(bs_ctx *ctx, int where, int k, int rows, double *gflops, void *stream);
+
 /* Test aid: all eigenvalues (ascending, w[n]) and the eigenvectors of the
  * lowest nvec (columns of Z, n x nvec row-major) of the symmetric n x n
  * matrix A (row-major, HOST), by the host FP64 solver bs_lanczos uses for T.

@@ -24,7 +24,7 @@ EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_ba
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_set_tuned", "bs_lanczos",
             "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_update", "bs_block_dots_noalloc",
-            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength", "bs_density"]
+            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength", "bs_density", "bs_gather_ceiling"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -92,6 +92,7 @@ def load():
     L.bs_strength.argtypes = [vp, ctypes.POINTER(bs_lanczos_opts), vp, ctypes.c_int, f64p, f64p,
                               ctypes.POINTER(bs_lanczos_report)]
     L.bs_density.argtypes = [vp, vp, vp, ctypes.c_int, f64p, vp]
+    L.bs_gather_ceiling.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, f64p, vp]
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.bs_debug_eigh_banded.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]
@@ -230,6 +231,13 @@ class Context:
         ptr = lambda t: vp(t if isinstance(t, int) else t.data_ptr())
         self._check(load().bs_density(self.h, ptr(F), ptr(X), k, rho.ctypes.data_as(f64p), vp(stream or 0)))
         return rho
+
+    def gather_ceiling(self, where, k, rows, stream=None):
+        """Measured GFLOP/s of the gather + FMA step (where 0: shared memory,
+        1: L2), k-float elements applied to `rows` accumulator rows."""
+        g = ctypes.c_double(0.0)
+        self._check(load().bs_gather_ceiling(self.h, where, k, rows, ctypes.byref(g), vp(stream or 0)))
+        return g.value
 
     def set_kernel(self, mode):
         self._check(load().bs_set_kernel(self.h, mode))

@@ -544,6 +544,18 @@ int bs_density(bs_ctx *c, const double *F, const double *X, int k, double *rho, 
     });
 }
 
+int bs_gather_ceiling(bs_ctx *c, int where, int k, int rows, double *gflops, void *stream)
+{
+    return guarded(c, [&]() -> int {
+        if (c->device < 0) { c->err = "context has no device"; return BS_EINVAL; }
+        if ((where != 0 && where != 1) || (k != 4 && k != 8) || (rows != 1 && rows != 2 && rows != 4) || !gflops) {
+            c->err = "gather ceiling: where 0 or 1, k 4 or 8, rows 1, 2 or 4, and an output";
+            return BS_EINVAL;
+        }
+        return run_gather_ceiling(c->device, where, k, rows, gflops, stream, c->err);
+    });
+}
+
 int bs_set_kernel(bs_ctx *c, int mode)
 {
     return guarded(c, [&]() -> int {

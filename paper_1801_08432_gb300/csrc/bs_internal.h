@@ -346,6 +346,7 @@ struct StrengthReq {
 int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *evals, double *evecs,
                 bs_lanczos_report *rep, const StrengthReq *sreq = nullptr);
 int run_density(bs_ctx *c, const double *F, const double *X, int k, double *rho_host, void *stream);
+int run_gather_ceiling(int device, int where, int k, int rows, double *gflops, void *stream, std::string &err);
 int pipe_variants();
 int core_variants();
 // allocates what launch_hx needs for (k, dtype) outside any stream capture

@@ -286,3 +286,20 @@ def test_set_tuned_replays_a_mode_and_rejects_bad_arguments():
         with pytest.raises(Exception):
             c.set_tuned(*bad)
     c.close()
+
+
+@pytest.mark.gpu
+def test_gather_ceiling_is_measured_and_ordered():
+    """bs_gather_ceiling: positive rates, below the FP32 FMA-issue rate of the
+    device, and more FLOP/s when each gathered element feeds more rows."""
+    orbits, spe, tb = I.space("sd")
+    c = N.make(orbits, spe, tb, 2, 2, 0, +1, device=0)
+    props = torch.cuda.get_device_properties(0)
+    issue = props.multi_processor_count * 128 * 2 * 2.2e9 / 1e9   # GFLOP/s at a 2.2 GHz upper clock
+    for where in (0, 1):
+        g = [c.gather_ceiling(where, 8, r) for r in (1, 2, 4)]
+        assert all(0 < x < issue for x in g), g
+        assert g[2] > g[0]
+    with pytest.raises(N.BSError):
+        c.gather_ceiling(2, 8, 1)
+    c.close()
