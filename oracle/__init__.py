@@ -427,6 +427,34 @@ class Oracle:
             off += o.twoj + 1
         return np.array(out)
 
+    # -- W truncation -----------------------------------------------------
+    def truncation_mask(self, weights, max_excite):
+        """Basis states kept by the W truncation (Sec. "Truncation of the
+        many-body space"): every orbit a carries a non-negative integer w_a,
+        a state's W is the sum of w over its occupied proton and neutron
+        states, W_min is the smallest W any Z-proton, N-neutron state can
+        have (the lowest-w states filled), and the kept states have
+        W <= W_min + max_excite.  Returns (mask over this basis, W_min,
+        largest possible excitation)."""
+        st = self.sp_states()
+        w_state = np.array([weights[a] for (a, _) in st], dtype=np.int64)
+        srt = np.sort(w_state)
+        w_min = int(srt[:self.Z].sum() + srt[:self.N].sum())
+        w_max = int(srt[::-1][:self.Z].sum() + srt[::-1][:self.N].sum())
+        P, Nn = self.states()
+        W = np.zeros(self.dim, dtype=np.int64)
+        for s_idx in range(self.ns):
+            bit = np.uint64(1) << np.uint64(s_idx)
+            W += w_state[s_idx] * (((P & bit) != 0).astype(np.int64) + ((Nn & bit) != 0).astype(np.int64))
+        return W <= w_min + max_excite, w_min, w_max - w_min
+
+    def truncated_matrix(self, weights, max_excite):
+        """The Hamiltonian of the truncated space: H restricted to the kept
+        basis states (rows and columns), in their basis order."""
+        mask, _, _ = self.truncation_mask(weights, max_excite)
+        idx = np.nonzero(mask)[0]
+        return self.matrix()[idx][:, idx]
+
     # -- one-body densities ----------------------------------------------
     def sp_states(self):
         """(orbit, 2m) of every single-particle state: orbit-major, 2m ascending."""

@@ -500,3 +500,48 @@ def test_targeted_thick_restart_finds_levels_nearest_the_target(sd22):
         near = np.sort(ev[np.argsort(np.abs(ev - Eb))[:3]])
         assert np.max(np.abs(rq - near)) < 1e-9
         assert np.max(np.abs(np.sort(e2) - np.sort((near - Eb) ** 2))) < 1e-9
+
+
+# ------------------------------------------------------ W truncation
+@pytest.mark.parametrize("Z,Nn,twoM", [(2, 2, 0), (3, 2, 1)])
+def test_w_truncation_without_excitation_is_the_single_orbit_space(Z, Nn, twoM):
+    # w = 0 on 0d5/2 and 1 on 1s1/2, 0d3/2, no excitation: every nucleon
+    # stays in 0d5/2, so the truncated H is the single-orbit problem, built
+    # independently on the orbit list (0d5/2) with its (0d5/2)^2 elements
+    orbits, spe, tb = I.space("sd")
+    o = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
+    ev_t = np.linalg.eigvalsh(o.truncated_matrix((0, 1, 1), 0).toarray())
+    tb1 = [t for t in tb if t[:4] == (1, 1, 1, 1)]
+    o1 = O.Oracle([orbits[0]], Z, Nn, twoM, 0).set_interaction([spe[0]], tb1)
+    ev1 = np.linalg.eigvalsh(o1.dense())
+    assert len(ev_t) == len(ev1)
+    assert np.max(np.abs(ev_t - ev1)) < 1e-11
+
+
+def test_w_truncation_keeps_rotational_invariance():
+    # w is a property of the orbit, so the truncated space is closed under
+    # J+-: each M = 1 level of a truncated space is a level of the M = 0 one
+    orbits, spe, tb = I.space("sd")
+    o0 = O.Oracle(orbits, 2, 2, 0, 0).set_interaction(spe, tb)
+    o1 = O.Oracle(orbits, 2, 2, 2, 0).set_interaction(spe, tb)
+    for E in (1, 2):
+        e0 = np.linalg.eigvalsh(o0.truncated_matrix((0, 1, 1), E).toarray())
+        e1 = np.linalg.eigvalsh(o1.truncated_matrix((0, 1, 1), E).toarray())
+        assert len(e1) < len(e0)
+        worst, _ = match_subset(e1, e0, 1e-9)
+        assert worst < 1e-9, (E, worst)
+
+
+def test_w_truncation_limits():
+    orbits, spe, tb = I.space("sd")
+    o = O.Oracle(orbits, 3, 2, 1, 0).set_interaction(spe, tb)
+    dims = []
+    for E in range(0, 7):
+        mask, w_min, e_max = o.truncation_mask((0, 1, 1), E)
+        dims.append(int(mask.sum()))
+    assert (w_min, e_max) == (0, 5)
+    assert dims == sorted(dims) and dims[5] == dims[6] == o.dim
+    full = np.linalg.eigvalsh(o.truncated_matrix((0, 1, 1), e_max).toarray())
+    assert np.max(np.abs(full - np.linalg.eigvalsh(o.dense()))) < 1e-11
+    # equal weights: no truncation possible
+    assert o.truncation_mask((2, 2, 2), 0)[0].all()
