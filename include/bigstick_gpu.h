@@ -220,7 +220,9 @@ typedef struct {
                            when use_graph = 1: capture needs a created stream) */
     int nthick;         /* thick restart (Sec. "Thick-restart block Lanczos"): Ritz vectors
                            kept per restart, a multiple of k with nthick / k + 1 < niter;
-                           0 = no restart */
+                           0 = no restart.  The method needs nthick > nkeep (the paper
+                           suggests about 3 nkeep): pairs beyond nthick are discarded at
+                           every restart and may not converge */
     int max_restarts;   /* restarts at most (ignored when nthick = 0) */
     double tol;         /* stop restarting once the residual estimate of each of the lowest
                            nkeep pairs is <= tol (0 = run all max_restarts restarts) */
