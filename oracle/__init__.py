@@ -14,8 +14,11 @@ Parts:
     rows of H*x and J+.
   * this module (numpy/scipy): Lanczos with full reorthogonalization (Sec.
     "Standard Lanczos algorithm", steps (1)-(6) with alpha computed first and
-    then orthogonalization against every earlier vector), dense
-    diagonalization, <J^2>, traces and Hellmann-Feynman gradients.
+    then orthogonalization against every earlier vector); thick-restart block
+    Lanczos, plain and targeted at interior levels; the block strength
+    function; dense diagonalization; <J^2>; orbit occupations; M-scheme and
+    reduced one-body densities; the W-truncated Hamiltonian; traces and
+    Hellmann-Feynman gradients.
 
 Parity pins: every function here is checked in tests/test_oracle_pins.py
 against closed forms, paper values or brute force (see that file's header).

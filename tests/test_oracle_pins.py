@@ -16,7 +16,16 @@ fixes, so that a dropped term, a wrong phase or a transposed index fails:
   * rotational invariance of the whole chain: eig(M=1) inside eig(M=0) and
     integer J from <J^2> = |J+ psi|^2 + M(M+1);
   * assembly: H = H^T, trace from occupation counts, reading in any label order;
-  * Lanczos: dense diagonalization.
+  * Lanczos: dense diagonalization;
+  * thick-restart block Lanczos: T = Q^T H Q after restarts, convergence to
+    dense, Ritz values that never rise, the no-restart limit, the targeted
+    run's levels nearest the target;
+  * strength function: the Lanczos moment identities, converged overlaps;
+  * one-body densities: the independent J+ route, occupations, particle
+    numbers; reduced densities: K = 0 occupations, the reduced J, M
+    independence, the transition symmetry;
+  * W truncation: the single-orbit limit, rotational invariance, the
+    untruncated limit.
 """
 import itertools
 import os
