@@ -430,6 +430,33 @@ class Oracle:
             off += o.twoj + 1
         return np.array(out)
 
+    def isospin_density(self, red, twoTf, twoTi):
+        """Doubly reduced (J and isospin) one-body densities from the reduced
+        proton-neutron ones ``red`` (as returned by ``reduced_density``), for
+        states of good isospin T_f, T_i (Sec. "Conversion from proton-neutron
+        to isospin"; protons m_t = +1/2, T_z = (Z - N)/2):
+
+            rho_T = [T_f] / (T_i T_z, T 0 | T_f T_z) [T]^-1
+                    sum_{m_t} (-1)^(1/2 - m_t) (1/2 m_t, 1/2 -m_t | T 0) rho_{m_t}
+
+        with the isospin time-reversal phase of c~ written out.  Returns
+        {(a, b, 2K, T): value}, NaN where the isospin coefficient vanishes."""
+        tTz = self.Z - self.N
+        out = {}
+        keys = {(a, b, tk) for (t, a, b, tk) in red}
+        for (a, b, tk) in keys:
+            for T in (0, 1):
+                c = cg(twoTi, tTz, 2 * T, 0, twoTf, tTz)
+                if abs(c) < 1e-12:
+                    out[(a, b, tk, T)] = np.nan
+                    continue
+                acc = 0.0
+                for t, tmt in ((0, 1), (1, -1)):   # protons m_t = +1/2, neutrons -1/2
+                    ph = 1.0 if t == 0 else -1.0   # (-1)^(1/2 - m_t)
+                    acc += ph * cg(1, tmt, 1, -tmt, 2 * T, 0) * red[(t, a, b, tk)]
+                out[(a, b, tk, T)] = np.sqrt(twoTf + 1.0) / c / np.sqrt(2 * T + 1.0) * acc
+        return out
+
     # -- W truncation -----------------------------------------------------
     def truncation_mask(self, weights, max_excite):
         """Basis states kept by the W truncation (Sec. "Truncation of the

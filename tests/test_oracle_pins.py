@@ -554,3 +554,71 @@ def test_w_truncation_limits():
     assert np.max(np.abs(full - np.linalg.eigvalsh(o.dense()))) < 1e-11
     # equal weights: no truncation possible
     assert o.truncation_mask((2, 2, 2), 0)[0].all()
+
+
+# ------------------------------------------------------ isospin densities
+def _t2_tables(orbits):
+    # T^2 as SPE 3/4 and diagonal pair elements T(T+1) - 3/2 (test helper)
+    return ([0.75] * len(orbits),
+            [(a, b, c, d, J, T, T * (T + 1.0) - 1.5) for (a, b, c, d, J, T) in I.tbme_labels(orbits) if (a, b) == (c, d)])
+
+
+def _levels_jt(Z, Nn, twoM, nlev):
+    orbits, spe, tb = I.space("sd")
+    o = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
+    up = O.Oracle(orbits, Z, Nn, twoM + 2, 0)
+    ot = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(*_t2_tables(orbits))
+    ev, X = o.eigh(nlev)
+    twoJ = [int(round(2 * O.j_from_j2(o.j2(X[:, m], up)))) for m in range(nlev)]
+    twoT = [int(round(2 * O.j_from_j2(X[:, m] @ ot.spmv(X[:, m])))) for m in range(nlev)]
+    return o, ev, X, twoJ, twoT
+
+
+@pytest.mark.parametrize("Z,Nn,twoM", [(3, 2, 1), (3, 1, 0), (2, 2, 0)])
+def test_isospin_density_special_case_and_occupations(Z, Nn, twoM):
+    # T_f = T_i: rho_{T=0} = [T]/sqrt2 (rho^p + rho^n), rho_{T=1} = [T]/sqrt2
+    # (rho^p - rho^n) sqrt(T(T+1)) / (sqrt3 T_z); and the proton and neutron
+    # occupations n = [1/2][j] / ([J][T]) 1/2 (rho_00 +- T_z sqrt3 /
+    # sqrt(T(T+1)) rho_01), against bit counts
+    o, ev, X, twoJ, twoT = _levels_jt(Z, Nn, twoM, 4)
+    Tz = (Z - Nn) / 2.0
+    st = o.sp_states()
+    for m in range(4):
+        T = twoT[m] / 2.0
+        rho = o.density(X[:, m], X[:, m])
+        red = o.reduced_density(rho, twoJ[m], twoJ[m])
+        iso = o.isospin_density(red, twoT[m], twoT[m])
+        for (a, b, tk, TT), v in iso.items():
+            rp, rn = red[(0, a, b, tk)], red[(1, a, b, tk)]
+            if not (np.isfinite(v) and np.isfinite(rp)):
+                continue
+            if TT == 0:
+                ref = np.sqrt(twoT[m] + 1.0) / np.sqrt(2.0) * (rp + rn)
+            else:
+                ref = np.sqrt(twoT[m] + 1.0) / np.sqrt(2.0) * (rp - rn) * np.sqrt(T * (T + 1)) / (np.sqrt(3.0) * Tz)
+            assert abs(v - ref) < 1e-12, (a, b, tk, TT)
+        for a, orb in enumerate(o.orbits):
+            n_p = sum(rho[0, i, i] for i, (oa, _) in enumerate(st) if oa == a)
+            n_n = sum(rho[1, i, i] for i, (oa, _) in enumerate(st) if oa == a)
+            pre = np.sqrt(2.0) * np.sqrt(orb.twoj + 1.0) / (np.sqrt(twoJ[m] + 1.0) * np.sqrt(twoT[m] + 1.0)) * 0.5
+            r0, r1 = iso[(a, a, 0, 0)], iso[(a, a, 0, 1)]
+            assert abs(2 * pre * r0 - (n_p + n_n)) < 1e-12
+            if Tz != 0:
+                assert abs(pre * (r0 + Tz * np.sqrt(3.0) / np.sqrt(T * (T + 1)) * r1) - n_p) < 1e-12
+                assert abs(pre * (r0 - Tz * np.sqrt(3.0) / np.sqrt(T * (T + 1)) * r1) - n_n) < 1e-12
+
+
+def test_isospin_transition_density_symmetry():
+    # rho^{if}_{K,T}(ba) = (-1)^(j_a - j_b + J_i - J_f + T_i - T_f) rho^{fi}_{K,T}(ab)
+    o, ev, X, twoJ, twoT = _levels_jt(3, 2, 1, 5)
+    n = 0
+    for f, i in [(0, 1), (1, 3), (0, 2), (2, 4)]:
+        rfi = o.isospin_density(o.reduced_density(o.density(X[:, f], X[:, i]), twoJ[f], twoJ[i]), twoT[f], twoT[i])
+        rif = o.isospin_density(o.reduced_density(o.density(X[:, i], X[:, f]), twoJ[i], twoJ[f]), twoT[i], twoT[f])
+        for (a, b, tk, TT), v in rfi.items():
+            w = rif[(b, a, tk, TT)]
+            if np.isfinite(v) and np.isfinite(w):
+                ph = (-1) ** ((o.orbits[a].twoj - o.orbits[b].twoj + twoJ[i] - twoJ[f] + twoT[i] - twoT[f]) // 2)
+                assert abs(w - ph * v) < 1e-12
+                n += 1
+    assert n > 50
