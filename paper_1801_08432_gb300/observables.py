@@ -1,6 +1,7 @@
 """Scalar observables: J^2 and T^2 as one- plus two-body operators in the
 interaction format, orbit occupations from the adjoint, and reduced one-body
-densities from the GPU's M-scheme densities.
+densities (proton-neutron and isospin form) from the GPU's M-scheme
+densities.
 
 The total angular momentum squared is J^2 = sum_i j_i^2 + sum_{i != j} j_i . j_j.
 Its single-particle part is j_a (j_a + 1) on every particle in orbit a, and
@@ -134,6 +135,36 @@ def reduced_densities(rho, orbits, twoM, twoJf, twoJi):
                     c = clebsch_gordan(twoJi, twoM, twoK, 0, twoJf, twoM)
                     out[(t, a, b, twoK)] = (float("nan") if abs(c) < 1e-12 else
                                             np.sqrt(twoJf + 1.0) * s / c / np.sqrt(twoK + 1.0))
+    return out
+
+
+def isospin_densities(red, Z, Nn, twoTf, twoTi):
+    """Doubly reduced one-body densities (J and isospin) from the reduced
+    proton-neutron densities ``red`` of reduced_densities, for states of good
+    isospin T_f, T_i (Sec. "Conversion from proton-neutron to isospin"),
+    with protons at m_t = +1/2, T_z = (Z - N)/2, and the isospin
+    time-reversal phase (-1)^(1/2 - m_t) of the annihilation operator:
+
+        rho_T = [T_f] / (T_i T_z, T 0 | T_f T_z) [T]^-1
+                sum_{m_t} (-1)^(1/2 - m_t) (1/2 m_t, 1/2 -m_t | T 0) rho_{m_t}.
+
+    For T_f = T_i this is rho_0 = [T](rho^p + rho^n)/sqrt2 and
+    rho_1 = [T](rho^p - rho^n) sqrt(T(T+1)) / (sqrt3 T_z).  Returns
+    {(a, b, 2K, T): value}, NaN where (T_i T_z, T 0 | T_f T_z) vanishes (T = 1
+    between equal T at T_z = 0)."""
+    tTz = Z - Nn
+    out = {}
+    for (t, a, b, tk) in red:
+        if t != 0:
+            continue
+        for T in (0, 1):
+            c = clebsch_gordan(twoTi, tTz, 2 * T, 0, twoTf, tTz)
+            if abs(c) < 1e-12:
+                out[(a, b, tk, T)] = float("nan")
+                continue
+            s = (clebsch_gordan(1, 1, 1, -1, 2 * T, 0) * red[(0, a, b, tk)]
+                 - clebsch_gordan(1, -1, 1, 1, 2 * T, 0) * red[(1, a, b, tk)])
+            out[(a, b, tk, T)] = np.sqrt(twoTf + 1.0) / c / np.sqrt(2 * T + 1.0) * s
     return out
 
 

@@ -63,3 +63,29 @@ def test_reduced_densities_nan_where_the_coupling_vanishes():
     r1 = OB.reduced_densities(rho, orbits, 2, 4, 4)
     for (t, a, b, twoK), v in r1.items():
         assert np.isnan(v) == (twoK > 8), (a, b, twoK)
+
+
+def test_isospin_densities_equal_the_oracle():
+    # the product's conversion (own Clebsch-Gordan) against the oracle's on
+    # the same reduced proton-neutron densities: levels and transitions of
+    # sd 3p2n (T_z = 1/2) and sd 2p2n (T_z = 0)
+    import oracle as O
+    orbits, spe, tb = I.space("sd")
+    t2 = ([0.75] * len(orbits),
+          [(a, b, c, d, J, T, T * (T + 1.0) - 1.5) for (a, b, c, d, J, T) in I.tbme_labels(orbits) if (a, b) == (c, d)])
+    for Z, Nn, twoM in ((3, 2, 1), (2, 2, 0)):
+        o = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
+        up = O.Oracle(orbits, Z, Nn, twoM + 2, 0)
+        ot = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(*t2)
+        ev, X = o.eigh(4)
+        twoJ = [int(round(2 * O.j_from_j2(o.j2(X[:, m], up)))) for m in range(4)]
+        twoT = [int(round(2 * O.j_from_j2(X[:, m] @ ot.spmv(X[:, m])))) for m in range(4)]
+        for f, i in [(0, 0), (1, 1), (0, 1), (2, 3)]:
+            red = o.reduced_density(o.density(X[:, f], X[:, i]), twoJ[f], twoJ[i])
+            ref = o.isospin_density(red, twoT[f], twoT[i])
+            got = OB.isospin_densities(red, Z, Nn, twoT[f], twoT[i])
+            assert set(ref) == set(got)
+            for key, v in ref.items():
+                assert np.isnan(v) == np.isnan(got[key])
+                if np.isfinite(v):
+                    assert abs(got[key] - v) < 1e-12, key
