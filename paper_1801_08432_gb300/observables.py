@@ -168,6 +168,71 @@ def isospin_densities(red, Z, Nn, twoTf, twoTi):
     return out
 
 
+def basis_states(ctx):
+    """(proton bits, neutron bits) of every basis state of a context, in
+    basis order (block offset + proton row x neutron count + neutron column)."""
+    B = ctx.export_basis()
+    P = np.zeros(ctx.dim, dtype=np.uint64)
+    Nb = np.zeros(ctx.dim, dtype=np.uint64)
+    for ps, ns_, off in B["blocks"]:
+        p0, pc = B["p_sec"][ps][2], B["p_sec"][ps][3]
+        n0, nc = B["n_sec"][ns_][2], B["n_sec"][ns_][3]
+        P[off:off + pc * nc] = np.repeat(B["p_bits"][p0:p0 + pc], nc)
+        Nb[off:off + pc * nc] = np.tile(B["n_bits"][n0:n0 + nc], pc)
+    return P, Nb
+
+
+def embed(X, ctx_small, orbits_small, ctx_big, orbits_big):
+    """Vectors of a smaller model space as vectors of a larger one with the
+    same Z, N, 2M and parity, e.g. to start block Lanczos from approximate
+    eigenvectors of the smaller space (Sec. "Block Lanczos": a bootstrapped
+    pivot).  Every orbit of the small space must appear in the big one
+    (same n, l, 2j) in the same relative order.  Single-particle states are
+    numbered orbit-major, 2m ascending, so the renaming of states is then
+    increasing and keeps the order of the creation operators (no sign); each
+    small-space SD is a big-space basis state.  X: numpy [dim_small] or
+    [dim_small][k]; returns numpy [dim_big](, k)."""
+    where = []
+    for o in orbits_small:
+        hits = [b for b, q in enumerate(orbits_big) if (q.n, q.l, q.twoj) == (o.n, o.l, o.twoj)]
+        if len(hits) != 1:
+            raise ValueError("embed: orbit (n=%d, l=%d, 2j=%d) not found once in the big space" % (o.n, o.l, o.twoj))
+        where.append(hits[0])
+    if where != sorted(where):
+        raise ValueError("embed: the small space's orbits must keep their order in the big space")
+    first_big, off = [], 0
+    for q in orbits_big:
+        first_big.append(off)
+        off += q.twoj + 1
+    smap = []   # small state -> big state
+    for a, o in enumerate(orbits_small):
+        smap += [first_big[where[a]] + i for i in range(o.twoj + 1)]
+
+    def remap(bits):
+        out = np.zeros_like(bits)
+        for s_small, s_big in enumerate(smap):
+            on = (bits >> np.uint64(s_small)) & np.uint64(1)
+            out |= on << np.uint64(s_big)
+        return out
+
+    Ps, Ns = basis_states(ctx_small)
+    Pb, Nb = basis_states(ctx_big)
+    if off > 32:
+        raise ValueError("embed: at most 32 single-particle states per species (64-bit state keys)")
+    nsb = np.uint64(off)
+    key_b = (Pb << nsb) | Nb
+    order = np.argsort(key_b)
+    key_s = (remap(Ps) << nsb) | remap(Ns)
+    pos = np.searchsorted(key_b[order], key_s)
+    if np.any(pos >= len(order)) or np.any(key_b[order][np.minimum(pos, len(order) - 1)] != key_s):
+        raise ValueError("embed: a small-space state is not in the big basis (Z, N, 2M or parity differ)")
+    idx = order[pos]
+    X = np.asarray(X)
+    out = np.zeros((ctx_big.dim,) + X.shape[1:], dtype=X.dtype)
+    out[idx] = X
+    return out
+
+
 def j2_context(orbits, Z, Nn, twoM, parity=+1, device=0):
     """A context on the (orbits, Z, N, 2M, parity) basis whose "interaction" is J^2."""
     spe, tb = j2_operator(orbits)

@@ -89,3 +89,27 @@ def test_isospin_densities_equal_the_oracle():
                 assert np.isnan(v) == np.isnan(got[key])
                 if np.isfinite(v):
                     assert abs(got[key] - v) < 1e-12, key
+
+
+def test_embed_single_orbit_eigenvectors_into_the_sd_space():
+    # the sd H restricted to states with every nucleon in 0d5/2 is the
+    # single-orbit H (see the W-truncation pins), so an embedded eigenvector
+    # of the 0d5/2 problem keeps its norm and its energy in the sd space
+    import oracle as O
+    from paper_1801_08432_gb300 import _native as N
+    orbits, spe, tb = I.space("sd")
+    small = [orbits[0]]
+    tb1 = [t for t in tb if t[:4] == (1, 1, 1, 1)]
+    for Z, Nn, twoM in ((2, 2, 0), (3, 2, 1)):
+        cs = N.Context(-1).build_basis(small, Z, Nn, twoM, +1)
+        cb = N.Context(-1).build_basis(orbits, Z, Nn, twoM, +1)
+        o1 = O.Oracle(small, Z, Nn, twoM, 0).set_interaction([spe[0]], tb1)
+        ob = O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
+        ev, X = np.linalg.eigh(o1.dense())
+        Xb = OB.embed(X[:, :4], cs, small, cb, orbits)
+        H = ob.matrix()
+        assert np.allclose(np.linalg.norm(Xb, axis=0), 1.0)
+        rq = np.einsum("ai,ai->i", Xb, H @ Xb)
+        assert np.max(np.abs(rq - ev[:4])) < 1e-11
+        with pytest.raises(ValueError):
+            OB.embed(X[:, :1], cs, small, cb, list(reversed(orbits)))
