@@ -133,6 +133,7 @@ class Oracle:
         L.orc_sizes(h, _p(sz, i32p))
         self.n_psd, self.n_nsd, self.n_psec, self.n_nsec, self.n_blocks = (int(v) for v in sz)
         self._csr = None
+        self._nnz = None
 
     def __del__(self):
         try:
@@ -177,6 +178,7 @@ class Oracle:
         if rc != 0:
             raise OracleError("orc_set_interaction rejected the interaction (%d)" % rc)
         self._csr = None
+        self._nnz = None
         return self
 
     def w_tables(self):
@@ -188,25 +190,34 @@ class Oracle:
         return wpp.reshape(s), wpn.reshape(s)
 
     # -- Hamiltonian -----------------------------------------------------
+    def build_matrix(self):
+        """Builds the explicit H in the C part (its columns, which are its rows
+        since H = H^T) and returns the number of stored elements.  spmv() needs
+        only this; matrix() also copies it out to scipy."""
+        if self._nnz is None:
+            nnz = lib().orc_build_matrix(self.h)
+            if nnz < 0:
+                raise OracleError("orc_build_matrix failed (%d)" % nnz)
+            self._nnz = int(nnz)
+        return self._nnz
+
     def matrix(self):
         """Explicit H as scipy.sparse.csr_matrix (FP64)."""
         import scipy.sparse as sp
         if self._csr is None:
-            L = lib()
-            nnz = L.orc_build_matrix(self.h)
-            if nnz < 0:
-                raise OracleError("orc_build_matrix failed (%d)" % nnz)
+            nnz = self.build_matrix()
             cp = np.zeros(self.dim + 1, dtype=np.int64)
             ri = np.zeros(max(nnz, 1), dtype=np.int64)
             va = np.zeros(max(nnz, 1))
-            L.orc_export_matrix(self.h, _p(cp, i64p), _p(ri, i64p), _p(va, f64p))
+            lib().orc_export_matrix(self.h, _p(cp, i64p), _p(ri, i64p), _p(va, f64p))
             # stored columns of H; csc -> csr through the transpose
             self._csr = sp.csc_matrix((va[:nnz], ri[:nnz], cp), shape=(self.dim, self.dim)).tocsr()
         return self._csr
 
     def spmv(self, x):
-        """y = H x with the explicit matrix, x [dim] or [dim][k]."""
-        self.matrix()
+        """y = H x with the explicit matrix, x [dim] or [dim][k] (the C part's
+        stored rows, OpenMP over rows)."""
+        self.build_matrix()
         x = np.ascontiguousarray(x, dtype=np.float64)
         k = 1 if x.ndim == 1 else x.shape[1]
         y = np.zeros_like(x)
@@ -237,8 +248,9 @@ class Oracle:
         w -= v_j <v_j|w> for every j <= i, twice (classical Gram-Schmidt);
         beta_i = |w|; v_{i+1} = w / beta_i.  Eigenvalues of the tridiagonal
         matrix by numpy.linalg.eigh; Ritz vectors from its eigenvectors.
+        H v is the explicit matrix's product (spmv), so a space as large as
+        pf 4p4n needs only the C part's copy of H.
         """
-        H = self.matrix()
         v = np.array(pivot, dtype=np.float64).reshape(-1)
         v = v / np.linalg.norm(v)
         niter = min(niter, self.dim)
@@ -248,7 +260,7 @@ class Oracle:
         n = 0
         for i in range(niter):
             V[i] = v
-            w = H @ v
+            w = self.spmv(v)
             alpha[i] = v @ w
             w = w - alpha[i] * v
             for _ in range(2):

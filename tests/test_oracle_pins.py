@@ -16,6 +16,11 @@ fixes, so that a dropped term, a wrong phase or a transposed index fails:
   * rotational invariance of the whole chain: eig(M=1) inside eig(M=0) and
     integer J from <J^2> = |J+ psi|^2 + M(M+1);
   * assembly: H = H^T, trace from occupation counts, reading in any label order;
+  * products: the on-the-fly rows (apply_rows, k = 1 and 4, and the |H| |x|
+    bound) equal rows of the explicit matrix times x, and spmv (k = 1, 2, 4,
+    8) equals the matrix times x, on sd 4p4n M = 0 and M = 1 and sd 5p6n,
+    random rows plus the first and last rows of every block and of its
+    proton rows (the row path is the checker of the large-space GPU tests);
   * Lanczos: dense diagonalization;
   * thick-restart block Lanczos: T = Q^T H Q after restarts, convergence to
     dense, Ritz values that never rise, the no-restart limit, the targeted
@@ -273,6 +278,59 @@ def test_trace_from_occupation_counts():
         for j in range(ns):
             tr += wpn[i, j, i, j] * pn[i, j]
     assert abs(o.trace() - tr) < 1e-9 * max(1.0, abs(tr))
+
+
+# ----------------------------------------------------------------- products
+@pytest.fixture(scope="module", params=[(4, 4, 0), (4, 4, 2), (5, 6, 1)], ids=lambda c: "sd-%dp%dn-2M%d" % c)
+def sd_product_case(request):
+    Z, Nn, twoM = request.param
+    orbits, spe, tb = I.space("sd")
+    return O.Oracle(orbits, Z, Nn, twoM, 0).set_interaction(spe, tb)
+
+
+def _boundary_rows(o, rng, n_random=3000):
+    """Random rows plus the first and last rows of every block and of the first
+    and last proton rows inside it."""
+    B = o.basis()
+    rows = set(rng.integers(0, o.dim, n_random).tolist())
+    for (ps, nsi, off) in B["blocks"]:
+        pc, nc = int(B["p_sec"][ps][3]), int(B["n_sec"][nsi][3])
+        for ip in {0, 1, pc - 2, pc - 1}:
+            if 0 <= ip < pc:
+                rows.update((int(off) + ip * nc, int(off) + ip * nc + nc - 1))
+    return np.array(sorted(rows), dtype=np.int64)
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_apply_rows_equal_matrix_rows(sd_product_case, k):
+    o = sd_product_case
+    rng = np.random.default_rng(11 + k)
+    rows = _boundary_rows(o, rng)
+    x = rng.standard_normal((o.dim, k))
+    H = o.matrix()
+    ref = H[rows] @ x
+    got = o.apply_rows(rows, x)
+    assert got.shape == (len(rows), k)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    # the |H| |x| bound, row by row
+    ref_abs = abs(H[rows]) @ np.abs(x)
+    got_abs = o.apply_rows(rows, x, absval=True)
+    assert np.max(np.abs(got_abs - ref_abs)) <= 1e-13 * np.max(ref_abs)
+    assert np.all(got_abs >= np.abs(got) - 1e-12 * np.max(ref_abs))
+    # a single vector passed as [dim] gives [nrows]
+    one = o.apply_rows(rows, x[:, 0])
+    assert one.shape == (len(rows),) and np.array_equal(one, got[:, 0])
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8])
+def test_spmv_equals_matrix_product(sd_product_case, k):
+    o = sd_product_case
+    x = np.random.default_rng(20 + k).standard_normal((o.dim, k))
+    ref = o.matrix() @ x
+    got = o.spmv(x)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
+    if k == 1:
+        assert np.max(np.abs(o.spmv(x[:, 0]) - ref[:, 0])) <= 1e-13 * np.max(np.abs(ref))
 
 
 # ----------------------------------------------------------------- rotational invariance
