@@ -102,52 +102,121 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_baseline(budget_s=12.0, seed=5):
-    """The FP64 oracle, as it stands, on a bounded sample of rows of the same
-    workload: H x row by row on the fly on all host cores."""
+def sample_rows(dim, frac, nchunks=64):
+    """A bounded sample of basis rows: nchunks contiguous runs spread evenly
+    through the basis, frac of all rows in total (every sector region is
+    represented in proportion)."""
+    n = max(nchunks, int(dim * frac))
+    per = max(1, n // nchunks)
+    starts = (np.arange(nchunks, dtype=np.int64) * dim) // nchunks
+    rows = (starts[:, None] + np.arange(per, dtype=np.int64)[None, :]).reshape(-1)
+    return np.unique(rows[rows < dim])
+
+
+def csr_sample(frac=0.10):
+    """The oracle of the workload with a sample of rows of its explicit FP64 H
+    stored (CSR, built from bit operations on all host cores).  Returns
+    (oracle, rows, nnz, build seconds)."""
     import oracle as O
     from paper_1801_08432_gb300 import inputs as I
     orbits, spe, tb = I.space(WORKLOAD["space"])
     o = O.Oracle(orbits, WORKLOAD["Z"], WORKLOAD["N"], WORKLOAD["twoM"], 0).set_interaction(spe, tb)
-    rng = np.random.default_rng(seed)
+    rows = sample_rows(o.dim, frac)
+    t0 = time.perf_counter()
+    nnz = o.build_rows(rows)
+    return o, rows, nnz, time.perf_counter() - t0
+
+
+def host_cores():
+    return int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+
+
+def cpu_baseline(budget_s=12.0, seed=5):
+    """The FP64 oracle, as it stands, on a bounded sample of the same workload:
+    its explicit-matrix product (CSR, FP64, OpenMP over all host cores) over a
+    10 % row sample of H, repeated for about budget_s seconds.  The sample's
+    rows are built first (reported, not timed); value = rows/s / dim."""
+    from paper_1801_08432_gb300 import inputs as I
+    o, rows, nnz, build_s = csr_sample()
     x = I.random_block(o.dim, 1, seed=seed)[:, 0]
-    n = 2000
-    t0 = time.perf_counter()
-    o.apply_rows(rng.integers(0, o.dim, n), x)
-    t1 = time.perf_counter()
-    rate = n / max(t1 - t0, 1e-9)
-    n2 = int(max(2000, min(5_000_000, rate * budget_s)))
-    rows = rng.integers(0, o.dim, n2)
-    t0 = time.perf_counter()
-    o.apply_rows(rows, x)
-    dt = time.perf_counter() - t0
-    rows_per_s = n2 / dt
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": rows_per_s / o.dim, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "%d random rows of H x (FP64, on the fly from bit operations) in %.1f s = %.0f rows/s; "
-                      "value = rows/s / dim" % (n2, dt, rows_per_s)}
+    o.spmv_rows(x)
+    reps, t0 = 0, time.perf_counter()
+    while True:
+        o.spmv_rows(x)
+        reps += 1
+        dt = time.perf_counter() - t0
+        if dt >= budget_s:
+            break
+    rows_per_s = reps * len(rows) / dt
+    return {"value": rows_per_s / o.dim, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+            "method": "explicit CSR SpMV, FP64, OpenMP over all host cores",
+            "sample": "%d of %d rows of H (64 runs spread over the basis, %d stored elements, built in %.1f s, "
+                      "not timed); their product repeated %d times in %.1f s = %.0f rows/s; value = rows/s / dim"
+                      % (len(rows), o.dim, nnz, build_s, reps, dt, rows_per_s),
+            "csr_build_s": round(build_s, 2), "csr_sample_rows": int(len(rows)), "csr_sample_nnz": int(nnz),
+            "nproc": os.cpu_count()}
 
 
 def reference_arm(args):
+    """The reference arm: the oracle as it stands on the host cores.  Each step
+    is one product of the sampled rows of the explicit FP64 H (CSR, OpenMP),
+    timed on its own; value = rows per second / dim."""
     rank, world, _ = dist_env()
     if rank != 0:
         return 0
-    steps_cb = []
+    from paper_1801_08432_gb300 import inputs as I
+    o, rows, nnz, build_s = csr_sample()
+    x = I.random_block(o.dim, 1, seed=5)[:, 0]
     for _ in range(args.warmup):
-        cpu_baseline(budget_s=1.0)
+        o.spmv_rows(x)
+    ts = []
     for _ in range(args.steps):
-        steps_cb.append(cpu_baseline(budget_s=max(2.0, 30.0 / max(1, args.steps))))
-    vals = [c["value"] for c in steps_cb]
-    v = float(np.mean(vals))
+        t0 = time.perf_counter()
+        o.spmv_rows(x)
+        ts.append(time.perf_counter() - t0)
+    t = float(np.sum(ts))
+    v = args.steps * len(rows) / t / o.dim
+    sample = ("%d of %d rows of H (64 runs spread over the basis, %d stored elements, built in %.1f s before the "
+              "steps); each step one product of them" % (len(rows), o.dim, nnz, build_s))
     line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": 1000.0 / v if v > 0 else None, "higher_is_better": True,
+            "warmup": args.warmup, "ms_per_step": 1000.0 * t / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": WORKLOAD_NAME, "k": 1, "sample": "bounded random rows per step"},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": steps_cb[-1]["cores"], "kind": "oracle",
-                             "sample": steps_cb[-1]["sample"]},
+            "config": {"workload": WORKLOAD_NAME, "k": 1, "sample": "10 % of the rows of H per step"},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
+                             "method": "explicit CSR SpMV, FP64, OpenMP over all host cores",
+                             "sample": sample, "csr_build_s": round(build_s, 2)},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_lanczos(args):
+    """The oracle's whole FP64 run on the workload: the explicit H (CSR) built
+    on all host cores, then its Lanczos with full reorthogonalization from the
+    seeded pivot for the bench's iteration count; one JSON line with the
+    times (not part of the default run: ~40 GB of host memory)."""
+    import oracle as O
+    from paper_1801_08432_gb300 import inputs as I
+    orbits, spe, tb = I.space(WORKLOAD["space"])
+    o = O.Oracle(orbits, WORKLOAD["Z"], WORKLOAD["N"], WORKLOAD["twoM"], 0).set_interaction(spe, tb)
+    t0 = time.perf_counter()
+    nnz = o.build_matrix()
+    build_s = time.perf_counter() - t0
+    x = I.random_block(o.dim, 1, seed=5)[:, 0]
+    o.spmv(x)
+    t0 = time.perf_counter()
+    for _ in range(5):
+        o.spmv(x)
+    spmv_s = (time.perf_counter() - t0) / 5
+    p = I.random_block(o.dim, 1, seed=I.PIVOT_SEED)[:, 0]
+    t0 = time.perf_counter()
+    ev = o.lanczos(p, args.cpu_lanczos, nkeep=5)
+    lan_s = time.perf_counter() - t0
+    print(json.dumps({"cpu_lanczos": True, "workload": WORKLOAD_NAME, "cores": host_cores(), "nnz": nnz,
+                      "csr_build_s": round(build_s, 1), "spmv_s": round(spmv_s, 3),
+                      "vector_matvecs_per_s": 1.0 / spmv_s, "iterations": args.cpu_lanczos,
+                      "lanczos_s": round(lan_s, 1), "evals_mev": [round(float(e), 9) for e in ev]}), flush=True)
     return 0
 
 
@@ -237,6 +306,20 @@ def lanczos_check(ctx, N, I, torch, stream):
     out["max_abs_diff_mev"] = max(d) if d else None
     out["within_1e-4_mev"] = bool(d) and max(d) <= 1e-4
     out["speedup_fp32_k8_vs_fp64_k1_wall"] = out["fp64_k1"]["ms_total"] / out["fp32_k8"]["ms_total"]
+    # against the FP64 oracle's levels (tests/golden/cr48_levels.txt, written by
+    # the oracle alone): every converged level of each GPU run
+    gold = os.path.join(ROOT, "tests", "golden", "cr48_levels.txt")
+    if os.path.exists(gold):
+        ev_o = [float(l.split()[1]) for l in open(gold) if l.strip() and not l.startswith("#")]
+        for name in ("fp64_k1", "fp32_k8", "fp32_k8_thick"):
+            r = out[name]
+            lv = [i for i in range(5) if r["residual_mev"][i] <= 1e-3]
+            d = [abs(r["evals_mev"][i] - ev_o[i]) for i in lv]
+            r["vs_oracle_levels"] = lv
+            r["max_abs_diff_vs_oracle_mev"] = max(d) if d else None
+        a = out["fp32_k8"]
+        out["fp32_k8_within_1e-4_mev_of_oracle"] = (a["max_abs_diff_vs_oracle_mev"] is not None and
+                                                    a["max_abs_diff_vs_oracle_mev"] <= 1e-4)
     return out
 
 
@@ -277,6 +360,54 @@ def traffic_from_profile(k, mode):
         if len(f) == 4 and f[0] == "traffic" and f[1] == "k=%d" % k and f[2] == "src=" + sha:
             return int(f[3].split("=")[1])
     return None
+
+
+def fe52_product(N, I, torch, device, mode=19, nrep=3):
+    """The largest workload (pf 6p6n M=0, 52Fe, dim 109,954,620) at its block
+    size k = 4: set-up (basis, decoupling, tables, upload) timed on the host,
+    then one warm-up and nrep timed FP32 block products H X in the
+    core-grouped mode that suits its wide neutron sectors (column-tiled
+    like-particle kernels), CUDA events around each product and around its
+    pn-core kernel.  Reported beside the main line, not part of its value."""
+    orbits, spe, tb = I.space("pf")
+    t0 = time.time()
+    ctx = N.make(orbits, spe, tb, 6, 6, 0, +1, device=device)
+    setup_s = time.time() - t0
+    dim, k = ctx.dim, 4
+    stats = ctx.table("stats", np.int64)
+    ctx.set_kernel(mode)
+    stream = torch.cuda.Stream()
+    sp = stream.cuda_stream
+    g = torch.Generator(device="cuda").manual_seed(52)
+    x = torch.randn((dim, k), device="cuda", dtype=torch.float32, generator=g)
+    y = torch.empty_like(x)
+    with torch.cuda.stream(stream):
+        ctx.apply_H(x, y, k, N.BS_F32, sp)
+    stream.synchronize()
+    ctx.time_kernel(nrep)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(nrep)]
+    for i in range(nrep):
+        ev[i][0].record(stream)
+        with torch.cuda.stream(stream):
+            ctx.apply_H(x, y, k, N.BS_F32, sp)
+        ev[i][1].record(stream)
+    stream.synchronize()
+    ms = [a.elapsed_time(b) for (a, b) in ev]
+    kern = [float(t) for t in ctx.kernel_times()]
+    ctx.time_kernel(0)
+    ctx.sync_status()
+    del x, y
+    ctx.close()
+    torch.cuda.empty_cache()
+    hx_ms = float(np.mean(ms))
+    kern_ms = float(np.mean(kern))
+    return {"workload": "pf shell 6p6n M=0 (52Fe), dim %d, 195 seeded random TBMEs" % dim, "k": k,
+            "kernel_mode": mode, "set_up_s": round(setup_s, 1), "products": nrep,
+            "hx_ms_per_block_product": round(hx_ms, 2), "vector_matvecs_per_s": k / (hx_ms / 1000.0),
+            "pn_core_kernel_ms": round(kern_ms, 2),
+            "pn_core_tflops": 2.0 * float(stats[8]) * k / (kern_ms / 1000.0) / 1e12,
+            "product_tflops": 2.0 * float(stats[5]) * k / (hx_ms / 1000.0) / 1e12,
+            "note": "L2 not flushed: the 1.76 GB vectors exceed it"}
 
 
 def fe52_run(args):
@@ -512,6 +643,26 @@ def ours(args):
     alg_bytes = 2.0 * dim * kbest * 4 + tbytes
     hbm_peak = (pk or {}).get("hbm_gbs", 6800.0)
     traffic = traffic_from_profile(kbest, args.mode or modes.get(kbest, 0))
+    # measured on-chip ceiling of the product's inner step (bs_gather_ceiling:
+    # random k-float gathers from shared memory or L2, each applied to 1, 2
+    # or 4 rows by packed FP32 FMAs), outside the timed region
+    ceil = {}
+    if kbest in (4, 8):
+        for where, name in ((0, "smem"), (1, "l2")):
+            for rows in (1, 2, 4):
+                ceil["ceil_%s_rows%d" % (name, rows)] = ctx.gather_ceiling(where, kbest, rows, sp) / 1e3
+    gathers = float(stats[11]) if len(stats) > 11 else 0.0
+    rpg = float(stats[8]) / gathers if core and gathers > 0 else None
+    if rpg is not None and ceil:
+        # linear in the rows between the measured 1-, 2- and 4-row rates
+        lo, hi = (1, 2) if rpg <= 2 else (2, 4)
+        c_lo, c_hi = ceil["ceil_smem_rows%d" % lo], ceil["ceil_smem_rows%d" % hi]
+        ceiling = c_lo + (min(rpg, 4.0) - lo) / (hi - lo) * (c_hi - c_lo)
+        peak, peak_note = ceiling, ("measured shared-memory gather + FMA ceiling (bs_gather_ceiling, k = %d) at the "
+                                    "kernel's %.3f rows per gathered element, between the measured %d- and %d-row "
+                                    "rates" % (kbest, rpg, lo, hi))
+    else:
+        peak, peak_note = fp32_peak, "FP32 FMA issue (derived)"
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
@@ -520,14 +671,17 @@ def ours(args):
                    "path": "FP32-mixed block H*X (core-grouped kernels)" if core else "FP32-mixed block H*X (one kernel)",
                    "l2": "flushed: 256 MB write before every timed launch", "parallelism": "replicas" if world > 1 else "1 GPU",
                    "set_up_s": round(setup_s, 2)},
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": fp32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / fp32_peak, "traffic": traffic,
-                     "kernel": "hx_core_kernel (pn term by proton cores)" if core else "the single H x kernel",
-                     "kernel_ms": dom_s * 1000.0, "flop_per_launch": flops,
-                     "peak_note": "FP32 FMA issue: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, not measured)" % (nsm, sm_mhz_max),
-                     "product": {"flop": 2.0 * ops * kbest, "ms": avg_launch_s * 1000.0,
-                                 "tflops": 2.0 * ops * kbest / avg_launch_s / 1e12,
-                                 "launches": launches_per_product(mode_used)}},
+        "roofline": dict({"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                          "frac": achieved / peak, "traffic": traffic,
+                          "kernel": "hx_core_kernel (pn term by proton cores)" if core else "the single H x kernel",
+                          "kernel_ms": dom_s * 1000.0, "flop_per_launch": flops, "peak_note": peak_note,
+                          "rows_per_gather": rpg,
+                          "fma_issue_peak": fp32_peak, "frac_fma_issue": achieved / fp32_peak,
+                          "fma_issue_note": "FP32 FMA issue: %d SMs x 128 lanes x 2 FLOP x %.0f MHz (derived, not "
+                                            "measured)" % (nsm, sm_mhz_max),
+                          "product_flop": 2.0 * ops * kbest, "product_ms": avg_launch_s * 1000.0,
+                          "product_tflops": 2.0 * ops * kbest / avg_launch_s / 1e12,
+                          "product_launches": launches_per_product(mode_used)}, **ceil),
         "hbm": {"algorithmic_bytes_per_launch": alg_bytes, "gbs": alg_bytes / avg_launch_s / 1e9,
                 "peak_gbs": hbm_peak, "frac": alg_bytes / avg_launch_s / 1e9 / hbm_peak,
                 "peak_note": "measured copy bandwidth (MEASURED_PEAKS.json)" if pk else "fallback"},
@@ -541,25 +695,15 @@ def ours(args):
         "gpu_launches": args.steps * launches_per_product(mode_used),
         "clocks": clocks,
     }
-    if kbest in (4, 8):
-        # measured on-chip ceiling of the product's inner step (bs_gather_ceiling:
-        # random k-float gathers from shared memory or L2, each applied to 1, 2
-        # or 4 rows by packed FP32 FMAs), outside the timed region
-        ceil = {}
-        for where, name in ((0, "smem"), (1, "l2")):
-            for rows in (1, 2, 4):
-                ceil["%s_rows%d" % (name, rows)] = ctx.gather_ceiling(where, kbest, rows, sp) / 1e3
-        line["roofline"]["gather_ceiling"] = dict(
-            unit="TFLOP/s", **ceil,
-            frac_vs_smem_rows4=achieved / ceil["smem_rows4"], frac_vs_smem_rows2=achieved / ceil["smem_rows2"],
-            note="the pn-core kernel applies each gathered element to 1, 2 or 4 rows (2.2 on average at 48Cr)")
     if not args.no_lanczos:
         line["lanczos"] = lanczos_check(ctx, N, I, torch, sp)
+    ctx.close()
+    if not args.no_fe52 and rank == 0:
+        line["fe52"] = fe52_product(N, I, torch, local)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
     if dist is not None:
         dist.destroy_process_group()
     return 0
@@ -574,6 +718,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--k", type=int, default=0, help="fix k instead of autotuning it")
     ap.add_argument("--no-lanczos", action="store_true", help="skip the Lanczos accuracy check")
+    ap.add_argument("--no-fe52", action="store_true", help="skip the pf 6p6n (52Fe) product key")
     ap.add_argument("--mode", type=int, default=0, help="fix the H x kernel mode (bs_set_kernel) instead of autotuning")
     ap.add_argument("--profile-only", action="store_true", help="only the FP32 H*X launches (for ncu)")
     ap.add_argument("--fe52", action="store_true", help="only the pf 6p6n (52Fe) block Lanczos, k = 4, 50 iterations")
@@ -583,11 +728,15 @@ def main():
     ap.add_argument("--tune-load", default="", help="replay kernel modes and k from a --tune-save file instead of autotuning")
     ap.add_argument("--profile-lanczos", type=int, default=0,
                     help="only an FP32 block Lanczos of this many block iterations (for ncu)")
+    ap.add_argument("--cpu-lanczos", type=int, default=0,
+                    help="only the oracle's full FP64 run on the host: build H, then this many Lanczos iterations")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         return reference_arm(args)
+    if args.cpu_lanczos:
+        return cpu_lanczos(args)
     if args.fe52:
         return fe52_run(args)
     return ours(args)

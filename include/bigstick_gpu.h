@@ -196,12 +196,19 @@ int bs_block_dots(bs_ctx *ctx, const void *V, int nb, const void *W, int k, bs_d
  * stream capture.  Every call writes all the partials it reads, so nothing is
  * carried over from the previous call, but all calls share the one array:
  * calls that overlap on the GPU (other streams, other host threads) race and
- * must be serialized by the caller.  Same precision and summation order as
- * bs_block_dots when nb*k*k <= BS_BLOCK_DOTS_NOALLOC_MAX / (2 x SMs); larger
- * requests run on fewer CTAs.  Runs on `stream` (a cudaStream_t) on the
- * current device.  Errors: BS_EINVAL (null pointer, nb < 1, dim < 1, k not in
- * 1, 2, 4, 8, bad dtype); BS_ENOMEM (nb*k*k > BS_BLOCK_DOTS_NOALLOC_MAX);
- * BS_ECUDA. */
+ * must be serialized by the caller.  It always runs the row-slot kernel
+ * (FP64 fused multiply-adds for FP64 vectors; exact FP32 products summed in
+ * double-float for FP32 vectors; per-CTA partials added in FP64 in a fixed
+ * order, so repeated calls are bit-identical).  bs_block_dots streams
+ * 16-byte-aligned blocks through another kernel whose summation order
+ * differs, so the two entry points agree to rounding, not bit for bit.  Up to
+ * 2 x SMs CTAs run while nb*k*k <= BS_BLOCK_DOTS_NOALLOC_MAX / (2 x SMs);
+ * larger requests run on fewer CTAs (one at the maximum).  V and W must be
+ * aligned to min(16, k x element size) bytes and C to 8 bytes.  Runs on
+ * `stream` (a cudaStream_t) on the current device.  Errors: BS_EINVAL (null
+ * pointer, misaligned pointer, nb < 1, dim < 1, k not in 1, 2, 4, 8, bad
+ * dtype; nothing is launched); BS_ENOMEM (nb*k*k >
+ * BS_BLOCK_DOTS_NOALLOC_MAX); BS_ECUDA. */
 int bs_block_dots_noalloc(const void *V, int nb, const void *W, int64_t dim, int k, bs_dtype dtype, double *C,
                           void *stream);
 
@@ -211,7 +218,7 @@ typedef struct {
     bs_dtype dtype;     /* precision of the stored Lanczos vectors and of H x */
     int niter;          /* block iterations; clamped to dim / k */
     int nkeep;          /* eigenvalues returned (lowest first) */
-    int refine;         /* 1: FP64 H psi of the lowest min(nkeep, 8) Ritz vectors,
+    int refine;         /* 1: FP64 H psi of the lowest min(nkeep, 64) Ritz vectors,
                            evals become FP64 Rayleigh quotients, residuals reported */
     int reorth_passes;  /* Gram-Schmidt passes against all stored blocks (2 = default) */
     int use_graph;      /* 1: capture one block iteration in a CUDA graph (kernels read the
@@ -238,7 +245,7 @@ typedef struct {
 typedef struct {
     int iterations;          /* block iterations done */
     int breakdowns;          /* Gram eigenvalues below 1e-24 of the largest, restarted with random columns */
-    int n_kept;              /* pairs with Ritz vectors / refinement (<= 8) */
+    int n_kept;              /* pairs with Ritz vectors / refinement (<= 64) */
     double residual[64];     /* |H psi - E psi| / |psi| in FP64, per refined pair */
     double delta_conv;       /* sum_{i <= nkeep+5} |E_i(n) - E_i(n-1)| / sqrt(nkeep+5) over the last iteration */
     double ms_matvec;        /* GPU time in H x */
@@ -257,7 +264,7 @@ typedef struct {
  * B_n = L^(1/2) U^T, V_(n+1) = W' U L^(-1/2)), all on the GPU.
  * pivot: device [dim][k] block in opts->dtype (any full-rank block; it is
  * orthonormalized).  evals: host array of nkeep doubles (lowest first).
- * evecs: device [dim][nkeep] FP64 Ritz vectors of the lowest min(nkeep, 8)
+ * evecs: device [dim][nkeep] FP64 Ritz vectors of the lowest min(nkeep, 64)
  * pairs, or NULL.  report may be NULL.  Inner products accumulate in
  * extended precision (FP64, or exact FP32 products summed in double-float);
  * T is diagonalized in FP64 on the host.
@@ -318,6 +325,17 @@ int bs_density(bs_ctx *ctx, const double *F, const double *X, int k, double *rho
  * (k = 4 or 8).  Uses the context's device; allocates and frees ~64 MB;
  * synchronizes the stream.  Errors: BS_EINVAL, BS_ENOMEM, BS_ECUDA. */
 int bs_gather_ceiling(bs_ctx *ctx, int where, int k, int rows, double *gflops, void *stream);
+
+/* Test aid for the failure path of the bounded waits: launches one warp on
+ * `stream` that waits on a shared-memory mbarrier nothing arrives at, through
+ * the same bounded wait as the TMA kernels but giving up after `limit` tries
+ * (1 .. 4,194,304, the kernels' own limit).  No copy is issued, so none is in
+ * flight when it gives up.  The expiry is recorded in the context's status
+ * word as a product kernel records it, so the next bs_sync_status returns
+ * BS_ETIMEOUT (and clears it); the context stays usable.  Errors:
+ * BS_ENOBASIS, BS_ENOINT (the status word comes with the interaction),
+ * BS_EINVAL (limit), BS_ECUDA. */
+int bs_debug_wait_expiry(bs_ctx *ctx, int limit, void *stream);
 
 /* Test aid: all eigenvalues (ascending, w[n]) and the eigenvectors of the
  * lowest nvec (columns of Z, n x nvec row-major) of the symmetric n x n

@@ -75,6 +75,9 @@ def lib():
             L.orc_build_matrix.restype = ctypes.c_int64
             L.orc_export_matrix.argtypes = [ctypes.c_void_p, i64p, i64p, f64p]
             L.orc_spmv.argtypes = [ctypes.c_void_p, f64p, f64p, ctypes.c_int]
+            L.orc_build_rows.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64]
+            L.orc_build_rows.restype = ctypes.c_int64
+            L.orc_spmv_rows.argtypes = [ctypes.c_void_p, f64p, f64p, ctypes.c_int]
             L.orc_apply_rows.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64, f64p, ctypes.c_int, f64p]
             L.orc_apply_rows_ex.argtypes = [ctypes.c_void_p, i64p, ctypes.c_int64, f64p, ctypes.c_int, f64p, ctypes.c_int]
             L.orc_jplus.argtypes = [ctypes.c_void_p, ctypes.c_void_p, f64p, f64p]
@@ -223,6 +226,25 @@ class Oracle:
         y = np.zeros_like(x)
         lib().orc_spmv(self.h, _p(x, f64p), _p(y, f64p), k)
         return y
+
+    def build_rows(self, rows):
+        """Stores the given rows of the explicit H (built as build_matrix()
+        builds every row) for spmv_rows(); returns their element count."""
+        rows = np.ascontiguousarray(rows, dtype=np.int64)
+        nnz = lib().orc_build_rows(self.h, _p(rows, i64p), len(rows))
+        if nnz < 0:
+            raise OracleError("orc_build_rows failed (%d)" % nnz)
+        self._sub_rows = rows
+        return int(nnz)
+
+    def spmv_rows(self, x):
+        """The rows stored by build_rows() of y = H x, x [dim] or [dim][k]:
+        the stored-matrix product (spmv) restricted to a sample of rows."""
+        x = np.ascontiguousarray(x, dtype=np.float64)
+        k = 1 if x.ndim == 1 else x.shape[1]
+        y = np.zeros((len(self._sub_rows), k))
+        lib().orc_spmv_rows(self.h, _p(x, f64p), _p(y, f64p), k)
+        return y[:, 0] if x.ndim == 1 else y
 
     def apply_rows(self, rows, x, absval=False):
         """Rows of y = H x computed on the fly (no stored matrix); with

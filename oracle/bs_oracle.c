@@ -144,6 +144,10 @@ typedef struct orc {
     int64_t *colptr, *rowidx;
     double *val;
     int64_t nnz;
+    /* the stored rows of a row sample (same format, rows listed in sub_rows) */
+    int64_t *sub_rows, *sub_ptr, *sub_idx;
+    double *sub_val;
+    int64_t nsub, sub_nnz;
 } orc;
 
 static int nsd_choose(int n, int k)
@@ -602,45 +606,76 @@ static int64_t merge_list(elist *L)
     return w;
 }
 
-/* Builds every column of H (CSC).  Returns nnz or a negative error. */
-int64_t orc_build_matrix(orc *o)
+/* Builds the columns of H at the basis indices cols[0..n) (CSC; a column is
+ * also the row of the same index, H being symmetric): *ptr[n+1], *idx[nnz],
+ * *val[nnz], allocated here.  Returns nnz or a negative error. */
+static int64_t build_columns(const orc *o, const int64_t *cols, int64_t n, int64_t **ptr_out, int64_t **idx_out,
+                             double **val_out)
 {
-    if (!o->have_int) return OR_EINVAL;
-    int64_t dim = o->dim;
-    free(o->colptr); free(o->rowidx); free(o->val);
-    o->colptr = (int64_t *)calloc((size_t)dim + 1, sizeof(int64_t));
-    entry **cols = (entry **)calloc((size_t)dim, sizeof(entry *));
-    int64_t *clen = (int64_t *)calloc((size_t)dim, sizeof(int64_t));
-    if (!o->colptr || !cols || !clen) return OR_ENOMEM;
+    int64_t *ptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    entry **cl = (entry **)calloc((size_t)(n ? n : 1), sizeof(entry *));
+    int64_t *clen = (int64_t *)calloc((size_t)(n ? n : 1), sizeof(int64_t));
+    if (!ptr || !cl || !clen) { free(ptr); free(cl); free(clen); return OR_ENOMEM; }
 #pragma omp parallel
     {
         elist L = {0, 0, 0};
 #pragma omp for schedule(dynamic, 64)
-        for (int64_t a = 0; a < dim; ++a) {
+        for (int64_t r = 0; r < n; ++r) {
             uint64_t P, Nb;
-            state_of_index(o, a, &P, &Nb);
+            state_of_index(o, cols ? cols[r] : r, &P, &Nb);
             L.n = 0;
             apply_H_state(o, P, Nb, &L);
             merge_list(&L);
-            cols[a] = (entry *)malloc(sizeof(entry) * (size_t)(L.n ? L.n : 1));
-            memcpy(cols[a], L.e, sizeof(entry) * (size_t)L.n);
-            clen[a] = L.n;
+            cl[r] = (entry *)malloc(sizeof(entry) * (size_t)(L.n ? L.n : 1));
+            memcpy(cl[r], L.e, sizeof(entry) * (size_t)L.n);
+            clen[r] = L.n;
         }
         free(L.e);
     }
-    for (int64_t a = 0; a < dim; ++a) o->colptr[a + 1] = o->colptr[a] + clen[a];
-    o->nnz = o->colptr[dim];
-    o->rowidx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(o->nnz ? o->nnz : 1));
-    o->val = (double *)malloc(sizeof(double) * (size_t)(o->nnz ? o->nnz : 1));
-    for (int64_t a = 0; a < dim; ++a) {
-        for (int64_t t = 0; t < clen[a]; ++t) {
-            o->rowidx[o->colptr[a] + t] = cols[a][t].idx;
-            o->val[o->colptr[a] + t] = cols[a][t].v;
+    for (int64_t r = 0; r < n; ++r) ptr[r + 1] = ptr[r] + clen[r];
+    const int64_t nnz = ptr[n];
+    int64_t *idx = (int64_t *)malloc(sizeof(int64_t) * (size_t)(nnz ? nnz : 1));
+    double *val = (double *)malloc(sizeof(double) * (size_t)(nnz ? nnz : 1));
+    for (int64_t r = 0; r < n; ++r) {
+        for (int64_t t = 0; t < clen[r]; ++t) {
+            idx[ptr[r] + t] = cl[r][t].idx;
+            val[ptr[r] + t] = cl[r][t].v;
         }
-        free(cols[a]);
+        free(cl[r]);
     }
-    free(cols); free(clen);
-    return o->nnz;
+    free(cl); free(clen);
+    *ptr_out = ptr; *idx_out = idx; *val_out = val;
+    return nnz;
+}
+
+/* Builds every column of H (CSC).  Returns nnz or a negative error. */
+int64_t orc_build_matrix(orc *o)
+{
+    if (!o->have_int) return OR_EINVAL;
+    free(o->colptr); free(o->rowidx); free(o->val);
+    o->colptr = NULL; o->rowidx = NULL; o->val = NULL;
+    const int64_t nnz = build_columns(o, NULL, o->dim, &o->colptr, &o->rowidx, &o->val);
+    if (nnz < 0) return nnz;
+    o->nnz = nnz;
+    return nnz;
+}
+
+/* Stores the rows rows[0..n) of H (a sample of the explicit matrix, built as
+ * orc_build_matrix builds every row).  Returns their element count or a
+ * negative error. */
+int64_t orc_build_rows(orc *o, const int64_t *rows, int64_t n)
+{
+    if (!o->have_int) return OR_EINVAL;
+    free(o->sub_rows); free(o->sub_ptr); free(o->sub_idx); free(o->sub_val);
+    o->sub_rows = (int64_t *)malloc(sizeof(int64_t) * (size_t)(n ? n : 1));
+    if (!o->sub_rows) return OR_ENOMEM;
+    memcpy(o->sub_rows, rows, sizeof(int64_t) * (size_t)n);
+    o->sub_ptr = NULL; o->sub_idx = NULL; o->sub_val = NULL;
+    const int64_t nnz = build_columns(o, rows, n, &o->sub_ptr, &o->sub_idx, &o->sub_val);
+    if (nnz < 0) return nnz;
+    o->nsub = n;
+    o->sub_nnz = nnz;
+    return nnz;
 }
 
 void orc_export_matrix(const orc *o, int64_t *colptr, int64_t *rowidx, double *val)
@@ -650,19 +685,33 @@ void orc_export_matrix(const orc *o, int64_t *colptr, int64_t *rowidx, double *v
     memcpy(val, o->val, sizeof(double) * (size_t)o->nnz);
 }
 
+/* y[r] = sum_t val[t] x[idx[t]] over the stored row r (ptr[r] <= t <
+ * ptr[r+1]), for n rows, x [dim][k], y [n][k]. */
+static void csr_apply(const int64_t *ptr, const int64_t *idx, const double *val, int64_t n, const double *x,
+                      double *y, int k)
+{
+#pragma omp parallel for schedule(dynamic, 256)
+    for (int64_t r = 0; r < n; ++r) {
+        for (int c = 0; c < k; ++c) {
+            double s = 0.0;
+            for (int64_t t = ptr[r]; t < ptr[r + 1]; ++t)
+                s += val[t] * x[idx[t] * k + c];
+            y[r * k + c] = s;
+        }
+    }
+}
+
 /* y = H x with the stored matrix, x and y [dim][k].  Uses H = H^T, so the
  * stored columns are rows. */
 void orc_spmv(const orc *o, const double *x, double *y, int k)
 {
-#pragma omp parallel for schedule(dynamic, 256)
-    for (int64_t r = 0; r < o->dim; ++r) {
-        for (int c = 0; c < k; ++c) {
-            double s = 0.0;
-            for (int64_t t = o->colptr[r]; t < o->colptr[r + 1]; ++t)
-                s += o->val[t] * x[o->rowidx[t] * k + c];
-            y[r * k + c] = s;
-        }
-    }
+    csr_apply(o->colptr, o->rowidx, o->val, o->dim, x, y, k);
+}
+
+/* The sampled rows of y = H x (orc_build_rows): y [nsub][k], x [dim][k]. */
+void orc_spmv_rows(const orc *o, const double *x, double *y, int k)
+{
+    csr_apply(o->sub_ptr, o->sub_idx, o->sub_val, o->nsub, x, y, k);
 }
 
 /* Selected rows of y = H x computed on the fly, without the matrix:
@@ -736,6 +785,7 @@ void orc_destroy(orc *o)
     free(o->blk_psec); free(o->blk_nsec); free(o->blk_off); free(o->blk_of_psec);
     free(o->V); free(o->Wpp); free(o->Wpn);
     free(o->colptr); free(o->rowidx); free(o->val);
+    free(o->sub_rows); free(o->sub_ptr); free(o->sub_idx); free(o->sub_val);
     free(o);
 }
 

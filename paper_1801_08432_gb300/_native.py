@@ -24,7 +24,8 @@ EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_ba
             "bs_export_basis", "bs_load_interaction", "bs_apply_H", "bs_apply_H_host",
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_set_tuned", "bs_lanczos",
             "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_update", "bs_block_dots_noalloc",
-            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength", "bs_density", "bs_gather_ceiling"]
+            "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength", "bs_density", "bs_gather_ceiling",
+            "bs_debug_wait_expiry"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -93,6 +94,7 @@ def load():
                               ctypes.POINTER(bs_lanczos_report)]
     L.bs_density.argtypes = [vp, vp, vp, ctypes.c_int, f64p, vp]
     L.bs_gather_ceiling.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, f64p, vp]
+    L.bs_debug_wait_expiry.argtypes = [vp, ctypes.c_int, vp]
     L.bs_debug_eigh.argtypes = [ctypes.c_int, vp, vp, vp, ctypes.c_int]
     L.bs_debug_eigh_banded.argtypes = [ctypes.c_int, ctypes.c_int, vp, ctypes.c_int, vp, vp, ctypes.c_int]
     L.bs_apply_H_backward.argtypes = [vp, vp, vp, vp, f64p, ctypes.c_int, ctypes.c_int, vp]

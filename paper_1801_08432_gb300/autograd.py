@@ -1,9 +1,13 @@
 """Differentiation of y = H(theta) x and of Lanczos eigenvalues w.r.t. the
 interaction theta = (SPEs, TBMEs), for fitting interactions.
 
-All arithmetic on basis vectors runs in the library's kernels (forward
-bs_apply_H, adjoint bs_apply_H_backward, Lanczos bs_lanczos); torch supplies
-the tape.  theta is a CPU float64 tensor: the SPEs (one per orbit) followed
+The products with H and their adjoints run in the library's kernels
+(forward bs_apply_H, adjoint bs_apply_H_backward, Lanczos bs_lanczos); torch
+supplies the tape.  The one exception is lanczos_k_loss: the dot products,
+vector updates and norms of its K-step recurrence are torch operations on the
+device, because the tape has to see them to differentiate through the steps
+(only its H v products go through the library).  theta is a CPU float64
+tensor: the SPEs (one per orbit) followed
 by the TBME values in the order of the label list the operator was built
 with.
 

@@ -556,6 +556,19 @@ int bs_gather_ceiling(bs_ctx *c, int where, int k, int rows, double *gflops, voi
     });
 }
 
+int bs_debug_wait_expiry(bs_ctx *c, int limit, void *stream)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, 1, BS_F64);
+        if (rc) return rc;
+        if (limit < 1 || limit > (int)tma_wait_limit()) {
+            c->err = "wait expiry: limit must be in 1 .. the kernels' own limit";
+            return BS_EINVAL;
+        }
+        return run_wait_expiry(c->device, (uint32_t)limit, c->dev.err, stream, c->err);
+    });
+}
+
 int bs_set_kernel(bs_ctx *c, int mode)
 {
     return guarded(c, [&]() -> int {
@@ -757,7 +770,8 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
             use(tmp.data(), tmp.size() * 8);
         } else if (s == "stats") {
             tmp = {T.n_pp, T.n_nn, T.n_p1, T.n_n1, (int64_t)T.links.size(), (int64_t)T.ops_per_vector, (int64_t)c->dev.ntasks,
-                   (int64_t)T.wsign, (int64_t)T.ops_pn, (int64_t)T.ops_pp, (int64_t)T.ops_nn};
+                   (int64_t)T.wsign, (int64_t)T.ops_pn, (int64_t)T.ops_pp, (int64_t)T.ops_nn,
+                   (int64_t)T.gathers_pn};
             use(tmp.data(), tmp.size() * 8);
         } else {
             c->err = "unknown table " + s;

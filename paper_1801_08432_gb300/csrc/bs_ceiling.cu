@@ -18,6 +18,7 @@
 #include <vector>
 
 #include "bs_internal.h"
+#include "bs_tma.cuh"
 
 namespace bs {
 namespace {
@@ -148,7 +149,40 @@ cudaError_t ceiling_k(int nsm, int where, int rows, const uint32_t *ids, const f
     }
 }
 
+// Test aid: one warp waits on an mbarrier that nothing arrives at, through
+// the same bounded wait the TMA kernels use, with a short limit.  No copy is
+// issued, so none is in flight when the wait gives up; the expiry is
+// recorded in the context's status word exactly as a product kernel records
+// it, and the kernel returns.
+__global__ void wait_expiry_kernel(uint32_t limit, int *err)
+{
+    __shared__ __align__(8) unsigned long long bar;
+    const uint32_t b = tma::su32(&bar);
+    if (threadIdx.x == 0) {
+        tma::bar_init(b, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (__any_sync(0xffffffffu, tma::bar_wait(b, 0u, limit))) {
+        if (threadIdx.x == 0) atomicExch(err, BS_ETIMEOUT);
+        return;
+    }
+}
+
 }  // namespace
+
+uint32_t tma_wait_limit() { return tma::kWaitLimit; }
+
+int run_wait_expiry(int device, uint32_t limit, int *err, void *stream, std::string &msg)
+{
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) {
+        wait_expiry_kernel<<<1, 32, 0, (cudaStream_t)stream>>>(limit, err);
+        e = cudaGetLastError();
+    }
+    if (e != cudaSuccess) { msg = std::string("wait expiry: ") + cudaGetErrorString(e); return BS_ECUDA; }
+    return BS_OK;
+}
 
 int run_gather_ceiling(int device, int where, int k, int rows, double *gflops, void *stream, std::string &err)
 {

@@ -198,6 +198,8 @@ struct Tables {
     int64_t n_pp = 0, n_nn = 0, n_p1 = 0, n_n1 = 0;
     double ops_per_vector = 0.0;         // multiply-adds of one H*x (structural)
     double ops_pn = 0.0, ops_pp = 0.0, ops_nn = 0.0;   // its split by term
+    double gathers_pn = 0.0;   // source elements the pn-core kernel gathers per vector (one per neutron
+                               // one-body jump of each source record; each feeds the unit's rows)
     // core-grouped pn term
     std::vector<CoreUnit> cunits;        // sorted by work, largest first
     std::vector<CoreSrc> csrc;
@@ -347,6 +349,8 @@ int run_lanczos(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, double *
                 bs_lanczos_report *rep, const StrengthReq *sreq = nullptr);
 int run_density(bs_ctx *c, const double *F, const double *X, int k, double *rho_host, void *stream);
 int run_gather_ceiling(int device, int where, int k, int rows, double *gflops, void *stream, std::string &err);
+int run_wait_expiry(int device, uint32_t limit, int *err, void *stream, std::string &msg);
+uint32_t tma_wait_limit();   // iteration limit of the kernels' bounded mbarrier waits
 int pipe_variants();
 int core_variants();
 // allocates what launch_hx needs for (k, dtype) outside any stream capture

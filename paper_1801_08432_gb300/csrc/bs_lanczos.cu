@@ -1405,28 +1405,30 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
         for (int i = 0; i < nk; ++i) evals[i] = wT[i];
         for (int i = nk; i < nkeep; ++i) evals[i] = NAN;
     }
-    // Ritz vectors (FP64) and the FP64 refinement of the kept pairs
+    // Ritz vectors (FP64) and the FP64 refinement of the kept pairs, in groups
+    // of at most 8 columns (the widest FP64 block product)
     if (rc == BS_OK && (evecs || o.refine)) {
-        const int kref = nk <= 1 ? 1 : nk <= 2 ? 2 : nk <= 4 ? 4 : 8;
+        if (nk > 64) { nk = 64; }
+        const int gmax = std::min(nk, 8);
+        const int kref = gmax <= 1 ? 1 : gmax <= 2 ? 2 : gmax <= 4 ? 4 : 8;
         double *X = evecs;
         double *Xown = nullptr, *HX = nullptr, *Yd = nullptr, *R = nullptr;
-        if (nk > 8) { nk = 8; }
-        Yd = (double *)alloc((size_t)nT * nk * sizeof(double));
+        Yd = (double *)alloc((size_t)nT * kref * sizeof(double));
         Xown = (double *)alloc((size_t)L.dim * kref * sizeof(double));
         HX = (double *)alloc((size_t)L.dim * kref * sizeof(double));
         R = (double *)alloc(2 * 64 * sizeof(double));
         if (!Yd || !Xown || !HX || !R) { rc = BS_ENOMEM; c->err = "lanczos: allocation failed"; }
-        if (rc == BS_OK) {
-            std::vector<double> Yh((size_t)nT * nk);
+        for (int g0 = 0; rc == BS_OK && g0 < nk; g0 += kref) {
+            const int ng = std::min(kref, nk - g0);
+            std::vector<double> Yh((size_t)nT * ng);
             for (int r = 0; r < nT; ++r)
-                for (int m = 0; m < nk; ++m) Yh[(size_t)r * nk + m] = Z[(size_t)r * nv + m];
+                for (int m = 0; m < ng; ++m) Yh[(size_t)r * ng + m] = Z[(size_t)r * nv + g0 + m];
             cudaMemcpyAsync(Yd, Yh.data(), Yh.size() * sizeof(double), cudaMemcpyHostToDevice, L.s);
             cudaMemsetAsync(Xown, 0, (size_t)L.dim * kref * sizeof(double), L.s);
-            blk_combine<T, K><<<L.ncta, 256, 0, L.s>>>(V, L.bstride, done, Yd, nk, Xown, kref, L.dim);
-        }
-        if (rc == BS_OK && o.refine) {
-            // FP64 H psi, Rayleigh quotients and residuals
-            if ((rc = launch_hx(c, Xown, HX, kref, BS_F64, L.s, c->err)) == BS_OK) {
+            blk_combine<T, K><<<L.ncta, 256, 0, L.s>>>(V, L.bstride, done, Yd, ng, Xown, kref, L.dim);
+            if (o.refine) {
+                // FP64 H psi, Rayleigh quotients and residuals
+                if ((rc = launch_hx(c, Xown, HX, kref, BS_F64, L.s, c->err)) != BS_OK) break;
                 LState L2 = L;
                 L2.bstride = L.dim * kref;
                 L2.padded = false;
@@ -1445,24 +1447,24 @@ static int lanczos_run(bs_ctx *c, const bs_lanczos_opts &o, const void *pivot, d
                 cudaMemcpyAsync(xh.data(), L.C, kref * kref * sizeof(double), cudaMemcpyDeviceToHost, L.s);
                 cudaStreamSynchronize(L.s);
                 std::vector<double> e(kref, 0.0);
-                for (int m = 0; m < nk; ++m) e[m] = xh[m * kref + m] / xx[m * kref + m];   // Rayleigh quotient
+                for (int m = 0; m < ng; ++m) e[m] = xh[m * kref + m] / xx[m * kref + m];   // Rayleigh quotient
                 cudaMemcpyAsync(R, e.data(), kref * sizeof(double), cudaMemcpyHostToDevice, L.s);
-                resid_inplace<<<L.ncta, 256, 0, L.s>>>(HX, Xown, R, nk, kref, L.dim);
+                resid_inplace<<<L.ncta, 256, 0, L.s>>>(HX, Xown, R, ng, kref, L.dim);
                 dots64(HX, HX, L.C);
                 cudaMemcpyAsync(hh.data(), L.C, kref * kref * sizeof(double), cudaMemcpyDeviceToHost, L.s);
                 cudaStreamSynchronize(L.s);
-                for (int m = 0; m < nk; ++m) {
-                    evals[m] = e[m];
-                    if (rep) rep->residual[m] = std::sqrt(std::max(hh[m * kref + m], 0.0) / xx[m * kref + m]);
+                for (int m = 0; m < ng; ++m) {
+                    evals[g0 + m] = e[m];
+                    if (rep) rep->residual[g0 + m] = std::sqrt(std::max(hh[m * kref + m], 0.0) / xx[m * kref + m]);
                 }
             }
+            if (X) {
+                // copy the group's columns to the caller's [dim][nkeep] buffer
+                cudaMemcpy2DAsync(X + g0, (size_t)nkeep * sizeof(double), Xown, (size_t)kref * sizeof(double),
+                                  (size_t)ng * sizeof(double), (size_t)L.dim, cudaMemcpyDeviceToDevice, L.s);
+            }
+            cudaStreamSynchronize(L.s);
         }
-        if (rc == BS_OK && X) {
-            // copy the kept columns to the caller's [dim][nkeep] buffer
-            cudaMemcpy2DAsync(X, (size_t)nkeep * sizeof(double), Xown, (size_t)kref * sizeof(double),
-                              (size_t)nk * sizeof(double), (size_t)L.dim, cudaMemcpyDeviceToDevice, L.s);
-        }
-        cudaStreamSynchronize(L.s);
     }
     stage("Ritz vectors and refinement");
     for (auto &e : ev) cudaEventDestroy(e);
@@ -1654,6 +1656,10 @@ extern "C" int bs_block_dots_noalloc(const void *V, int nb, const void *W, int64
     if (k != 1 && k != 2 && k != 4 && k != 8) return BS_EINVAL;
     if (dtype != BS_F64 && dtype != BS_F32) return BS_EINVAL;
     if ((int64_t)nb * k * k > BS_BLOCK_DOTS_NOALLOC_MAX) return BS_ENOMEM;
+    // the row-slot kernel loads a basis state's k values as 16-byte vectors
+    // once they span 16 bytes or more: refuse pointers it would fault on
+    const uintptr_t elem = (uintptr_t)k * (dtype == BS_F64 ? 8u : 4u), need = elem < 16 ? elem : 16;
+    if ((uintptr_t)V % need || (uintptr_t)W % need || (uintptr_t)C % 8) return BS_EINVAL;
     int dev = 0, nsm = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return BS_ECUDA;
     if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return BS_ECUDA;

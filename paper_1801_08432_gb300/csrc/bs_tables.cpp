@@ -400,6 +400,7 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
     T.csrc.clear();
     T.wc.clear();
     T.n_wtab = 0;
+    T.gathers_pn = 0.0;
     const Species &P = B.sp[0];
     const int ns = (int)B.st.size();
     if (P.nparticles < 1 || T.links.empty()) return;
@@ -514,6 +515,19 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
             }
             x.u.nsrc = (int)x.src.size();
             x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)x.u.dblock].nN;
+            for (int k : by_key) {
+                if (c >> k & 1) continue;
+                const int g = I.ops.group_of_op[(size_t)(i0 * ns + k)];
+                if (g < 0 || I.conj_group[(size_t)g] < 0) continue;
+                int blk, row;
+                locate(c | (1ULL << k), blk, row);
+                if (blk < 0) continue;
+                const int l = link_of(x.u.dblock, blk);
+                if (l < 0) continue;
+                const OneBodyClass &NC = T.n1.cls[(size_t)T.links[(size_t)l].ncls];
+                const int nN = B.blocks[(size_t)x.u.dblock].nN;
+                T.gathers_pn += (double)(T.n1.ptr[NC.ptr_off + nN] - T.n1.ptr[NC.ptr_off]);
+            }
             units.push_back(std::move(x));
         }
     std::stable_sort(units.begin(), units.end(), [](const U &a, const U &b) { return a.cost > b.cost; });

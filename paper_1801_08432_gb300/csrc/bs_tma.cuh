@@ -42,12 +42,12 @@ __device__ __forceinline__ bool bar_try(uint32_t b, uint32_t parity)
     return ok != 0;
 }
 
-// bounded wait; true if it expired
-__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity)
+// bounded wait; true if it expired (after `limit` unsuccessful tries)
+__device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, uint32_t limit = kWaitLimit)
 {
     uint32_t spins = 0;
     while (!bar_try(b, parity))
-        if (++spins > kWaitLimit) return true;
+        if (++spins > limit) return true;
     return false;
 }
 

@@ -6,8 +6,14 @@
     (no proton entries, neutron trace 3) and the strength sum rule;
   * thick restart in a space smaller than one cycle's Krylov space
     (p shell, 1 proton + 1 neutron, dim 10): the run ends with the exact
-    spectrum instead of failing.
+    spectrum instead of failing;
+  * the failure path of the kernels' bounded waits: a wait on an mbarrier
+    that nothing arrives at gives up after its limit, the kernel returns,
+    bs_sync_status reports BS_ETIMEOUT once, and the context still computes
+    H x equal to the oracle's.
 """
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -72,3 +78,30 @@ def test_thick_restart_in_a_tiny_space():
     ev, rep = c.lanczos(p, 2, N.BS_F64, 4, 3, refine=True, nthick=4, max_restarts=5, tol=1e-10)
     assert np.max(np.abs(ev - ev_d[:3])) < 1e-9, (ev, ev_d[:3])
     c.sync_status()
+
+
+@pytest.mark.gpu
+def test_bounded_wait_expiry_is_reported_and_the_context_stays_usable():
+    orbits, spe, tb = I.space("sd")
+    c = N.make(orbits, spe, tb, 2, 2, 0, +1, device=0)
+    o = O.Oracle(orbits, 2, 2, 0, 0).set_interaction(spe, tb)
+    L = N.load()
+    st = torch.cuda.Stream()
+    sp = ctypes.c_void_p(st.cuda_stream)
+    assert L.bs_sync_status(c.h, sp) == 0
+    assert L.bs_debug_wait_expiry(c.h, 0, sp) == -1               # BS_EINVAL: limit
+    assert L.bs_debug_wait_expiry(c.h, (1 << 22) + 1, sp) == -1
+    for _ in range(2):
+        assert L.bs_debug_wait_expiry(c.h, 2000, sp) == 0
+        assert L.bs_sync_status(c.h, sp) == -7                    # BS_ETIMEOUT, read and cleared
+        assert b"wait" in L.bs_last_error(c.h)
+        assert L.bs_sync_status(c.h, sp) == 0
+    assert torch.cuda.synchronize() is None                        # no CUDA error left behind
+    x = I.random_block(o.dim, 4, seed=9)
+    ref = o.spmv(x)
+    xd = torch.from_numpy(x).to("cuda", torch.float64)
+    yd = torch.full_like(xd, float("nan"))
+    c.apply_H(xd, yd, 4, N.BS_F64, st.cuda_stream)
+    c.sync_status(st.cuda_stream)
+    y = yd.cpu().numpy()
+    assert np.max(np.abs(y - ref)) <= 1e-12 * np.max(np.abs(ref))

@@ -4,10 +4,9 @@
     oracle's explicit H (1e-9 MeV) and the Ritz vectors are eigenvectors.
   * FP64, k = 1, sd 4p4n (dim 28,503): equal to the oracle's own Lanczos from
     the same pivot, iteration by iteration the same Krylov space (1e-8 MeV).
-  * FP32-mixed block Lanczos (k = 4, 8) against FP64: after the FP64
-    refinement the converged eigenvalues agree within 1e-4 MeV, with FP64
-    residuals reported.
-  * rotational invariance on the GPU path: the M=1 spectrum sits inside M=0.
+  * rotational invariance on the GPU path: the M=1 spectrum sits inside M=0
+    (FP64, every level checked).
+  * (FP32-mixed levels against the oracle: test_gpu_fp32_vs_oracle.py.)
   * the host eigensolver of T against numpy.
 """
 import numpy as np
@@ -87,17 +86,6 @@ def test_fp64_lanczos_sd44_equals_oracle_lanczos():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("k", [4, 8])
-def test_fp32_mixed_block_lanczos_within_1e4_mev(k):
-    c, o = ctx_oracle("sd", 6, 6, 0, with_oracle=False)
-    ev64, rep64 = c.lanczos(pivot(c.dim, 1, N.BS_F64), 1, N.BS_F64, 300, 5, refine=True)
-    ev32, rep32 = c.lanczos(pivot(c.dim, k, N.BS_F32), k, N.BS_F32, 600 // k, 5, refine=True)
-    assert max(rep64["residual"]) < 1e-6
-    assert max(rep32["residual"]) < 1e-2
-    assert np.max(np.abs(ev32 - ev64)) < 1e-4, (ev32, ev64, rep32)
-
-
-@pytest.mark.gpu
 def test_fp32_block_lanczos_48cr_reproducible_and_within_1e4_mev():
     """48Cr (pf 4p4n, dim 1,963,461), FP32 k = 8, 80 block iterations: two runs
     give bit-identical eigenvalues (the streamed block products keep a fixed
@@ -120,11 +108,17 @@ def test_fp32_block_lanczos_48cr_reproducible_and_within_1e4_mev():
 def test_gpu_j_degeneracy_m1_inside_m0():
     c0, _ = ctx_oracle("sd", 4, 4, 0, with_oracle=False)
     c1, _ = ctx_oracle("sd", 4, 4, 2, with_oracle=False)
-    e0, r0 = c0.lanczos(pivot(c0.dim, 1, N.BS_F64), 1, N.BS_F64, 300, 8, refine=True)
-    e1, r1 = c1.lanczos(pivot(c1.dim, 1, N.BS_F64), 1, N.BS_F64, 300, 4, refine=True)
-    # each converged M=1 level is some M=0 level (J >= 1 states appear in both)
-    for e in e1:
-        assert np.min(np.abs(e0 - e)) < 1e-6 or e > e0[-1]
+    e0, r0 = c0.lanczos(pivot(c0.dim, 1, N.BS_F64), 1, N.BS_F64, 300, 16, refine=True)
+    e1, r1 = c1.lanczos(pivot(c1.dim, 1, N.BS_F64), 1, N.BS_F64, 300, 8, refine=True)
+    assert max(r0["residual"]) < 1e-6 and max(r1["residual"]) < 1e-6
+    # each M=1 level is a distinct M=0 level (J >= 1 states appear in both); the
+    # 16 lowest M=0 levels reach above the 8 lowest M=1 ones, so none escapes
+    assert e1.max() < e0.max()
+    left = list(e0)
+    for e in np.sort(e1):
+        j = int(np.argmin(np.abs(np.array(left) - e)))
+        assert abs(left[j] - e) < 1e-6, (e, left)
+        left.pop(j)
 
 
 @pytest.mark.gpu

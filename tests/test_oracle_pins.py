@@ -18,7 +18,8 @@ fixes, so that a dropped term, a wrong phase or a transposed index fails:
   * assembly: H = H^T, trace from occupation counts, reading in any label order;
   * products: the on-the-fly rows (apply_rows, k = 1 and 4, and the |H| |x|
     bound) equal rows of the explicit matrix times x, and spmv (k = 1, 2, 4,
-    8) equals the matrix times x, on sd 4p4n M = 0 and M = 1 and sd 5p6n,
+    8) and its sampled-row form (spmv_rows) equal the matrix times x, on sd
+    4p4n M = 0 and M = 1 and sd 5p6n,
     random rows plus the first and last rows of every block and of its
     proton rows (the row path is the checker of the large-space GPU tests);
   * Lanczos: dense diagonalization;
@@ -320,6 +321,20 @@ def test_apply_rows_equal_matrix_rows(sd_product_case, k):
     # a single vector passed as [dim] gives [nrows]
     one = o.apply_rows(rows, x[:, 0])
     assert one.shape == (len(rows),) and np.array_equal(one, got[:, 0])
+
+
+@pytest.mark.parametrize("k", [1, 4])
+def test_sampled_stored_rows_equal_matrix_rows(sd_product_case, k):
+    o = sd_product_case
+    rng = np.random.default_rng(30 + k)
+    rows = _boundary_rows(o, rng, 1000)
+    x = rng.standard_normal((o.dim, k))
+    H = o.matrix()
+    nnz = o.build_rows(rows)
+    assert nnz == H[rows].nnz
+    ref = H[rows] @ x
+    got = o.spmv_rows(x)
+    assert np.max(np.abs(got - ref)) <= 1e-13 * np.max(np.abs(ref))
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 8])
