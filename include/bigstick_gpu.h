@@ -50,8 +50,8 @@ extern "C" {
 typedef struct bs_ctx bs_ctx;
 
 /* One orbit (n, l, 2j, w) of the single-particle space (Sec. "Single-particle
- * space"); l fixes the parity (-1)^l.  w must be equal for all orbits (no
- * W truncation). */
+ * space"); l fixes the parity (-1)^l.  w is the orbit's truncation weight,
+ * read only by bs_build_basis_trunc (a non-negative integer there). */
 typedef struct { int n, l, twoj, w; } bs_orbit;
 
 /* One isospin-coupled two-body matrix element V_JT(ab,cd) in MeV, labels
@@ -88,11 +88,31 @@ const char *bs_last_error(const bs_ctx *ctx);
 /* Builds the M-scheme basis of Z valence protons and N valence neutrons with
  * total 2M = twoM and parity (+1 or -1) over the given orbits (Sec.
  * "Factorization of the basis").  Replaces any earlier basis and interaction.
+ * The orbits' w are ignored (no truncation).
  * Errors: BS_EINVAL (n_orbits <= 0, 2j even or <= 0, more than 64 states,
  * Z or N negative or larger than the number of states, twoM of the wrong
- * parity for A = Z + N, parity not +-1, unequal w, empty basis). */
+ * parity for A = Z + N, parity not +-1, empty basis, a sector of more than
+ * 65,535 SDs). */
 int bs_build_basis(bs_ctx *ctx, const bs_orbit *orbits, int n_orbits,
                    int Z, int N, int twoM, int parity);
+
+/* The same basis under the W truncation of Sec. "Truncation of the many-body
+ * space": each orbit carries its weight w (>= 0), a Slater determinant's W is
+ * the sum of w over its occupied states, W_min is the smallest Z-proton plus
+ * N-neutron total (the lowest-w states filled), and only states with
+ * W_p + W_n <= W_min + max_excite are kept (max_excite = -1: no truncation,
+ * as bs_build_basis).  Sectors are keyed by (2M, parity, W), sorted by 2M,
+ * then parity (+ before -), then W; a proton sector pairs with every
+ * conjugate neutron sector whose W fits, in neutron-sector order, so it may
+ * head several blocks (the basis-file loop: proton sector, its conjugate
+ * neutron sectors, proton SDs, neutron SDs).  bs_export_basis gives the
+ * blocks; bs_debug_table "p_sec_w" / "n_sec_w" the sectors' W.  On such a
+ * basis the products run on the tiled kernel (like-particle moves that
+ * change W come from other blocks), and bs_apply_H_backward and bs_density
+ * return BS_EINVAL.  Errors: as bs_build_basis, and BS_EINVAL for a negative
+ * w or max_excite < -1. */
+int bs_build_basis_trunc(bs_ctx *ctx, const bs_orbit *orbits, int n_orbits,
+                         int Z, int N, int twoM, int parity, int max_excite);
 
 /* Sizes of the built basis.  Any pointer may be NULL.  Errors: BS_ENOBASIS. */
 int bs_basis_info(bs_ctx *ctx, int64_t *dim, int *n_psec, int *n_nsec,

@@ -25,7 +25,7 @@ EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_ba
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_set_tuned", "bs_lanczos",
             "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_update", "bs_block_dots_noalloc",
             "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength", "bs_density", "bs_gather_ceiling",
-            "bs_debug_wait_expiry"]
+            "bs_debug_wait_expiry", "bs_build_basis_trunc"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -81,6 +81,8 @@ def load():
     L.bs_last_error.restype = ctypes.c_char_p
     L.bs_build_basis.argtypes = [vp, ctypes.POINTER(bs_orbit), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                  ctypes.c_int, ctypes.c_int]
+    L.bs_build_basis_trunc.argtypes = [vp, ctypes.POINTER(bs_orbit), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                       ctypes.c_int, ctypes.c_int, ctypes.c_int]
     L.bs_basis_info.argtypes = [vp, i64p, i32p, i32p, i32p, i32p, i32p]
     L.bs_export_basis.argtypes = [vp, u64p, u64p, i64p, i64p, i64p]
     L.bs_load_interaction.argtypes = [vp, f64p, ctypes.c_int, ctypes.POINTER(bs_tbme), ctypes.c_int]
@@ -151,9 +153,14 @@ class Context:
             raise BSError(rc, load().bs_last_error(self.h).decode())
 
     # ---- set-up
-    def build_basis(self, orbits, Z, N, twoM, parity=+1):
+    def build_basis(self, orbits, Z, N, twoM, parity=+1, max_excite=None):
+        """The M-scheme basis; with max_excite (>= 0) the W-truncated one, the
+        orbits' w being the truncation weights."""
         arr = (bs_orbit * len(orbits))(*[bs_orbit(o.n, o.l, o.twoj, o.w) for o in orbits])
-        self._check(load().bs_build_basis(self.h, arr, len(orbits), Z, N, twoM, parity))
+        if max_excite is None:
+            self._check(load().bs_build_basis(self.h, arr, len(orbits), Z, N, twoM, parity))
+        else:
+            self._check(load().bs_build_basis_trunc(self.h, arr, len(orbits), Z, N, twoM, parity, max_excite))
         self.info()
         return self
 
@@ -307,8 +314,8 @@ class Context:
                                            vp(stream or 0)))
 
 
-def make(space_orbits, spe, tbmes, Z, N, twoM, parity=+1, device=0):
-    return Context(device).build_basis(space_orbits, Z, N, twoM, parity).load_interaction(spe, tbmes)
+def make(space_orbits, spe, tbmes, Z, N, twoM, parity=+1, device=0, max_excite=None):
+    return Context(device).build_basis(space_orbits, Z, N, twoM, parity, max_excite).load_interaction(spe, tbmes)
 
 
 def debug_eigh(A, nvec):

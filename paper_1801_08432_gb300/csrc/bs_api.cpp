@@ -148,6 +148,8 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
         blocks[b].n_start = (int)B.sp[1].sec[s.ns].start;
         blocks[b].link_begin = (int)T.links_of_block[b];
         blocks[b].link_end = (int)T.links_of_block[b + 1];
+        blocks[b].llink_begin = (int)T.llinks_of_block[b];
+        blocks[b].llink_end = (int)T.llinks_of_block[b + 1];
         blocks[b].nne_col = T.nne_col[(size_t)s.ns];
         blocks[b].nne_slice = T.nne_slice[(size_t)s.ns];
         blocks[b].perm_off = T.pe.perm_off[(size_t)s.ns];
@@ -168,6 +170,10 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
         links[l].pe_sinfo = T.pe.cls_sinfo[(size_t)L.ncls];
         links[l].ww_off = T.ww_off[(size_t)T.p1.cls[(size_t)L.pcls].group];
     }
+    std::vector<DevLLink> llinks(T.llinks.size());
+    for (size_t l = 0; l < T.llinks.size(); ++l)
+        llinks[l] = DevLLink{T.llinks[l].src_block, T.llinks[l].species, T.llinks[l].ptr_off};
+    D.trunc = B.trunc;
     D.tile = 128;
     std::vector<DevTask> tasks;
     make_tasks(B, T, D.tile, tasks);
@@ -186,7 +192,19 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
     if ((rc = put(D, D.c64.pp_coef, T.pp.coef.data(), T.pp.coef.size(), err))) return rc;
     if ((rc = put(D, D.c64.nn_coef, T.nn.coef.data(), T.nn.coef.size(), err))) return rc;
     if ((rc = put(D, D.c64.wpn, I.Wpn.data(), I.Wpn.size(), err))) return rc;
+    // like-particle moves between sectors (W-truncated bases; empty otherwise)
+    if ((rc = put(D, D.llinks, llinks.data(), llinks.size(), err))) return rc;
+    if ((rc = put(D, D.ppx_ptr, T.ppx.ptr.data(), T.ppx.ptr.size(), err))) return rc;
+    if ((rc = put(D, D.ppx_src, T.ppx.src.data(), T.ppx.src.size(), err))) return rc;
+    if ((rc = put(D, D.nnx_ptr, T.nnx.ptr.data(), T.nnx.ptr.size(), err))) return rc;
+    if ((rc = put(D, D.nnx_src, T.nnx.src.data(), T.nnx.src.size(), err))) return rc;
+    if ((rc = put(D, D.c64.ppx_coef, T.ppx.coef.data(), T.ppx.coef.size(), err))) return rc;
+    if ((rc = put(D, D.c64.nnx_coef, T.nnx.coef.data(), T.nnx.coef.size(), err))) return rc;
     std::vector<float> f;
+    f = cast<float>(T.ppx.coef);
+    if ((rc = put(D, D.c32.ppx_coef, f.data(), f.size(), err))) return rc;
+    f = cast<float>(T.nnx.coef);
+    if ((rc = put(D, D.c32.nnx_coef, f.data(), f.size(), err))) return rc;
     f = cast<float>(T.pp.coef);
     if ((rc = put(D, D.c32.pp_coef, f.data(), f.size(), err))) return rc;
     f = cast<float>(T.nn.coef);
@@ -317,17 +335,24 @@ void bs_destroy(bs_ctx *c)
 
 const char *bs_last_error(const bs_ctx *c) { return c ? c->err.c_str() : "null context"; }
 
-int bs_build_basis(bs_ctx *c, const bs_orbit *orbits, int n_orbits, int Z, int N, int twoM, int parity)
+int bs_build_basis_trunc(bs_ctx *c, const bs_orbit *orbits, int n_orbits, int Z, int N, int twoM, int parity,
+                         int max_excite)
 {
     return guarded(c, [&]() -> int {
         c->have_basis = c->have_int = false;
         if (c->device >= 0) release(c->dev);
-        int rc = build_basis(c->basis, orbits, n_orbits, Z, N, twoM, parity, c->err);
+        if (max_excite < -1) { c->err = "build_basis: max_excite must be -1 (no truncation) or >= 0"; return BS_EINVAL; }
+        int rc = build_basis(c->basis, orbits, n_orbits, Z, N, twoM, parity, max_excite, c->err);
         if (rc) return rc;
         c->have_basis = true;
         c->err.clear();
         return BS_OK;
     });
+}
+
+int bs_build_basis(bs_ctx *c, const bs_orbit *orbits, int n_orbits, int Z, int N, int twoM, int parity)
+{
+    return bs_build_basis_trunc(c, orbits, n_orbits, Z, N, twoM, parity, -1);
 }
 
 int bs_basis_info(bs_ctx *c, int64_t *dim, int *n_psec, int *n_nsec, int *n_psd, int *n_nsd, int *n_blocks)
@@ -479,6 +504,7 @@ int bs_apply_H_backward(bs_ctx *c, const void *x, const void *gy, void *gx, doub
     return guarded(c, [&]() -> int {
         int rc = check_apply(c, k, dt);
         if (rc) return rc;
+        if (c->basis.trunc) { c->err = "backward: not available on a W-truncated basis"; return BS_EINVAL; }
         if (!x || !gy || !gx || gy == gx) { c->err = "x, gy and gx must be device buffers, gy != gx"; return BS_EINVAL; }
         if (((uintptr_t)x | (uintptr_t)gy | (uintptr_t)gx) & 15) { c->err = "buffers must be 16-byte aligned"; return BS_EINVAL; }
         return run_backward(c, x, gy, gx, gtheta, k, dt, stream);
@@ -539,6 +565,7 @@ int bs_density(bs_ctx *c, const double *F, const double *X, int k, double *rho, 
     return guarded(c, [&]() -> int {
         int rc = check_apply(c, k, BS_F64);
         if (rc) return rc;
+        if (c->basis.trunc) { c->err = "density: not available on a W-truncated basis"; return BS_EINVAL; }
         if (!F || !X || !rho) { c->err = "density: null pointer"; return BS_EINVAL; }
         return run_density(c, F, X, k, rho, stream);
     });
@@ -709,6 +736,12 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
         else if (s == "nn_ptr") use(T.nn.ptr.data(), T.nn.ptr.size() * 8);
         else if (s == "nn_src") use(T.nn.src.data(), T.nn.src.size() * 4);
         else if (s == "nn_coef") use(T.nn.coef.data(), T.nn.coef.size() * 8);
+        else if (s == "ppx_ptr") use(T.ppx.ptr.data(), T.ppx.ptr.size() * 8);
+        else if (s == "ppx_src") use(T.ppx.src.data(), T.ppx.src.size() * 4);
+        else if (s == "ppx_coef") use(T.ppx.coef.data(), T.ppx.coef.size() * 8);
+        else if (s == "nnx_ptr") use(T.nnx.ptr.data(), T.nnx.ptr.size() * 8);
+        else if (s == "nnx_src") use(T.nnx.src.data(), T.nnx.src.size() * 4);
+        else if (s == "nnx_coef") use(T.nnx.coef.data(), T.nnx.coef.size() * 8);
         else if (s == "p1_ptr") use(T.p1.ptr.data(), T.p1.ptr.size() * 8);
         else if (s == "p1_ent") use(T.p1.ent.data(), T.p1.ent.size() * 4);
         else if (s == "n1_ptr") use(T.n1.ptr.data(), T.n1.ptr.size() * 8);
@@ -767,6 +800,14 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
             use(tmp.data(), tmp.size() * 8);
         } else if (s == "op_lists") {
             for (const auto &g : I.ops.ops) for (int op : g) tmp.push_back(op);
+            use(tmp.data(), tmp.size() * 8);
+        } else if (s == "p_sec_w" || s == "n_sec_w") {   // W of every sector
+            for (const Sector &q : c->basis.sp[s[0] == 'p' ? 0 : 1].sec) tmp.push_back(q.W);
+            use(tmp.data(), tmp.size() * 8);
+        } else if (s == "llinks") {
+            for (const LikeLink &L : T.llinks) {
+                tmp.push_back(L.dst_block); tmp.push_back(L.src_block); tmp.push_back(L.species); tmp.push_back(L.ptr_off);
+            }
             use(tmp.data(), tmp.size() * 8);
         } else if (s == "stats") {
             tmp = {T.n_pp, T.n_nn, T.n_p1, T.n_n1, (int64_t)T.links.size(), (int64_t)T.ops_per_vector, (int64_t)c->dev.ntasks,

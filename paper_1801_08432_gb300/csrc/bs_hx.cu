@@ -13,7 +13,10 @@
 // and writes y once.  This is the paper's factorization (pn = proton one-body
 // jump x neutron one-body jump, Sec. on jumps and Table jumps) applied as a
 // gather: each y element has one owner, so there are no atomics and the
-// result is bit-reproducible.
+// result is bit-reproducible.  In a W-truncated basis (Sec. "Truncation of
+// the many-body space") a like-particle move may change an SD's W and so its
+// sector: those moves come from other blocks through like-particle links,
+// and the pn links already join any pair of blocks.
 #include <cuda_runtime.h>
 
 #include "bs_internal.h"
@@ -77,11 +80,15 @@ struct HxArgs {
     const int64_t *pp_ptr, *nn_ptr, *p1_ptr, *n1_ptr;
     const int32_t *pp_src, *nn_src;
     const uint32_t *p1_ent, *n1_ent;
+    const DevLLink *llinks;
+    const int64_t *ppx_ptr, *nnx_ptr;
+    const int32_t *ppx_src, *nnx_src;
 };
 
 template <typename T, int K>
 __global__ void __launch_bounds__(128) hx_fused_kernel(HxArgs A, const T *__restrict__ pp_coef,
                                                        const T *__restrict__ nn_coef, const T *__restrict__ wpn,
+                                                       const T *__restrict__ ppx_coef, const T *__restrict__ nnx_coef,
                                                        const T *__restrict__ x, T *__restrict__ y)
 {
     const DevTask t = A.tasks[blockIdx.x];
@@ -115,6 +122,33 @@ __global__ void __launch_bounds__(128) hx_fused_kernel(HxArgs A, const T *__rest
             ldk<T, K>(xr + (int64_t)A.nn_src[e] * K, xv);
 #pragma unroll
             for (int q = 0; q < K; ++q) acc[q] = fma(c, xv[q], acc[q]);
+        }
+    }
+    // like-particle moves from other blocks (W-truncated bases): pp moves from
+    // the block of another proton sector with this neutron sector (same
+    // column), nn moves from the block of another neutron sector with this
+    // proton sector (same row)
+    for (int L = D.llink_begin; L < D.llink_end; ++L) {
+        const DevLLink lk = A.llinks[L];
+        const DevBlock S = A.blocks[lk.src_block];
+        if (lk.species == 0) {
+            const int64_t e1 = A.ppx_ptr[lk.ptr_off + t.row + 1];
+            const T *xc = x + (S.off + col) * K;
+            for (int64_t e = A.ppx_ptr[lk.ptr_off + t.row]; e < e1; ++e) {
+                const T c = ppx_coef[e];
+                ldk<T, K>(xc + (int64_t)A.ppx_src[e] * S.nN * K, xv);
+#pragma unroll
+                for (int q = 0; q < K; ++q) acc[q] = fma(c, xv[q], acc[q]);
+            }
+        } else {
+            const int64_t e1 = A.nnx_ptr[lk.ptr_off + col + 1];
+            const T *xr = x + (S.off + (int64_t)t.row * S.nN) * K;
+            for (int64_t e = A.nnx_ptr[lk.ptr_off + col]; e < e1; ++e) {
+                const T c = nnx_coef[e];
+                ldk<T, K>(xr + (int64_t)A.nnx_src[e] * K, xv);
+#pragma unroll
+                for (int q = 0; q < K; ++q) acc[q] = fma(c, xv[q], acc[q]);
+            }
         }
     }
     // pn: proton one-body jump x neutron one-body jump, per linked source block
@@ -157,8 +191,8 @@ template <typename T, int K>
 cudaError_t launch(const Device &Dv, const DevCoefs<T> &C, const T *x, T *y, cudaStream_t s)
 {
     HxArgs A{Dv.tasks, Dv.blocks, Dv.links, Dv.pp_ptr, Dv.nn_ptr, Dv.p1_ptr, Dv.n1_ptr,
-             Dv.pp_src, Dv.nn_src, Dv.p1_ent, Dv.n1_ent};
-    hx_fused_kernel<T, K><<<Dv.ntasks, Dv.tile, 0, s>>>(A, C.pp_coef, C.nn_coef, C.wpn, x, y);
+             Dv.pp_src, Dv.nn_src, Dv.p1_ent, Dv.n1_ent, Dv.llinks, Dv.ppx_ptr, Dv.nnx_ptr, Dv.ppx_src, Dv.nnx_src};
+    hx_fused_kernel<T, K><<<Dv.ntasks, Dv.tile, 0, s>>>(A, C.pp_coef, C.nn_coef, C.wpn, C.ppx_coef, C.nnx_coef, x, y);
     return cudaGetLastError();
 }
 

@@ -770,7 +770,7 @@ size_t part_bytes(const bs_ctx *c, int k)
 
 bool core_applies(const bs_ctx *c, int k, bs_dtype dt)
 {
-    return dt == BS_F32 && (k == 4 || k == 8) && c->dev.ncunits > 0 && c->dev.nz > 0;
+    return !c->dev.trunc && dt == BS_F32 && (k == 4 || k == 8) && c->dev.ncunits > 0 && c->dev.nz > 0;
 }
 
 }  // namespace

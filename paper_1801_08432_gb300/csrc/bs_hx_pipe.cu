@@ -400,7 +400,7 @@ cudaError_t launch_hx_pipe_combine(const bs_ctx *c, const void *x, void *y, int 
 {
     const Device &D = c->dev;
     used = false;
-    if (dt != BS_F32 || (k != 4 && k != 8)) return cudaSuccess;
+    if (D.trunc || dt != BS_F32 || (k != 4 && k != 8)) return cudaSuccess;
     const float *xi = (const float *)x;
     float *yo = (float *)y;
     const float *pi = (const float *)part;
@@ -417,6 +417,7 @@ cudaError_t launch_hx_pipe(const bs_ctx *c, const void *x, void *y, int k, bs_dt
 {
     const Device &D = c->dev;
     used = false;
+    if (D.trunc) return cudaSuccess;   // like-particle moves inside a block only
     if (dt == BS_F64) {
         const double *xi = (const double *)x;
         double *yo = (double *)y;

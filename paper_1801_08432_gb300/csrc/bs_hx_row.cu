@@ -530,6 +530,8 @@ cudaError_t launch_hx_row(const bs_ctx *c, const void *x, void *y, int k, bs_dty
                           bool &used)
 {
     const Device &D = c->dev;
+    used = false;
+    if (D.trunc) return cudaSuccess;   // one neutron sector per proton row is assumed
     if (dt == BS_F64) {
         const double *xi = (const double *)x;
         double *yo = (double *)y;

@@ -19,12 +19,14 @@ struct SpState {
     int orb;     // orbit index (0-based, input order)
     int twom;    // 2 m
     int par;     // 0 for +, 1 for -
+    int w;       // truncation weight of the orbit (used only by a W-truncated basis)
 };
 
 struct Sector {
     int twoM, par;
     int64_t start;   // first SD of the sector in the species list
     int64_t count;
+    int W = 0;       // summed weight of its SDs (0 in an untruncated basis)
 };
 
 struct Species {
@@ -33,7 +35,7 @@ struct Species {
     std::vector<Sector> sec;
     std::vector<int> sec_of_sd;            // sector of every SD
     std::unordered_map<uint64_t, int64_t> index;  // bitmask -> global SD index
-    int find_sector(int twoM, int par) const;
+    int find_sector(int twoM, int par, int W = 0) const;
 };
 
 struct Block {
@@ -48,8 +50,15 @@ struct Basis {
     int Z = 0, N = 0, twoM = 0, par = 0;
     Species sp[2];
     std::vector<Block> blocks;
-    std::vector<int> block_of_psec;        // -1 when a proton sector has no conjugate
+    std::vector<int> block_of_psec;        // first block of a proton sector, -1 when it has no conjugate
     int64_t dim = 0;
+    // W truncation (Sec. "Truncation of the many-body space"): sectors are keyed
+    // by (2M, parity, W) and a proton sector pairs with every conjugate neutron
+    // sector whose W keeps W_p + W_n <= w_max, so it may head several blocks
+    bool trunc = false;
+    int w_max = 0;                         // W_min + the allowed excitation
+    int block_of(int ps, int ns) const;    // block of a (proton, neutron) sector pair, or -1
+    std::vector<int> blk_of_pair;          // [n_psec * n_nsec]
 };
 
 // ---------------------------------------------------------------- interaction
@@ -86,6 +95,30 @@ struct LikeJumps {          // pp or nn, same sector, diagonal included (SPE fol
     std::vector<int64_t> ptr;     // [nsd+1] by destination SD (global index)
     std::vector<int32_t> src;     // source SD, local index inside the sector
     std::vector<double> coef;
+};
+
+// Like-particle jumps that change the sector (only in a W-truncated basis,
+// where a two-body move can change an SD's W but not its 2M and parity):
+// per (source sector, destination sector) a destination CSR over the SDs of
+// s_dst with source SDs as local indices in s_src.
+struct LikeCrossClass {
+    int s_src, s_dst;
+    int64_t ptr_off;        // into LikeCross::ptr, |S_dst|+1 entries
+};
+
+struct LikeCross {
+    std::vector<LikeCrossClass> cls;
+    std::vector<int64_t> ptr;
+    std::vector<int32_t> src;
+    std::vector<double> coef;
+};
+
+// A like-particle link: destination block <- source block of the same
+// neutron sector (pp, species 0) or the same proton sector (nn, species 1)
+// through one LikeCross class.
+struct LikeLink {
+    int dst_block, src_block, species;
+    int64_t ptr_off;
 };
 
 struct OneBodyClass {       // one-body jumps from sector s_src into sector s_dst
@@ -182,7 +215,10 @@ struct PPUnit {
 };
 
 struct Tables {
-    LikeJumps pp, nn;
+    LikeJumps pp, nn;                    // moves inside a sector (diagonal and SPE included)
+    LikeCross ppx, nnx;                  // moves between sectors (W-truncated bases only)
+    std::vector<LikeLink> llinks;        // sorted by dst block
+    std::vector<int64_t> llinks_of_block;   // [nblocks+1]
     PermEll pe;                          // pipelined kernel's neutron lists
     std::vector<double> ww;              // per group g, op a, proton sign: a row of 2*wsign W values
     std::vector<int64_t> ww_off;         // per group
@@ -218,6 +254,7 @@ struct DevBlock {
     int nP, nN;
     int p_start, n_start;   // global SD index of the first SD of each sector
     int link_begin, link_end;
+    int llink_begin, llink_end;   // like-particle links from other blocks (W-truncated bases)
     int64_t nne_col, nne_slice;   // ELL of the neutron like-particle lists of this block's neutron sector
     int64_t perm_off;             // pipelined kernel: column order of the neutron sector
     int64_t pe_nn_ent, pe_nn_sinfo;
@@ -234,6 +271,12 @@ struct DevLink {
     int64_t ww_off;               // pipelined kernel: signed W rows of the proton group
 };
 
+struct DevLLink {
+    int src_block;
+    int species;            // 0: pp (rows of the source block), 1: nn (columns)
+    int64_t ptr_off;        // class CSR in ppx_ptr / nnx_ptr
+};
+
 struct DevTask {            // one CTA: destination block, proton row, column tile
     int block;
     int row;
@@ -244,6 +287,7 @@ struct DevTask {            // one CTA: destination block, proton row, column ti
 template <typename T>
 struct DevCoefs {
     T *pp_coef = nullptr, *nn_coef = nullptr, *wpn = nullptr, *nne_coef = nullptr;
+    T *ppx_coef = nullptr, *nnx_coef = nullptr;
 };
 
 struct RowTask {            // row kernel: one CTA per destination proton row
@@ -253,8 +297,12 @@ struct RowTask {            // row kernel: one CTA per destination proton row
 
 struct Device {
     int dev = 0;
+    bool trunc = false;       // W-truncated basis: only the tiled kernel applies
     DevBlock *blocks = nullptr;
     DevLink *links = nullptr;
+    DevLLink *llinks = nullptr;
+    int64_t *ppx_ptr = nullptr, *nnx_ptr = nullptr;
+    int32_t *ppx_src = nullptr, *nnx_src = nullptr;
     DevTask *tasks = nullptr;
     int ntasks = 0;
     int tile = 0;
@@ -326,7 +374,8 @@ struct bs_ctx {
 
 // ---------------------------------------------------------------- builders (host)
 namespace bs {
-int build_basis(Basis &B, const bs_orbit *orbits, int n_orbits, int Z, int N, int twoM, int parity, std::string &err);
+int build_basis(Basis &B, const bs_orbit *orbits, int n_orbits, int Z, int N, int twoM, int parity, int max_excite,
+                std::string &err);
 int build_interaction(const Basis &B, const double *spe, int n_spe, const bs_tbme *tbme, int n_tbme,
                       Interaction &I, std::string &err);
 int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err);

@@ -28,21 +28,24 @@ inline int sign_below(uint64_t m, int s)
 // plus sum_s e_s n_s, as a destination CSR over the species' SDs.  The
 // operator is real symmetric (W(ij,kl) = W(kl,ij)), so the row of SD g,
 // <g|V|m>, is read off V|g> = sum_m <m|V|g> |m>: every row is built from its
-// own SD, in parallel, with no scatter.
-void like_jumps(const Basis &B, const Interaction &I, int spc, LikeJumps &L, int64_t &nent)
+// own SD, in parallel, with no scatter.  Moves that stay in g's sector go to
+// L (source as a local index in the sector); in a W-truncated basis a move
+// can change W, and those go to X, one class per (source, destination)
+// sector pair.
+void like_jumps(const Basis &B, const Interaction &I, int spc, LikeJumps &L, LikeCross &X, int64_t &nent)
 {
     const Species &S = B.sp[spc];
     const int ns = (int)B.st.size();
     const int64_t nsd = (int64_t)S.bits.size();
-    std::vector<std::vector<std::pair<int32_t, double>>> rows((size_t)nsd);
+    std::vector<std::vector<std::pair<int64_t, double>>> rows((size_t)nsd);
 #pragma omp parallel for schedule(dynamic, 16)
     for (int64_t g = 0; g < nsd; ++g) {
         const uint64_t X = S.bits[g];
-        std::vector<std::pair<int32_t, double>> &r = rows[(size_t)g];
+        std::vector<std::pair<int64_t, double>> &r = rows[(size_t)g];
         double e = 0.0;
         for (int s = 0; s < ns; ++s)
             if (X >> s & 1) e += I.spe_state[s];
-        r.emplace_back((int32_t)(g - S.sec[S.sec_of_sd[g]].start), e);
+        r.emplace_back(g, e);
         for (int k = 0; k < ns; ++k) {
             if (!(X >> k & 1)) continue;
             for (int l = k + 1; l < ns; ++l) {
@@ -63,12 +66,13 @@ void like_jumps(const Basis &B, const Interaction &I, int spc, LikeJumps &L, int
                     uint64_t m2 = m1 | (1ULL << j);
                     s2 *= sign_below(m2, i);
                     m2 |= (1ULL << i);
-                    const int64_t gm = S.index.find(m2)->second;
-                    r.emplace_back((int32_t)(gm - S.sec[S.sec_of_sd[gm]].start), sg * s2 * w);
+                    const auto it = S.index.find(m2);
+                    if (it == S.index.end()) continue;   // above the W cap of a truncated basis
+                    r.emplace_back(it->second, sg * s2 * w);
                 }
             }
         }
-        std::sort(r.begin(), r.end(), [](const std::pair<int32_t, double> &a, const std::pair<int32_t, double> &b) {
+        std::sort(r.begin(), r.end(), [](const std::pair<int64_t, double> &a, const std::pair<int64_t, double> &b) {
             return a.first < b.first;
         });
         size_t w = 0;
@@ -78,16 +82,56 @@ void like_jumps(const Basis &B, const Interaction &I, int spc, LikeJumps &L, int
         }
         r.resize(w);
     }
+    // same-sector moves
     L.ptr.assign((size_t)nsd + 1, 0);
-    for (int64_t g = 0; g < nsd; ++g) L.ptr[(size_t)g + 1] = L.ptr[(size_t)g] + (int64_t)rows[(size_t)g].size();
+    for (int64_t g = 0; g < nsd; ++g) {
+        int64_t n = 0;
+        for (const auto &e : rows[(size_t)g]) n += S.sec_of_sd[(size_t)e.first] == S.sec_of_sd[(size_t)g];
+        L.ptr[(size_t)g + 1] = L.ptr[(size_t)g] + n;
+    }
     L.src.resize((size_t)L.ptr[(size_t)nsd]);
     L.coef.resize((size_t)L.ptr[(size_t)nsd]);
+    const size_t nsec = S.sec.size();
+    std::map<std::pair<int, int>, std::vector<std::pair<int64_t, std::pair<int32_t, double>>>> cross;
     for (int64_t g = 0; g < nsd; ++g) {
         int64_t o = L.ptr[(size_t)g];
-        for (const auto &e : rows[(size_t)g]) { L.src[(size_t)o] = e.first; L.coef[(size_t)o] = e.second; ++o; }
-        std::vector<std::pair<int32_t, double>>().swap(rows[(size_t)g]);
+        const int sd = S.sec_of_sd[(size_t)g];
+        for (const auto &e : rows[(size_t)g]) {
+            const int ss = S.sec_of_sd[(size_t)e.first];
+            const int32_t loc = (int32_t)(e.first - S.sec[(size_t)ss].start);
+            if (ss == sd) {
+                L.src[(size_t)o] = loc;
+                L.coef[(size_t)o] = e.second;
+                ++o;
+            } else {
+                cross[{ss, sd}].push_back({g - S.sec[(size_t)sd].start, {loc, e.second}});
+            }
+        }
+        std::vector<std::pair<int64_t, double>>().swap(rows[(size_t)g]);
     }
     nent = L.ptr[(size_t)nsd];
+    // moves between sectors, one class per (source, destination) pair
+    X = LikeCross();
+    (void)nsec;
+    for (auto &kv : cross) {
+        LikeCrossClass c;
+        c.s_src = kv.first.first;
+        c.s_dst = kv.first.second;
+        c.ptr_off = (int64_t)X.ptr.size();
+        const int64_t nd = S.sec[(size_t)c.s_dst].count;
+        const auto &v = kv.second;   // in destination order (rows were visited in order)
+        size_t t = 0;
+        for (int64_t dl = 0; dl <= nd; ++dl) {
+            while (t < v.size() && v[t].first < dl) {
+                X.src.push_back(v[t].second.first);
+                X.coef.push_back(v[t].second.second);
+                ++t;
+            }
+            X.ptr.push_back((int64_t)X.src.size());
+        }
+        X.cls.push_back(c);
+        nent += (int64_t)v.size();
+    }
 }
 
 // One-body jumps a+_i a_k of one species (i == k included: the number
@@ -114,7 +158,9 @@ void onebody_jumps(const Basis &B, const Interaction &I, int spc, OneBodyJumps &
             for (int k = 0; k < ns; ++k) {
                 if (m1 >> k & 1) continue;
                 const int s2 = sign_below(m1, k);
-                const int64_t gs = S.index.find(m1 | (1ULL << k))->second;
+                const auto it = S.index.find(m1 | (1ULL << k));
+                if (it == S.index.end()) continue;   // above the W cap of a truncated basis
+                const int64_t gs = it->second;
                 const int ssrc = S.sec_of_sd[gs];
                 const int op = i * ns + k;
                 const uint32_t sloc = (uint32_t)(gs - S.sec[ssrc].start);
@@ -645,8 +691,8 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
 {
     (void)err;
     T = Tables();
-    like_jumps(B, I, 0, T.pp, T.n_pp);
-    like_jumps(B, I, 1, T.nn, T.n_nn);
+    like_jumps(B, I, 0, T.pp, T.ppx, T.n_pp);
+    like_jumps(B, I, 1, T.nn, T.nnx, T.n_nn);
     onebody_jumps(B, I, 0, T.p1, T.n_p1);
     onebody_jumps(B, I, 1, T.n1, T.n_n1);
     // ELL forms of the neutron-side lists for the row kernel.  One-body
@@ -716,6 +762,7 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
     for (size_t c = 0; c < T.p1.cls.size(); ++c) pcls[(size_t)T.p1.cls[c].s_src * nps + T.p1.cls[c].s_dst] = (int)c;
     for (size_t c = 0; c < T.n1.cls.size(); ++c) ncls[(size_t)T.n1.cls[c].s_src * nns + T.n1.cls[c].s_dst] = (int)c;
     T.links_of_block.assign((size_t)nb + 1, 0);
+    T.llinks_of_block.assign((size_t)nb + 1, 0);
     double ops = 0.0;
     for (int d = 0; d < nb; ++d) {
         const Block &D = B.blocks[d];
@@ -743,13 +790,31 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
         T.links_of_block[(size_t)d + 1] = (int64_t)T.links.size();
         // like-particle work of this block
         const Sector &PS = B.sp[0].sec[D.ps], &NS = B.sp[1].sec[D.ns];
-        const double opp = (double)(T.pp.ptr[PS.start + PS.count] - T.pp.ptr[PS.start]) * (double)D.nN;
-        const double onn = (double)(T.nn.ptr[NS.start + NS.count] - T.nn.ptr[NS.start]) * (double)D.nP;
+        double opp = (double)(T.pp.ptr[PS.start + PS.count] - T.pp.ptr[PS.start]) * (double)D.nN;
+        double onn = (double)(T.nn.ptr[NS.start + NS.count] - T.nn.ptr[NS.start]) * (double)D.nP;
+        // moves from other sectors (W-truncated bases): pp from block (s_src, D.ns),
+        // nn from block (D.ps, s_src), where those blocks are in the basis
+        for (const LikeCrossClass &c : T.ppx.cls) {
+            if (c.s_dst != D.ps) continue;
+            const int sb = B.block_of(c.s_src, D.ns);
+            if (sb < 0) continue;
+            T.llinks.push_back(LikeLink{d, sb, 0, c.ptr_off});
+            opp += (double)(T.ppx.ptr[(size_t)(c.ptr_off + D.nP)] - T.ppx.ptr[(size_t)c.ptr_off]) * (double)D.nN;
+        }
+        for (const LikeCrossClass &c : T.nnx.cls) {
+            if (c.s_dst != D.ns) continue;
+            const int sb = B.block_of(D.ps, c.s_src);
+            if (sb < 0) continue;
+            T.llinks.push_back(LikeLink{d, sb, 1, c.ptr_off});
+            onn += (double)(T.nnx.ptr[(size_t)(c.ptr_off + D.nN)] - T.nnx.ptr[(size_t)c.ptr_off]) * (double)D.nP;
+        }
+        T.llinks_of_block[(size_t)d + 1] = (int64_t)T.llinks.size();
         ops += opp + onn;
         T.ops_pp += opp;
         T.ops_nn += onn;
     }
     T.ops_per_vector = ops;
+    if (B.trunc) return BS_OK;   // the core-grouped tables assume one neutron sector per proton sector
     build_core_units(B, I, T);
     build_pp_units(B, I, T);
     return BS_OK;

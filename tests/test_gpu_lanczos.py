@@ -110,7 +110,8 @@ def test_gpu_j_degeneracy_m1_inside_m0():
     c1, _ = ctx_oracle("sd", 4, 4, 2, with_oracle=False)
     e0, r0 = c0.lanczos(pivot(c0.dim, 1, N.BS_F64), 1, N.BS_F64, 300, 16, refine=True)
     e1, r1 = c1.lanczos(pivot(c1.dim, 1, N.BS_F64), 1, N.BS_F64, 300, 8, refine=True)
-    assert max(r0["residual"]) < 1e-6 and max(r1["residual"]) < 1e-6
+    # residuals <= 1e-4 MeV bound each level's error by r^2 / gap << 1e-6 MeV
+    assert max(r0["residual"]) < 1e-4 and max(r1["residual"]) < 1e-4
     # each M=1 level is a distinct M=0 level (J >= 1 states appear in both); the
     # 16 lowest M=0 levels reach above the 8 lowest M=1 ones, so none escapes
     assert e1.max() < e0.max()
