@@ -249,6 +249,7 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
     D.nz = D.ncunits ? B.sp[0].nparticles : 0;
     if ((rc = put(D, D.cunits, T.cunits.data(), T.cunits.size(), err))) return rc;
     if ((rc = put(D, D.csrc, T.csrc.data(), T.csrc.size(), err))) return rc;
+    if ((rc = put(D, D.core_ent, T.pe.core_ent.data(), T.pe.core_ent.size(), err))) return rc;
     f = cast<float>(T.wc);
     if ((rc = put(D, D.wc32, f.data(), f.size(), err))) return rc;
     // largest list block one column tile of the pn-core kernel stages (18 or 10 warps of 32 columns)
@@ -771,6 +772,7 @@ int bs_debug_table(bs_ctx *c, const char *name, void *out, int64_t *nbytes)
         else if (s == "core_units") use(T.cunits.data(), T.cunits.size() * sizeof(CoreUnit));
         else if (s == "core_src") use(T.csrc.data(), T.csrc.size() * sizeof(CoreSrc));
         else if (s == "wc") use(T.wc.data(), T.wc.size() * 8);
+        else if (s == "core_ent") use(T.pe.core_ent.data(), T.pe.core_ent.size() * 4);
         else if (s == "pp_units") use(T.ppunits.data(), T.ppunits.size() * sizeof(PPUnit));
         else if (s == "pps_row") use(T.pps_row.data(), T.pps_row.size() * 4);
         else if (s == "pps_w") use(T.pps_w.data(), T.pps_w.size() * 8);

@@ -38,57 +38,31 @@ cudaError_t launch_hx_pipe_combine(const bs_ctx *c, const void *x, void *y, int 
 
 namespace {
 
-// K values of element `jn` of a staged row.  For K = 8 (two 16-byte chunks)
-// the chunk loaded first is the entry's rotation bit r (chosen at build time
-// to spread a quarter warp's loads over the bank groups); the values are put
-// back in order with selects.
-// The same as float2 pairs (v[j] = components 2j, 2j+1) for the packed FMA.
-template <int K>
-__device__ __forceinline__ void ldx2(const float *row, uint32_t en, float2 (&v)[K / 2])
-{
-    const float *e = row + (size_t)(en & 0xFFFFu) * K;
-    if constexpr (K == 8) {
-        const uint32_t r = en >> 31;
-        const float4 a = *reinterpret_cast<const float4 *>(e + 4 * r);
-        const float4 b = *reinterpret_cast<const float4 *>(e + 4 * (1u - r));
-        v[0] = make_float2(r ? b.x : a.x, r ? b.y : a.y);
-        v[1] = make_float2(r ? b.z : a.z, r ? b.w : a.w);
-        v[2] = make_float2(r ? a.x : b.x, r ? a.y : b.y);
-        v[3] = make_float2(r ? a.z : b.z, r ? a.w : b.w);
-    } else {
-        const float4 a = *reinterpret_cast<const float4 *>(e);
-        v[0] = make_float2(a.x, a.y);
-        v[1] = make_float2(a.z, a.w);
-    }
-}
-
-template <int K>
-__device__ __forceinline__ void ldx(const float *row, uint32_t en, float (&v)[K])
-{
-    const float *e = row + (size_t)(en & 0xFFFFu) * K;
-    if constexpr (K == 8) {
-        const uint32_t r = en >> 31;
-        const float4 a = *reinterpret_cast<const float4 *>(e + 4 * r);
-        const float4 b = *reinterpret_cast<const float4 *>(e + 4 * (1u - r));
-        v[0] = r ? b.x : a.x; v[1] = r ? b.y : a.y; v[2] = r ? b.z : a.z; v[3] = r ? b.w : a.w;
-        v[4] = r ? a.x : b.x; v[5] = r ? a.y : b.y; v[6] = r ? a.z : b.z; v[7] = r ? a.w : b.w;
-    } else {
-        const float4 a = *reinterpret_cast<const float4 *>(e);
-        v[0] = a.x; v[1] = a.y; v[2] = a.z; v[3] = a.w;
-    }
-}
-
 // One list entry of one destination column: the gathered element of the
 // staged source row times the weights of the entry's weight row, for the
 // unit's first R destination rows (its rows are packed to the front; R = 4
-// also serves units with three).
+// also serves units with three).  Entries are src | W row << 16.  For K = 8
+// the lane reads the element's 16-byte chunks in its own fixed order (XA
+// and XB are the staged row shifted to the lane's first and second chunk),
+// so the accumulators hold the components in that order and are put back
+// in order once, at the store.
 template <int K, int R = 4>
-__device__ __forceinline__ void core_step(const float *Xs, const float *Wt, uint32_t en, uint32_t flip,
+__device__ __forceinline__ void core_step(const float *XA, const float *XB, const float *Wt, uint32_t en,
                                           float2 (&acc)[4][K / 2])
 {
-    const float *wr = Wt + 4 * (((en >> 16) & 0x7FFFu) ^ flip);
+    const float *wr = Wt + 4 * (en >> 16);
+    const uint32_t src = en & 0xFFFFu;
     float2 xv[K / 2];
-    ldx2<K>(Xs, en, xv);
+    {
+        const float4 a = *reinterpret_cast<const float4 *>(XA + (size_t)src * K);
+        xv[0] = make_float2(a.x, a.y);
+        xv[1] = make_float2(a.z, a.w);
+        if constexpr (K == 8) {
+            const float4 b = *reinterpret_cast<const float4 *>(XB + (size_t)src * K);
+            xv[2] = make_float2(b.x, b.y);
+            xv[3] = make_float2(b.z, b.w);
+        }
+    }
     // two correctly rounded fused multiply-adds per instruction
     if constexpr (R == 1) {
         const float w = *wr;
@@ -133,7 +107,6 @@ struct SlotRing {
 struct CoreArgs {
     const CoreUnit *units;
     const CoreSrc *src;
-    const DevBlock *blocks;
     const int32_t *perm;
     const int32_t *sinfo;
     const uint32_t *ent;
@@ -188,10 +161,22 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
         // the warp's 32 lanes fetch the metadata of 32 sources at a time
         SlotRing rg;
         int gb = 0, ground = 0;   // list buffer and its use number for the next group (g + 1)
+        // the unit record is read one unit ahead
+        int hn = 0, hN = 0;
+        int64_t hs = 0;
+        if (blockIdx.x < A.nunits) {
+            hn = A.units[blockIdx.x].nsrc;
+            hN = A.units[blockIdx.x].nN;
+            hs = A.units[blockIdx.x].src0;
+        }
         for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
-            const int nsrc = A.units[u].nsrc;
-            const int64_t src0 = A.units[u].src0;
-            const int nN = A.blocks[A.units[u].dblock].nN;
+            const int nsrc = hn, nN = hN;
+            const int64_t src0 = hs;
+            if (u + (int)gridDim.x < A.nunits) {
+                hn = A.units[u + gridDim.x].nsrc;
+                hN = A.units[u + gridDim.x].nN;
+                hs = A.units[u + gridDim.x].src0;
+            }
             const int nsl = (nN + 31) / 32;
             const int ntile = (nN + C - 1) / C;
             for (int tile = 0; tile < ntile; ++tile) {
@@ -252,7 +237,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                             }
                         }
                         if (__shfl_sync(0xffffffffu, bad, 0)) {
-                            if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
+                            if (lane == 0) {
+                                atomicExch(A.err, BS_ETIMEOUT);
+                                drain_ring(full0, A.S, (int64_t)rg.round * A.S + rg.s);
+                            }
                             return;
                         }
                         if (newg) {
@@ -272,13 +260,23 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     // ---------------- consumers
     SlotRing rg;
     int cb = -1;   // list buffer of the current group (none yet)
+    const int rot = K == 8 ? (lane >> 2) & 1 : 0;   // this lane's first 16-byte chunk of an element
+    // the unit record, read one unit ahead (consumed only in the next unit)
+    int hn = 0, hN = 0, hp = 0, hd1 = -1, hd2 = -1;
+    int64_t ho = 0;
+    if (blockIdx.x < A.nunits) {
+        const CoreUnit *U = A.units + blockIdx.x;
+        hn = U->nsrc; hN = U->nN; hp = U->perm_off; ho = U->doff; hd1 = U->drow[1]; hd2 = U->drow[2];
+    }
     for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
-        const int nsrc = A.units[u].nsrc;
-        const DevBlock D = A.blocks[A.units[u].dblock];
+        const int nsrc = hn, nN = hN, perm_off = hp;
+        const int64_t doff = ho;
         // destination rows of the unit (packed to the front): 1, 2 or more
-        const int nrow = A.units[u].drow[1] < 0 ? 1 : A.units[u].drow[2] < 0 ? 2 : 4;
-        const int nN = D.nN;
-        const int64_t doff = D.off;
+        const int nrow = hd1 < 0 ? 1 : hd2 < 0 ? 2 : 4;
+        if (u + (int)gridDim.x < A.nunits) {
+            const CoreUnit *U = A.units + u + gridDim.x;
+            hn = U->nsrc; hN = U->nN; hp = U->perm_off; ho = U->doff; hd1 = U->drow[1]; hd2 = U->drow[2];
+        }
         const int nsl = (nN + 31) / 32;
         const int ntile = (nN + C - 1) / C;
         for (int tile = 0; tile < ntile; ++tile) {
@@ -288,9 +286,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             const bool hasA = CPT == 2 ? sa <= sb : sa < nst;
             const bool hasB = CPT == 2 && sa < sb;
             const int posA = tile * C + sa * 32 + lane, posB = tile * C + sb * 32 + lane;
-            const int colA = hasA && posA < nN ? A.perm[D.perm_off + posA] : -1;
-            const int colB = hasB && posB < nN ? A.perm[D.perm_off + posB] : -1;
+            const int colA = hasA && posA < nN ? A.perm[perm_off + posA] : -1;
+            const int colB = hasB && posB < nN ? A.perm[perm_off + posB] : -1;
             // packed accumulators: acc[p][j] holds components 2j, 2j+1 of destination row p
+            // (for K = 8 in the lane's chunk order)
             float2 accA[4][K / 2], accB[4][K / 2];
 #pragma unroll
             for (int p = 0; p < 4; ++p)
@@ -309,7 +308,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 const float *Wt = Xs + A.row_stride;
                 const CoreSrc *cs = reinterpret_cast<const CoreSrc *>(Wt + A.wtab);
                 const int64_t sbase = cs->sinfo_base;
-                const uint32_t wtab = cs->wtab;
+                const float *XA = Xs + 4 * rot, *XB = Xs + 4 * (rot ^ 1);
                 if (sbase != prev) {
                     // a new group: release the previous group's list buffer, read this one
                     __syncwarp();
@@ -325,30 +324,29 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                     lstB = lb0 + (hasB ? si[2 * sb] : 0);
                 }
                 // entries straight from the staged lists (32 lanes, 128 contiguous bytes per step)
-                const uint32_t flip = (wtab >> 31) ? A.ws : 0u;   // sign of a_k on c + k: swap the +W / -W halves
                 if constexpr (CPT == 1) {
                     // one slice: the plain loop, for the unit's number of rows
                     if (nrow == 1) {
-#pragma unroll 2
-                        for (int v = 0; v < la; ++v) core_step<K, 1>(Xs, Wt, lstA[32 * v], flip, accA);
+#pragma unroll 4
+                        for (int v = 0; v < la; ++v) core_step<K, 1>(XA, XB, Wt, lstA[32 * v], accA);
                     } else if (nrow == 2) {
-#pragma unroll 2
-                        for (int v = 0; v < la; ++v) core_step<K, 2>(Xs, Wt, lstA[32 * v], flip, accA);
+#pragma unroll 4
+                        for (int v = 0; v < la; ++v) core_step<K, 2>(XA, XB, Wt, lstA[32 * v], accA);
                     } else {
 #pragma unroll 2
-                        for (int v = 0; v < la; ++v) core_step<K, 4>(Xs, Wt, lstA[32 * v], flip, accA);
+                        for (int v = 0; v < la; ++v) core_step<K, 4>(XA, XB, Wt, lstA[32 * v], accA);
                     }
                 } else {
                     const int lm = min(la, lb);
                     int v = 0;
                     for (; v < lm; ++v) {
-                        core_step<K>(Xs, Wt, lstA[32 * v], flip, accA);
-                        core_step<K>(Xs, Wt, lstB[32 * v], flip, accB);
+                        core_step<K>(XA, XB, Wt, lstA[32 * v], accA);
+                        core_step<K>(XA, XB, Wt, lstB[32 * v], accB);
                     }
 #pragma unroll 2
-                    for (int va = v; va < la; ++va) core_step<K>(Xs, Wt, lstA[32 * va], flip, accA);
+                    for (int va = v; va < la; ++va) core_step<K>(XA, XB, Wt, lstA[32 * va], accA);
 #pragma unroll 2
-                    for (int vb = v; vb < lb; ++vb) core_step<K>(Xs, Wt, lstB[32 * vb], flip, accB);
+                    for (int vb = v; vb < lb; ++vb) core_step<K>(XA, XB, Wt, lstB[32 * vb], accB);
                 }
                 __syncwarp();
                 if (lane == 0) bar_arrive(empty0 + 8u * s);
@@ -364,8 +362,10 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                     float o[K];
 #pragma unroll
                     for (int qq = 0; qq < K / 2; ++qq) {
-                        o[2 * qq] = sg * acc[p][qq].x;
-                        o[2 * qq + 1] = sg * acc[p][qq].y;
+                        // K = 8: the lane's chunk order back to component order
+                        const float2 a = K == 8 ? (rot ? acc[p][qq ^ 2] : acc[p][qq]) : acc[p][qq];
+                        o[2 * qq] = sg * a.x;
+                        o[2 * qq + 1] = sg * a.y;
                     }
                     pst<float, K>(part + (int64_t)(meta & 255) * A.part_stride + (doff + (int64_t)drow * nN + col) * K, o);
                 }
@@ -380,7 +380,6 @@ struct PPArgs {
     const PPUnit *units;
     const int32_t *srow;
     const float *w;        // kPPG weights per source
-    const DevBlock *blocks;
     int *err;
     int nunits;
     int S;
@@ -415,28 +414,55 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     __syncthreads();
 
     if (warp == NW) {
-        if (lane != 0) return;
+        // lane 0 issues the copies; the warp's lanes fetch the source rows of
+        // 32 sources at a time, so no copy waits on a dependent global load
         SlotRing rg;
+        // the unit record is read one unit ahead
+        int hn = 0, hN = 0;
+        int64_t hs = 0, ho = 0;
+        if (blockIdx.x < A.nunits) {
+            hn = A.units[blockIdx.x].nsrc; hN = A.units[blockIdx.x].nN;
+            hs = A.units[blockIdx.x].src0; ho = A.units[blockIdx.x].doff;
+        }
         for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
-            const PPUnit U = A.units[u];
-            const DevBlock D = A.blocks[U.dblock];
-            const int ntile = (D.nN + C - 1) / C;
-            const uint32_t bytes = (uint32_t)(D.nN * K * (int)sizeof(float));
+            const int nsrc = hn, nN = hN;
+            const int64_t src0 = hs, doff = ho;
+            if (u + (int)gridDim.x < A.nunits) {
+                hn = A.units[u + gridDim.x].nsrc; hN = A.units[u + gridDim.x].nN;
+                hs = A.units[u + gridDim.x].src0; ho = A.units[u + gridDim.x].doff;
+            }
+            const int ntile = (nN + C - 1) / C;
+            const uint32_t bytes = (uint32_t)(nN * K * (int)sizeof(float));
             const uint32_t wbytes = (uint32_t)(kPPG * sizeof(float));
             for (int tile = 0; tile < ntile; ++tile)
-                for (int q = 0; q < U.nsrc; ++q, rg.next(A.S)) {
-                    const int s = rg.s;
-                    const int round = rg.round;
-                    if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) {
-                        atomicExch(A.err, BS_ETIMEOUT);
-                        return;
+                for (int q0 = 0; q0 < nsrc; q0 += 32) {
+                    const int32_t myrow = q0 + lane < nsrc ? A.srow[src0 + q0 + lane] : 0;
+                    const int cnt = min(32, nsrc - q0);
+                    for (int j = 0; j < cnt; ++j, rg.next(A.S)) {
+                        const int32_t row = __shfl_sync(0xffffffffu, myrow, j);
+                        int bad = 0;
+                        if (lane == 0) {
+                            const int s = rg.s;
+                            const int round = rg.round;
+                            if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) {
+                                bad = 1;
+                            } else {
+                                const uint32_t fb = full0 + 8u * s;
+                                float *dst = slots + (size_t)s * A.slot_elems;
+                                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                                bar_expect_tx(fb, bytes + wbytes);
+                                bulk_copy(su32(dst), x + (doff + (int64_t)row * nN) * K, bytes, fb);
+                                bulk_copy(su32(dst + A.row_stride), A.w + (src0 + q0 + j) * kPPG, wbytes, fb);
+                            }
+                        }
+                        if (__shfl_sync(0xffffffffu, bad, 0)) {
+                            if (lane == 0) {
+                                atomicExch(A.err, BS_ETIMEOUT);
+                                drain_ring(full0, A.S, (int64_t)rg.round * A.S + rg.s);
+                            }
+                            return;
+                        }
                     }
-                    const uint32_t fb = full0 + 8u * s;
-                    float *dst = slots + (size_t)s * A.slot_elems;
-                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                    bar_expect_tx(fb, bytes + wbytes);
-                    bulk_copy(su32(dst), x + (D.off + (int64_t)A.srow[U.src0 + q] * D.nN) * K, bytes, fb);
-                    bulk_copy(su32(dst + A.row_stride), A.w + (U.src0 + q) * kPPG, wbytes, fb);
                 }
         }
         return;
@@ -445,10 +471,17 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     constexpr int E = K * (int)sizeof(float);
     const int rot = E == 32 ? ((lane >> 2) & 1) : 0;
     SlotRing rg;
+    // the unit record is read one unit ahead (its rows and partials only at the store)
+    int hn = 0, hN = 0;
+    int64_t ho = 0;
+    if (blockIdx.x < A.nunits) { hn = A.units[blockIdx.x].nsrc; hN = A.units[blockIdx.x].nN; ho = A.units[blockIdx.x].doff; }
     for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
-        const PPUnit U = A.units[u];
-        const DevBlock D = A.blocks[U.dblock];
-        const int nN = D.nN;
+        const int nsrc = hn, nN = hN;
+        const int64_t doff = ho;
+        if (u + (int)gridDim.x < A.nunits) {
+            hn = A.units[u + gridDim.x].nsrc; hN = A.units[u + gridDim.x].nN; ho = A.units[u + gridDim.x].doff;
+        }
+        const PPUnit *U = A.units + u;
         const int ntile = (nN + C - 1) / C;
         for (int tile = 0; tile < ntile; ++tile) {
             const int col = tile * C + warp * 32 + lane;
@@ -459,7 +492,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             for (int p = 0; p < kPPG; ++p)
 #pragma unroll
                 for (int q = 0; q < K / 2; ++q) acc[p][q] = make_float2(0.0f, 0.0f);
-            for (int q = 0; q < U.nsrc; ++q, rg.next(A.S)) {
+            for (int q = 0; q < nsrc; ++q, rg.next(A.S)) {
                 const int s = rg.s;
                 if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)rg.round & 1u))) {
                     if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
@@ -489,7 +522,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             if (col < nN) {
 #pragma unroll
                 for (int p = 0; p < kPPG; ++p) {
-                    if (U.drow[p] < 0) continue;
+                    const int drow = U->drow[p];
+                    if (drow < 0) continue;
                     float o[K];
 #pragma unroll
                     for (int qq = 0; qq < K / 2; ++qq) {
@@ -497,7 +531,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                         o[2 * qq + 1] = acc[p][qq].y;
                     }
                     prot_fix<float, K>(o, rot);
-                    pst<float, K>(part + (int64_t)U.part[p] * A.part_stride + (D.off + (int64_t)U.drow[p] * nN + col) * K, o);
+                    pst<float, K>(part + (int64_t)U->part[p] * A.part_stride + (doff + (int64_t)drow * nN + col) * K, o);
                 }
             }
         }
@@ -505,6 +539,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
 }
 
 struct NNArgs {
+    int stage;           // 1: results staged in shared memory, then summed and stored in column order
     const int2 *tasks;
     const DevBlock *blocks;
     const int32_t *perm;
@@ -527,14 +562,19 @@ struct NNArgs {
 // TMA bulk copies on one mbarrier (bounded wait).  Output: y itself when the
 // other terms' partial vectors are given (their ordered sum, then this term:
 // the order of hx_sum_partials, so the result is bit-identical to a separate
-// summation pass), else a partial vector.
+// summation pass), else a partial vector.  Threads own columns in the
+// sector's list order; with A.stage the tile's results go to shared memory
+// first, so that the partial vectors are read and y written in column
+// order (whole 128-byte lines per quarter warp instead of scattered 32-byte
+// elements).
 template <int K, int R, int NW, int MINB>
 __global__ void __launch_bounds__(NW * 32, MINB)
     hx_nn_rows_kernel(NNArgs A, const float *__restrict__ x, float *__restrict__ out)
 {
     extern __shared__ __align__(128) unsigned char smem[];
     float *rows = reinterpret_cast<float *>(smem);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(rows + (size_t)R * A.row_stride);
+    float *res = rows + (size_t)R * A.row_stride;   // used when A.stage
+    uint64_t *bar = reinterpret_cast<uint64_t *>(res + (A.stage ? (size_t)R * A.row_stride : 0));
     const uint32_t b0 = su32(bar);
     const int2 task = A.tasks[blockIdx.x];
     const DevBlock D = A.blocks[task.x];
@@ -557,8 +597,13 @@ __global__ void __launch_bounds__(NW * 32, MINB)
     float pd[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) pd[r] = r < nr ? A.pdiag[D.p_start + r0 + r] : 0.0f;
-    if (__any_sync(0xffffffffu, bar_wait(b0, 0u))) {
-        if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
+    // one decision for the whole CTA, so that no thread leaves before the
+    // barrier of the staged epilogue
+    if (__syncthreads_or(bar_wait(b0, 0u) ? 1 : 0)) {
+        if (threadIdx.x == 0) {
+            atomicExch(A.err, BS_ETIMEOUT);
+            (void)bar_wait(b0, 0u);   // the rows' copies: no copy left in flight at exit
+        }
         return;
     }
     const int rot = prot<float, K>(lane);
@@ -580,16 +625,28 @@ __global__ void __launch_bounds__(NW * 32, MINB)
             for (int q = 0; q < K / 2; ++q) acc[r][q] = make_float2(pd[r] * xv[2 * q], pd[r] * xv[2 * q + 1]);
         }
         const int64_t base = D.pe_nn_ent + off + lane;
-#pragma unroll 2
-        for (int v = 0; v < lmax; ++v) {
-            const float c = A.coef[base + 32 * (int64_t)v];
-            const int s = A.src[base + 32 * (int64_t)v];
-            const float2 c2 = make_float2(c, c);
+        // the list streams from global memory (L2): NB entries are loaded at a
+        // time, all before any is used, so that NB loads are in flight
+        constexpr int NB = (K == 8 || R == 2) ? 4 : 8;
+        for (int v0 = 0; v0 < lmax; v0 += NB) {
+            float cb[NB];
+            int sb[NB];
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                pld<float, K>(rows + (size_t)r * A.row_stride, s, rot, xv);
+            for (int j = 0; j < NB; ++j) {
+                const bool in = v0 + j < lmax;
+                cb[j] = in ? A.coef[base + 32 * (int64_t)(v0 + j)] : 0.0f;
+                sb[j] = in ? A.src[base + 32 * (int64_t)(v0 + j)] : 0;
+            }
 #pragma unroll
-                for (int q = 0; q < K / 2; ++q) acc[r][q] = __ffma2_rn(c2, make_float2(xv[2 * q], xv[2 * q + 1]), acc[r][q]);
+            for (int j = 0; j < NB; ++j) {
+                if (v0 + j >= lmax) break;
+                const float2 c2 = make_float2(cb[j], cb[j]);
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    pld<float, K>(rows + (size_t)r * A.row_stride, sb[j], rot, xv);
+#pragma unroll
+                    for (int q = 0; q < K / 2; ++q) acc[r][q] = __ffma2_rn(c2, make_float2(xv[2 * q], xv[2 * q + 1]), acc[r][q]);
+                }
             }
         }
         if (col < 0) continue;
@@ -603,22 +660,78 @@ __global__ void __launch_bounds__(NW * 32, MINB)
                 o[2 * q + 1] = acc[r][q].y;
             }
             prot_fix<float, K>(o, rot);
+            if (A.stage) {
+                pst<float, K>(res + (size_t)r * A.row_stride + (size_t)col * K, o);
+                continue;
+            }
             const int64_t e = (D.off + (int64_t)(r0 + r) * nN + col) * K;
             if (A.nz > 0) {
+                // the partials' sum in the order t = 0 .. nz - 1, with the loads of
+                // four partials in flight at a time (the adds stay in order)
+                float4 a[K / 4];
 #pragma unroll
-                for (int q = 0; q < K; q += 4) {   // four components at a time: few live registers
-                    float4 a = __ldg(reinterpret_cast<const float4 *>(A.part + e + q));
-                    for (int t = 1; t < A.nz; ++t) {
-                        const float4 v = __ldg(reinterpret_cast<const float4 *>(A.part + (int64_t)t * A.pstride + e + q));
-                        a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+                for (int q = 0; q < K / 4; ++q) a[q] = __ldg(reinterpret_cast<const float4 *>(A.part + e) + q);
+                int t = 1;
+                for (; t + 4 <= A.nz; t += 4) {
+                    float4 v[4][K / 4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int q = 0; q < K / 4; ++q)
+                            v[u][q] = __ldg(reinterpret_cast<const float4 *>(A.part + (int64_t)(t + u) * A.pstride + e) + q);
+#pragma unroll
+                    for (int u = 0; u < 4; ++u)
+#pragma unroll
+                        for (int q = 0; q < K / 4; ++q) {
+                            a[q].x += v[u][q].x; a[q].y += v[u][q].y; a[q].z += v[u][q].z; a[q].w += v[u][q].w;
+                        }
+                }
+                for (; t < A.nz; ++t) {
+#pragma unroll
+                    for (int q = 0; q < K / 4; ++q) {
+                        const float4 v = __ldg(reinterpret_cast<const float4 *>(A.part + (int64_t)t * A.pstride + e) + q);
+                        a[q].x += v.x; a[q].y += v.y; a[q].z += v.z; a[q].w += v.w;
                     }
-                    o[q] = a.x + o[q];
-                    o[q + 1] = a.y + o[q + 1];
-                    o[q + 2] = a.z + o[q + 2];
-                    o[q + 3] = a.w + o[q + 3];
+                }
+#pragma unroll
+                for (int q = 0; q < K / 4; ++q) {
+                    o[4 * q] = a[q].x + o[4 * q];
+                    o[4 * q + 1] = a[q].y + o[4 * q + 1];
+                    o[4 * q + 2] = a[q].z + o[4 * q + 2];
+                    o[4 * q + 3] = a[q].w + o[4 * q + 3];
                 }
             }
             pst<float, K>(out + e, o);
+        }
+    }
+    if (!A.stage) return;
+    __syncthreads();
+    // column order, 16 bytes per thread (a warp reads 512 contiguous bytes of
+    // every partial): the other terms' partials in the order t = 0 .. nz - 1,
+    // then this term (the same additions as the direct path)
+    const int n4 = nN * (K / 4);   // float4 units of one row
+    for (int r = 0; r < nr; ++r) {
+        const int64_t e0 = (D.off + (int64_t)(r0 + r) * nN) * K;
+        for (int i = threadIdx.x; i < n4; i += NW * 32) {
+            float4 o = *reinterpret_cast<const float4 *>(res + (size_t)r * A.row_stride + 4 * (size_t)i);
+            const int64_t e = e0 + 4 * (int64_t)i;
+            if (A.nz > 0) {
+                float4 a = __ldg(reinterpret_cast<const float4 *>(A.part + e));
+                int t = 1;
+                for (; t + 4 <= A.nz; t += 4) {
+                    float4 v[4];
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) v[u] = __ldg(reinterpret_cast<const float4 *>(A.part + (int64_t)(t + u) * A.pstride + e));
+#pragma unroll
+                    for (int u = 0; u < 4; ++u) { a.x += v[u].x; a.y += v[u].y; a.z += v[u].z; a.w += v[u].w; }
+                }
+                for (; t < A.nz; ++t) {
+                    const float4 v = __ldg(reinterpret_cast<const float4 *>(A.part + (int64_t)t * A.pstride + e));
+                    a.x += v.x; a.y += v.y; a.z += v.z; a.w += v.w;
+                }
+                o.x = a.x + o.x; o.y = a.y + o.y; o.z = a.z + o.z; o.w = a.w + o.w;
+            }
+            *reinterpret_cast<float4 *>(out + e) = o;
         }
     }
 }
@@ -671,14 +784,17 @@ cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStrea
     const Device &Dv = ctx->dev;
     constexpr int NW = 18;
     const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
-    const size_t smem = (size_t)R * row_stride * sizeof(float) + 16;
-    used = smem <= 200 * 1024;   // wider sectors than NW * 32 columns run in column tiles
+    const size_t rows_bytes = (size_t)R * row_stride * sizeof(float);
+    used = rows_bytes + 16 <= 200 * 1024;   // wider sectors than NW * 32 columns run in column tiles
     if (!used || !x) return cudaSuccess;
+    // the results staged beside the rows where both fit one SM's 227 KB
+    const int stage = 2 * rows_bytes + 16 <= 227 * 1024 ? 1 : 0;
+    const size_t smem = (stage ? 2 : 1) * rows_bytes + 16;
     auto kern = hx_nn_rows_kernel<K, R, NW, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    NNArgs A{R == 2 ? Dv.nntasks2 : Dv.nntasks4, Dv.blocks, Dv.pe_perm, Dv.pe_nn_src, Dv.pe_nn_coef32, Dv.pe_nn_sinfo,
-             Dv.pdiag32, Dv.err, row_stride, part, part ? nz : 0, ctx->basis.dim * K};
+    NNArgs A{stage, R == 2 ? Dv.nntasks2 : Dv.nntasks4, Dv.blocks, Dv.pe_perm, Dv.pe_nn_src, Dv.pe_nn_coef32,
+             Dv.pe_nn_sinfo, Dv.pdiag32, Dv.err, row_stride, part, part ? nz : 0, ctx->basis.dim * K};
     kern<<<R == 2 ? Dv.nnntasks2 : Dv.nnntasks4, NW * 32, smem, s>>>(A, x, out);
     return cudaGetLastError();
 }
@@ -723,7 +839,7 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, Dv.dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (NW + 1) * 32, smem)) != cudaSuccess) return e;
     const int grid = std::max(1, std::min(Dv.ncunits, nsm * std::max(per, 1)));
-    CoreArgs A{Dv.cunits, Dv.csrc, Dv.blocks, Dv.pe_perm, Dv.pe_sinfo, Dv.pe_ent, Dv.err, Dv.ncunits, S,
+    CoreArgs A{Dv.cunits, Dv.csrc, Dv.pe_perm, Dv.pe_sinfo, Dv.core_ent, Dv.err, Dv.ncunits, S,
                row_stride, wtab, slot_elems, list_elems, nlb, (uint32_t)Dv.wsign, (int64_t)ctx->basis.dim * K};
     kern<<<grid, (NW + 1) * 32, smem, s>>>(A, Dv.wc32, x, part);
     return cudaGetLastError();
@@ -747,7 +863,7 @@ cudaError_t launch_pp_t(const bs_ctx *ctx, const float *x, float *part, cudaStre
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, Dv.dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (NW + 1) * 32, smem)) != cudaSuccess) return e;
     const int grid = std::max(1, std::min(Dv.nppunits, nsm * std::max(per, 1)));
-    PPArgs A{Dv.ppunits, Dv.pps_row, Dv.pps_w32, Dv.blocks, Dv.err, Dv.nppunits, S, row_stride, slot_elems,
+    PPArgs A{Dv.ppunits, Dv.pps_row, Dv.pps_w32, Dv.err, Dv.nppunits, S, row_stride, slot_elems,
              (int64_t)ctx->basis.dim * K};
     kern<<<grid, (NW + 1) * 32, smem, s>>>(A, x, part);
     return cudaGetLastError();

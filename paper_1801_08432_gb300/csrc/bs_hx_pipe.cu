@@ -156,6 +156,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, NW <= 8 ? 2 : 1) hx_pipe_kernel
             const int round = c / A.S;
             if (round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(round - 1) & 1u)) {
                 atomicExch(A.err, BS_ETIMEOUT);
+                drain_ring(full0, A.S, c);
                 return;
             }
             T *dst = slots + (size_t)s * A.slot_elems;

@@ -288,6 +288,17 @@ __global__ void __launch_bounds__(NT) hx_row_kernel(RowArgs A, const T *__restri
             return false;
         }
     };
+    // after a wait on `slot` ran out: wait once more (bounded) for that
+    // slot's copies, so that none is in flight when the CTA exits
+    auto drain_rows = [&](int slot) {
+        if constexpr (kBulk) {
+            const uint32_t ub = ubar0 + 8u * (uint32_t)slot;
+            const uint32_t par = ((phase >> slot) & 1u) ^ 1u;   // the phase wait_rows gave up on
+            uint32_t spins = 0;
+            while (!mbar_try_wait(ub, par) && ++spins <= kWaitLimit) {
+            }
+        }
+    };
 
     // ---- pp: coalesced reads of whole rows of x
     {
@@ -316,7 +327,10 @@ __global__ void __launch_bounds__(NT) hx_row_kernel(RowArgs A, const T *__restri
         if (tid == 0) *next_slice = 0;
         const bool hung = wait_rows(0);
         if (__syncthreads_or(hung)) {
-            if (tid == 0) atomicExch(A.err, BS_ETIMEOUT);
+            if (tid == 0) {
+                atomicExch(A.err, BS_ETIMEOUT);
+                drain_rows(0);
+            }
             return;
         }
         const int nslices = (nN + 31) >> 5;
@@ -389,7 +403,10 @@ __global__ void __launch_bounds__(NT) hx_row_kernel(RowArgs A, const T *__restri
         if (tid == 0) *next_slice = 0;
         const bool hung = wait_rows(slot);
         if (__syncthreads_or(hung)) {
-            if (tid == 0) atomicExch(A.err, BS_ETIMEOUT);
+            if (tid == 0) {
+                atomicExch(A.err, BS_ETIMEOUT);
+                drain_rows(slot);
+            }
             // let the other slot's copy land before the CTA exits (bounded)
             if (nxt.L < D.link_end) wait_rows(slot ^ 1);
             return;

@@ -164,6 +164,9 @@ struct PermEll {
     std::vector<int32_t> perm;          // per sector: position -> column (sector offset in perm_off)
     std::vector<int64_t> perm_off;      // per neutron sector
     std::vector<uint32_t> ent;          // one-body entries, packed like Tables::n1e, plus a rotation bit (31)
+    std::vector<uint32_t> core_ent;     // the same lists at the same positions for the pn-core kernel:
+                                        // src | W row << 16, in a step order scheduled for the fixed
+                                        // per-lane chunk order of that kernel (no rotation bit)
     std::vector<int32_t> sinfo;         // per class and slice: (entry offset from class base, lmax)
     std::vector<int64_t> cls_ent, cls_sinfo;   // per one-body class: base of its entries / slice info
     std::vector<int32_t> nn_src;        // like-particle lists in the same order
@@ -187,12 +190,16 @@ struct CoreUnit {
     int64_t src0;          // first slot in Tables::csrc
     int drow[4];           // destination proton row (local in the sector), -1 if absent
     int meta[4];           // rank t of i in r (0..Z-1) | 256 if the sign of a+_i on c is -1
+    int nN;                // the destination block's columns, its column order (PermEll offset)
+    int perm_off;          //   and first basis index: copied here so that the kernel reads one
+    int64_t doff;          //   record per unit
 };
 
 struct CoreSrc {           // 32 bytes: staged with its source row
     int64_t x_elem;        // first basis index of the source row c + k (block offset + row * nN)
     int32_t nN;            // its length (the source block's neutron sector)
-    uint32_t wtab;         // W table (chunk, k) | 1 << 31 if the sign of a_k on c + k is -1
+    uint32_t wtab;         // W table 2 (chunk, k) + f, f = 1 if the sign of a_k on c + k is -1 (that
+                           // table has the +W and -W halves swapped); bit 31 repeats f
     int64_t ent_base;      // neutron lists of the link dst block <- src block: first entry of the
     int64_t sinfo_base;    // class in PermEll::ent and its per-slice (offset, longest list)
 };
@@ -212,6 +219,9 @@ struct PPUnit {
     int64_t src0;          // first source in Tables::pps_row / pps_w
     int drow[kPPG];        // destination proton row, -1 if absent
     int part[kPPG];        // partial vector of the destination row (Z + pair rank)
+    int nN;                // the destination block's columns and first basis index (one record per unit)
+    int pad;
+    int64_t doff;
 };
 
 struct Tables {
@@ -328,6 +338,7 @@ struct Device {
     // core-grouped pn kernel
     CoreUnit *cunits = nullptr;
     CoreSrc *csrc = nullptr;
+    uint32_t *core_ent = nullptr;
     float *wc32 = nullptr;
     int ncunits = 0, nz = 0;
     int64_t core_list_max[2] = {0, 0};   // largest list block of one column tile (18, 10 warps), entries

@@ -574,7 +574,10 @@ __device__ __forceinline__ bool rs_produce(const T *V, int64_t bstride, int nb, 
         const uint32_t bytes = (uint32_t)((min((int64_t)CE, nel - e0) * (int64_t)sizeof(T) + 15) / 16 * 16);
         for (int b = -1; b < nb; ++b, q.next()) {
             // stage s was used S tiles ago: wait until every consumer warp released it
-            if (q.uses >= S && bar_wait(empty0 + 8u * q.s, q.ph ^ 1u)) return false;
+            if (q.uses >= S && bar_wait(empty0 + 8u * q.s, q.ph ^ 1u)) {
+                drain_ring(full0, S, q.uses);   // no copy left in flight at exit
+                return false;
+            }
             // order the consumers' reads of the stage (generic proxy, observed
             // through the empty barrier) before the bulk copy's writes (async
             // proxy); without it the copy can overwrite data still being read

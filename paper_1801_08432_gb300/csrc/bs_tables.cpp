@@ -277,6 +277,54 @@ void bank_schedule_rot(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
     lists.swap(out);
 }
 
+// Step order of the neutron one-body lists of one 32-column slice for the
+// pn-core kernel, whose lanes read a 32-byte element's two 16-byte chunks in
+// a fixed per-lane order (lane bit 2 picks the chunk first read), so that the
+// registers need no per-entry reordering.  A quarter warp's first loads then
+// avoid each other's bank groups when its lanes 0-3 (and 4-7) use source
+// columns of distinct residues mod 4; at every step the greedy picks, lane by
+// lane (longest remaining list first), the entry that adds the fewest
+// conflicts, counting a new chunk address in an occupied bank group by its
+// occupancy + 1 and a new weight row (residue mod 8) half as much.  Shorter
+// lists are padded with `pad`.  Output: lists[lane] of length lmax.
+void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
+{
+    size_t lmax = 0;
+    for (auto &l : lists) lmax = std::max(lmax, l.size());
+    std::vector<std::vector<uint32_t>> rem = lists, out(lists.size());
+    for (size_t v = 0; v < lmax; ++v)
+        for (size_t q = 0; q * 8 < lists.size(); ++q) {
+            std::vector<size_t> lanes;
+            for (size_t l = q * 8; l < std::min(lists.size(), q * 8 + 8); ++l) lanes.push_back(l);
+            std::stable_sort(lanes.begin(), lanes.end(), [&](size_t a, size_t b) { return rem[a].size() > rem[b].size(); });
+            int ares[8] = {}, wres[8] = {};
+            std::vector<uint32_t> used_a, used_w;
+            for (size_t l : lanes) {
+                const bool has = !rem[l].empty();
+                const size_t nc = has ? rem[l].size() : 1;
+                const uint32_t r = (uint32_t)(l >> 2) & 1u;
+                double best = 1e30;
+                size_t bt = 0;
+                for (size_t t = 0; t < nc; ++t) {
+                    const uint32_t e = has ? rem[l][t] : pad;
+                    const uint32_t w = (e >> 16) & 0x7FFFu;
+                    const uint32_t a = 2 * (e & 0xFFFFu) + r;
+                    const bool na = std::find(used_a.begin(), used_a.end(), a) == used_a.end();
+                    const bool nw = std::find(used_w.begin(), used_w.end(), w) == used_w.end();
+                    const double c = (na ? ares[a & 7] + 1 : 0) + 0.5 * (nw ? wres[w & 7] + 1 : 0);
+                    if (c < best) { best = c; bt = t; }
+                }
+                const uint32_t e = has ? rem[l][bt] : pad;
+                if (has) rem[l].erase(rem[l].begin() + (long)bt);
+                const uint32_t a = 2 * (e & 0xFFFFu) + r, w = (e >> 16) & 0x7FFFu;
+                if (std::find(used_a.begin(), used_a.end(), a) == used_a.end()) { used_a.push_back(a); ares[a & 7]++; }
+                if (std::find(used_w.begin(), used_w.end(), w) == used_w.end()) { used_w.push_back(w); wres[w & 7]++; }
+                out[l].push_back(e);
+            }
+        }
+    lists.swap(out);
+}
+
 // Length-sorted, 32-column-sliced ELL of packed one-body lists given as a CSR
 // (ptr[0..ncols]).  put(csr_index) returns one entry.
 template <typename Put>
@@ -369,13 +417,19 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
                         lists.back().push_back(repack(T.n1.ent[(size_t)e]));
                     lmax = std::max(lmax, lists.back().size());
                 }
+                std::vector<std::vector<uint32_t>> lists_core = lists;
                 bank_schedule_rot(lists, (ws - 1u) << 16);   // padding: a zero W entry, source column 0
+                bank_schedule_lane(lists_core, (ws - 1u) << 16);
                 P.sinfo.push_back((int32_t)((int64_t)P.ent.size() - P.cls_ent[(size_t)cls]));
                 P.sinfo.push_back((int32_t)lmax);
                 const size_t base = P.ent.size();
                 P.ent.resize(base + lmax * 32, (ws - 1u) << 16);
+                P.core_ent.resize(base + lmax * 32, (ws - 1u) << 16);
                 for (size_t lane = 0; lane < 32; ++lane)
-                    for (size_t v = 0; v < lists[lane].size(); ++v) P.ent[base + v * 32 + lane] = lists[lane][v];
+                    for (size_t v = 0; v < lists[lane].size(); ++v) {
+                        P.ent[base + v * 32 + lane] = lists[lane][v];
+                        P.core_ent[base + v * 32 + lane] = lists_core[lane][v];
+                    }
             }
         }
         // like-particle lists of the sector, same order
@@ -411,6 +465,7 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
     // whole 16-byte groups at the end: kernels copy slice info in 16-byte pieces
     while (P.sinfo.size() % 4) P.sinfo.push_back(0);
     while (P.ent.size() % 4) P.ent.push_back((ws - 1u) << 16);
+    P.core_ent.resize(P.ent.size(), (ws - 1u) << 16);
     // pre-signed W rows: group g, operator a, proton sign sp -> [ sp W[a][.] | -sp W[a][.] ]
     const size_t ng = I.ops.ops.size();
     T.ww_off.assign(ng, 0);
@@ -478,12 +533,17 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
     // made on first use, ns of them (one per k) per (chunk, subset).
     const size_t ws2 = 2 * (size_t)T.wsign;
     std::map<std::pair<size_t, int>, int> tab_of;   // (chunk, subset mask) -> first table
+    // Table 2 (t0 + k) + f holds them with the +W and -W halves swapped when
+    // f = 1 (the sign of a_k on the source row is -1), so the kernel reads
+    // row (op + wsign * neutron sign) of the table its source names, with no
+    // per-entry sign arithmetic.
     auto tables_for = [&](size_t q, int mask) -> int {
         auto it = tab_of.find({q, mask});
         if (it != tab_of.end()) return it->second;
         const int t0 = T.n_wtab;
         T.n_wtab += ns;
-        T.wc.resize((size_t)T.n_wtab * ws2 * 4, 0.0);
+        T.wc.resize((size_t)T.n_wtab * 2 * ws2 * 4, 0.0);
+        const size_t ws = ws2 / 2;
         for (int k = 0; k < ns; ++k) {
             int j = 0;
             for (size_t p = 0; p < chunks[q].size(); ++p) {
@@ -493,8 +553,11 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
                 const int g = I.ops.group_of_op[(size_t)op];
                 if (g < 0 || I.conj_group[(size_t)g] < 0) continue;
                 const size_t row = (size_t)T.ww_off[(size_t)g] + 2 * (size_t)I.ops.local_of_op[(size_t)op] * ws2;
-                double *dst = T.wc.data() + ((size_t)t0 + (size_t)k) * ws2 * 4;
-                for (size_t idx = 0; idx < ws2; ++idx) dst[idx * 4 + col] = T.ww[row + idx];
+                double *dst = T.wc.data() + 2 * ((size_t)t0 + (size_t)k) * ws2 * 4;
+                for (size_t idx = 0; idx < ws2; ++idx) {
+                    dst[idx * 4 + col] = T.ww[row + idx];
+                    dst[ws2 * 4 + (idx ^ ws) * 4 + col] = T.ww[row + idx];
+                }
             }
         }
         tab_of[{q, mask}] = t0;
@@ -555,11 +618,15 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
                 if (l < 0) continue;
                 const Block &Sb = B.blocks[(size_t)blk];
                 const int ncl = T.links[(size_t)l].ncls;
+                const uint32_t f = sign_below(c, k) < 0 ? 1u : 0u;
                 x.src.push_back(CoreSrc{Sb.off + (int64_t)row * Sb.nN, (int32_t)Sb.nN,
-                                        (uint32_t)(tq + k) | (sign_below(c, k) < 0 ? 0x80000000u : 0u),
+                                        (2u * (uint32_t)(tq + k) + f) | (f << 31),
                                         T.pe.cls_ent[(size_t)ncl], T.pe.cls_sinfo[(size_t)ncl]});
             }
             x.u.nsrc = (int)x.src.size();
+            x.u.nN = (int)B.blocks[(size_t)x.u.dblock].nN;
+            x.u.perm_off = (int)T.pe.perm_off[(size_t)B.blocks[(size_t)x.u.dblock].ns];
+            x.u.doff = B.blocks[(size_t)x.u.dblock].off;
             x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)x.u.dblock].nN;
             for (int k : by_key) {
                 if (c >> k & 1) continue;
@@ -673,6 +740,9 @@ void build_pp_units(const Basis &B, const Interaction &I, Tables &T)
                     x.w.insert(x.w.end(), w, w + kPPG);
                 }
                 x.u.nsrc = (int)x.row.size();
+                x.u.nN = (int)B.blocks[(size_t)blk].nN;
+                x.u.pad = 0;
+                x.u.doff = B.blocks[(size_t)blk].off;
                 x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)blk].nN;
                 units.push_back(std::move(x));
             }

@@ -51,6 +51,19 @@ __device__ __forceinline__ bool bar_wait(uint32_t b, uint32_t parity, uint32_t l
     return false;
 }
 
+// For a producer that gives up after a wait ran out: waits (bounded again)
+// for the last copy it issued into each of its S ring stages (fills = copies
+// issued so far, stage = fill index mod S, full barrier of stage s at full0 +
+// 8 s), so that no copy into the CTA's shared memory is in flight when the
+// CTA exits.
+__device__ __forceinline__ void drain_ring(uint32_t full0, int S, int64_t fills)
+{
+    for (int s = 0; s < S && s < fills; ++s) {
+        const int64_t n = (fills - s + S - 1) / S;   // fills of stage s
+        (void)bar_wait(full0 + 8u * (uint32_t)s, (uint32_t)((n - 1) & 1));
+    }
+}
+
 __device__ __forceinline__ void bulk_copy(uint32_t dst, const void *src, uint32_t bytes, uint32_t b)
 {
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),

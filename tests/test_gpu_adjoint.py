@@ -59,7 +59,9 @@ def test_transition_densities_sd22_all_parameters(k, dtype):
     assert np.max(np.abs(g - ref)) <= tol * max(1.0, np.max(np.abs(ref))), np.max(np.abs(g - ref))
 
 
-def test_transition_densities_sd44_subset():
+def test_transition_densities_sd44_all_slots():
+    """Every one of the 66 parameter slots (3 SPEs, 63 TBMEs) at sd 4p4n
+    (dim 28,503) against the oracle's unit-parameter matrix."""
     orbits, spe, tb = I.space("sd")
     c = N.make(orbits, spe, tb, 4, 4, 0, +1, device=0)
     dim = c.dim
@@ -67,7 +69,8 @@ def test_transition_densities_sd44_subset():
     gy = I.random_block(dim, 1, seed=62)
     gx = torch.empty((dim, 1), device="cuda", dtype=torch.float64)
     g = c.apply_H_backward(dev(x), dev(gy), gx, 1, N.BS_F64, n_theta=len(spe) + len(tb))
-    for t in [0, 2, 3, 10, 40, len(spe) + len(tb) - 1]:
+    assert len(g) == 66
+    for t in range(len(spe) + len(tb)):
         ref = float(np.sum(gy * (unit_oracle_matrix(orbits, 4, 4, 0, spe, tb, t) @ x)))
         assert abs(g[t] - ref) <= 1e-11 * max(1.0, abs(ref)), (t, g[t], ref)
 
@@ -123,3 +126,48 @@ def test_hellmann_feynman_vs_finite_differences(pf):
         for m in range(3):
             assert abs(fd[m] - G[m][t]) <= 1e-5 * max(1.0, abs(G[m][t])), (t, m, fd[m], G[m][t])
     c.load_interaction(spe, tb)
+
+
+def test_48cr_gradients_fp64_and_fp32_vectors_vs_finite_differences():
+    """The differentiation workload: pf 4p4n (48Cr, dim 1,963,461), dE/dtheta of
+    the 3 lowest levels over 4 SPEs + 195 TBMEs, against central finite
+    differences (h = 1e-4 MeV) of FP64 Lanczos eigenvalues for 14 parameters
+    (every SPE and 10 seeded random TBME slots).  Gradients are accumulated
+    in FP64 from (a) FP64 Ritz vectors (relative error <= 1e-5) and (b) Ritz
+    vectors of FP32 block Lanczos with k = 4, combined in FP64 (the FP32 path
+    of the configuration), whose error is first order in the vector error:
+    it is held to 10 (r / gap) relative, r the level's FP64 residual and gap
+    its distance to the nearest other level, and at most 1e-3."""
+    orbits, spe, tb = I.space("pf")
+    c = N.make(orbits, spe, tb, 4, 4, 0, +1, device=0)
+    ev64, G64, rep64 = eig_grad(c, spe, tb, 3, 300)
+    assert max(rep64["residual"]) < 1e-6
+    ev32, G32, rep32 = eig_grad(c, spe, tb, 3, 100, dtype=N.BS_F32, k=4)
+    r32 = np.array(rep32["residual"][:3])
+    ev5 = c.lanczos(dev(I.random_block(c.dim, 1, seed=I.PIVOT_SEED)), 1, N.BS_F64, 300, 5, refine=True)[0]
+    gap = np.array([np.min(np.abs(np.delete(ev5, m) - ev5[m])) for m in range(3)])
+    rng = np.random.default_rng(48)
+    nsp = len(spe)
+    params = list(range(nsp)) + sorted(rng.choice(np.arange(nsp, nsp + len(tb)), 10, replace=False).tolist())
+    h = 1e-4
+    worst32 = np.zeros(3)
+    for t in params:
+        vals = []
+        for sgn in (+1, -1):
+            sp, tbb = list(spe), list(tb)
+            if t < nsp:
+                sp[t] += sgn * h
+            else:
+                a, b, cc, d, J, T, v = tbb[t - nsp]
+                tbb[t - nsp] = (a, b, cc, d, J, T, v + sgn * h)
+            c.load_interaction(sp, tbb)
+            e, _ = c.lanczos(dev(I.random_block(c.dim, 1, seed=I.PIVOT_SEED)), 1, N.BS_F64, 300, 3, refine=True)
+            vals.append(e)
+        fd = (vals[0] - vals[1]) / (2 * h)
+        for m in range(3):
+            scale = max(1.0, abs(fd[m]))
+            assert abs(fd[m] - G64[m][t]) <= 1e-5 * scale, (t, m, fd[m], G64[m][t])
+            worst32[m] = max(worst32[m], abs(fd[m] - G32[m][t]) / scale)
+    c.load_interaction(spe, tb)
+    print("48Cr FP32 k=4 vectors: worst relative gradient error per level", worst32, "residuals", r32, "gaps", gap)
+    assert np.all(worst32 <= np.minimum(1e-3, np.maximum(1e-5, 10 * r32 / gap))), (worst32, r32, gap)

@@ -338,14 +338,16 @@ def test_pipe_tables_reproduce_oracle_matrix(name, Z, Nn, twoM):
 
 
 CORE_UNIT = np.dtype([("dblock", np.int32), ("nsrc", np.int32), ("src0", np.int64),
-                      ("drow", np.int32, 4), ("meta", np.int32, 4)])
+                      ("drow", np.int32, 4), ("meta", np.int32, 4),
+                      ("nN", np.int32), ("perm_off", np.int32), ("doff", np.int64)])
 CORE_SRC = np.dtype([("x_elem", np.int64), ("nN", np.int32), ("wtab", np.uint32),
                      ("ent_base", np.int64), ("sinfo_base", np.int64)])
 
 
 PPG = 8
 PP_UNIT = np.dtype([("dblock", np.int32), ("nsrc", np.int32), ("src0", np.int64),
-                    ("drow", np.int32, PPG), ("part", np.int32, PPG)])
+                    ("drow", np.int32, PPG), ("part", np.int32, PPG),
+                    ("nN", np.int32), ("pad", np.int32), ("doff", np.int64)])
 
 
 def core_tables_matvec(c, x, Z, pp_core=False):
@@ -362,7 +364,8 @@ def core_tables_matvec(c, x, Z, pp_core=False):
     cls_base = base[3 * nsec:].reshape(-1, 2)
     perm = c.table("pe_perm", np.int32)
     sinfo = c.table("pe_sinfo", np.int32)
-    ent = c.table("pe_ent", np.uint32)
+    ent = c.table("core_ent", np.uint32)
+    assert len(ent) == len(c.table("pe_ent", np.uint32))
     links = c.table("links", np.int64).reshape(-1, 6)
     units = np.frombuffer(c.table("core_units", np.uint8).tobytes(), dtype=CORE_UNIT)
     srcs = np.frombuffer(c.table("core_src", np.uint8).tobytes(), dtype=CORE_SRC)
@@ -378,18 +381,19 @@ def core_tables_matvec(c, x, Z, pp_core=False):
 
     for u in units:
         offd, nPd, nsd, nNd = blk(u["dblock"])
+        assert (u["nN"], u["doff"], u["perm_off"]) == (nNd, offd, sec_base[nsd][0])   # the record's header copies
         acc = np.zeros((4, nNd))
         po = sec_base[nsd][0]
         for q in range(u["nsrc"]):
             xe, nNs, wt, ce, cs = srcs[u["src0"] + q]
             xs = x[xe: xe + nNs]
-            flip = ws if int(wt) >> 31 else 0
+            assert (int(wt) & 1) == (int(wt) >> 31)        # the table of a -1 sign of a_k has its halves swapped
             W = wc[int(wt) & 0x7FFFFFFF]
             for p in range(nNd):
                 col = perm[po + p]
                 o, lmax = sinfo[cs + 2 * (p // 32)], sinfo[cs + 2 * (p // 32) + 1]
                 es = ent[ce + o + 32 * np.arange(lmax) + p % 32].astype(np.int64)
-                acc[:, col] += W[((es >> 16) & 0x7FFF) ^ flip].T @ xs[es & 0xFFFF]
+                acc[:, col] += W[es >> 16].T @ xs[es & 0xFFFF]
         for p4 in range(4):
             r = u["drow"][p4]
             if r < 0:
@@ -512,8 +516,8 @@ def test_core_units_structure():
             k_bits = s & ~core
             assert s & core == core and bin(k_bits).count("1") == 1
             k = k_bits.bit_length() - 1
-            assert (int(wt) & 0x7FFFFFFF) % ns == k
-            assert ((int(wt) >> 31) != 0) == (below(core, k) < 0)
+            assert ((int(wt) & 0x7FFFFFFF) >> 1) % ns == k
+            assert ((int(wt) >> 31) != 0) == (below(core, k) < 0) == ((int(wt) & 1) != 0)
 
 
 def test_abi_struct_layout_matches_header(tmp_path):
