@@ -287,6 +287,36 @@ void bank_schedule_rot(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
 // conflicts, counting a new chunk address in an occupied bank group by its
 // occupancy + 1 and a new weight row (residue mod 8) half as much.  Shorter
 // lists are padded with `pad`.  Output: lists[lane] of length lmax.
+// Cost of one quarter warp's step: the wavefronts of the two chunk loads
+// (the most distinct addresses in one bank group) plus half those of the
+// weight-row load.
+double quarter_cost(const uint32_t *e, const uint32_t *rot, int n)
+{
+    double tot = 0.0;
+    for (uint32_t chunk = 0; chunk < 2; ++chunk) {
+        uint32_t addr[8];
+        int cnt[8] = {}, mx = 0;
+        for (int i = 0; i < n; ++i) {
+            const uint32_t a = 2 * (e[i] & 0xFFFFu) + (rot[i] ^ chunk);
+            bool seen = false;
+            for (int j = 0; j < i; ++j) seen = seen || addr[j] == a;
+            addr[i] = a;
+            if (!seen) mx = std::max(mx, ++cnt[a & 7]);
+        }
+        tot += mx;
+    }
+    uint32_t wrow[8];
+    int cnt[8] = {}, mx = 0;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t w = (e[i] >> 16) & 0x7FFFu;
+        bool seen = false;
+        for (int j = 0; j < i; ++j) seen = seen || wrow[j] == w;
+        wrow[i] = w;
+        if (!seen) mx = std::max(mx, ++cnt[w & 7]);
+    }
+    return tot + 0.5 * mx;
+}
+
 void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
 {
     size_t lmax = 0;
@@ -299,10 +329,14 @@ void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
             std::stable_sort(lanes.begin(), lanes.end(), [&](size_t a, size_t b) { return rem[a].size() > rem[b].size(); });
             int ares[8] = {}, wres[8] = {};
             std::vector<uint32_t> used_a, used_w;
-            for (size_t l : lanes) {
+            std::vector<uint32_t> pick(lanes.size());
+            uint32_t rots[8];
+            for (size_t k = 0; k < lanes.size(); ++k) {
+                const size_t l = lanes[k];
                 const bool has = !rem[l].empty();
                 const size_t nc = has ? rem[l].size() : 1;
                 const uint32_t r = (uint32_t)(l >> 2) & 1u;
+                rots[k] = r;
                 double best = 1e30;
                 size_t bt = 0;
                 for (size_t t = 0; t < nc; ++t) {
@@ -315,11 +349,32 @@ void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
                     if (c < best) { best = c; bt = t; }
                 }
                 const uint32_t e = has ? rem[l][bt] : pad;
-                if (has) rem[l].erase(rem[l].begin() + (long)bt);
+                pick[k] = e;
                 const uint32_t a = 2 * (e & 0xFFFFu) + r, w = (e >> 16) & 0x7FFFu;
                 if (std::find(used_a.begin(), used_a.end(), a) == used_a.end()) { used_a.push_back(a); ares[a & 7]++; }
                 if (std::find(used_w.begin(), used_w.end(), w) == used_w.end()) { used_w.push_back(w); wres[w & 7]++; }
-                out[l].push_back(e);
+            }
+            // then single-lane exchanges while they lower the quarter's cost
+            double cur = quarter_cost(pick.data(), rots, (int)pick.size());
+            for (int it = 0; it < 3; ++it) {
+                bool better = false;
+                for (size_t k = 0; k < lanes.size(); ++k) {
+                    const size_t l = lanes[k];
+                    for (uint32_t e : rem[l]) {
+                        if (e == pick[k]) continue;
+                        const uint32_t old = pick[k];
+                        pick[k] = e;
+                        const double c = quarter_cost(pick.data(), rots, (int)pick.size());
+                        if (c < cur - 1e-9) { cur = c; better = true; }
+                        else pick[k] = old;
+                    }
+                }
+                if (!better) break;
+            }
+            for (size_t k = 0; k < lanes.size(); ++k) {
+                const size_t l = lanes[k];
+                if (!rem[l].empty()) rem[l].erase(std::find(rem[l].begin(), rem[l].end(), pick[k]));
+                out[l].push_back(pick[k]);
             }
         }
     lists.swap(out);
