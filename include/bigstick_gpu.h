@@ -379,19 +379,20 @@ int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, do
  * warps, columns per thread, ring depth, shared-memory budget) of the
  * pipelined kernel (a producer warp fills a ring of shared-memory slots by
  * TMA, consumer warps keep their columns' sums in registers; needs k values
- * of 16 bytes or more per basis state); 11..19 = the core-grouped path for
+ * of 16 bytes or more per basis state); 11..20 = the core-grouped path for
  * FP32 with k = 4 or 8: a persistent kernel computes the pn term per
  * (Z-1)-proton core (up to four destination rows per staged source row) into
  * Z partial vectors (11, 13, 15, 16: 18 consumer warps with one 32-column
  * slice each; 12, 14: 9 warps with two slices each, a long and a short list;
  * 15, 16: as 13 with the whole 227 KB of shared memory and three or four
- * neutron-list buffers; 17, 18, 19: 227 KB, two list buffers); in 11, 12, 17
+ * neutron-list buffers; 17, 18, 19: 227 KB, two list buffers; 20: 227 KB,
+ * three list buffers); in 11, 12, 17
  * the pipelined kernel computes the like-particle terms into one more (17:
  * the first pipelined variant that fits, for neutron sectors wider than 576
- * columns); in 13..16, 18 and 19 a second persistent kernel computes the pp
+ * columns); in 13..16 and 18..20 a second persistent kernel computes the pp
  * two-body term per
  * (Z-2)-proton core into C(Z,2) more and a row-tile kernel (4 rows per CTA,
- * 2 in 19, column tiles of 576 for wider sectors; 18: the first pipelined
+ * 2 in 19 and 20, column tiles of 576 for wider sectors; 18: the first pipelined
  * variant that fits) the nn term and the proton single-particle energies
  * into one more; a last kernel
  * sums the partial vectors in a fixed order (workspace: up to
@@ -405,7 +406,7 @@ int bs_debug_eigh_banded(int n, int bw, const double *A, int nval, double *w, do
 int bs_set_kernel(bs_ctx *ctx, int mode);
 
 /* Number of selectable H x kernel modes (1..BS_KERNEL_MODES). */
-#define BS_KERNEL_MODES 19
+#define BS_KERNEL_MODES 20
 
 /* Times every kernel mode 1..BS_KERNEL_MODES for (k, dtype) on `stream` on
  * scratch vectors it allocates and frees (2 x dim x k elements), and records
@@ -433,7 +434,7 @@ int bs_sync_status(bs_ctx *ctx, void *stream);
 
 /* Kernel timing: records a pair of CUDA events, on the product's stream,
  * around the dominant kernel of each of the next n (<= BS_TIME_MAX) products
- * y = H x (the pn kernel in the core-grouped modes 11..19, else the one
+ * y = H x (the pn kernel in the core-grouped modes 11..20, else the one
  * kernel); n = 0 stops.  Discards earlier records.  Errors: BS_EINVAL,
  * BS_ECUDA. */
 int bs_time_kernel(bs_ctx *ctx, int n);

@@ -15,7 +15,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libbsgpu.so")
 
 BS_F64, BS_F32 = 0, 1
-KERNEL_MODES = 19          # BS_KERNEL_MODES: selectable H x kernel modes 1..19
+KERNEL_MODES = 20          # BS_KERNEL_MODES: selectable H x kernel modes 1..20
 ERRORS = {0: "BS_OK", -1: "BS_EINVAL", -2: "BS_ENOBASIS", -3: "BS_ENOINT", -4: "BS_ENOMEM",
           -5: "BS_ECUDA", -6: "BS_EBREAKDOWN", -7: "BS_ETIMEOUT"}
 

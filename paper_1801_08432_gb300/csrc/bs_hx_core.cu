@@ -769,13 +769,14 @@ struct CoreVariant {
 // like-particle terms (17: pp and nn; 18: nn, after the pp-core kernel) to
 // the first pipelined variant that fits the basis: for source rows of up to
 // ~64 KB (pf 6p6n: 3,952 columns of 16 bytes at k = 4).  Mode 19 is 18 with
-// the nn term in row tiles of 2 rows.
+// the nn term in row tiles of 2 rows (two CTAs per SM); mode 20 pairs those
+// 2-row tiles with the three list buffers of mode 15.
 constexpr CoreVariant kCoreVariants[] = {{18, 1, 200 * 1024, false, 0, 0}, {9, 2, 200 * 1024, false, 0, 0},
                                          {18, 1, 200 * 1024, true, 4, 0},  {9, 2, 200 * 1024, true, 4, 0},
                                          {18, 1, 227 * 1024, true, 4, 3},  {18, 1, 227 * 1024, true, 4, 4},
                                          {18, 1, 227 * 1024, false, 0, 2}, {18, 1, 227 * 1024, true, 0, 2},
-                                         {18, 1, 227 * 1024, true, 2, 2}};
-constexpr int kNumCore = 9;
+                                         {18, 1, 227 * 1024, true, 2, 2},  {18, 1, 227 * 1024, true, 2, 3}};
+constexpr int kNumCore = 10;
 
 template <int K, int R, int MINB>
 cudaError_t launch_nn_t(const bs_ctx *ctx, const float *x, float *out, cudaStream_t s, bool &used,

@@ -153,7 +153,7 @@ def test_pf_4p4n_sampled_rows(k, dtype):
     assert np.all(np.isfinite(y))
 
 
-@pytest.mark.parametrize("mode", [17, 18, 19])
+@pytest.mark.parametrize("mode", [17, 18, 19, 20])
 def test_pf_6p6n_core_grouped_modes(mode):
     """The core-grouped pn path at the pf 6p6n size (neutron sectors up to
     3,952 columns, source rows of 63 KB at k = 4), with the like-particle terms
@@ -241,7 +241,7 @@ def test_autotune_picks_a_valid_mode():
     c.sync_status()
 
 
-@pytest.mark.parametrize("mode", [11, 12, 13, 14, 15, 16, 17, 18, 19])
+@pytest.mark.parametrize("mode", [11, 12, 13, 14, 15, 16, 17, 18, 19, 20])
 @pytest.mark.parametrize("k", [4, 8])
 def test_pf_4p4n_core_grouped_modes(mode, k):
     """The core-grouped pn path (FP32, k = 4, 8) at the benchmark size: sampled
