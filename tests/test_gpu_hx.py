@@ -299,7 +299,43 @@ def test_gather_ceiling_is_measured_and_ordered():
     for where in (0, 1):
         g = [c.gather_ceiling(where, 8, r) for r in (1, 2, 4)]
         assert all(0 < x < issue for x in g), g
-        assert g[2] > g[0]
+        # each doubling of the rows fed per gather raises the rate by a factor in
+        # [1.4, 2.1]: the gathers stay the same, the FMAs per gather double (a
+        # microbenchmark that lost its gathers or its FMAs would fall outside)
+        assert 1.4 <= g[1] / g[0] <= 2.1 and 1.4 <= g[2] / g[1] <= 2.1, g
     with pytest.raises(N.BSError):
         c.gather_ceiling(2, 8, 1)
     c.close()
+
+
+def test_pn_core_kernel_stays_below_its_gather_ceiling():
+    """The dominant kernel of the 48Cr k = 8 product (the pn term by proton
+    cores, mode 20) against the measured shared-memory ceiling at its own
+    rows per gathered element (multiply-adds / gathers, both counted in the
+    tables), interpolated between the measured 2- and 4-row rates: a kernel
+    faster than that ceiling would mean the ceiling does not bound it."""
+    c, _ = setup("pf", 4, 4, 0)
+    stats = c.table("stats", np.int64)
+    fma, gathers = float(stats[8]), float(stats[11])
+    rpg = fma / gathers
+    assert 1.0 <= rpg <= 4.0
+    g2, g4 = (c.gather_ceiling(0, 8, r) / 1e3 for r in (2, 4))
+    lo, hi, clo, chi = (2, 4, g2, g4) if rpg >= 2 else (1, 2, c.gather_ceiling(0, 8, 1) / 1e3, g2)
+    ceiling = clo + (rpg - lo) / (hi - lo) * (chi - clo)
+    x = torch.randn((c.dim, 8), device="cuda", dtype=torch.float32, generator=torch.Generator(device="cuda").manual_seed(3))
+    y = torch.empty_like(x)
+    c.set_kernel(20)
+    try:
+        for _ in range(2):
+            c.apply_H(x, y, 8, N.BS_F32)
+        c.time_kernel(5)
+        for _ in range(5):
+            c.apply_H(x, y, 8, N.BS_F32)
+        ms = float(np.mean(c.kernel_times()))
+        c.time_kernel(0)
+    finally:
+        c.set_kernel(0)
+    tflops = 2.0 * fma * 8 / (ms / 1e3) / 1e12
+    print("pn-core kernel %.3f ms, %.2f TFLOP/s, ceiling at %.3f rows per gather %.2f TFLOP/s, fraction %.3f"
+          % (ms, tflops, rpg, ceiling, tflops / ceiling))
+    assert 0.1 * ceiling < tflops <= 1.05 * ceiling
