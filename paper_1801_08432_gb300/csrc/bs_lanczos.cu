@@ -199,21 +199,42 @@ __global__ void __launch_bounds__(kDotThreads) blk_dots(const T *__restrict__ V,
     }
 }
 
-// out[e] = sum over CTAs of partial[cta][e], e < n (fixed order)
+// out[e] = sum over CTAs of partial[cta][e], e < n, in a fixed order: thread
+// (slice q, e) adds the CTAs q, q + kRedSl, ... in turn, then the kRedSl
+// slices are added in order.
 __device__ __forceinline__ double part_value(double p) { return p; }
 __device__ __forceinline__ double part_value(float2 p) { return (double)p.x + (double)p.y; }
+constexpr int kRedE = 32;   // outputs per CTA
+constexpr int kRedSl = 8;   // slices of the partials per output
 
 template <typename P>
-__global__ void dots_reduce(const P *__restrict__ partial, int ncta, int n, double *__restrict__ out,
-                            const int *__restrict__ nb_iter, const int *__restrict__ out_iter, int kk)
+__global__ void __launch_bounds__(kRedE * kRedSl) dots_reduce(const P *__restrict__ partial, int ncta, int n,
+                                                              double *__restrict__ out, const int *__restrict__ nb_iter,
+                                                              const int *__restrict__ out_iter, int kk)
 {
     if (nb_iter) n = (*nb_iter + 1) * kk;       // graph replay: n+1 blocks of k x k
     if (out_iter) out += (int64_t)(*out_iter) * kk;   // graph replay: block n of a history array
-    const int e = blockIdx.x * blockDim.x + threadIdx.x;
-    if (e >= n) return;
+    __shared__ double sl[kRedSl][kRedE];
+    const int el = threadIdx.x % kRedE, q = threadIdx.x / kRedE;
+    const int e = blockIdx.x * kRedE + el;
     double t = 0.0;
-    for (int c = 0; c < ncta; ++c) t += part_value(partial[(int64_t)c * n + e]);
-    out[e] = t;
+    if (e < n)
+        for (int c = q; c < ncta; c += kRedSl) t += part_value(partial[(int64_t)c * n + e]);
+    sl[q][el] = t;
+    __syncthreads();
+    if (q == 0 && e < n) {
+        double u = sl[0][el];
+        for (int r = 1; r < kRedSl; ++r) u += sl[r][el];
+        out[e] = u;
+    }
+}
+
+// n_launch: the largest n the launch may see (graph replay reads n from nb_iter)
+template <typename P>
+void reduce_parts(const P *partial, int ncta, int n_launch, int n, double *out, const int *nb_iter, const int *out_iter,
+                  int kk, cudaStream_t s)
+{
+    dots_reduce<P><<<(n_launch + kRedE - 1) / kRedE, kRedE * kRedSl, 0, s>>>(partial, ncta, n, out, nb_iter, out_iter, kk);
 }
 
 // W[alpha][j] -= sum_b sum_i V_b[alpha][i] C[b][i][j]   (C: nb blocks of K x K, FP64)
@@ -858,6 +879,270 @@ __global__ void __launch_bounds__(kRsCons + 64, sizeof(T) == 4 ? 2 : 1)
     }
 }
 
+// V_b^T W for FP32 blocks of K = 4 or 8 vectors with W held in shared memory
+// (the Gram-Schmidt coefficients, plain products).  A CTA owns one contiguous
+// range of rows and walks it in pieces of kRwWT tiles: the piece of W sits in
+// kRwWT slots, each loaded once per piece by TMA, while the matching tiles of
+// every block V_b stream through a ring of kRwS tiles.  A W slot is released
+// when the last block's tile at that position has been consumed, so the next
+// piece's W loads overlap the end of the current one.
+// Consumer thread t owns the rows t, t + 256, ... of each tile and keeps all
+// K x K plain FP32 sums of its rows in registers (packed FMAs, V elements
+// duplicated into pairs).  For K = 8 a lane reads the two 16-byte halves of
+// its rows in the order (lane >> 2) & 1, which makes the quarter-warp reads
+// conflict-free; the sums are put back in order before they are combined.
+// Every kChunk products (16 rows) the warp combines its lanes' sums by a
+// butterfly that leaves each lane with K^2 / 32 of the warp's K^2 sums (five
+// FP32 addition levels), which the lane adds to its double-float sums.  At the
+// end of a block's piece the 8 warps' sums are added in a fixed order into this
+// CTA's partial for the block.  So a plain sum holds at most 16 products and
+// 5 further roundings before it reaches double-float.  Deterministic: fixed
+// orders throughout, and dots_reduce adds the CTAs' partials in a fixed
+// order.  Needs the TMA rules of the kernel above.
+constexpr int kRwCons = 384;    // consumer threads (12 warps) + one producer warp
+constexpr int kRwTile = 24576;  // bytes per V or W tile slot
+constexpr int kRwS = 4;         // V ring stages
+constexpr int kRwWT = 4;        // W slots: tiles per piece
+
+template <int K>
+__host__ __device__ constexpr size_t rw_smem()
+{
+    return 256 + (size_t)(kRwWT + kRwS) * kRwTile + 2 * (size_t)(kRwCons / 32) * K * K * sizeof(float2);
+}
+
+// One butterfly step over the warp on x[0 .. N) of each lane: the lanes with
+// bit O set keep the upper half of their values, the others the lower half,
+// and each adds its partner's copy of the half it keeps (pairs of values at a
+// time).  After it, x[0 .. N / 2) holds the kept half.
+template <int N, int O>
+__device__ __forceinline__ void rw_bfly_step(float *x, int lane)
+{
+    const bool up = (lane & O) != 0;
+#pragma unroll
+    for (int p = 0; p < N / 2; p += 2) {
+        const float k0 = up ? x[p + N / 2] : x[p], k1 = up ? x[p + 1 + N / 2] : x[p + 1];
+        const float s0 = up ? x[p] : x[p + N / 2], s1 = up ? x[p + 1] : x[p + 1 + N / 2];
+        const float2 r = make_float2(__shfl_xor_sync(0xffffffffu, s0, O), __shfl_xor_sync(0xffffffffu, s1, O));
+        const float2 t = __fadd2_rn(make_float2(k0, k1), r);
+        x[p] = t.x;
+        x[p + 1] = t.y;
+    }
+}
+
+template <int K>
+__global__ void __launch_bounds__(kRwCons + 32, 1)
+    rs_dots_w(const float *__restrict__ V, int64_t bstride, int nb, const float *__restrict__ W, int64_t dim,
+              float2 *__restrict__ partial, const int *__restrict__ nb_iter, int *err)
+{
+    using namespace tma;
+    static_assert(K == 4 || K == 8, "K = 4 or 8");
+    constexpr int RB = K * 4;                // bytes per row
+    constexpr int RPT = kRwTile / RB / kRwCons;   // rows per thread per tile
+    constexpr int TR = RPT * kRwCons;             // rows per tile (at most kRwTile bytes)
+    constexpr int PR = kRwWT * TR;                // rows per piece
+    constexpr int FL = kChunk / RPT < kRwWT ? kChunk / RPT : kRwWT;   // tiles per plain FP32 sum
+    constexpr int NCW = kRwCons / 32;
+    constexpr int NL = K * K >= 32 ? K * K / 32 : 1;   // sums per lane after the butterfly
+    static_assert(RPT >= 1 && RPT * FL <= kChunk && kRwWT % FL == 0, "plain sums of at most kChunk products");
+    if (nb_iter) nb = *nb_iter + 1;
+    extern __shared__ __align__(128) unsigned char smem[];
+    uint64_t *bars = reinterpret_cast<uint64_t *>(smem);   // full[kRwS], empty[kRwS], wfull[kRwWT], wempty[kRwWT]
+    float *Wp = reinterpret_cast<float *>(smem + 256);
+    float *ring = Wp + (size_t)kRwWT * (kRwTile / 4);
+    float2 *red = reinterpret_cast<float2 *>(ring + (size_t)kRwS * (kRwTile / 4));   // [2][NCW][K * K]
+    const uint32_t full0 = su32(bars), empty0 = su32(bars + kRwS);
+    const uint32_t wfull0 = su32(bars + 2 * kRwS), wempty0 = su32(bars + 2 * kRwS + kRwWT);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    if (tid == 0) {
+        for (int s = 0; s < kRwS; ++s) {
+            bar_init(full0 + 8u * s, 1);
+            bar_init(empty0 + 8u * s, NCW);
+        }
+        for (int s = 0; s < kRwWT; ++s) {
+            bar_init(wfull0 + 8u * s, 1);
+            bar_init(wempty0 + 8u * s, NCW);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // this CTA's rows: a contiguous range
+    const int64_t rpc = (dim + gridDim.x - 1) / gridDim.x;
+    const int64_t r0 = (int64_t)blockIdx.x * rpc, r1 = min(dim, r0 + rpc);
+    float2 *part = partial + (int64_t)blockIdx.x * nb * K * K;
+    if (warp == NCW) {   // producer
+        if (lane != 0) return;
+        int64_t tiles = 0, wcopies = 0;
+        int piece = 0;
+        bool ok = true;
+        for (int64_t p0 = r0; ok && p0 < r1; p0 += PR, ++piece) {
+            const int64_t pr = min((int64_t)PR, r1 - p0);
+            const int nt = (int)((pr + TR - 1) / TR);
+            int s = (int)(tiles % kRwS);
+            for (int b = 0; ok && b < nb; ++b)
+                for (int t = 0; t < nt; ++t, ++tiles, s = s + 1 == kRwS ? 0 : s + 1) {
+                    const uint32_t bytes = (uint32_t)(min((int64_t)TR, pr - (int64_t)t * TR) * RB);
+                    if (b == 0) {   // W slot t: free once the previous piece's last block used it
+                        if (piece > 0 && bar_wait(wempty0 + 8u * t, (uint32_t)(piece - 1) & 1u)) { ok = false; break; }
+                        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                        bar_expect_tx(wfull0 + 8u * t, bytes);
+                        bulk_copy(su32(Wp + (size_t)t * (kRwTile / 4)), W + (p0 + (int64_t)t * TR) * K, bytes, wfull0 + 8u * t);
+                        ++wcopies;
+                    }
+                    const int64_t use = tiles / kRwS;
+                    if (use > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(use - 1) & 1u)) { ok = false; break; }
+                    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                    bar_expect_tx(full0 + 8u * s, bytes);
+                    bulk_copy(su32(ring + (size_t)s * (kRwTile / 4)), V + (int64_t)b * bstride + (p0 + (int64_t)t * TR) * K,
+                              bytes, full0 + 8u * s);
+                }
+        }
+        if (!ok) {   // no copy left in flight at exit
+            atomicExch(err, BS_ETIMEOUT);
+            drain_ring(full0, kRwS, tiles);
+            drain_ring(wfull0, kRwWT, wcopies);
+        }
+        return;
+    }
+    // consumers: rows tid + kRwCons m of each tile; for K = 8 the halves in the order hf, 1 - hf
+    // (conflict-free quarter-warp reads)
+    const int hf = K == 8 ? (lane >> 2) & 1 : 0;
+    const int o0 = 4 * hf, o1 = 4 - 4 * hf;
+    float2 acc[K][K / 2];   // plain sums of the current rows: (i, 2q), (i, 2q + 1)
+#pragma unroll
+    for (int i = 0; i < K; ++i)
+#pragma unroll
+        for (int q = 0; q < K / 2; ++q) acc[i][q] = make_float2(0.f, 0.f);
+    int s = 0;
+    uint32_t ph = 0;   // stage and parity of the next tile
+    int piece = 0, nred = 0;
+    bool bad = false;
+    for (int64_t p0 = r0; p0 < r1; p0 += PR, ++piece) {
+        const int64_t pr = min((int64_t)PR, r1 - p0);
+        const int nt = (int)((pr + TR - 1) / TR);
+        for (int b = 0; b < nb; ++b, ++nred) {
+            // this block's running partial, read now so that the load is done by the end of the piece
+            float2 prev = make_float2(0.f, 0.f);
+            if (piece > 0 && tid < K * K) prev = part[(int64_t)b * K * K + tid];
+            DF d[NL];
+#pragma unroll
+            for (int u = 0; u < NL; ++u) d[u] = DF{0.f, 0.f};
+            const int trl = (int)(pr - (int64_t)(nt - 1) * TR);   // rows of the piece's last tile
+#pragma unroll
+            for (int t = 0; t < kRwWT; ++t) {   // unrolled: slot addresses and barriers are constants
+                if (t >= nt) break;
+                if (b == 0 && !bad && __any_sync(0xffffffffu, bar_wait(wfull0 + 8u * t, (uint32_t)piece & 1u))) {
+                    bad = true;
+                    if (lane == 0) atomicExch(err, BS_ETIMEOUT);
+                }
+                if (!bad && __any_sync(0xffffffffu, bar_wait(full0 + 8u * s, ph))) {
+                    bad = true;
+                    if (lane == 0) atomicExch(err, BS_ETIMEOUT);
+                }
+                if (!bad) {
+                    const int tr = t == nt - 1 ? trl : TR;
+                    const float *tile = ring + (size_t)s * (kRwTile / 4);
+                    const float *wt = Wp + (size_t)t * (kRwTile / 4);
+#pragma unroll
+                    for (int m = 0; m < RPT; ++m) {
+                        const int a = tid + kRwCons * m;
+                        const bool first = t % FL == 0 && m == 0;   // a plain sum starts: multiply, no add
+                        if (a < tr) {
+                            float v[K];
+                            float2 w[K / 2];
+                            const float4 va = *reinterpret_cast<const float4 *>(tile + a * K + o0);
+                            const float4 wa = *reinterpret_cast<const float4 *>(wt + a * K + o0);
+                            v[0] = va.x, v[1] = va.y, v[2] = va.z, v[3] = va.w;
+                            w[0] = make_float2(wa.x, wa.y), w[1] = make_float2(wa.z, wa.w);
+                            if constexpr (K == 8) {
+                                const float4 vb = *reinterpret_cast<const float4 *>(tile + a * K + o1);
+                                const float4 wb = *reinterpret_cast<const float4 *>(wt + a * K + o1);
+                                v[4] = vb.x, v[5] = vb.y, v[6] = vb.z, v[7] = vb.w;
+                                w[2] = make_float2(wb.x, wb.y), w[3] = make_float2(wb.z, wb.w);
+                            }
+#pragma unroll
+                            for (int i = 0; i < K; ++i) {
+                                const float2 vi = make_float2(v[i], v[i]);
+#pragma unroll
+                                for (int q = 0; q < K / 2; ++q)
+                                    acc[i][q] = first ? __fmul2_rn(vi, w[q]) : __ffma2_rn(vi, w[q], acc[i][q]);
+                            }
+                        } else if (first) {
+#pragma unroll
+                            for (int i = 0; i < K; ++i)
+#pragma unroll
+                                for (int q = 0; q < K / 2; ++q) acc[i][q] = make_float2(0.f, 0.f);
+                        }
+                    }
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    bar_arrive(empty0 + 8u * s);
+                    if (b == nb - 1) bar_arrive(wempty0 + 8u * t);
+                }
+                if (++s == kRwS) {
+                    s = 0;
+                    ph ^= 1u;
+                }
+                if ((t + 1) % FL == 0 || t == nt - 1) {   // end of a plain sum: combine the warp's lanes
+                    float *xs = &acc[0][0].x;   // K * K values, (i, j) row-major in register order
+                    if constexpr (K == 8) {
+                        // lanes L and L ^ 4 first.  A lane with hf = 1 holds value (i ^ 4, j ^ 4) at
+                        // (i, j), i.e. index e ^ 36 at e, and its partner has the other hf, so
+                        // keeping values 0..31 and adding the partner's values (e + 32) ^ 4 combines
+                        // equal indices without selects.  Then offsets 16, 8, 2, 1; lane L ends with
+                        // the indices base(L), base(L) + 1 (the swap of index bit 2 stays with hf).
+#pragma unroll
+                        for (int p = 0; p < 32; p += 2) {
+                            const float2 r = make_float2(__shfl_xor_sync(0xffffffffu, xs[(p + 32) ^ 4], 4),
+                                                         __shfl_xor_sync(0xffffffffu, xs[(p + 33) ^ 4], 4));
+                            const float2 t2 = __fadd2_rn(make_float2(xs[p], xs[p + 1]), r);
+                            xs[p] = t2.x;
+                            xs[p + 1] = t2.y;
+                        }
+                        rw_bfly_step<32, 16>(xs, lane);
+                        rw_bfly_step<16, 8>(xs, lane);
+                        rw_bfly_step<8, 2>(xs, lane);
+                        rw_bfly_step<4, 1>(xs, lane);
+                    } else {   // offsets 16, 8, 4, 2, then 1 on the one value left: lanes L, L ^ 1 hold index L / 2
+                        rw_bfly_step<16, 16>(xs, lane);
+                        rw_bfly_step<8, 8>(xs, lane);
+                        rw_bfly_step<4, 4>(xs, lane);
+                        rw_bfly_step<2, 2>(xs, lane);
+                        xs[0] += __shfl_xor_sync(0xffffffffu, xs[0], 1);
+                    }
+#pragma unroll
+                    for (int u = 0; u < NL; ++u) df_add(d[u], xs[u]);
+                }
+            }
+            // the warps in order; lane L holds sums base(L), base(L) + 1 (K = 8) or L / 2 (K = 4)
+            float2 *rb = red + (size_t)(nred & 1) * NCW * K * K;
+            if constexpr (K == 8) {
+                const int b2 = (lane >> 2) & 1;
+                const int base = 32 * b2 + 16 * ((lane >> 4) & 1) + 8 * ((lane >> 3) & 1) + 4 * (((lane >> 1) & 1) ^ b2) +
+                                 2 * (lane & 1);
+#pragma unroll
+                for (int u = 0; u < NL; ++u) rb[(size_t)warp * K * K + base + u] = make_float2(d[u].hi, d[u].lo);
+            } else {
+                if ((lane & 1) == 0) rb[(size_t)warp * K * K + (lane >> 1)] = make_float2(d[0].hi, d[0].lo);
+            }
+            asm volatile("bar.sync 1, %0;" ::"n"(kRwCons) : "memory");   // the consumer warps only
+            if (tid < K * K) {   // a fixed pairwise tree over the warps (depth 4, not a chain of NCW - 1)
+                float2 t2[NCW];
+#pragma unroll
+                for (int w2 = 0; w2 < NCW; ++w2) t2[w2] = rb[(size_t)w2 * K * K + tid];
+#pragma unroll
+                for (int h = 1; h < NCW; h *= 2)
+#pragma unroll
+                    for (int w2 = 0; w2 + h < NCW; w2 += 2 * h) t2[w2] = df_sum(t2[w2], t2[w2 + h]);
+                part[(int64_t)b * K * K + tid] = piece == 0 ? t2[0] : df_sum(prev, t2[0]);
+            }
+        }
+    }
+    if (r0 >= r1) {   // no rows for this CTA: its partials are zero
+        for (int e = tid; e < nb * K * K; e += kRwCons) part[e] = make_float2(0.f, 0.f);
+    }
+}
+
 // W[alpha][j] -= sum_b sum_i V_b[alpha][i] C[b][i][j]  (C: FP64, used in the vectors' precision).
 // Tiles of kRsCEU elements: thread t owns the whole rows t + 256 m, m <
 // kRsCEU / (256 K), of each chunk (its W values in registers), reads each of
@@ -985,6 +1270,25 @@ void dots(LState &L, const T *V, int nb, const T *W, double *out, const int *nb_
           const int *out_iter = nullptr, int nb_max = 0)
 {
     const int n = (nb_iter ? nb_max : nb) * K * K;
+    if constexpr (!EXACT && std::is_same<T, float>::value && (K == 4 || K == 8)) {
+        if (rs_applies<T, K>(L, V, W)) {
+            constexpr size_t smem = rw_smem<K>();
+            static unsigned long long attr = 0;   // per instantiation: devices already configured
+            int dev = 0, nsm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+            if (dev < 64 && !(attr >> dev & 1ull)) {
+                cudaFuncSetAttribute(rs_dots_w<K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                attr |= 1ull << dev;
+            }
+            const int g = std::min(nsm, L.ncta);   // one CTA per SM; the partials hold L.ncta
+            rs_dots_w<K><<<g, kRwCons + 32, smem, L.s>>>(V, L.bstride, nb, W, L.dim, reinterpret_cast<float2 *>(L.partial),
+                                                        nb_iter, L.err);
+            reduce_parts<float2>(reinterpret_cast<const float2 *>(L.partial), g, n, nb * K * K, out, nb_iter, out_iter,
+                                 K * K, L.s);
+            return;
+        }
+    }
     if (rs_applies<T, K>(L, V, W)) {
         using Sv = typename RsRed<T>::S;
         constexpr int S = rs_stages<T>();
@@ -1004,12 +1308,12 @@ void dots(LState &L, const T *V, int nb, const T *W, double *out, const int *nb_
         rs_dots<T, K, EXACT, S><<<L.ncta, kRsCons + 64, smem, L.s>>>(V, L.bstride, nb, W, L.dim * K,
                                                                      reinterpret_cast<Sv *>(L.partial), acc_in_smem,
                                                                      nb_iter, L.err);
-        dots_reduce<Sv><<<(n + 255) / 256, 256, 0, L.s>>>(reinterpret_cast<const Sv *>(L.partial), L.ncta, nb * K * K,
-                                                          out, nb_iter, out_iter, K * K);
+        reduce_parts<Sv>(reinterpret_cast<const Sv *>(L.partial), L.ncta, n, nb * K * K, out, nb_iter, out_iter, K * K,
+                         L.s);
         return;
     }
     blk_dots<T, K, EXACT><<<L.ncta, kDotThreads, 0, L.s>>>(V, L.bstride, nb, W, L.dim, L.partial, nb_iter);
-    dots_reduce<double><<<(n + 255) / 256, 256, 0, L.s>>>(L.partial, L.ncta, nb * K * K, out, nb_iter, out_iter, K * K);
+    reduce_parts<double>(L.partial, L.ncta, n, nb * K * K, out, nb_iter, out_iter, K * K, L.s);
 }
 
 template <typename T, int K>
@@ -1644,7 +1948,7 @@ int noalloc_dots_run(const void *V, int nb, const void *W, int64_t dim, double *
     // as many CTAs as the fixed array holds partial blocks for, at most 2 per SM
     const int ncta = (int)std::max<int64_t>(1, std::min<int64_t>(2 * (int64_t)nsm, BS_BLOCK_DOTS_NOALLOC_MAX / per));
     blk_dots<T, K><<<ncta, kDotThreads, 0, s>>>((const T *)V, dim * K, nb, (const T *)W, dim, scratch, nullptr);
-    dots_reduce<double><<<(int)((per + 255) / 256), 256, 0, s>>>(scratch, ncta, (int)per, C, nullptr, nullptr, K * K);
+    reduce_parts<double>(scratch, ncta, (int)per, (int)per, C, nullptr, nullptr, K * K, s);
     return cudaGetLastError() == cudaSuccess ? BS_OK : BS_ECUDA;
 }
 
