@@ -367,12 +367,19 @@ __global__ void __launch_bounds__(32) small_gram(int K, const double *__restrict
         a[e] = 0.5 * (O[i * K + jj] + O[jj * K + i]);
         u[e] = i == jj ? 1.0 : 0.0;
     }
-    if (A && lane == 0) {
-        for (int i = 0; i < K; ++i)
-            for (int jj = i + 1; jj < K; ++jj) {
-                const double sv = 0.5 * (A[i * K + jj] + A[jj * K + i]);
-                A[i * K + jj] = A[jj * K + i] = sv;
-            }
+    if (A) {   // one lane per pair (i < jj): every read before any write
+        double sv[2];   // K * K <= 64: two elements per lane
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = lane + 32 * h, i = e / K, jj = e % K;
+            sv[h] = e < K * K && i < jj ? 0.5 * (A[i * K + jj] + A[jj * K + i]) : 0.0;
+        }
+        __syncwarp();
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int e = lane + 32 * h, i = e / K, jj = e % K;
+            if (e < K * K && i < jj) A[i * K + jj] = A[jj * K + i] = sv[h];
+        }
     }
     __syncwarp();
     const int np = K / 2;                  // rotations per round
@@ -389,7 +396,10 @@ __global__ void __launch_bounds__(32) small_gram(int K, const double *__restrict
             off += __shfl_xor_sync(0xffffffffu, off, o);
             tot += __shfl_xor_sync(0xffffffffu, tot, o);
         }
-        if (off <= 1e-32 * tot) break;
+        // off-diagonal at ~1e-15 of the matrix: rounding level.  (The column and row
+        // updates round differently, so the lower triangle keeps ~1e-16 residues that
+        // no rotation removes; a tighter test would run every remaining sweep.)
+        if (off <= 1e-30 * tot) break;
         for (int t = 0; t < K - 1; ++t) {
             if (lane < np) {
                 // circle method: position i holds state 0 (i = 0) or 1 + (i - 1 + t) mod (K - 1)
@@ -400,12 +410,24 @@ __global__ void __launch_bounds__(32) small_gram(int K, const double *__restrict
                 pq[lane][1] = q;
                 const double apq = a[p * K + q];
                 double c = 1.0, sn = 0.0;
-                if (apq != 0.0) {
-                    // rotation angle that zeroes a[p][q]
-                    const double theta = 0.5 * (a[q * K + q] - a[p * K + p]) / apq;
-                    const double tt = (theta >= 0.0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
-                    c = 1.0 / sqrt(tt * tt + 1.0);
-                    sn = tt * c;
+                const float apq32 = (float)apq;
+                if (apq32 != 0.0f) {
+                    // The angle that zeroes a[p][q], in FP32: the rotation leaves a[p][q] at
+                    // ~1e-7 of itself and the next sweep removes the rest (the stopping test
+                    // stays in FP64).  FP64 divisions and square roots are slow here.
+                    const float th = 0.5f * (float)(a[q * K + q] - a[p * K + p]) / apq32;
+                    const float tt = copysignf(1.0f, th) / (fabsf(th) + sqrtf(fmaf(th, th, 1.0f)));   // 0 for huge th
+                    const float c32 = rsqrtf(fmaf(tt, tt, 1.0f));
+                    // (c, s) made orthonormal in FP64: two Newton steps of 1 / sqrt(c^2 + s^2)
+                    // from 1 (c^2 + s^2 is within ~1e-7 of 1), so U stays orthogonal to FP64 rounding
+                    c = (double)c32;
+                    sn = (double)(tt * c32);
+#pragma unroll
+                    for (int it = 0; it < 2; ++it) {
+                        const double g = fma(-0.5, fma(c, c, sn * sn), 1.5);
+                        c *= g;
+                        sn *= g;
+                    }
                 }
                 cs[lane][0] = c;
                 cs[lane][1] = sn;
