@@ -8,6 +8,7 @@
 // applies its transpose for the "back" half; here both directions are kept so
 // that every output element has one owner and no atomics are needed).
 #include <algorithm>
+#include <cmath>
 #include <map>
 #include <numeric>
 
@@ -380,6 +381,74 @@ void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
     lists.swap(out);
 }
 
+// Whole-slice refinement of the pn-core step order (lmax steps x 32 lanes at E,
+// [step][lane]) under the cost of quarter_cost: per quarter warp, a move
+// either swaps one lane's entries at two steps or, for a padding entry (zero
+// weight row), sets its source column to 0..3 (when the source row has 4 or
+// more), so that it takes a free bank group.  Moves are accepted by the
+// Metropolis rule under a temperature falling linearly to zero, and the best
+// order seen is kept.  The stepwise greedy above cannot trade entries between
+// steps; this can.  Deterministic: a splitmix64 stream seeded per slice.
+// ipe = moves per entry.
+void anneal_slice(uint32_t *E, size_t lmax, uint32_t pad, int64_t nsrc, uint64_t seed, int ipe)
+{
+    if (lmax < 1 || ipe < 1) return;
+    uint64_t st = seed;
+    auto next = [&st]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto unif = [&next]() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); };
+    const uint32_t rots[8] = {0, 0, 0, 0, 1, 1, 1, 1};
+    std::vector<uint32_t> q8(lmax * 8), best(lmax * 8);
+    std::vector<double> cost(lmax);
+    for (size_t q = 0; q < 4; ++q) {
+        for (size_t v = 0; v < lmax; ++v)
+            for (size_t k = 0; k < 8; ++k) q8[v * 8 + k] = E[v * 32 + q * 8 + k];
+        double cur = 0.0;
+        for (size_t v = 0; v < lmax; ++v) cur += (cost[v] = quarter_cost(&q8[v * 8], rots, 8));
+        double bestc = cur;
+        best = q8;
+        const int64_t n = (int64_t)ipe * (int64_t)lmax * 8;
+        for (int64_t it = 0; it < n; ++it) {
+            const double T = 0.6 * (1.0 - (double)it / (double)n) + 1e-3;
+            const size_t k = (size_t)(next() % 8), v1 = (size_t)(next() % lmax);
+            uint32_t &a = q8[v1 * 8 + k];
+            if ((a >> 16) == (pad >> 16) && nsrc >= 4 && next() % 10 < 3) {   // a padding entry's source column
+                const uint32_t old = a;
+                a = pad | (uint32_t)(next() % 4);
+                const double c1 = quarter_cost(&q8[v1 * 8], rots, 8), d = c1 - cost[v1];
+                if (d < 0 || unif() < std::exp(-d / T)) {
+                    cost[v1] = c1;
+                    cur += d;
+                    if (cur < bestc - 1e-9) { bestc = cur; best = q8; }
+                } else {
+                    a = old;
+                }
+                continue;
+            }
+            const size_t v2 = (size_t)(next() % lmax);
+            uint32_t &b = q8[v2 * 8 + k];
+            if (v1 == v2 || a == b) continue;
+            std::swap(a, b);
+            const double c1 = quarter_cost(&q8[v1 * 8], rots, 8), c2 = quarter_cost(&q8[v2 * 8], rots, 8);
+            const double d = c1 + c2 - cost[v1] - cost[v2];
+            if (d < 0 || unif() < std::exp(-d / T)) {
+                cost[v1] = c1;
+                cost[v2] = c2;
+                cur += d;
+                if (cur < bestc - 1e-9) { bestc = cur; best = q8; }
+            } else {
+                std::swap(a, b);
+            }
+        }
+        for (size_t v = 0; v < lmax; ++v)
+            for (size_t k = 0; k < 8; ++k) E[v * 32 + q * 8 + k] = best[v * 8 + k];
+    }
+}
+
 // Length-sorted, 32-column-sliced ELL of packed one-body lists given as a CSR
 // (ptr[0..ncols]).  put(csr_index) returns one entry.
 template <typename Put>
@@ -434,6 +503,11 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
     P.cls_sinfo.assign(T.n1.cls.size(), 0);
     P.sec_nn_ent.assign(nsec, 0);
     P.sec_nn_sinfo.assign(nsec, 0);
+    struct CoreSlice {
+        size_t base, lmax;
+        int64_t nsrc;
+    };
+    std::vector<CoreSlice> core_slices;
     for (size_t s = 0; s < nsec; ++s) {
         const int64_t n = NS.sec[s].count;
         // column order: lexicographic (descending) by the per-class list lengths
@@ -475,6 +549,7 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
                 std::vector<std::vector<uint32_t>> lists_core = lists;
                 bank_schedule_rot(lists, (ws - 1u) << 16);   // padding: a zero W entry, source column 0
                 bank_schedule_lane(lists_core, (ws - 1u) << 16);
+                core_slices.push_back({P.ent.size(), lmax, B.sp[1].sec[(size_t)T.n1.cls[(size_t)cls].s_src].count});
                 P.sinfo.push_back((int32_t)((int64_t)P.ent.size() - P.cls_ent[(size_t)cls]));
                 P.sinfo.push_back((int32_t)lmax);
                 const size_t base = P.ent.size();
@@ -521,6 +596,17 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
     while (P.sinfo.size() % 4) P.sinfo.push_back(0);
     while (P.ent.size() % 4) P.ent.push_back((ws - 1u) << 16);
     P.core_ent.resize(P.ent.size(), (ws - 1u) << 16);
+    {   // refine the pn-core order, slices in parallel: ~100 moves per entry, fewer
+        // for very large tables (at most ~1.5e8 moves in all)
+        const double tot = (double)std::max<size_t>(P.core_ent.size(), 1);
+        const int ipe = (int)std::max(1.0, std::min(100.0, 1.5e8 / tot));
+#pragma omp parallel for schedule(dynamic, 8)
+        for (int64_t i = 0; i < (int64_t)core_slices.size(); ++i) {
+            const CoreSlice &c = core_slices[(size_t)i];
+            anneal_slice(P.core_ent.data() + c.base, c.lmax, (ws - 1u) << 16, c.nsrc,
+                         0x5DEECE66Dull * (uint64_t)(i + 1), ipe);
+        }
+    }
     // pre-signed W rows: group g, operator a, proton sign sp -> [ sp W[a][.] | -sp W[a][.] ]
     const size_t ng = I.ops.ops.size();
     T.ww_off.assign(ng, 0);
