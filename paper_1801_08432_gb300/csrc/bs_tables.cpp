@@ -449,6 +449,71 @@ void anneal_slice(uint32_t *E, size_t lmax, uint32_t pad, int64_t nsrc, uint64_t
     }
 }
 
+// The like-particle lists (src, coef) of one quarter warp q (lanes 8q .. 8q+7)
+// of one 32-column slice, [step][lane]: the same refinement for the kernels
+// that read a 32-byte element's chunks lane parity first, at the cost of the
+// two chunk loads of the quarter (no weights); src and coef move together.
+// Quarters touch disjoint lanes, so they can run in parallel.
+void anneal_nn_quarter(int32_t *src, double *coef, size_t lmax, size_t q, uint64_t seed, int ipe)
+{
+    if (lmax < 2 || ipe < 1) return;
+    uint64_t st = seed;
+    auto next = [&st]() {
+        uint64_t z = (st += 0x9E3779B97F4A7C15ull);
+        z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+        z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+        return z ^ (z >> 31);
+    };
+    auto unif = [&next]() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); };
+    const uint32_t rots[8] = {0, 1, 0, 1, 0, 1, 0, 1};
+    auto cost8 = [&rots](const uint32_t *e) { return quarter_cost(e, rots, 8) - 0.5; };   // weight rows all 0: 0.5
+    std::vector<uint32_t> q8(lmax * 8), best(lmax * 8);
+    std::vector<uint32_t> idx(lmax * 8), bidx(lmax * 8);   // the entries' original steps, to move coef
+    std::vector<double> cost(lmax);
+    for (size_t v = 0; v < lmax; ++v)
+        for (size_t k = 0; k < 8; ++k) {
+            q8[v * 8 + k] = (uint32_t)src[v * 32 + q * 8 + k] & 0xFFFFu;
+            idx[v * 8 + k] = (uint32_t)v;
+        }
+    double cur = 0.0;
+    for (size_t v = 0; v < lmax; ++v) cur += (cost[v] = cost8(&q8[v * 8]));
+    double bestc = cur;
+    best = q8;
+    bidx = idx;
+    const int64_t n = (int64_t)ipe * (int64_t)lmax * 8;
+    for (int64_t it = 0; it < n; ++it) {
+        const double T = 0.6 * (1.0 - (double)it / (double)n) + 1e-3;
+        const size_t k = (size_t)(next() % 8), v1 = (size_t)(next() % lmax), v2 = (size_t)(next() % lmax);
+        if (v1 == v2 || q8[v1 * 8 + k] == q8[v2 * 8 + k]) continue;
+        std::swap(q8[v1 * 8 + k], q8[v2 * 8 + k]);
+        std::swap(idx[v1 * 8 + k], idx[v2 * 8 + k]);
+        const double a = cost8(&q8[v1 * 8]), b = cost8(&q8[v2 * 8]);
+        const double d = a + b - cost[v1] - cost[v2];
+        if (d < 0 || unif() < std::exp(-d / T)) {
+            cost[v1] = a;
+            cost[v2] = b;
+            cur += d;
+            if (cur < bestc - 1e-9) { bestc = cur; best = q8; bidx = idx; }
+        } else {
+            std::swap(q8[v1 * 8 + k], q8[v2 * 8 + k]);
+            std::swap(idx[v1 * 8 + k], idx[v2 * 8 + k]);
+        }
+    }
+    std::vector<int32_t> s2(lmax * 8);
+    std::vector<double> c2(lmax * 8);
+    for (size_t v = 0; v < lmax; ++v)
+        for (size_t k = 0; k < 8; ++k) {
+            const size_t from = (size_t)bidx[v * 8 + k] * 32 + q * 8 + k;
+            s2[v * 8 + k] = src[from];
+            c2[v * 8 + k] = coef[from];
+        }
+    for (size_t v = 0; v < lmax; ++v)
+        for (size_t k = 0; k < 8; ++k) {
+            src[v * 32 + q * 8 + k] = s2[v * 8 + k];
+            coef[v * 32 + q * 8 + k] = c2[v * 8 + k];
+        }
+}
+
 // Length-sorted, 32-column-sliced ELL of packed one-body lists given as a CSR
 // (ptr[0..ncols]).  put(csr_index) returns one entry.
 template <typename Put>
@@ -507,7 +572,7 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
         size_t base, lmax;
         int64_t nsrc;
     };
-    std::vector<CoreSlice> core_slices;
+    std::vector<CoreSlice> core_slices, nn_slices;
     for (size_t s = 0; s < nsec; ++s) {
         const int64_t n = NS.sec[s].count;
         // column order: lexicographic (descending) by the per-class list lengths
@@ -583,6 +648,7 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
             P.nn_sinfo.push_back((int32_t)((int64_t)P.nn_src.size() - P.sec_nn_ent[s]));
             P.nn_sinfo.push_back((int32_t)lmax);
             const size_t base = P.nn_src.size();
+            nn_slices.push_back({base, lmax, 0});
             P.nn_src.resize(base + lmax * 32, 0);
             P.nn_coef.resize(base + lmax * 32, 0.0);
             for (size_t lane = 0; lane < 32; ++lane)
@@ -596,8 +662,8 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
     while (P.sinfo.size() % 4) P.sinfo.push_back(0);
     while (P.ent.size() % 4) P.ent.push_back((ws - 1u) << 16);
     P.core_ent.resize(P.ent.size(), (ws - 1u) << 16);
-    {   // refine the pn-core order, slices in parallel: ~100 moves per entry, fewer
-        // for very large tables (at most ~1.5e8 moves in all)
+    {   // refine the pn-core and like-particle orders, slices in parallel: ~100 moves
+        // per entry, fewer for very large tables (at most ~1.5e8 moves for each)
         const double tot = (double)std::max<size_t>(P.core_ent.size(), 1);
         const int ipe = (int)std::max(1.0, std::min(100.0, 1.5e8 / tot));
 #pragma omp parallel for schedule(dynamic, 8)
@@ -605,6 +671,14 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
             const CoreSlice &c = core_slices[(size_t)i];
             anneal_slice(P.core_ent.data() + c.base, c.lmax, (ws - 1u) << 16, c.nsrc,
                          0x5DEECE66Dull * (uint64_t)(i + 1), ipe);
+        }
+        const double totn = (double)std::max<size_t>(P.nn_src.size(), 1);
+        const int ipn = (int)std::max(1.0, std::min(100.0, 1.5e8 / totn));
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t i = 0; i < 4 * (int64_t)nn_slices.size(); ++i) {
+            const CoreSlice &c = nn_slices[(size_t)(i / 4)];
+            anneal_nn_quarter(P.nn_src.data() + c.base, P.nn_coef.data() + c.base, c.lmax, (size_t)(i % 4),
+                              0x2545F4914F6CDD1Dull * (uint64_t)(i + 1), ipn);
         }
     }
     // pre-signed W rows: group g, operator a, proton sign sp -> [ sp W[a][.] | -sp W[a][.] ]
