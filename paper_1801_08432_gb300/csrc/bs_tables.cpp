@@ -291,7 +291,7 @@ void bank_schedule_rot(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
 // Cost of one quarter warp's step: the wavefronts of the two chunk loads
 // (the most distinct addresses in one bank group) plus half those of the
 // weight-row load.
-double quarter_cost(const uint32_t *e, const uint32_t *rot, int n)
+void quarter_terms(const uint32_t *e, const uint32_t *rot, int n, double &chunks, double &weights)
 {
     double tot = 0.0;
     for (uint32_t chunk = 0; chunk < 2; ++chunk) {
@@ -315,7 +315,43 @@ double quarter_cost(const uint32_t *e, const uint32_t *rot, int n)
         wrow[i] = w;
         if (!seen) mx = std::max(mx, ++cnt[w & 7]);
     }
-    return tot + 0.5 * mx;
+    chunks = tot;
+    weights = mx;
+}
+
+double quarter_cost(const uint32_t *e, const uint32_t *rot, int n)
+{
+    double x, w;
+    quarter_terms(e, rot, n, x, w);
+    return x + 0.5 * w;
+}
+
+// Wavefronts of one quarter warp's element load when an element is one
+// 16-byte chunk (k = 4 FP32 vectors): the most distinct source columns that
+// share a bank group (src mod 8).
+double quarter_cost_k4(const uint32_t *e, int n)
+{
+    uint32_t addr[8];
+    int cnt[8] = {}, mx = 0;
+    for (int i = 0; i < n; ++i) {
+        const uint32_t a = e[i] & 0xFFFFu;
+        bool seen = false;
+        for (int j = 0; j < i; ++j) seen = seen || addr[j] == a;
+        addr[i] = a;
+        if (!seen) mx = std::max(mx, ++cnt[a & 7]);
+    }
+    return mx;
+}
+
+
+// The annealing objective of the pn-core order: the k = 8 chunk loads, the
+// weight load counted in full and half the k = 4 element load, so that one
+// order serves both block widths the product runs at.
+double pn_order_cost(const uint32_t *e, const uint32_t *rot)
+{
+    double x, w;
+    quarter_terms(e, rot, 8, x, w);
+    return x + w + 0.5 * quarter_cost_k4(e, 8);
 }
 
 void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
@@ -382,7 +418,7 @@ void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
 }
 
 // Whole-slice refinement of the pn-core step order (lmax steps x 32 lanes at E,
-// [step][lane]) under the cost of quarter_cost: per quarter warp, a move
+// [step][lane]) under pn_order_cost: per quarter warp, a move
 // either swaps one lane's entries at two steps or, for a padding entry (zero
 // weight row), sets its source column to 0..3 (when the source row has 4 or
 // more), so that it takes a free bank group.  Moves are accepted by the
@@ -408,7 +444,7 @@ void anneal_slice(uint32_t *E, size_t lmax, uint32_t pad, int64_t nsrc, uint64_t
         for (size_t v = 0; v < lmax; ++v)
             for (size_t k = 0; k < 8; ++k) q8[v * 8 + k] = E[v * 32 + q * 8 + k];
         double cur = 0.0;
-        for (size_t v = 0; v < lmax; ++v) cur += (cost[v] = quarter_cost(&q8[v * 8], rots, 8));
+        for (size_t v = 0; v < lmax; ++v) cur += (cost[v] = pn_order_cost(&q8[v * 8], rots));
         double bestc = cur;
         best = q8;
         const int64_t n = (int64_t)ipe * (int64_t)lmax * 8;
@@ -419,7 +455,7 @@ void anneal_slice(uint32_t *E, size_t lmax, uint32_t pad, int64_t nsrc, uint64_t
             if ((a >> 16) == (pad >> 16) && nsrc >= 4 && next() % 10 < 3) {   // a padding entry's source column
                 const uint32_t old = a;
                 a = pad | (uint32_t)(next() % 4);
-                const double c1 = quarter_cost(&q8[v1 * 8], rots, 8), d = c1 - cost[v1];
+                const double c1 = pn_order_cost(&q8[v1 * 8], rots), d = c1 - cost[v1];
                 if (d < 0 || unif() < std::exp(-d / T)) {
                     cost[v1] = c1;
                     cur += d;
@@ -433,7 +469,7 @@ void anneal_slice(uint32_t *E, size_t lmax, uint32_t pad, int64_t nsrc, uint64_t
             uint32_t &b = q8[v2 * 8 + k];
             if (v1 == v2 || a == b) continue;
             std::swap(a, b);
-            const double c1 = quarter_cost(&q8[v1 * 8], rots, 8), c2 = quarter_cost(&q8[v2 * 8], rots, 8);
+            const double c1 = pn_order_cost(&q8[v1 * 8], rots), c2 = pn_order_cost(&q8[v2 * 8], rots);
             const double d = c1 + c2 - cost[v1] - cost[v2];
             if (d < 0 || unif() < std::exp(-d / T)) {
                 cost[v1] = c1;
@@ -451,8 +487,9 @@ void anneal_slice(uint32_t *E, size_t lmax, uint32_t pad, int64_t nsrc, uint64_t
 
 // The like-particle lists (src, coef) of one quarter warp q (lanes 8q .. 8q+7)
 // of one 32-column slice, [step][lane]: the same refinement for the kernels
-// that read a 32-byte element's chunks lane parity first, at the cost of the
-// two chunk loads of the quarter (no weights); src and coef move together.
+// that read a 32-byte element's chunks lane parity first (k = 8) or a
+// 16-byte element (k = 4), at the cost of the quarter's two chunk loads plus
+// its k = 4 element load (no weights); src and coef move together.
 // Quarters touch disjoint lanes, so they can run in parallel.
 void anneal_nn_quarter(int32_t *src, double *coef, size_t lmax, size_t q, uint64_t seed, int ipe)
 {
@@ -466,7 +503,11 @@ void anneal_nn_quarter(int32_t *src, double *coef, size_t lmax, size_t q, uint64
     };
     auto unif = [&next]() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); };
     const uint32_t rots[8] = {0, 1, 0, 1, 0, 1, 0, 1};
-    auto cost8 = [&rots](const uint32_t *e) { return quarter_cost(e, rots, 8) - 0.5; };   // weight rows all 0: 0.5
+    auto cost8 = [&rots](const uint32_t *e) {   // k = 8 chunk loads + the k = 4 element load
+        double x, w;
+        quarter_terms(e, rots, 8, x, w);
+        return x + quarter_cost_k4(e, 8);
+    };
     std::vector<uint32_t> q8(lmax * 8), best(lmax * 8);
     std::vector<uint32_t> idx(lmax * 8), bidx(lmax * 8);   // the entries' original steps, to move coef
     std::vector<double> cost(lmax);
@@ -663,17 +704,20 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
     while (P.ent.size() % 4) P.ent.push_back((ws - 1u) << 16);
     P.core_ent.resize(P.ent.size(), (ws - 1u) << 16);
     {   // refine the pn-core and like-particle orders, slices in parallel: ~100 moves
-        // per entry, fewer for very large tables (at most ~1.5e8 moves for each)
-        const double tot = (double)std::max<size_t>(P.core_ent.size(), 1);
-        const int ipe = (int)std::max(1.0, std::min(100.0, 1.5e8 / tot));
+        // per entry, fewer for large tables (at most ~1.5e8 moves for each); below
+        // 10 moves per entry the search gains nothing and is skipped
+        auto moves = [](size_t n) {
+            const double m = std::min(100.0, 1.5e8 / (double)std::max<size_t>(n, 1));
+            return m < 10.0 ? 0 : (int)m;
+        };
+        const int ipe = moves(P.core_ent.size());
 #pragma omp parallel for schedule(dynamic, 8)
         for (int64_t i = 0; i < (int64_t)core_slices.size(); ++i) {
             const CoreSlice &c = core_slices[(size_t)i];
             anneal_slice(P.core_ent.data() + c.base, c.lmax, (ws - 1u) << 16, c.nsrc,
                          0x5DEECE66Dull * (uint64_t)(i + 1), ipe);
         }
-        const double totn = (double)std::max<size_t>(P.nn_src.size(), 1);
-        const int ipn = (int)std::max(1.0, std::min(100.0, 1.5e8 / totn));
+        const int ipn = moves(P.nn_src.size());
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t i = 0; i < 4 * (int64_t)nn_slices.size(); ++i) {
             const CoreSlice &c = nn_slices[(size_t)(i / 4)];
