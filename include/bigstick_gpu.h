@@ -37,6 +37,11 @@
  *   - Every call returns BS_OK (0) or a negative code; on error the output
  *     buffers are unspecified and bs_last_error() holds a message.  No C++
  *     exception crosses this interface.  A context is not thread-safe.
+ *   - Calls that apply H (bs_apply_H, bs_apply_H_host, bs_apply_H_backward,
+ *     bs_lanczos, bs_strength) share device workspace the context owns (the
+ *     partial vectors of the core-grouped kernels, the host entry point's
+ *     staging buffers).  Issue them on one stream, or order them with
+ *     events: two such calls running at the same time on the GPU race.
  */
 #ifndef BIGSTICK_GPU_H
 #define BIGSTICK_GPU_H
