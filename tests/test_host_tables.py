@@ -551,3 +551,36 @@ def test_abi_struct_layout_matches_header(tmp_path):
 def ctypes_sizeof(S):
     import ctypes
     return ctypes.sizeof(S)
+
+
+_ORDER_SCRIPT = r"""
+import hashlib, sys
+import numpy as np
+sys.path.insert(0, sys.argv[1])
+from paper_1801_08432_gb300 import _native as N, inputs as I
+o, s, t = I.space("sd")
+c = N.Context(-1).build_basis(o, 6, 6, 0, 1).load_interaction(s, t)
+h = hashlib.sha256()
+for name, dt in (("core_ent", np.uint32), ("pe_ent", np.uint32), ("pe_nn_src", np.int32), ("pe_nn_coef", np.float64)):
+    h.update(c.table(name, dt).tobytes())
+print(h.hexdigest())
+"""
+
+
+def test_list_orders_do_not_depend_on_the_thread_count():
+    """The list step orders (greedy, then the seeded annealing of each slice,
+    run in parallel) are the same for any number of host threads, so the
+    product is bit-reproducible across machines: sd 6p6n (28Si) tables built
+    with 1 and with 4 OpenMP threads, in fresh processes."""
+    import os
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    out = []
+    for nt in (1, 4):
+        env = dict(os.environ, OMP_NUM_THREADS=str(nt))
+        r = subprocess.run([sys.executable, "-c", _ORDER_SCRIPT, root], env=env, capture_output=True, text=True,
+                           timeout=600)
+        assert r.returncode == 0, r.stderr[-2000:]
+        out.append(r.stdout.strip().splitlines()[-1])
+    assert out[0] == out[1]
