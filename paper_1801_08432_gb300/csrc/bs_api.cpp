@@ -234,6 +234,8 @@ int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std
     if ((rc = put(D, D.c32.nne_coef, f.data(), f.size(), err))) return rc;
     int zero = 0;
     if ((rc = put(D, D.err, &zero, 1, err))) return rc;
+    const int zeros[4] = {0, 0, 0, 0};
+    if ((rc = put(D, D.core_next, zeros, 4, err))) return rc;
     // pipelined kernel
     if ((rc = put(D, D.pe_perm, T.pe.perm.data(), T.pe.perm.size(), err))) return rc;
     if ((rc = put(D, D.pe_sinfo, T.pe.sinfo.data(), T.pe.sinfo.size(), err))) return rc;
@@ -415,7 +417,12 @@ int bs_load_interaction(bs_ctx *c, const double *spe, int n_spe, const bs_tbme *
             c->tbme_in.swap(tb);
         }
         if (rc) return rc;
-        rc = build_tables(c->basis, c->inter, c->tab, c->err);
+        int nsm = 152;   // the persistent kernels run one CTA per SM: balance their units for this device
+        if (c->device >= 0 && cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+            (void)cudaGetLastError();
+            nsm = 152;
+        }
+        rc = build_tables(c->basis, c->inter, c->tab, c->err, nsm);
         if (rc) return rc;
         if (c->device >= 0) {
             if (c->adj_gpp) { cudaFree(c->adj_gpp); cudaFree(c->adj_gnn); cudaFree(c->adj_rho); }

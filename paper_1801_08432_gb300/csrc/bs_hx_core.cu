@@ -105,6 +105,7 @@ struct SlotRing {
 };
 
 struct CoreArgs {
+    int *next;         // units claimed beyond the first grid's worth (zeroed before the launch), or null: static
     const CoreUnit *units;
     const CoreSrc *src;
     const int32_t *perm;
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     uint32_t *lists = reinterpret_cast<uint32_t *>(slots + (size_t)A.S * A.slot_elems);
     int32_t *sinf = reinterpret_cast<int32_t *>(lists + (size_t)A.nlb * A.list_elems);
     uint64_t *bars = reinterpret_cast<uint64_t *>(sinf + A.nlb * SI);
+    int *uidp = reinterpret_cast<int *>(bars + 2 * A.S + A.nlb);   // per slot: the unit after the current one
     const uint32_t full0 = su32(bars), empty0 = su32(bars + A.S), lempty0 = su32(bars + 2 * A.S);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
 
@@ -169,13 +171,41 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             hN = A.units[blockIdx.x].nN;
             hs = A.units[blockIdx.x].src0;
         }
-        for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
+        // units: blockIdx.x first, then each one claims the next (a counter shared by
+        // the CTAs, offset by the grid, or blockIdx.x + grid, + 2 grid, ... without
+        // one); the next unit rides in the current unit's first slot to the consumers
+        for (int u = blockIdx.x, un = 0; u < A.nunits; u = un) {
             const int nsrc = hn, nN = hN;
             const int64_t src0 = hs;
-            if (u + (int)gridDim.x < A.nunits) {
-                hn = A.units[u + gridDim.x].nsrc;
-                hN = A.units[u + gridDim.x].nN;
-                hs = A.units[u + gridDim.x].src0;
+            {
+                int v = 0;
+                if (lane == 0) v = A.next ? (int)gridDim.x + atomicAdd(A.next, 1) : u + (int)gridDim.x;
+                un = __shfl_sync(0xffffffffu, v, 0);
+            }
+            if (un < A.nunits) {
+                hn = A.units[un].nsrc;
+                hN = A.units[un].nN;
+                hs = A.units[un].src0;
+            }
+            if (nsrc == 0) {   // no sources: one empty slot carries the next unit
+                int bad = 0;
+                if (lane == 0) {
+                    const int s = rg.s;
+                    if (rg.round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(rg.round - 1) & 1u)) {
+                        bad = 1;
+                    } else {
+                        uidp[s] = un;
+                        bar_arrive(full0 + 8u * s);
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, bad, 0)) {
+                    if (lane == 0) {
+                        atomicExch(A.err, BS_ETIMEOUT);
+                        drain_ring(full0, A.S, (int64_t)rg.round * A.S + rg.s);
+                    }
+                    return;
+                }
+                rg.next(A.S);
             }
             const int nsl = (nN + 31) / 32;
             const int ntile = (nN + C - 1) / C;
@@ -225,6 +255,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                                 const uint32_t wbytes = (uint32_t)(A.wtab * (int)sizeof(float));
                                 float *dst = slots + (size_t)s * A.slot_elems;
                                 const uint32_t fb = full0 + 8u * s;
+                                if (tile == 0 && q0 + j == 0) uidp[s] = un;   // published by the arrive below
                                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                                 bar_expect_tx(fb, bytes + wbytes + 32u + lbytes + sbytes);
                                 bulk_copy(su32(dst), x + xe * K, bytes, fb);
@@ -268,15 +299,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
         const CoreUnit *U = A.units + blockIdx.x;
         hn = U->nsrc; hN = U->nN; hp = U->perm_off; ho = U->doff; hd1 = U->drow[1]; hd2 = U->drow[2];
     }
-    for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
+    for (int u = blockIdx.x, un = A.nunits; u < A.nunits; u = un) {
         const int nsrc = hn, nN = hN, perm_off = hp;
         const int64_t doff = ho;
         // destination rows of the unit (packed to the front): 1, 2 or more
         const int nrow = hd1 < 0 ? 1 : hd2 < 0 ? 2 : 4;
-        if (u + (int)gridDim.x < A.nunits) {
-            const CoreUnit *U = A.units + u + gridDim.x;
-            hn = U->nsrc; hN = U->nN; hp = U->perm_off; ho = U->doff; hd1 = U->drow[1]; hd2 = U->drow[2];
-        }
         const int nsl = (nN + 31) / 32;
         const int ntile = (nN + C - 1) / C;
         for (int tile = 0; tile < ntile; ++tile) {
@@ -298,11 +325,24 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             int64_t prev = -1;
             int la = 0, lb = 0;
             const uint32_t *lstA = lists, *lstB = lists;
-            for (int q = 0; q < nsrc; ++q, rg.next(A.S)) {
+            // a unit without sources still takes one (empty) slot: the one with the next unit
+            for (int q = 0; q < nsrc || (nsrc == 0 && tile == 0 && q == 0); ++q, rg.next(A.S)) {
                 const int s = rg.s;
                 if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)rg.round & 1u))) {
                     if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
                     return;
+                }
+                if (tile == 0 && q == 0) {   // the next unit: read its record now, use it after this one
+                    un = uidp[s];
+                    if (un < A.nunits) {
+                        const CoreUnit *U = A.units + un;
+                        hn = U->nsrc; hN = U->nN; hp = U->perm_off; ho = U->doff; hd1 = U->drow[1]; hd2 = U->drow[2];
+                    }
+                }
+                if (nsrc == 0) {
+                    __syncwarp();
+                    if (lane == 0) bar_arrive(empty0 + 8u * s);
+                    continue;
                 }
                 const float *Xs = slots + (size_t)s * A.slot_elems;
                 const float *Wt = Xs + A.row_stride;
@@ -377,6 +417,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
 }
 
 struct PPArgs {
+    int *next;             // as CoreArgs::next
     const PPUnit *units;
     const int32_t *srow;
     const float *w;        // kPPG weights per source
@@ -400,6 +441,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     extern __shared__ __align__(128) unsigned char smem[];
     float *slots = reinterpret_cast<float *>(smem);
     uint64_t *bars = reinterpret_cast<uint64_t *>(slots + (size_t)A.S * A.slot_elems);
+    int *uidp = reinterpret_cast<int *>(bars + 2 * A.S);   // per slot: the unit after the current one
     const uint32_t full0 = su32(bars), empty0 = su32(bars + A.S);
     constexpr int C = NW * 32;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -424,12 +466,38 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             hn = A.units[blockIdx.x].nsrc; hN = A.units[blockIdx.x].nN;
             hs = A.units[blockIdx.x].src0; ho = A.units[blockIdx.x].doff;
         }
-        for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
+        // units claimed as in the pn kernel; the next one rides in the first slot
+        for (int u = blockIdx.x, un = 0; u < A.nunits; u = un) {
             const int nsrc = hn, nN = hN;
             const int64_t src0 = hs, doff = ho;
-            if (u + (int)gridDim.x < A.nunits) {
-                hn = A.units[u + gridDim.x].nsrc; hN = A.units[u + gridDim.x].nN;
-                hs = A.units[u + gridDim.x].src0; ho = A.units[u + gridDim.x].doff;
+            {
+                int v = 0;
+                if (lane == 0) v = A.next ? (int)gridDim.x + atomicAdd(A.next, 1) : u + (int)gridDim.x;
+                un = __shfl_sync(0xffffffffu, v, 0);
+            }
+            if (un < A.nunits) {
+                hn = A.units[un].nsrc; hN = A.units[un].nN;
+                hs = A.units[un].src0; ho = A.units[un].doff;
+            }
+            if (nsrc == 0) {   // no sources: one empty slot carries the next unit
+                int bad = 0;
+                if (lane == 0) {
+                    const int s = rg.s;
+                    if (rg.round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(rg.round - 1) & 1u)) {
+                        bad = 1;
+                    } else {
+                        uidp[s] = un;
+                        bar_arrive(full0 + 8u * s);
+                    }
+                }
+                if (__shfl_sync(0xffffffffu, bad, 0)) {
+                    if (lane == 0) {
+                        atomicExch(A.err, BS_ETIMEOUT);
+                        drain_ring(full0, A.S, (int64_t)rg.round * A.S + rg.s);
+                    }
+                    return;
+                }
+                rg.next(A.S);
             }
             const int ntile = (nN + C - 1) / C;
             const uint32_t bytes = (uint32_t)(nN * K * (int)sizeof(float));
@@ -449,6 +517,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                             } else {
                                 const uint32_t fb = full0 + 8u * s;
                                 float *dst = slots + (size_t)s * A.slot_elems;
+                                if (tile == 0 && q0 + j == 0) uidp[s] = un;   // published by the arrive below
                                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                                 bar_expect_tx(fb, bytes + wbytes);
                                 bulk_copy(su32(dst), x + (doff + (int64_t)row * nN) * K, bytes, fb);
@@ -475,12 +544,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     int hn = 0, hN = 0;
     int64_t ho = 0;
     if (blockIdx.x < A.nunits) { hn = A.units[blockIdx.x].nsrc; hN = A.units[blockIdx.x].nN; ho = A.units[blockIdx.x].doff; }
-    for (int u = blockIdx.x; u < A.nunits; u += gridDim.x) {
+    for (int u = blockIdx.x, un = A.nunits; u < A.nunits; u = un) {
         const int nsrc = hn, nN = hN;
         const int64_t doff = ho;
-        if (u + (int)gridDim.x < A.nunits) {
-            hn = A.units[u + gridDim.x].nsrc; hN = A.units[u + gridDim.x].nN; ho = A.units[u + gridDim.x].doff;
-        }
         const PPUnit *U = A.units + u;
         const int ntile = (nN + C - 1) / C;
         for (int tile = 0; tile < ntile; ++tile) {
@@ -492,13 +558,18 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             for (int p = 0; p < kPPG; ++p)
 #pragma unroll
                 for (int q = 0; q < K / 2; ++q) acc[p][q] = make_float2(0.0f, 0.0f);
-            for (int q = 0; q < nsrc; ++q, rg.next(A.S)) {
+            // a unit without sources still takes one (empty) slot: the one with the next unit
+            for (int q = 0; q < nsrc || (nsrc == 0 && tile == 0 && q == 0); ++q, rg.next(A.S)) {
                 const int s = rg.s;
                 if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)rg.round & 1u))) {
                     if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
                     return;
                 }
-                if (active) {
+                if (tile == 0 && q == 0) {   // the next unit: read its record now, use it after this one
+                    un = uidp[s];
+                    if (un < A.nunits) { hn = A.units[un].nsrc; hN = A.units[un].nN; ho = A.units[un].doff; }
+                }
+                if (active && nsrc > 0) {
                     const float *Xs = slots + (size_t)s * A.slot_elems;
                     float w[kPPG];
 #pragma unroll
@@ -825,11 +896,12 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     // deeper ring pays more than a third buffer)
     int nlb = nlb_req > 0 ? nlb_req : 3, S = 0;
     for (; nlb >= 2; --nlb) {
-        const size_t fixed = (size_t)nlb * list_elems * 4 + (size_t)nlb * SI * 4 + 8 * (size_t)nlb;
+        const size_t fixed = (size_t)nlb * list_elems * 4 + (size_t)nlb * SI * 4 + 8 * (size_t)nlb + 64;
         S = target > fixed ? (int)std::min<size_t>(8, (target - fixed) / slot_bytes) : 0;
         if (nlb_req > 0 || S >= 7 || nlb == 2) break;
     }
-    const size_t fixed = (size_t)nlb * list_elems * 4 + (size_t)nlb * SI * 4 + 8 * (size_t)nlb;
+    // (+ 64 bytes: the slots' next-unit words after the barriers, S <= 8)
+    const size_t fixed = (size_t)nlb * list_elems * 4 + (size_t)nlb * SI * 4 + 8 * (size_t)nlb + 64;
     used = S >= 2;
     if (!used) return cudaSuccess;
     const size_t smem = (size_t)S * slot_elems * sizeof(float) + fixed + 16 * (size_t)S;
@@ -840,7 +912,7 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, Dv.dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (NW + 1) * 32, smem)) != cudaSuccess) return e;
     const int grid = std::max(1, std::min(Dv.ncunits, nsm * std::max(per, 1)));
-    CoreArgs A{Dv.cunits, Dv.csrc, Dv.pe_perm, Dv.pe_sinfo, Dv.core_ent, Dv.err, Dv.ncunits, S,
+    CoreArgs A{Dv.core_next, Dv.cunits, Dv.csrc, Dv.pe_perm, Dv.pe_sinfo, Dv.core_ent, Dv.err, Dv.ncunits, S,
                row_stride, wtab, slot_elems, list_elems, nlb, (uint32_t)Dv.wsign, (int64_t)ctx->basis.dim * K};
     kern<<<grid, (NW + 1) * 32, smem, s>>>(A, Dv.wc32, x, part);
     return cudaGetLastError();
@@ -853,10 +925,10 @@ cudaError_t launch_pp_t(const bs_ctx *ctx, const float *x, float *part, cudaStre
     const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
     const int slot_elems = row_stride + 32;   // row, kPPG weights, padded to 128 bytes
     const size_t slot_bytes = (size_t)slot_elems * sizeof(float) + 16;
-    const int S = (int)std::min<size_t>(8, target / slot_bytes);
+    const int S = target > 64 ? (int)std::min<size_t>(8, (target - 64) / slot_bytes) : 0;
     used = S >= 2;
     if (!used) return cudaSuccess;
-    const size_t smem = (size_t)S * slot_elems * sizeof(float) + 16 * (size_t)S;
+    const size_t smem = (size_t)S * slot_elems * sizeof(float) + 16 * (size_t)S + 64;   // + the slots' next-unit words
     auto kern = hx_ppcore_kernel<K, NW, MINB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -864,7 +936,7 @@ cudaError_t launch_pp_t(const bs_ctx *ctx, const float *x, float *part, cudaStre
     if ((e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, Dv.dev)) != cudaSuccess) return e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kern, (NW + 1) * 32, smem)) != cudaSuccess) return e;
     const int grid = std::max(1, std::min(Dv.nppunits, nsm * std::max(per, 1)));
-    PPArgs A{Dv.ppunits, Dv.pps_row, Dv.pps_w32, Dv.err, Dv.nppunits, S, row_stride, slot_elems,
+    PPArgs A{Dv.core_next ? Dv.core_next + 1 : nullptr, Dv.ppunits, Dv.pps_row, Dv.pps_w32, Dv.err, Dv.nppunits, S, row_stride, slot_elems,
              (int64_t)ctx->basis.dim * K};
     kern<<<grid, (NW + 1) * 32, smem, s>>>(A, x, part);
     return cudaGetLastError();
@@ -944,6 +1016,9 @@ cudaError_t launch_hx_core(const bs_ctx *c, const void *x, void *y, int k, bs_dt
     if (e != cudaSuccess || !fits) return e;
     float *part = (float *)c->core_part;
     const float *xf = (const float *)x;
+    // the pn and pp kernels' unit counters start at zero for every product (a memset
+    // node in a captured graph), before the timed window of the dominant kernel
+    if (c->dev.core_next && (e = cudaMemsetAsync(c->dev.core_next, 0, 2 * sizeof(int), s)) != cudaSuccess) return e;
     if (t0 && (e = cudaEventRecord(t0, s)) != cudaSuccess) return e;
     e = k == 8 ? launch_core_k<8>(c, xf, part, s, v, used) : launch_core_k<4>(c, xf, part, s, v, used);
     if (e != cudaSuccess || !used) return e;

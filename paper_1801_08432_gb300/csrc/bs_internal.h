@@ -225,6 +225,7 @@ struct PPUnit {
 };
 
 struct Tables {
+    int grid = 152;                      // CTAs of the persistent core-grouped kernels (units are balanced for it)
     LikeJumps pp, nn;                    // moves inside a sector (diagonal and SPE included)
     LikeCross ppx, nnx;                  // moves between sectors (W-truncated bases only)
     std::vector<LikeLink> llinks;        // sorted by dst block
@@ -330,6 +331,7 @@ struct Device {
     uint32_t *n1e_ent = nullptr;
     int max_nN = 0, max_nb = 0, max_pu = 0, wsign = 0;   // widest neutron sector, widest W row, most proton jumps per (row, link)
     int *err = nullptr;                       // device status word (BS_ETIMEOUT from bounded waits)
+    int *core_next = nullptr;                 // unit counters of the persistent core-grouped kernels: pn, pp
     // pipelined kernel
     int32_t *pe_perm = nullptr, *pe_sinfo = nullptr, *pe_nn_src = nullptr, *pe_nn_sinfo = nullptr;
     uint32_t *pe_ent = nullptr;
@@ -389,7 +391,7 @@ int build_basis(Basis &B, const bs_orbit *orbits, int n_orbits, int Z, int N, in
                 std::string &err);
 int build_interaction(const Basis &B, const double *spe, int n_spe, const bs_tbme *tbme, int n_tbme,
                       Interaction &I, std::string &err);
-int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err);
+int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err, int grid = 152);
 int upload(const Basis &B, const Interaction &I, const Tables &T, Device &D, std::string &err);
 void release(Device &D);
 int launch_hx(const bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dt, void *stream, std::string &err);

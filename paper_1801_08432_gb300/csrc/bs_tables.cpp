@@ -754,6 +754,42 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
 // (2m, parity) key.  Sources of a unit: the SDs c + k for every state k not in
 // c whose block is linked to the unit's destination block, ordered by the key
 // of k so that consecutive sources share one link (one set of neutron lists).
+// Order of units for a persistent kernel whose CTA b takes units b, b + G,
+// b + 2G, ... (G = grid): the units come sorted by decreasing cost, and each
+// round of G goes heaviest first to the CTAs with the least cost so far, so
+// that the CTAs end within about one unit of each other (round-robin on the
+// sorted list gives CTA 0 the heaviest unit of every round).  Every CTA keeps
+// the same number of units (one more for the first n mod G), so the result is
+// again a round-robin layout: position j G + b holds CTA b's j-th unit.
+template <typename U>
+void balance_round_robin(std::vector<U> &units, int G)
+{
+    const size_t n = units.size(), g = (size_t)std::max(1, G);
+    if (n <= g) return;
+    std::vector<std::vector<size_t>> cta(g);
+    std::vector<double> load(g, 0.0);
+    std::vector<size_t> by(g);
+    for (size_t r0 = 0; r0 < n; r0 += g) {
+        const size_t m = std::min(g, n - r0);
+        for (size_t b = 0; b < g; ++b) by[b] = b;
+        std::stable_sort(by.begin(), by.end(), [&](size_t a, size_t b) { return load[a] < load[b]; });
+        for (size_t j = 0; j < m; ++j) {
+            cta[by[j]].push_back(r0 + j);
+            load[by[j]] += units[r0 + j].cost;
+        }
+    }
+    // the CTAs with the extra unit take the first labels
+    std::vector<size_t> lab(g);
+    for (size_t b = 0; b < g; ++b) lab[b] = b;
+    std::stable_sort(lab.begin(), lab.end(), [&](size_t a, size_t b) { return cta[a].size() > cta[b].size(); });
+    std::vector<U> out;
+    out.reserve(n);
+    for (size_t j = 0; out.size() < n; ++j)
+        for (size_t b = 0; b < g; ++b)
+            if (j < cta[lab[b]].size()) out.push_back(std::move(units[cta[lab[b]][j]]));
+    units.swap(out);
+}
+
 void build_core_units(const Basis &B, const Interaction &I, Tables &T)
 {
     T.cunits.clear();
@@ -886,7 +922,20 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
             x.u.nN = (int)B.blocks[(size_t)x.u.dblock].nN;
             x.u.perm_off = (int)T.pe.perm_off[(size_t)B.blocks[(size_t)x.u.dblock].ns];
             x.u.doff = B.blocks[(size_t)x.u.dblock].off;
-            x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)x.u.dblock].nN;
+            {   // cost: per source and tile of 18 column slices, the longest list (all warps
+                // wait for it) weighted by the shared-memory wavefronts of a step with this
+                // many rows (entry + element + weights: 10, 11, 13), plus a slot overhead
+                const int nN = (int)B.blocks[(size_t)x.u.dblock].nN, nsl = (nN + 31) / 32;
+                const double rf = nr <= 1 ? 1.0 : nr == 2 ? 1.1 : 1.3;
+                x.cost = 0.0;
+                for (const CoreSrc &cs : x.src)
+                    for (int t0 = 0; t0 < nsl; t0 += 18) {
+                        int lm = 0;
+                        for (int sl = t0; sl < std::min(nsl, t0 + 18); ++sl)
+                            lm = std::max(lm, (int)T.pe.sinfo[(size_t)(cs.sinfo_base + 2 * sl + 1)]);
+                        x.cost += rf * lm + 4.0;
+                    }
+            }
             for (int k : by_key) {
                 if (c >> k & 1) continue;
                 const int g = I.ops.group_of_op[(size_t)(i0 * ns + k)];
@@ -903,6 +952,7 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
             units.push_back(std::move(x));
         }
     std::stable_sort(units.begin(), units.end(), [](const U &a, const U &b) { return a.cost > b.cost; });
+    balance_round_robin(units, T.grid);
     for (U &x : units) {
         x.u.src0 = (int64_t)T.csrc.size();
         T.csrc.insert(T.csrc.end(), x.src.begin(), x.src.end());
@@ -1002,11 +1052,14 @@ void build_pp_units(const Basis &B, const Interaction &I, Tables &T)
                 x.u.nN = (int)B.blocks[(size_t)blk].nN;
                 x.u.pad = 0;
                 x.u.doff = B.blocks[(size_t)blk].off;
-                x.cost = (double)(x.u.nsrc + 1) * (double)B.blocks[(size_t)blk].nN;
+                // cost: one slot per source and tile of 576 columns (one element per
+                // thread each), plus the stores of the unit's rows
+                x.cost = (double)(x.u.nsrc + 3) * (double)((B.blocks[(size_t)blk].nN + 575) / 576);
                 units.push_back(std::move(x));
             }
         }
     std::stable_sort(units.begin(), units.end(), [](const U &a, const U &b) { return a.cost > b.cost; });
+    balance_round_robin(units, T.grid);
     for (U &x : units) {
         x.u.src0 = (int64_t)T.pps_row.size();
         T.pps_row.insert(T.pps_row.end(), x.row.begin(), x.row.end());
@@ -1016,10 +1069,11 @@ void build_pp_units(const Basis &B, const Interaction &I, Tables &T)
 }
 }  // namespace
 
-int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err)
+int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &err, int grid)
 {
     (void)err;
     T = Tables();
+    T.grid = std::max(1, grid);
     like_jumps(B, I, 0, T.pp, T.ppx, T.n_pp);
     like_jumps(B, I, 1, T.nn, T.nnx, T.n_nn);
     onebody_jumps(B, I, 0, T.p1, T.n_p1);
