@@ -116,16 +116,19 @@ struct CoreArgs {
     int S;             // ring slots
     int row_stride;    // floats per staged row (multiple of 32)
     int wtab;          // floats per weight table (2 wsign x 4)
-    int slot_elems;    // row_stride + wtab + 8 (the slot's CoreSrc)
+    int slot_elems;    // row_stride + wtab + 16 (the slot's CoreSrc, then the unit's rows and ranks)
     int list_elems;    // entries per list buffer (multiple of 32)
     int nlb;           // list buffers (2..4)
     uint32_t ws;       // wsign
     int64_t part_stride;   // dim * K
 };
 
-// Shared memory: S slots [source row | weight table | CoreSrc], nlb list
-// buffers (one link's neutron lists for the tile's slices) with their slice
-// info, then the barriers: full[S], empty[S], list_empty[nlb].  A "group" is a
+// Shared memory: S slots [source row | weight table | CoreSrc | the unit's
+// drow and meta (only in a tile's last slot, which the consumers keep until
+// they have stored the tile)], nlb list buffers (one link's neutron lists for
+// the tile's slices) with their slice info, then the barriers: full[S],
+// empty[S], list_empty[nlb], then one int per slot: the next unit (written
+// into a unit's first slot).  A "group" is a
 // run of slots of one tile that share a link; its lists arrive with its first
 // slot, in buffer (group % nlb), and each consumer warp releases the buffer
 // when it starts the next group, so the producer can run nlb - 1 groups ahead.
@@ -187,31 +190,35 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 hN = A.units[un].nN;
                 hs = A.units[un].src0;
             }
-            if (nsrc == 0) {   // no sources: one empty slot carries the next unit
-                int bad = 0;
-                if (lane == 0) {
-                    const int s = rg.s;
-                    if (rg.round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(rg.round - 1) & 1u)) {
-                        bad = 1;
-                    } else {
-                        uidp[s] = un;
-                        bar_arrive(full0 + 8u * s);
-                    }
-                }
-                if (__shfl_sync(0xffffffffu, bad, 0)) {
-                    if (lane == 0) {
-                        atomicExch(A.err, BS_ETIMEOUT);
-                        drain_ring(full0, A.S, (int64_t)rg.round * A.S + rg.s);
-                    }
-                    return;
-                }
-                rg.next(A.S);
-            }
             const int nsl = (nN + 31) / 32;
             const int ntile = (nN + C - 1) / C;
             for (int tile = 0; tile < ntile; ++tile) {
                 const int sl0 = tile * SL, sl1 = min(nsl, sl0 + SL);
                 int64_t prev = -1;
+                if (nsrc == 0) {   // no sources: one empty slot per tile (the first carries the next unit)
+                    int bad = 0;
+                    if (lane == 0) {
+                        const int s = rg.s;
+                        if (rg.round > 0 && bar_wait(empty0 + 8u * s, (uint32_t)(rg.round - 1) & 1u)) {
+                            bad = 1;
+                        } else {   // the slot brings the unit's rows and partial ranks (the store needs them)
+                            uidp[s] = un;
+                            const uint32_t fb = full0 + 8u * s;
+                            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                            bar_expect_tx(fb, 32u);
+                            bulk_copy(su32(slots + (size_t)s * A.slot_elems + A.row_stride + A.wtab + 8), A.units[u].drow, 32u,
+                                      fb);
+                        }
+                    }
+                    if (__shfl_sync(0xffffffffu, bad, 0)) {
+                        if (lane == 0) {
+                            atomicExch(A.err, BS_ETIMEOUT);
+                            drain_ring(full0, A.S, (int64_t)rg.round * A.S + rg.s);
+                        }
+                        return;
+                    }
+                    rg.next(A.S);
+                }
                 for (int q0 = 0; q0 < nsrc; q0 += 32) {
                     const int qm = q0 + lane;
                     int64_t mx = 0, msb = -1, mof = 0, mol = 0;
@@ -256,11 +263,14 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                                 float *dst = slots + (size_t)s * A.slot_elems;
                                 const uint32_t fb = full0 + 8u * s;
                                 if (tile == 0 && q0 + j == 0) uidp[s] = un;   // published by the arrive below
+                                // the tile's last slot also brings the unit's rows and partial ranks
+                                const uint32_t rbytes = q0 + j == nsrc - 1 ? 32u : 0u;
                                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-                                bar_expect_tx(fb, bytes + wbytes + 32u + lbytes + sbytes);
+                                bar_expect_tx(fb, bytes + wbytes + 32u + rbytes + lbytes + sbytes);
                                 bulk_copy(su32(dst), x + xe * K, bytes, fb);
                                 bulk_copy(su32(dst + A.row_stride), wc + (size_t)(wt & 0x7FFFFFFFu) * A.wtab, wbytes, fb);
                                 bulk_copy(su32(dst + A.row_stride + A.wtab), A.src + src0 + q0 + j, 32u, fb);
+                                if (rbytes) bulk_copy(su32(dst + A.row_stride + A.wtab + 8), A.units[u].drow, rbytes, fb);
                                 if (newg) {
                                     if (lbytes) bulk_copy(su32(lists + (size_t)b * A.list_elems), A.ent + lsrc, lbytes, fb);
                                     bulk_copy(su32(sinf + b * SI), A.sinfo + sb + 2 * sl0, sbytes, fb);
@@ -325,8 +335,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             int64_t prev = -1;
             int la = 0, lb = 0;
             const uint32_t *lstA = lists, *lstB = lists;
-            // a unit without sources still takes one (empty) slot: the one with the next unit
-            for (int q = 0; q < nsrc || (nsrc == 0 && tile == 0 && q == 0); ++q, rg.next(A.S)) {
+            int ls = 0;   // the tile's last slot: kept until the store, which reads the unit's rows from it
+            // a unit without sources still takes one (empty) slot per tile; the first has the next unit
+            for (int q = 0; q < nsrc || (nsrc == 0 && q == 0); ++q, rg.next(A.S)) {
                 const int s = rg.s;
                 if (__any_sync(0xffffffffu, bar_wait(full0 + 8u * s, (uint32_t)rg.round & 1u))) {
                     if (lane == 0) atomicExch(A.err, BS_ETIMEOUT);
@@ -339,11 +350,9 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                         hn = U->nsrc; hN = U->nN; hp = U->perm_off; ho = U->doff; hd1 = U->drow[1]; hd2 = U->drow[2];
                     }
                 }
-                if (nsrc == 0) {
-                    __syncwarp();
-                    if (lane == 0) bar_arrive(empty0 + 8u * s);
-                    continue;
-                }
+                const bool last = q == (nsrc > 0 ? nsrc : 1) - 1;
+                if (last) ls = s;
+                if (nsrc == 0) continue;
                 const float *Xs = slots + (size_t)s * A.slot_elems;
                 const float *Wt = Xs + A.row_stride;
                 const CoreSrc *cs = reinterpret_cast<const CoreSrc *>(Wt + A.wtab);
@@ -388,15 +397,17 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
 #pragma unroll 2
                     for (int vb = v; vb < lb; ++vb) core_step<K>(XA, XB, Wt, lstB[32 * vb], accB);
                 }
+                if (last) continue;   // released after the store
                 __syncwarp();
                 if (lane == 0) bar_arrive(empty0 + 8u * s);
             }
-            const CoreUnit *U = A.units + u;
+            // the unit's destination rows and partial ranks, brought by its last slot
+            const int *rec = reinterpret_cast<const int *>(slots + (size_t)ls * A.slot_elems + A.row_stride + A.wtab + 8);
             auto store = [&](int col, float2 (&acc)[4][K / 2]) {
                 if (col < 0) return;
 #pragma unroll
                 for (int p = 0; p < 4; ++p) {
-                    const int drow = U->drow[p], meta = U->meta[p];
+                    const int drow = rec[p], meta = rec[4 + p];
                     if (drow < 0) continue;
                     const float sg = (meta & 256) ? -1.0f : 1.0f;
                     float o[K];
@@ -412,6 +423,8 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
             };
             store(colA, accA);
             if (CPT == 2) store(colB, accB);
+            __syncwarp();
+            if (lane == 0) bar_arrive(empty0 + 8u * ls);   // the last slot, now that its record is read
         }
     }
 }
@@ -886,7 +899,7 @@ cudaError_t launch_core_t(const bs_ctx *ctx, const float *x, float *part, cudaSt
     const Device &Dv = ctx->dev;
     const int row_stride = ((Dv.max_nN * K + 31) / 32) * 32;
     const int wtab = 8 * Dv.wsign;
-    const int slot_elems = row_stride + wtab + 8;
+    const int slot_elems = row_stride + wtab + 16;   // + the source record (8 floats) and the unit's rows (8)
     const size_t slot_bytes = (size_t)slot_elems * sizeof(float) + 16;
     static_assert(NW * CPT == 18 || NW * CPT == 10, "list bounds are built for tiles of 18 or 10 slices");
     const int64_t lmaxe = Dv.core_list_max[NW * CPT == 18 ? 0 : 1];
