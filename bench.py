@@ -622,9 +622,27 @@ def ours(args):
         ctx.apply_H_host(xa, ya, kbest, N.BS_F32, sp)
     bar()
     e2e_s = time.perf_counter() - t0
+    # the same through the asynchronous host-buffer call: two streams and two staging
+    # slots, so that one step's copies in and out run while the other's product does
+    # (every step still copies its input block in and its result block out)
+    xs = [xh, torch.randn((dim, kbest), dtype=torch.float32).pin_memory()]
+    ys = [yh, torch.empty_like(xh).pin_memory()]
+    sts = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for i in range(4):
+        ctx.apply_H_host_async(xs[i % 2], ys[i % 2], kbest, N.BS_F32, sts[i % 2].cuda_stream, i % 2)
+    for st in sts:
+        st.synchronize()
+    bar()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        ctx.apply_H_host_async(xs[i % 2], ys[i % 2], kbest, N.BS_F32, sts[i % 2].cuda_stream, i % 2)
+    for st in sts:
+        st.synchronize()
+    bar()
+    e2e_pipe_s = time.perf_counter() - t0
 
     t_ms = float(np.sum(ms32))
-    t_max, e2e_max = aggregate_max([t_ms, e2e_s], dist)
+    t_max, e2e_max, e2e_pipe_max = aggregate_max([t_ms, e2e_s, e2e_pipe_s], dist)
     value = world * args.steps * kbest / (t_max / 1000.0)
     avg_launch_s = t_ms / args.steps / 1000.0
     fp64_rate = 1.0 / (float(np.mean(ms64)) / 1000.0)
@@ -691,8 +709,11 @@ def ours(args):
         "autotune_k": {str(k): v for k, v in tune.items()},
         "kernel_mode": {"f32": {str(k): m for k, m in modes.items()}, "f64_k1": mode64,
                         "ms_per_mode_f32": {str(k): v for k, v in mode_ms.items()}, "ms_per_mode_f64_k1": ms64modes},
-        "e2e": {"value": world * args.steps * kbest / e2e_max, "unit": UNIT,
-                "h2d_bytes_per_step": dim * kbest * 4, "d2h_bytes_per_step": dim * kbest * 4},
+        "e2e": {"value": world * args.steps * kbest / e2e_pipe_max, "unit": UNIT,
+                "h2d_bytes_per_step": dim * kbest * 4, "d2h_bytes_per_step": dim * kbest * 4,
+                "call": "bs_apply_H_host_async on two streams and two staging slots (pinned host buffers)",
+                "value_synchronous": world * args.steps * kbest / e2e_max,
+                "call_synchronous": "bs_apply_H_host, which returns after its copy out"},
         "gpu_launches": args.steps * launches_per_product(mode_used),
         "clocks": clocks,
     }

@@ -42,6 +42,7 @@
  *     partial vectors of the core-grouped kernels, the host entry point's
  *     staging buffers).  Issue them on one stream, or order them with
  *     events: two such calls running at the same time on the GPU race.
+ *     bs_apply_H_host_async orders its own products among themselves.
  */
 #ifndef BIGSTICK_GPU_H
 #define BIGSTICK_GPU_H
@@ -156,6 +157,21 @@ int bs_apply_H(bs_ctx *ctx, const void *x, void *y, int k, bs_dtype dtype, void 
  * Errors as bs_apply_H plus BS_ENOMEM. */
 int bs_apply_H_host(bs_ctx *ctx, const void *x_host, void *y_host, int k,
                     bs_dtype dtype, void *stream);
+
+/* The same product with HOST buffers, enqueued on `stream` without waiting:
+ * x_host is copied into the context's staging slot `slot` (0 or 1), H is
+ * applied, and the result is copied into y_host.  On the GPU, the copy in
+ * waits until the slot's previous call has finished copying out, and the
+ * product waits until the previous call's product (on any stream) has ended,
+ * since products share the context's workspace.  A caller that alternates
+ * two streams and the two slots therefore overlaps one call's copies with
+ * the other's product.  x_host and y_host must be pinned (cudaHostAlloc or
+ * cudaHostRegister) for the copies to run asynchronously.  The caller must
+ * not read y_host or rewrite x_host until `stream` has been synchronized.
+ * The staging buffers are allocated on first use and reused (2 x 2 blocks).
+ * Errors as bs_apply_H_host; BS_EINVAL for a slot other than 0 or 1. */
+int bs_apply_H_host_async(bs_ctx *ctx, const void *x_host, void *y_host, int k,
+                          bs_dtype dtype, void *stream, int slot);
 
 /* Adjoint of y = H(theta) x, theta = (spe[n_spe], tbme values in the order
  * they were loaded).  gx = H gy (H is symmetric; device, [dim][k], dtype),

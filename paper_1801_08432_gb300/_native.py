@@ -25,7 +25,7 @@ EXPORTED = ["bs_create", "bs_destroy", "bs_last_error", "bs_build_basis", "bs_ba
             "bs_debug_table", "bs_set_kernel", "bs_sync_status", "bs_autotune", "bs_set_tuned", "bs_lanczos",
             "bs_debug_eigh", "bs_apply_H_backward", "bs_block_dots", "bs_block_update", "bs_block_dots_noalloc",
             "bs_debug_eigh_banded", "bs_time_kernel", "bs_kernel_times", "bs_strength", "bs_density", "bs_gather_ceiling",
-            "bs_debug_wait_expiry", "bs_build_basis_trunc"]
+            "bs_debug_wait_expiry", "bs_build_basis_trunc", "bs_apply_H_host_async"]
 
 
 class bs_orbit(ctypes.Structure):
@@ -88,6 +88,7 @@ def load():
     L.bs_load_interaction.argtypes = [vp, f64p, ctypes.c_int, ctypes.POINTER(bs_tbme), ctypes.c_int]
     L.bs_apply_H.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
     L.bs_apply_H_host.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp]
+    L.bs_apply_H_host_async.argtypes = [vp, vp, vp, ctypes.c_int, ctypes.c_int, vp, ctypes.c_int]
     L.bs_debug_table.argtypes = [vp, ctypes.c_char_p, vp, i64p]
     L.bs_set_kernel.argtypes = [vp, ctypes.c_int]
     L.bs_set_tuned.argtypes = [vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]
@@ -312,6 +313,16 @@ class Context:
         """y = H x with host numpy buffers (copies inside)."""
         self._check(load().bs_apply_H_host(self.h, x.ctypes.data_as(vp), y.ctypes.data_as(vp), k, dtype,
                                            vp(stream or 0)))
+
+    def apply_H_host_async(self, x, y, k, dtype, stream, slot):
+        """y = H x with pinned host buffers (torch tensors, numpy arrays or raw
+        addresses), enqueued on `stream` in staging slot 0 or 1 without waiting;
+        synchronize the stream before reading y or rewriting x."""
+        def ptr(t):
+            if isinstance(t, int):
+                return vp(t)
+            return vp(t.data_ptr()) if hasattr(t, "data_ptr") else t.ctypes.data_as(vp)
+        self._check(load().bs_apply_H_host_async(self.h, ptr(x), ptr(y), k, dtype, vp(stream or 0), slot))
 
 
 def make(space_orbits, spe, tbmes, Z, N, twoM, parity=+1, device=0, max_excite=None):

@@ -330,6 +330,12 @@ void bs_destroy(bs_ctx *c)
         if (c->adj_rho) cudaFree(c->adj_rho);
         if (c->hx_x) cudaFree(c->hx_x);
         if (c->hx_y) cudaFree(c->hx_y);
+        for (int i = 0; i < 2; ++i) {
+            if (c->hxa_x[i]) cudaFree(c->hxa_x[i]);
+            if (c->hxa_y[i]) cudaFree(c->hxa_y[i]);
+            if (c->hxa_free[i]) cudaEventDestroy(c->hxa_free[i]);
+        }
+        if (c->hxa_prod) cudaEventDestroy(c->hxa_prod);
         if (c->core_part) cudaFree(c->core_part);
         for (cudaEvent_t ev : c->tev) cudaEventDestroy(ev);
     }
@@ -479,6 +485,53 @@ int bs_apply_H_host(bs_ctx *c, const void *xh, void *yh, int k, bs_dtype dt, voi
         if ((rc = launch_hx(c, c->hx_x, c->hx_y, k, dt, stream, c->err))) return rc;
         if ((e = cudaMemcpyAsync(yh, c->hx_y, bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess) return cuda_fail(c, e, "cudaMemcpyAsync");
         if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return cuda_fail(c, e, "cudaStreamSynchronize");
+        return BS_OK;
+    });
+}
+
+int bs_apply_H_host_async(bs_ctx *c, const void *xh, void *yh, int k, bs_dtype dt, void *stream, int slot)
+{
+    return guarded(c, [&]() -> int {
+        int rc = check_apply(c, k, dt);
+        if (rc) return rc;
+        if (!xh || !yh) { c->err = "null host buffer"; return BS_EINVAL; }
+        if (slot < 0 || slot > 1) { c->err = "host async: slot must be 0 or 1"; return BS_EINVAL; }
+        const size_t bytes = (size_t)c->basis.dim * (size_t)k * (dt == BS_F64 ? 8 : 4);
+        cudaError_t e;
+        for (int i = 0; i < 2; ++i)
+            if (!c->hxa_free[i] && (e = cudaEventCreateWithFlags(&c->hxa_free[i], cudaEventDisableTiming)) != cudaSuccess)
+                return cuda_fail(c, e, "cudaEventCreate");
+        if (!c->hxa_prod && (e = cudaEventCreateWithFlags(&c->hxa_prod, cudaEventDisableTiming)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaEventCreate");
+        if (bytes > c->hxa_bytes) {
+            // larger blocks: wait for every use of the old buffers, then replace them
+            for (int i = 0; i < 2; ++i)
+                if ((e = cudaEventSynchronize(c->hxa_free[i])) != cudaSuccess) return cuda_fail(c, e, "cudaEventSynchronize");
+            for (int i = 0; i < 2; ++i) {
+                if (c->hxa_x[i]) cudaFree(c->hxa_x[i]);
+                if (c->hxa_y[i]) cudaFree(c->hxa_y[i]);
+                c->hxa_x[i] = c->hxa_y[i] = nullptr;
+            }
+            c->hxa_bytes = 0;
+            for (int i = 0; i < 2; ++i) {
+                if ((e = cudaMalloc(&c->hxa_x[i], bytes)) != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+                if ((e = cudaMalloc(&c->hxa_y[i], bytes)) != cudaSuccess) return cuda_fail(c, e, "cudaMalloc");
+            }
+            c->hxa_bytes = bytes;
+        }
+        cudaStream_t s = (cudaStream_t)stream;
+        // the slot's previous use (its copy out) has ended; then x in, which may run while
+        // another stream's product does
+        if ((e = cudaStreamWaitEvent(s, c->hxa_free[slot], 0)) != cudaSuccess) return cuda_fail(c, e, "cudaStreamWaitEvent");
+        if ((e = cudaMemcpyAsync(c->hxa_x[slot], xh, bytes, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaMemcpyAsync");
+        // the previous product has ended: products share the context's workspace
+        if ((e = cudaStreamWaitEvent(s, c->hxa_prod, 0)) != cudaSuccess) return cuda_fail(c, e, "cudaStreamWaitEvent");
+        if ((rc = launch_hx(c, c->hxa_x[slot], c->hxa_y[slot], k, dt, stream, c->err))) return rc;
+        if ((e = cudaEventRecord(c->hxa_prod, s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
+        if ((e = cudaMemcpyAsync(yh, c->hxa_y[slot], bytes, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+            return cuda_fail(c, e, "cudaMemcpyAsync");
+        if ((e = cudaEventRecord(c->hxa_free[slot], s)) != cudaSuccess) return cuda_fail(c, e, "cudaEventRecord");
         return BS_OK;
     });
 }

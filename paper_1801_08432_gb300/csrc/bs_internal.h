@@ -367,6 +367,11 @@ struct bs_ctx {
     // host-buffer entry point workspace
     void *hx_x = nullptr, *hx_y = nullptr;
     size_t hx_bytes = 0;
+    // asynchronous host-buffer entry point: two staging slots, the event that ends
+    // each slot's last use, and the event that ends the last product
+    void *hxa_x[2] = {nullptr, nullptr}, *hxa_y[2] = {nullptr, nullptr};
+    size_t hxa_bytes = 0;
+    cudaEvent_t hxa_free[2] = {nullptr, nullptr}, hxa_prod = nullptr;
     int hx_mode = 0;         // 0: autotuned, 1: tiled kernel, 2 + v: row kernel variant v, then pipelined, then core
     // partial sums of the core-grouped pn kernel: nz x dim x k elements, grown on demand
     mutable void *core_part = nullptr;

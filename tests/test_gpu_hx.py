@@ -111,6 +111,31 @@ def test_host_buffer_entry_point_pinned_and_pageable():
     c.close()
 
 
+def test_async_host_entry_point_two_streams_two_slots():
+    """bs_apply_H_host_async: six calls alternating two streams and the two
+    staging slots, each with its own input block (pinned), synchronized only at
+    the end: every result equals the device-buffer product bit for bit (FP32
+    k = 8 and 4, FP64 k = 1 on sd 6p6n); slots other than 0 and 1 are
+    rejected before anything is enqueued."""
+    orbits, spe, tb = I.space("sd")
+    c = N.make(orbits, spe, tb, 6, 6, 0, +1, device=0)
+    sts = [torch.cuda.Stream(), torch.cuda.Stream()]
+    for k, dt, npt in ((8, N.BS_F32, np.float32), (4, N.BS_F32, np.float32), (1, N.BS_F64, np.float64)):
+        xs = [torch.from_numpy(I.random_block(c.dim, k, seed=20 + i).astype(npt)).pin_memory() for i in range(6)]
+        ys = [torch.full_like(x, float("nan")).pin_memory() for x in xs]
+        for i in range(6):
+            c.apply_H_host_async(xs[i], ys[i], k, dt, sts[i % 2].cuda_stream, i % 2)
+        for st in sts:
+            st.synchronize()
+        for i in range(6):
+            assert np.array_equal(ys[i].numpy(), gpu_apply(c, xs[i].numpy(), k, dt)), (k, i)
+    x = torch.zeros((c.dim, 1), dtype=torch.float64).pin_memory()
+    for slot in (-1, 2):
+        with pytest.raises(N.BSError):
+            c.apply_H_host_async(x, x.clone(), 1, N.BS_F64, 0, slot)
+    c.close()
+
+
 def test_rejects_bad_calls():
     c, o = setup("sd", 2, 2, 0)
     xd = torch.zeros((o.dim, 3), device="cuda", dtype=torch.float64)
