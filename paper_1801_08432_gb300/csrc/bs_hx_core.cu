@@ -553,14 +553,24 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
     constexpr int E = K * (int)sizeof(float);
     const int rot = E == 32 ? ((lane >> 2) & 1) : 0;
     SlotRing rg;
-    // the unit record is read one unit ahead (its rows and partials only at the store)
-    int hn = 0, hN = 0;
+    // the unit record is read one unit ahead; lane p < kPPG keeps destination
+    // row p and its partial rank, packed as drow << 8 | part (-1: no row; the
+    // host keeps drow < 2^23 and part < 256), until the store
+    auto packed = [&](const PPUnit *U) {
+        if (lane >= kPPG) return 0;
+        const int d = U->drow[lane];
+        return d < 0 ? -1 : (d << 8) | U->part[lane];
+    };
+    int hn = 0, hN = 0, hrec = 0;
     int64_t ho = 0;
-    if (blockIdx.x < A.nunits) { hn = A.units[blockIdx.x].nsrc; hN = A.units[blockIdx.x].nN; ho = A.units[blockIdx.x].doff; }
+    if (blockIdx.x < A.nunits) {
+        const PPUnit *U = A.units + blockIdx.x;
+        hn = U->nsrc; hN = U->nN; ho = U->doff;
+        hrec = packed(U);
+    }
     for (int u = blockIdx.x, un = A.nunits; u < A.nunits; u = un) {
-        const int nsrc = hn, nN = hN;
+        const int nsrc = hn, nN = hN, rec = hrec;
         const int64_t doff = ho;
-        const PPUnit *U = A.units + u;
         const int ntile = (nN + C - 1) / C;
         for (int tile = 0; tile < ntile; ++tile) {
             const int col = tile * C + warp * 32 + lane;
@@ -580,7 +590,11 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 }
                 if (tile == 0 && q == 0) {   // the next unit: read its record now, use it after this one
                     un = uidp[s];
-                    if (un < A.nunits) { hn = A.units[un].nsrc; hN = A.units[un].nN; ho = A.units[un].doff; }
+                    if (un < A.nunits) {
+                        const PPUnit *U = A.units + un;
+                        hn = U->nsrc; hN = U->nN; ho = U->doff;
+                        hrec = packed(U);
+                    }
                 }
                 if (active && nsrc > 0) {
                     const float *Xs = slots + (size_t)s * A.slot_elems;
@@ -603,11 +617,13 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                 __syncwarp();
                 if (lane == 0) bar_arrive(empty0 + 8u * s);
             }
-            if (col < nN) {
+            // every lane takes part in the shuffles; only columns inside the block store
 #pragma unroll
-                for (int p = 0; p < kPPG; ++p) {
-                    const int drow = U->drow[p];
-                    if (drow < 0) continue;
+            for (int p = 0; p < kPPG; ++p) {
+                const int pk = __shfl_sync(0xffffffffu, rec, p);
+                if (col < nN) {
+                    if (pk < 0) continue;
+                    const int drow = pk >> 8, prt = pk & 255;
                     float o[K];
 #pragma unroll
                     for (int qq = 0; qq < K / 2; ++qq) {
@@ -615,7 +631,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                         o[2 * qq + 1] = acc[p][qq].y;
                     }
                     prot_fix<float, K>(o, rot);
-                    pst<float, K>(part + (int64_t)U->part[p] * A.part_stride + (doff + (int64_t)drow * nN + col) * K, o);
+                    pst<float, K>(part + (int64_t)prt * A.part_stride + (doff + (int64_t)drow * nN + col) * K, o);
                 }
             }
         }

@@ -1198,6 +1198,12 @@ int build_tables(const Basis &B, const Interaction &I, Tables &T, std::string &e
     }
     T.ops_per_vector = ops;
     if (B.trunc) return BS_OK;   // the core-grouped tables assume one neutron sector per proton sector
+    {   // the pp-core kernel packs a destination row and its partial rank into one int
+        const int Z = B.sp[0].nparticles;
+        int64_t maxsec = 0;
+        for (const Sector &S : B.sp[0].sec) maxsec = std::max<int64_t>(maxsec, (int64_t)S.count);
+        if (Z + Z * (Z - 1) / 2 > 255 || maxsec >= (int64_t)1 << 23) return BS_OK;
+    }
     build_core_units(B, I, T);
     build_pp_units(B, I, T);
     return BS_OK;
