@@ -344,14 +344,46 @@ double quarter_cost_k4(const uint32_t *e, int n)
 }
 
 
+// Wavefronts of one quarter warp's loads for the step orders (8 lanes, entries
+// src | weight row << 16): m0 for each of the two k = 8 chunk loads, m4 for
+// the k = 4 element load, mw for the weight-row load; each is the most
+// distinct addresses that share one of the 8 bank groups.  The second chunk's
+// addresses are the first's with the low bit flipped (a lane reads the other
+// half of its element), a bijection that maps bank group g to g ^ 1, so both
+// chunk loads take the same count; one pass over the lane pairs finds all
+// three (the values of quarter_terms and quarter_cost_k4, at a third of the
+// comparisons).
+inline void quarter_counts(const uint32_t *e, const uint32_t *rot, int &m0, int &m4, int &mw)
+{
+    uint32_t s[8], w[8];
+    for (int i = 0; i < 8; ++i) {
+        s[i] = e[i] & 0xFFFFu;
+        w[i] = (e[i] >> 16) & 0x7FFFu;
+    }
+    int c0[8] = {}, c4[8] = {}, cw[8] = {};
+    m0 = m4 = mw = 0;
+    for (int i = 0; i < 8; ++i) {
+        bool d0 = false, d4 = false, dw = false;
+        for (int j = 0; j < i; ++j) {
+            const bool eq = s[j] == s[i];
+            d4 = d4 || eq;
+            d0 = d0 || (eq && rot[j] == rot[i]);
+            dw = dw || w[j] == w[i];
+        }
+        if (!d0) m0 = std::max(m0, ++c0[(2 * s[i] + rot[i]) & 7]);
+        if (!d4) m4 = std::max(m4, ++c4[s[i] & 7]);
+        if (!dw) mw = std::max(mw, ++cw[w[i] & 7]);
+    }
+}
+
 // The annealing objective of the pn-core order: the k = 8 chunk loads, the
 // weight load counted in full and half the k = 4 element load, so that one
 // order serves both block widths the product runs at.
 double pn_order_cost(const uint32_t *e, const uint32_t *rot)
 {
-    double x, w;
-    quarter_terms(e, rot, 8, x, w);
-    return x + w + 0.5 * quarter_cost_k4(e, 8);
+    int m0, m4, mw;
+    quarter_counts(e, rot, m0, m4, mw);
+    return 2.0 * m0 + mw + 0.5 * m4;
 }
 
 void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
@@ -422,9 +454,10 @@ void bank_schedule_lane(std::vector<std::vector<uint32_t>> &lists, uint32_t pad)
 // either swaps one lane's entries at two steps or, for a padding entry (zero
 // weight row), sets its source column to 0..3 (when the source row has 4 or
 // more), so that it takes a free bank group.  Moves are accepted by the
-// Metropolis rule under a temperature falling linearly to zero, and the best
-// order seen is kept.  The stepwise greedy above cannot trade entries between
-// steps; this can.  Deterministic: a splitmix64 stream seeded per slice.
+// Metropolis rule under a temperature falling linearly from 0.3 wavefronts to
+// zero, and the best order seen is kept.  The stepwise greedy above cannot
+// trade entries between steps; this can.  Deterministic: a splitmix64 stream
+// seeded per slice.
 // ipe = moves per entry.
 void anneal_slice(uint32_t *E, size_t lmax, uint32_t pad, int64_t nsrc, uint64_t seed, int ipe)
 {
@@ -449,7 +482,7 @@ void anneal_slice(uint32_t *E, size_t lmax, uint32_t pad, int64_t nsrc, uint64_t
         best = q8;
         const int64_t n = (int64_t)ipe * (int64_t)lmax * 8;
         for (int64_t it = 0; it < n; ++it) {
-            const double T = 0.6 * (1.0 - (double)it / (double)n) + 1e-3;
+            const double T = 0.3 * (1.0 - (double)it / (double)n) + 1e-3;
             const size_t k = (size_t)(next() % 8), v1 = (size_t)(next() % lmax);
             uint32_t &a = q8[v1 * 8 + k];
             if ((a >> 16) == (pad >> 16) && nsrc >= 4 && next() % 10 < 3) {   // a padding entry's source column
@@ -504,9 +537,9 @@ void anneal_nn_quarter(int32_t *src, double *coef, size_t lmax, size_t q, uint64
     auto unif = [&next]() { return (double)(next() >> 11) * (1.0 / 9007199254740992.0); };
     const uint32_t rots[8] = {0, 1, 0, 1, 0, 1, 0, 1};
     auto cost8 = [&rots](const uint32_t *e) {   // k = 8 chunk loads + the k = 4 element load
-        double x, w;
-        quarter_terms(e, rots, 8, x, w);
-        return x + quarter_cost_k4(e, 8);
+        int m0, m4, mw;
+        quarter_counts(e, rots, m0, m4, mw);
+        return 2.0 * m0 + m4;
     };
     std::vector<uint32_t> q8(lmax * 8), best(lmax * 8);
     std::vector<uint32_t> idx(lmax * 8), bidx(lmax * 8);   // the entries' original steps, to move coef
@@ -703,21 +736,22 @@ void build_perm_ell(const Basis &B, const Interaction &I, Tables &T)
     while (P.sinfo.size() % 4) P.sinfo.push_back(0);
     while (P.ent.size() % 4) P.ent.push_back((ws - 1u) << 16);
     P.core_ent.resize(P.ent.size(), (ws - 1u) << 16);
-    {   // refine the pn-core and like-particle orders, slices in parallel: ~100 moves
-        // per entry, fewer for large tables (at most ~1.5e8 moves for each); below
-        // 10 moves per entry the search gains nothing and is skipped
-        auto moves = [](size_t n) {
-            const double m = std::min(100.0, 1.5e8 / (double)std::max<size_t>(n, 1));
+    {   // refine the pn-core and like-particle orders, slices in parallel: up to 200
+        // (pn) and 100 (like-particle) moves per entry, fewer for large tables (at
+        // most ~1.5e8 moves for each); below 10 moves per entry the search gains
+        // nothing and is skipped
+        auto moves = [](size_t n, double cap) {
+            const double m = std::min(cap, 1.5e8 / (double)std::max<size_t>(n, 1));
             return m < 10.0 ? 0 : (int)m;
         };
-        const int ipe = moves(P.core_ent.size());
+        const int ipe = moves(P.core_ent.size(), 200.0);
 #pragma omp parallel for schedule(dynamic, 8)
         for (int64_t i = 0; i < (int64_t)core_slices.size(); ++i) {
             const CoreSlice &c = core_slices[(size_t)i];
             anneal_slice(P.core_ent.data() + c.base, c.lmax, (ws - 1u) << 16, c.nsrc,
                          0x5DEECE66Dull * (uint64_t)(i + 1), ipe);
         }
-        const int ipn = moves(P.nn_src.size());
+        const int ipn = moves(P.nn_src.size(), 100.0);
 #pragma omp parallel for schedule(dynamic, 1)
         for (int64_t i = 0; i < 4 * (int64_t)nn_slices.size(); ++i) {
             const CoreSlice &c = nn_slices[(size_t)(i / 4)];
