@@ -25,6 +25,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <type_traits>
 
 #include "bs_internal.h"
 #include "bs_tma.cuh"
@@ -41,7 +42,8 @@ namespace {
 // One list entry of one destination column: the gathered element of the
 // staged source row times the weights of the entry's weight row, for the
 // unit's first R destination rows (its rows are packed to the front; R = 4
-// also serves units with three).  Entries are src | W row << 16.  For K = 8
+// also serves units with three).  The source's weight table has rows of R
+// floats.  Entries are src | W row << 16.  For K = 8
 // the lane reads the element's 16-byte chunks in its own fixed order (XA
 // and XB are the staged row shifted to the lane's first and second chunk),
 // so the accumulators hold the components in that order and are put back
@@ -50,7 +52,7 @@ template <int K, int R = 4>
 __device__ __forceinline__ void core_step(const float *XA, const float *XB, const float *Wt, uint32_t en,
                                           float2 (&acc)[4][K / 2])
 {
-    const float *wr = Wt + 4 * (en >> 16);
+    const float *wr = Wt + R * (en >> 16);
     const uint32_t src = en & 0xFFFFu;
     float2 xv[K / 2];
     {
@@ -386,16 +388,23 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
                         for (int v = 0; v < la; ++v) core_step<K, 4>(XA, XB, Wt, lstA[32 * v], accA);
                     }
                 } else {
-                    const int lm = min(la, lb);
-                    int v = 0;
-                    for (; v < lm; ++v) {
-                        core_step<K>(XA, XB, Wt, lstA[32 * v], accA);
-                        core_step<K>(XA, XB, Wt, lstB[32 * v], accB);
-                    }
+                    // two slices, for the unit's number of rows (the weight rows are R floats)
+                    auto run = [&](auto rt) {
+                        constexpr int R = decltype(rt)::value;
+                        const int lm = min(la, lb);
+                        int v = 0;
+                        for (; v < lm; ++v) {
+                            core_step<K, R>(XA, XB, Wt, lstA[32 * v], accA);
+                            core_step<K, R>(XA, XB, Wt, lstB[32 * v], accB);
+                        }
 #pragma unroll 2
-                    for (int va = v; va < la; ++va) core_step<K>(XA, XB, Wt, lstA[32 * va], accA);
+                        for (int va = v; va < la; ++va) core_step<K, R>(XA, XB, Wt, lstA[32 * va], accA);
 #pragma unroll 2
-                    for (int vb = v; vb < lb; ++vb) core_step<K>(XA, XB, Wt, lstB[32 * vb], accB);
+                        for (int vb = v; vb < lb; ++vb) core_step<K, R>(XA, XB, Wt, lstB[32 * vb], accB);
+                    };
+                    if (nrow == 1) run(std::integral_constant<int, 1>{});
+                    else if (nrow == 2) run(std::integral_constant<int, 2>{});
+                    else run(std::integral_constant<int, 4>{});
                 }
                 if (last) continue;   // released after the store
                 __syncwarp();

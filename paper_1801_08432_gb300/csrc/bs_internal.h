@@ -250,7 +250,8 @@ struct Tables {
     // core-grouped pn term
     std::vector<CoreUnit> cunits;        // sorted by work, largest first
     std::vector<CoreSrc> csrc;
-    std::vector<double> wc;              // per (chunk, k): [2 wsign][4] weights W(i_p ., k .), +W then -W
+    std::vector<double> wc;              // per (chunk, k): [2 wsign][R] weights W(i_p ., k .), +W then -W, R = 1, 2, 4
+                                         // by the unit's rows, at the front of a [2 wsign][4] slot
     int n_wtab = 0;
     // core-grouped pp term
     std::vector<PPUnit> ppunits;         // sorted by work, largest first

@@ -858,8 +858,12 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
     // the pre-signed W row of op a+_i a_k (+ variant, then - variant) for the
     // j-th state i of the subset.  A unit's destination rows are the chunk
     // states its core leaves free, packed to the front, so that the kernel
-    // can skip the padded rows of units with one or two of them.  Tables are
-    // made on first use, ns of them (one per k) per (chunk, subset).
+    // can skip the padded rows of units with one or two of them.  Rows are
+    // R = 1, 2 or 4 floats apart (one, two, three or four states), packed at
+    // the front of the table: a lane's 4- or 8-byte weight load then meets
+    // 32 or 16 bank positions across the rows instead of the 8 that a
+    // 16-byte row stride leaves.  Tables are made on first use, ns of them
+    // (one per k) per (chunk, subset).
     const size_t ws2 = 2 * (size_t)T.wsign;
     std::map<std::pair<size_t, int>, int> tab_of;   // (chunk, subset mask) -> first table
     // Table 2 (t0 + k) + f holds them with the +W and -W halves swapped when
@@ -873,6 +877,8 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
         T.n_wtab += ns;
         T.wc.resize((size_t)T.n_wtab * 2 * ws2 * 4, 0.0);
         const size_t ws = ws2 / 2;
+        const int cnt = __builtin_popcount((unsigned)mask);
+        const size_t rs = cnt <= 1 ? 1 : cnt == 2 ? 2 : 4;   // floats per table row
         for (int k = 0; k < ns; ++k) {
             int j = 0;
             for (size_t p = 0; p < chunks[q].size(); ++p) {
@@ -884,8 +890,8 @@ void build_core_units(const Basis &B, const Interaction &I, Tables &T)
                 const size_t row = (size_t)T.ww_off[(size_t)g] + 2 * (size_t)I.ops.local_of_op[(size_t)op] * ws2;
                 double *dst = T.wc.data() + 2 * ((size_t)t0 + (size_t)k) * ws2 * 4;
                 for (size_t idx = 0; idx < ws2; ++idx) {
-                    dst[idx * 4 + col] = T.ww[row + idx];
-                    dst[ws2 * 4 + (idx ^ ws) * 4 + col] = T.ww[row + idx];
+                    dst[idx * rs + col] = T.ww[row + idx];
+                    dst[ws2 * 4 + (idx ^ ws) * rs + col] = T.ww[row + idx];
                 }
             }
         }

@@ -369,7 +369,7 @@ def core_tables_matvec(c, x, Z, pp_core=False):
     links = c.table("links", np.int64).reshape(-1, 6)
     units = np.frombuffer(c.table("core_units", np.uint8).tobytes(), dtype=CORE_UNIT)
     srcs = np.frombuffer(c.table("core_src", np.uint8).tobytes(), dtype=CORE_SRC)
-    wc = c.table("wc", np.float64).reshape(-1, 2 * ws, 4)
+    wc = c.table("wc", np.float64).reshape(-1, 2 * ws * 4)   # one [2 wsign][4] slot per table
     dim = len(x)
     nz = Z + (Z * (Z - 1) // 2 if pp_core else 0)
     part = np.zeros((nz, dim))
@@ -384,11 +384,14 @@ def core_tables_matvec(c, x, Z, pp_core=False):
         assert (u["nN"], u["doff"], u["perm_off"]) == (nNd, offd, sec_base[nsd][0])   # the record's header copies
         acc = np.zeros((4, nNd))
         po = sec_base[nsd][0]
+        # weight rows of R floats at the front of the slot: R = 1, 2 or 4 by the unit's rows
+        R = 1 if u["drow"][1] < 0 else 2 if u["drow"][2] < 0 else 4
         for q in range(u["nsrc"]):
             xe, nNs, wt, ce, cs = srcs[u["src0"] + q]
             xs = x[xe: xe + nNs]
             assert (int(wt) & 1) == (int(wt) >> 31)        # the table of a -1 sign of a_k has its halves swapped
-            W = wc[int(wt) & 0x7FFFFFFF]
+            W = np.zeros((2 * ws, 4))
+            W[:, :R] = wc[int(wt) & 0x7FFFFFFF][:2 * ws * R].reshape(2 * ws, R)
             for p in range(nNd):
                 col = perm[po + p]
                 o, lmax = sinfo[cs + 2 * (p // 32)], sinfo[cs + 2 * (p // 32) + 1]
