@@ -908,15 +908,16 @@ __global__ void __launch_bounds__(kRsCons + 64, sizeof(T) == 4 ? 2 : 1)
 // every block V_b stream through a ring of kRwS tiles.  A W slot is released
 // when the last block's tile at that position has been consumed, so the next
 // piece's W loads overlap the end of the current one.
-// Consumer thread t owns the rows t, t + 256, ... of each tile and keeps all
+// Consumer thread t owns the rows t, t + 384, ... of each tile and keeps all
 // K x K plain FP32 sums of its rows in registers (packed FMAs, V elements
 // duplicated into pairs).  For K = 8 a lane reads the two 16-byte halves of
 // its rows in the order (lane >> 2) & 1, which makes the quarter-warp reads
 // conflict-free; the sums are put back in order before they are combined.
-// Every kChunk products (16 rows) the warp combines its lanes' sums by a
+// After at most kChunk = 16 products per sum (FL tiles of RPT rows: 8 rows at
+// K = 8, 16 at K = 4) the warp combines its lanes' sums by a
 // butterfly that leaves each lane with K^2 / 32 of the warp's K^2 sums (five
 // FP32 addition levels), which the lane adds to its double-float sums.  At the
-// end of a block's piece the 8 warps' sums are added in a fixed order into this
+// end of a block's piece the 12 warps' sums are added in a fixed order into this
 // CTA's partial for the block.  So a plain sum holds at most 16 products and
 // 5 further roundings before it reaches double-float.  Deterministic: fixed
 // orders throughout, and dots_reduce adds the CTAs' partials in a fixed
