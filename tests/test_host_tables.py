@@ -465,6 +465,37 @@ def test_core_tables_reproduce_oracle_matrix(name, Z, Nn, twoM, pp_core):
     assert np.max(np.abs(y - y_ref)) <= 1e-12 * np.max(np.abs(y_ref))
 
 
+def test_core_weight_rows_match_the_unit_row_count():
+    """The weight table a pn-core source names has rows of R floats, R = 1, 2
+    or 4 for units with one, two, or three and four destination rows, packed
+    at the front of its [2 wsign][4] slot: every nonzero weight lies in the
+    first 2 wsign R floats, and row p of entry o sits at o R + p (the
+    layout the kernel indexes).  Checked against the slot read in the
+    4-float layout of the operator rows: the packed table equals it column
+    by column."""
+    c = host_ctx("sd", 4, 4, 0)
+    ws = int(c.table("stats", np.int64)[7])
+    units = np.frombuffer(c.table("core_units", np.uint8).tobytes(), dtype=CORE_UNIT)
+    srcs = np.frombuffer(c.table("core_src", np.uint8).tobytes(), dtype=CORE_SRC)
+    wc = c.table("wc", np.float64).reshape(-1, 2 * ws * 4)
+    tabs = {}   # table -> (R, real rows) of the units that name it
+    for u in units:
+        nreal = int((u["drow"] >= 0).sum())
+        assert np.all(u["drow"][:nreal] >= 0) and np.all(u["drow"][nreal:] < 0)   # packed to the front
+        R = 1 if nreal == 1 else 2 if nreal == 2 else 4
+        for t in (srcs["wtab"][u["src0"]: u["src0"] + u["nsrc"]].astype(np.int64) & 0x7FFFFFFF).tolist():
+            assert tabs.setdefault(t, (R, nreal)) == (R, nreal)   # one layout per table
+    assert {r for r, _ in tabs.values()} == {1, 2, 4}
+    for t, (R, nreal) in tabs.items():
+        slot = wc[t]
+        assert not np.any(slot[2 * ws * R:]), (t, R)   # nothing past the packed rows
+        rows = slot[:2 * ws * R].reshape(2 * ws, R)
+        assert not np.any(rows[:, nreal:]), (t, R)     # the padded fourth column of 3-row units
+        # the +W and -W halves: table 2 j + 1 is table 2 j with its halves swapped
+        mate = wc[t ^ 1][:2 * ws * R].reshape(2 * ws, R)
+        assert np.array_equal(rows, np.roll(mate, ws, axis=0))
+
+
 def test_core_units_structure():
     """Each unit: one core c (Z-1 states) shared by its destination rows and
     sources; destination states of one (2m, parity); the stored rank t and the
