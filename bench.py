@@ -609,7 +609,10 @@ def ours(args):
     kern_ms = timed.kernel_ms
     ms64, _, _ = timed(1, N.BS_F64, max(3, args.steps // 2), max(3, args.warmup))
 
-    # end to end through the host-buffer call: pinned host input, H*X, result back
+    # end to end through the host-buffer call: pinned host input, H*X, result back;
+    # at least 80 calls, so that the two-slot pipeline's fill and drain (one copy in,
+    # one copy out) are a small part of the timed region
+    n_e2e = max(args.steps, 80)
     xh = torch.randn((dim, kbest), dtype=torch.float32).pin_memory()
     yh = torch.empty_like(xh).pin_memory()
     xa = xh.numpy()
@@ -618,7 +621,7 @@ def ours(args):
         ctx.apply_H_host(xa, ya, kbest, N.BS_F32, sp)
     bar()
     t0 = time.perf_counter()
-    for _ in range(args.steps):
+    for _ in range(n_e2e):
         ctx.apply_H_host(xa, ya, kbest, N.BS_F32, sp)
     bar()
     e2e_s = time.perf_counter() - t0
@@ -634,7 +637,7 @@ def ours(args):
         st.synchronize()
     bar()
     t0 = time.perf_counter()
-    for i in range(args.steps):
+    for i in range(n_e2e):
         ctx.apply_H_host_async(xs[i % 2], ys[i % 2], kbest, N.BS_F32, sts[i % 2].cuda_stream, i % 2)
     for st in sts:
         st.synchronize()
@@ -709,10 +712,11 @@ def ours(args):
         "autotune_k": {str(k): v for k, v in tune.items()},
         "kernel_mode": {"f32": {str(k): m for k, m in modes.items()}, "f64_k1": mode64,
                         "ms_per_mode_f32": {str(k): v for k, v in mode_ms.items()}, "ms_per_mode_f64_k1": ms64modes},
-        "e2e": {"value": world * args.steps * kbest / e2e_pipe_max, "unit": UNIT,
+        "e2e": {"value": world * n_e2e * kbest / e2e_pipe_max, "unit": UNIT,
                 "h2d_bytes_per_step": dim * kbest * 4, "d2h_bytes_per_step": dim * kbest * 4,
+                "steps": n_e2e,
                 "call": "bs_apply_H_host_async on two streams and two staging slots (pinned host buffers)",
-                "value_synchronous": world * args.steps * kbest / e2e_max,
+                "value_synchronous": world * n_e2e * kbest / e2e_max,
                 "call_synchronous": "bs_apply_H_host, which returns after its copy out"},
         "gpu_launches": args.steps * launches_per_product(mode_used),
         "clocks": clocks,
