@@ -384,7 +384,7 @@ __global__ void __launch_bounds__((NW + 1) * 32, MINB)
 #pragma unroll 4
                         for (int v = 0; v < la; ++v) core_step<K, 2>(XA, XB, Wt, lstA[32 * v], accA);
                     } else {
-#pragma unroll 2
+#pragma unroll 4
                         for (int v = 0; v < la; ++v) core_step<K, 4>(XA, XB, Wt, lstA[32 * v], accA);
                     }
                 } else {
